@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs: solid masks and initial component densities.
+
+This module holds none of the method's arithmetic: it only draws geometries shaped like the
+paper's test cases (a droplet resting on a cylinder, Sec. 3.2; a droplet in a confined channel,
+Sec. 3.3; immiscible displacement, Sec. 3.4; co-current layers, Sec. 3.1) and initial density
+fields.  Both the CUDA library's callers and the CPU checker receive these arrays as inputs.
+
+Conventions: arrays are indexed [y, x]; ``solid`` is uint8 (1 = solid node); component A is the
+paper's fluid 1 and B its fluid 2.  Initial densities are a sharp step between the main density
+rho^m and the dissolved density rho^d (Sec. 2.1), plus independent uniform noise in
+[-amp, amp) on each fluid node and component from a counter-based generator (SplitMix64 of
+(seed, node, component)), so any node's noise can be regenerated on its own.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+RHO_M = 1.0
+RHO_D = 0.03
+NOISE_AMP = 1.0e-4
+
+
+def mean_field_G(rho_m: float = RHO_M, rho_d: float = RHO_D, cs2: float = 1.0 / 3.0) -> float:
+    """Inter-component strength at which the mean-field coexisting densities of the symmetric
+    two-component mixture are (rho_m, rho_d), for stencil weights normalised to
+    sum_e w e_x^2 = 1: G (rho_m - rho_d) = c_s^2 ln(rho_m / rho_d)."""
+    return cs2 * math.log(rho_m / rho_d) / (rho_m - rho_d)
+
+
+# Default G_AB: 1.205 for 1.0 / 0.03.  (G_AB = 3.5 in this weight normalisation diverges within two
+# steps on the 96x96 cylinder case.)
+G_DEFAULT = round(mean_field_G(), 3)
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea, Flood 2014) applied to uint64 counters."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def node_noise(seed: int, ny: int, nx: int, comp: int, amp: float = NOISE_AMP) -> np.ndarray:
+    """Uniform noise in [-amp, amp) for every node of an ny x nx grid and one component.
+    Counter = seed << 40 | node << 1 | comp, node = y*nx + x; u = top 53 bits / 2^53."""
+    node = np.arange(ny * nx, dtype=np.uint64)
+    ctr = (np.uint64(seed) << np.uint64(40)) | (node << np.uint64(1)) | np.uint64(comp)
+    u = (splitmix64(ctr) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (amp * (2.0 * u - 1.0)).reshape(ny, nx)
+
+
+def lambda_for_angle(theta_deg: float) -> float:
+    """Strength coefficient lambda for a target contact angle from the paper's empirical
+    correlation theta = -13.76 lambda^2 + 94.62 lambda + 9.47 (Sec. 3.2, Fig. 7): smaller root."""
+    a, b, c = -13.76, 94.62, 9.47 - theta_deg
+    disc = b * b - 4 * a * c
+    if disc < 0:
+        raise ValueError("angle outside the correlation's range")
+    return (-b + math.sqrt(disc)) / (2 * a)
+
+
+@dataclass
+class Scenario:
+    """One lattice case: geometry, initial densities and model parameters."""
+    name: str
+    solid: np.ndarray          # (ny, nx) uint8
+    rhoA0: np.ndarray          # (ny, nx) float64
+    rhoB0: np.ndarray          # (ny, nx) float64
+    bc_x: str = "periodic"     # periodic | wall | open
+    bc_y: str = "wall"         # periodic | wall
+    scheme: str = "improved"
+    tau: tuple = (1.0, 1.0)
+    G: float = G_DEFAULT
+    lam: float = 1.0
+    Gw2: float | None = None
+    delta: float = 0.8
+    g: tuple = (0.0, 0.0)
+    u_in: float = 0.0
+    rho_in: tuple = (RHO_M, RHO_D)
+    surface: dict | None = None  # for the contact angle: {"kind": "flat"|"circle", ...}
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ny(self) -> int:
+        return self.solid.shape[0]
+
+    @property
+    def nx(self) -> int:
+        return self.solid.shape[1]
+
+    def params(self) -> dict:
+        return dict(bc_x=self.bc_x, bc_y=self.bc_y, scheme=self.scheme, tau=tuple(self.tau),
+                    G=self.G, lam=self.lam, Gw2=self.Gw2, delta=self.delta, g=tuple(self.g),
+                    u_in=self.u_in, rho_in=tuple(self.rho_in))
+
+
+def _grid(ny, nx):
+    y, x = np.mgrid[0:ny, 0:nx]
+    return y.astype(np.float64), x.astype(np.float64)
+
+
+def _phase_fields(inside_A: np.ndarray, solid: np.ndarray, seed: int, amp: float = NOISE_AMP):
+    ny, nx = solid.shape
+    rA = np.where(inside_A, RHO_M, RHO_D) + node_noise(seed, ny, nx, 0, amp)
+    rB = np.where(inside_A, RHO_D, RHO_M) + node_noise(seed, ny, nx, 1, amp)
+    rA[solid.astype(bool)] = 0.0
+    rB[solid.astype(bool)] = 0.0
+    return rA, rB
+
+
+def cylinder_droplet(n: int = 96, R: float | None = None, r: float | None = None, lam: float = 1.0,
+                     seed: int = 1, scheme: str = "improved", G: float = G_DEFAULT, tau=(1.0, 1.0),
+                     nx: int | None = None, amp: float = NOISE_AMP) -> Scenario:
+    """Droplet of A resting on a solid cylinder (Sec. 3.2, Fig. 5) at the 96x96 scale: rows 0 and
+    ny-1 solid, x periodic, a cylinder of radius R = n/6 centred on the bottom row, a droplet of
+    radius r = 5n/24 centred 0.6 r above the cylinder top (the paper's 300x350 case has the droplet
+    centre 0.6 r above the cylinder top as well)."""
+    ny = n
+    nx = n if nx is None else nx
+    R = n / 6.0 if R is None else R
+    r = 5.0 * n / 24.0 if r is None else r
+    y, x = _grid(ny, nx)
+    cx, cy = nx // 2, 0
+    solid = ((x - cx) ** 2 + (y - cy) ** 2 <= R * R)
+    solid[0, :] = True
+    solid[ny - 1, :] = True
+    dcy = cy + R + 0.6 * r
+    inside = (x - cx) ** 2 + (y - dcy) ** 2 <= r * r
+    solid = solid.astype(np.uint8)
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    return Scenario(f"cylinder_droplet_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
+                    scheme=scheme, tau=tuple(tau), G=G, lam=lam,
+                    surface={"kind": "circle", "cx": float(cx), "cy": float(cy), "R": R + 0.5})
+
+
+def flat_droplet(nx: int = 64, ny: int = 48, r: float = 12.0, lam: float = 1.0, seed: int = 11,
+                 scheme: str = "improved", G: float = G_DEFAULT, h: float | None = None,
+                 amp: float = NOISE_AMP) -> Scenario:
+    """Droplet of A on a flat wall: rows 0 and ny-1 solid, x periodic, droplet of radius r centred
+    at (nx/2 - 1/2, 0.6 r) -- mirror-symmetric about x = nx/2 - 1/2 when the noise is off."""
+    y, x = _grid(ny, nx)
+    solid = np.zeros((ny, nx), bool)
+    solid[0, :] = True
+    solid[ny - 1, :] = True
+    h = 0.6 * r if h is None else h
+    inside = (x - (nx - 1) / 2.0) ** 2 + (y - h) ** 2 <= r * r
+    solid = solid.astype(np.uint8)
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    return Scenario(f"flat_droplet_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
+                    scheme=scheme, G=G, lam=lam,
+                    surface={"kind": "flat", "y_w": 0.5, "normal": 1})
+
+
+def free_droplet(n: int = 64, R: float = 12.0, seed: int = 21, G: float = G_DEFAULT,
+                 amp: float = NOISE_AMP) -> Scenario:
+    """Free droplet of A in B, fully periodic, no solid (Laplace-law case)."""
+    y, x = _grid(n, n)
+    inside = (x - n / 2.0) ** 2 + (y - n / 2.0) ** 2 <= R * R
+    solid = np.zeros((n, n), np.uint8)
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    return Scenario(f"free_droplet_{n}_R{R:g}", solid, rA, rB, bc_x="periodic", bc_y="periodic", G=G)
+
+
+def throat_channel(nx: int = 2048, ny: int = 512, R: float = 180.0, r: float = 120.0, seed: int = 3,
+                   g: float = 1e-6, lam: float | None = None, G: float = G_DEFAULT) -> Scenario:
+    """Droplet through a confined geometry (Sec. 3.3 shape): rows 0, ny-1 solid, x periodic, two
+    opposing half-disks of radius R centred at (nx/2, 0) and (nx/2, ny-1), a droplet of radius r at
+    (nx*400/2048, ny/2) in B, body force g along x."""
+    y, x = _grid(ny, nx)
+    solid = ((x - nx / 2) ** 2 + y ** 2 <= R * R) | ((x - nx / 2) ** 2 + (y - (ny - 1)) ** 2 <= R * R)
+    solid[0, :] = True
+    solid[ny - 1, :] = True
+    inside = (x - nx * 400.0 / 2048.0) ** 2 + (y - ny / 2.0) ** 2 <= r * r
+    solid = solid.astype(np.uint8)
+    rA, rB = _phase_fields(inside, solid, seed)
+    lam = lambda_for_angle(90.0) if lam is None else lam
+    return Scenario(f"throat_channel_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
+                    g=(g, 0.0), lam=lam, G=G)
+
+
+def porous_disks(nx: int = 4096, ny: int = 2048, porosity: float = 0.6, rmin: float = 12.0,
+                 rmax: float = 40.0, seed: int = 4, keep_out: tuple = (64, 64), u_in: float = 0.005,
+                 G: float = G_DEFAULT, lam: float | None = None, max_tries: int = 2_000_000) -> Scenario:
+    """Immiscible displacement in a synthetic porous medium (Sec. 3.4 shape): rows 0, ny-1 solid;
+    random non-overlapping disks with radii uniform in [rmin, rmax] placed by rejection sampling
+    until the porosity drops to ``porosity``, kept out of the first and last ``keep_out`` columns;
+    filled with B; A enters through a velocity inlet at x = 0 (u_in), outflow at x = nx-1."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((ny, nx), bool)
+    solid[0, :] = True
+    solid[ny - 1, :] = True
+    target_solid = (1.0 - porosity) * nx * ny
+    cell = int(2 * rmax) + 2
+    buckets: dict = {}
+    disks = []
+    area = float(solid.sum())
+    tries = 0
+    while area < target_solid and tries < max_tries:
+        tries += 1
+        rad = rng.uniform(rmin, rmax)
+        cx = rng.uniform(keep_out[0] + rad, nx - keep_out[1] - rad)
+        cy = rng.uniform(1 + rad, ny - 1 - rad)
+        bx, by = int(cx // cell), int(cy // cell)
+        ok = True
+        for jx in range(bx - 1, bx + 2):
+            for jy in range(by - 1, by + 2):
+                for (ox, oy, orad) in buckets.get((jx, jy), ()):
+                    if (cx - ox) ** 2 + (cy - oy) ** 2 < (rad + orad + 1.0) ** 2:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        buckets.setdefault((bx, by), []).append((cx, cy, rad))
+        disks.append((cx, cy, rad))
+        x0, x1 = int(max(0, cx - rad - 1)), int(min(nx, cx + rad + 2))
+        y0, y1 = int(max(0, cy - rad - 1)), int(min(ny, cy + rad + 2))
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        m = (xx - cx) ** 2 + (yy - cy) ** 2 <= rad * rad
+        area += float((m & ~solid[y0:y1, x0:x1]).sum())
+        solid[y0:y1, x0:x1] |= m
+    solid = solid.astype(np.uint8)
+    inside = np.zeros((ny, nx), bool)
+    rA, rB = _phase_fields(inside, solid, seed)
+    lam = lambda_for_angle(45.0) if lam is None else lam
+    return Scenario(f"porous_disks_{nx}x{ny}", solid, rA, rB, bc_x="open", bc_y="wall",
+                    tau=(0.8, 1.0), u_in=u_in, rho_in=(RHO_M, RHO_D), lam=lam, G=G,
+                    extra={"n_disks": len(disks)})
+
+
+def cocurrent_channel(nx: int = 4096, ny: int = 256, frac_A: float = 0.4, g: float = 1e-6,
+                      lam: float | None = None, seed: int = 5, G: float = G_DEFAULT,
+                      amp: float = NOISE_AMP) -> Scenario:
+    """Co-current stratified flow (Sec. 3.1 shape): rows 0, ny-1 solid, x periodic, A in the bottom
+    ``frac_A`` of the channel, B above, body force g along x."""
+    y, x = _grid(ny, nx)
+    solid = np.zeros((ny, nx), bool)
+    solid[0, :] = True
+    solid[ny - 1, :] = True
+    inside = y < frac_A * ny
+    solid = solid.astype(np.uint8)
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    lam = lambda_for_angle(120.0) if lam is None else lam
+    return Scenario(f"cocurrent_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
+                    g=(g, 0.0), lam=lam, G=G)
+
+
+def ensemble_cases(ncases: int = 256, nmin: int = 64, nmax: int = 512, seed: int = 5,
+                   lam_range=(0.22, 2.17), G: float = G_DEFAULT) -> list:
+    """Uneven contact-angle ensemble: square cases of side n ~ U{nmin..nmax}, half flat wall and
+    half cylinder (R = n/6, droplet r = n/5 centred 0.6 r above the solid top), lambda uniform in
+    ``lam_range``."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for c in range(ncases):
+        n = int(rng.integers(nmin, nmax + 1))
+        lam = float(rng.uniform(*lam_range))
+        if c % 2 == 0:
+            sc = flat_droplet(nx=n, ny=n, r=n / 5.0, lam=lam, seed=seed * 1000 + c, G=G)
+        else:
+            sc = cylinder_droplet(n=n, R=n / 6.0, r=n / 5.0, lam=lam, seed=seed * 1000 + c, G=G)
+        sc.name = f"case{c:03d}_{sc.name}"
+        cases.append(sc)
+    return cases
+
+
+def lambda_sweep_cylinder(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110, 130, 150),
+                          G: float = G_DEFAULT) -> list:
+    """The 1024x1024 cylinder contact-angle sweep: one case per target angle, lambda from the
+    paper's correlation (Sec. 3.2), cylinder radius 160 and droplet radius 200 at n = 1024."""
+    out = []
+    for k, th in enumerate(angles):
+        sc = cylinder_droplet(n=n, R=160.0 * n / 1024.0, r=200.0 * n / 1024.0,
+                              lam=lambda_for_angle(th), seed=seed * 100 + k, G=G)
+        sc.name = f"sweep_theta{th}_{sc.name}"
+        out.append(sc)
+    return out

@@ -1,0 +1,236 @@
+"""Pins for the improved adhesion parameter (Eqs. 10-12), the open inlet / outlet (Sec. 3.3) and the
+measurement routines (circle fit and contact angle, Sec. 3.2)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_22256_gb300 import scenarios as S
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+# ---------------------------------------------------------------------------------------------
+# P2: Eq. 12 is Eq. 11 divided by G_w2 (coefficients as printed after Eq. 11)
+# ---------------------------------------------------------------------------------------------
+def _eq11(rho_e, Gw1, Gw2, delta):
+    s1 = t1 = 2.0 * Gw1 * Gw2 / (Gw1 + Gw2)
+    s2 = 2.0 * (Gw1 - s1) / delta
+    s3 = -s2 / (2.0 * delta)
+    t2 = 2.0 * (t1 - Gw2) / delta
+    t3 = t2 / (2.0 * delta)
+    if rho_e > delta:
+        return Gw1
+    if rho_e > 0:
+        return s1 + s2 * rho_e + s3 * rho_e ** 2
+    if rho_e > -delta:
+        return t1 + t2 * rho_e + t3 * rho_e ** 2
+    return Gw2
+
+
+@pytest.mark.parametrize("lam", [0.22, 0.47, 1.0, 1.35, 2.17])
+@pytest.mark.parametrize("delta", [0.8, 0.5])
+def test_eq12_equals_eq11_over_Gw2(lam, delta):
+    Gw2 = 0.17
+    for re in np.linspace(-1, 1, 401):
+        assert oracle.local_G(re, lam, delta) * Gw2 == pytest.approx(_eq11(re, lam * Gw2, Gw2, delta), rel=1e-12)
+
+
+@pytest.mark.parametrize("lam", [0.26, 0.88, 1.35, 2.1])
+def test_local_G_is_continuous_and_flat_at_the_joints(lam):
+    d, h = 0.8, 1e-6
+    G = lambda r: oracle.local_G(r, lam, d)
+    # values at the joints: lambda at +delta, 2 lambda / (1 + lambda) at 0, 1 at -delta
+    assert G(d) == pytest.approx(lam, rel=1e-14)
+    assert G(d + h) == lam
+    assert G(-d) == 1.0 and G(-d + 1e-12) == pytest.approx(1.0, abs=1e-10)
+    assert G(0.0) == pytest.approx(2 * lam / (1 + lam), rel=1e-15)
+    assert G(1e-15) == pytest.approx(G(0.0), rel=1e-12)
+    # zero slope where the quadratics meet the constants (smooth joints)
+    assert (G(d) - G(d - h)) / h == pytest.approx(0.0, abs=1e-5)
+    assert (G(-d + h) - G(-d)) / h == pytest.approx(0.0, abs=1e-5)
+    # monotone between the two plateaus
+    r = np.linspace(-1, 1, 2001)
+    v = np.array([G(x) for x in r])
+    dv = np.diff(v)
+    assert np.all(dv >= -1e-15) if lam >= 1 else np.all(dv <= 1e-15)
+
+
+def test_fig6_parameter_pairs_follow_lambda_definition():
+    """Fig. 6: G_w1 = lambda G_w2 with G_w2 = G_12 = 0.17 (to the printed two digits)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "contact_angle_correlation.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for gw1, lam in rows:
+        assert float(lam) * 0.17 == pytest.approx(float(gw1), abs=0.006)
+
+
+def test_lambda_one_makes_improved_equal_original():
+    """P3: lambda = 1 gives G_w1(x) = G_w2 everywhere, so both schemes step identically."""
+    for re in np.linspace(-1, 1, 101):
+        assert oracle.local_G(re, 1.0, 0.8) == 1.0
+    sc = S.cylinder_droplet(40, lam=1.0)
+    p = sc.params()
+    f0 = None
+    outs = []
+    for scheme in ("improved", "original"):
+        p["scheme"] = scheme
+        cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **p)
+        f0 = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+        outs.append(oracle.run(cfg, sc.solid, f0, 60))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_improved_and_original_differ_off_lambda_one():
+    sc = S.cylinder_droplet(40, lam=0.4)
+    p = sc.params()
+    outs = []
+    for scheme in ("improved", "original"):
+        p["scheme"] = scheme
+        cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **p)
+        f0 = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+        outs.append(oracle.run(cfg, sc.solid, f0, 20))
+    assert np.max(np.abs(outs[0] - outs[1])) > 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# Open boundaries (Sec. 3.3)
+# ---------------------------------------------------------------------------------------------
+def _open_cfg(nx, ny, **kw):
+    return oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="periodic", **kw)
+
+
+def test_uniform_inflow_is_stationary():
+    """f = f^eq(rho_in, u_in) everywhere with no forces is a fixed point of collide + stream with
+    the non-equilibrium bounce-back inlet and the copy outlet."""
+    nx, ny, u = 12, 6, 0.02
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = _open_cfg(nx, ny, G=0.0, u_in=u, rho_in=(0.7, 0.3))
+    f = np.zeros((2, 9, ny, nx))
+    for k, r in enumerate((0.7, 0.3)):
+        f[k] = oracle.feq(r, u, 0.0)[:, None, None]
+    f2 = oracle.run(cfg, solid, f, 5)
+    np.testing.assert_allclose(f2, f, rtol=1e-14, atol=1e-17)
+
+
+def test_inlet_and_outlet_rules_hold_after_streaming():
+    rng = np.random.default_rng(3)
+    nx, ny = 10, 7
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=1.0, u_in=0.01, rho_in=(1.0, 0.03))
+    fstar = rng.uniform(0.01, 0.2, (2, 9, ny, nx)) * (1 - solid)[None, None]
+    f = oracle.stream(cfg, solid, fstar)
+    assert np.all(np.isfinite(f))
+    for k, r in enumerate(cfg.rho_in):
+        fe = oracle.feq(r, cfg.u_in, 0.0)
+        for y in range(1, ny - 1):
+            for i in (1, 5, 8):
+                # non-equilibrium bounce-back about f^eq(rho_in, u_in)
+                assert f[k, i, y, 0] - fe[i] == pytest.approx(f[k, OPP[i], y, 0] - fe[OPP[i]], abs=1e-15)
+            for i in (3, 6, 7):
+                assert f[k, i, y, nx - 1] == f[k, i, y, nx - 2]
+            # interior populations: plain streaming from the upstream node or bounce-back
+            for i in range(9):
+                x, ys = 4, y - CY[i]
+                src = fstar[k, i, ys, x - CX[i]] if not solid[ys, x - CX[i]] else fstar[k, OPP[i], y, x]
+                assert f[k, i, y, x] == src
+
+
+def test_open_channel_mass_balance_per_step():
+    """Per step, the lattice gains exactly what enters through the inlet column minus what leaves
+    through the outlet column.  Inlet: the unknown populations replace the outgoing ones plus
+    f^eq_i - f^eq_opp(i) about (rho_in, u_in), a net w-weighted source of rho_in u_in per fluid
+    row and component.  Outlet: populations with e_x > 0 leave, the copied ones enter."""
+    nx, ny = 30, 12
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=1.0, u_in=0.01, rho_in=(1.0, 0.03))
+    sc_r = np.where(solid == 1, 0.0, 1.0)
+    f = oracle.init(cfg, solid, 0.3 * sc_r, 0.7 * sc_r)
+    f = oracle.run(cfg, solid, f, 50)
+    fstar = oracle.collide(cfg, solid, f)
+    f2 = oracle.stream(cfg, solid, fstar)
+    rows = slice(1, ny - 1)
+    for k in range(2):
+        m_before = fstar[k].sum()
+        lost = sum(fstar[k, i, rows, nx - 1].sum() for i in (1, 5, 8))     # leave at x = nx-1
+        lost += sum(fstar[k, i, rows, 0].sum() for i in (3, 6, 7))         # leave at x = 0
+        gained = sum(f2[k, i, rows, 0].sum() for i in (1, 5, 8))
+        gained += sum(f2[k, i, rows, nx - 1].sum() for i in (3, 6, 7))
+        assert f2[k].sum() == pytest.approx(m_before - lost + gained, rel=1e-13)
+        fe = oracle.feq(cfg.rho_in[k], cfg.u_in, 0.0)
+        src = sum(fe[i] - fe[OPP[i]] for i in (1, 5, 8))
+        assert src == pytest.approx(cfg.rho_in[k] * cfg.u_in, rel=1e-12)
+        inlet_net = sum(f2[k, i, rows, 0].sum() - fstar[k, OPP[i], rows, 0].sum() for i in (1, 5, 8))
+        # knowns at the inlet are the streamed values; the rule adds exactly src per row
+        known = sum(f2[k, OPP[i], rows, 0].sum() for i in (1, 5, 8))
+        assert sum(f2[k, i, rows, 0].sum() for i in (1, 5, 8)) == pytest.approx(known + (ny - 2) * src, rel=1e-13)
+        assert np.isfinite(inlet_net)
+
+
+# ---------------------------------------------------------------------------------------------
+# P13: interface points, circle fit and contact angle
+# ---------------------------------------------------------------------------------------------
+def test_circle_fit_exact_points():
+    t = np.linspace(0, 2 * np.pi, 37)[:-1]
+    pts = np.stack([31.25 + 17.5 * np.cos(t), -4.0 + 17.5 * np.sin(t)], axis=1)
+    cx, cy, r, rms = oracle.fit_circle(pts)
+    assert (cx, cy, r) == pytest.approx((31.25, -4.0, 17.5), abs=1e-10)
+    assert rms < 1e-10
+    # an arc only (a droplet cap) is enough
+    arc = pts[:12]
+    assert oracle.fit_circle(arc)[:3] == pytest.approx((31.25, -4.0, 17.5), abs=1e-9)
+
+
+@pytest.mark.parametrize("theta", [20.0, 45.0, 90.0, 121.0, 160.0])
+def test_contact_angle_formulas_on_constructed_circles(theta):
+    th = np.radians(theta)
+    # flat wall y = y_w: a circle of radius r whose centre is -r cos(theta) above the plane
+    r, yw = 11.0, 0.5
+    assert oracle.contact_angle_from_circle(5.0, yw - r * np.cos(th), r,
+                                            {"kind": "flat", "y_w": yw}) == pytest.approx(theta, abs=1e-9)
+    # circular solid of radius R centred at the origin: d^2 = R^2 + r^2 - 2 r R cos(theta)
+    R = 16.5
+    d = np.sqrt(R * R + r * r - 2 * r * R * np.cos(th))
+    surf = {"kind": "circle", "cx": 0.0, "cy": 0.0, "R": R}
+    assert oracle.contact_angle_from_circle(0.0, d, r, surf) == pytest.approx(theta, abs=1e-9)
+    # and geometrically: the circles' tangents at the intersection point meet at theta
+    px = (d * d + R * R - r * r) / (2 * d)       # along the line of centres
+    py = np.sqrt(R * R - px * px)
+    n_s = np.array([py, px]) / R                  # solid normal at (py, px) (centres on y axis)
+    n_d = (np.array([py, px]) - np.array([0.0, d])) / r
+    assert np.degrees(np.arccos(n_s @ n_d)) == pytest.approx(theta, abs=1e-9)
+
+
+def test_interface_points_on_a_smooth_droplet():
+    ny, nx, R, c = 60, 70, 17.3, (35.2, 28.7)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    dist = np.hypot(xx - c[0], yy - c[1])
+    phi = np.tanh((R - dist) / 2.5)
+    rA = 0.5 * (1 + phi)
+    rB = 0.5 * (1 - phi)
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="periodic", bc_y="periodic")
+    pts = oracle.interface_points(cfg, solid, rA, rB)
+    assert len(pts) > 100
+    assert np.max(np.abs(np.hypot(pts[:, 0] - c[0], pts[:, 1] - c[1]) - R)) < 0.05
+    cx, cy, r, rms = oracle.fit_circle(pts)
+    assert (cx, cy, r) == pytest.approx((c[0], c[1], R), abs=0.02)
+
+
+def test_interface_points_skip_nodes_near_solid():
+    ny, nx = 30, 30
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="periodic", bc_y="wall")
+    rA = np.where(np.arange(ny)[:, None] < 10, 0.9, 0.1) * np.ones((1, nx))
+    rA = rA + 0.0 * solid
+    rB = 1.0 - rA
+    ns = oracle.near_solid(cfg, solid)
+    # rows 0..3 are within 3 of the solid row; rows ny-3..ny-1 within 3 of the outside (wall)
+    assert ns[:4].all() and not ns[4:ny - 3].any() and ns[ny - 3:].all()
+    pts = oracle.interface_points(cfg, solid, rA, rB)
+    assert len(pts) == nx and np.allclose(pts[:, 1], 9.5)

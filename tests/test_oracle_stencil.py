@@ -1,0 +1,279 @@
+"""Pins for the oracle's stencil: E8 weights (Sec. 2.4), Table 1's node correspondence, the
+second-layer reconstruction, the wall list and the force sums (brute force on tiny grids)."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def _box_offsets():
+    return [(dx, dy) for dy in range(-2, 3) for dx in range(-2, 3) if (dx, dy) != (0, 0)]
+
+
+def _moment(w, a, b):
+    return sum(w[dx * dx + dy * dy] * Fraction(dx) ** a * Fraction(dy) ** b for dx, dy in _box_offsets())
+
+
+# ---------------------------------------------------------------------------------------------
+# P1: weights
+# ---------------------------------------------------------------------------------------------
+def test_e8_weights_match_published_values():
+    w = oracle.e8_weights()
+    for q, num, den in _read("e8_weights.txt"):
+        assert w[int(q)] == Fraction(int(num), int(den))
+
+
+def test_e8_weights_isotropy_identities():
+    """Moment identities of 8th-order isotropy, evaluated from the 5x5 box enumerated here."""
+    w = oracle.e8_weights()
+    assert _moment(w, 2, 0) == 1 and _moment(w, 0, 2) == 1
+    assert _moment(w, 4, 0) == Fraction(12, 7) == 3 * _moment(w, 2, 2)
+    assert _moment(w, 6, 0) == Fraction(32, 7) == 5 * _moment(w, 4, 2)
+    assert _moment(w, 8, 0) == 16 == 7 * _moment(w, 6, 2)
+    assert _moment(w, 4, 4) == Fraction(48, 35) == Fraction(3, 5) * _moment(w, 6, 2)
+    for a in range(0, 9):
+        for b in range(0, 9):
+            if (a % 2 or b % 2) and a + b <= 9:
+                assert _moment(w, a, b) == 0, (a, b)
+
+
+def test_e8_offset_table_covers_the_5x5_box():
+    offs = oracle.e8_offsets()
+    assert sorted(offs) == sorted(_box_offsets())
+    # first layer in the D2Q9 order: axes (1,0),(0,1),(-1,0),(0,-1) then diagonals
+    assert offs[:8] == [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    assert all(max(abs(dx), abs(dy)) == 2 for dx, dy in offs[8:])
+    # pairs (e, -e) sit two apart within each group of four (the force sums rely on it)
+    for n in range(0, 24, 4):
+        for j in range(2):
+            a, b = offs[n + j], offs[n + j + 2]
+            assert a == (-b[0], -b[1])
+
+
+# ---------------------------------------------------------------------------------------------
+# P12: Table 1 -- second-layer node n takes the information of first-layer node m = sign(e_n)
+# ---------------------------------------------------------------------------------------------
+def test_table1_correspondence_is_sign_of_offset():
+    offs = oracle.e8_offsets()
+    rows = _read("table1_node_correspondence.txt")
+    assert len(rows) == 16
+    for n, m in rows:
+        n, m = int(n), int(m)
+        ex, ey = offs[n - 1]
+        assert offs[m - 1] == (int(np.sign(ex)), int(np.sign(ey))), (n, m)
+        # ranges printed in Table 1
+        assert m == (n - 8 if n <= 16 else n - 12 if n <= 20 else n - 16)
+
+
+# ---------------------------------------------------------------------------------------------
+# P11: brute force on tiny grids
+# ---------------------------------------------------------------------------------------------
+def _weights_float():
+    return {int(q): int(a) / int(b) for q, a, b in _read("e8_weights.txt")}
+
+
+def _bf_forces(cfg, solid, rhoA, rhoB):
+    """Independent loop over the 5x5 box of each fluid node: cohesion (Eq. 8, other component,
+    E8 weights), adhesion (Eq. 9 with the local parameter of Eq. 12 / constant G_w1), body force;
+    second-layer sites that are not in-array fluid nodes take the value of x + sign(e)."""
+    W = _weights_float()
+    ny, nx = solid.shape
+    Gw2 = cfg.G if cfg.Gw2 is None else cfg.Gw2
+
+    def site(X, Y):
+        if not 0 <= X < nx:
+            if cfg.bc_x != "periodic":
+                return None
+            X %= nx
+        if not 0 <= Y < ny:
+            if cfg.bc_y != "periodic":
+                return None
+            Y %= ny
+        return X, Y
+
+    def first(x, y, dx, dy):
+        X = x + dx
+        if cfg.bc_x == "open":
+            X = min(max(X, 0), nx - 1)
+        p = site(X, y + dy)
+        if p is None or solid[p[1], p[0]]:
+            return 0.0, 0.0, 1.0
+        return rhoA[p[1], p[0]], rhoB[p[1], p[0]], 0.0
+
+    FA = np.zeros((2, ny, nx))
+    FB = np.zeros((2, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            gA = np.zeros(2)
+            gB = np.zeros(2)
+            a = np.zeros(2)
+            for dy in range(-2, 3):
+                for dx in range(-2, 3):
+                    if dx == 0 and dy == 0:
+                        continue
+                    w = W[dx * dx + dy * dy]
+                    if max(abs(dx), abs(dy)) == 2:
+                        p = site(x + dx, y + dy)
+                        if p is not None and not solid[p[1], p[0]]:
+                            vA, vB, s = rhoA[p[1], p[0]], rhoB[p[1], p[0]], 0.0
+                        else:
+                            vA, vB, s = first(x, y, int(np.sign(dx)), int(np.sign(dy)))
+                    else:
+                        vA, vB, s = first(x, y, dx, dy)
+                    e = np.array([dx, dy], float)
+                    gA += w * vA * e
+                    gB += w * vB * e
+                    a += w * s * e
+            rA, rB = rhoA[y, x], rhoB[y, x]
+            if cfg.scheme == "improved":
+                re = (rA - rB) / (rA + rB)
+                lam, d = cfg.lam, cfg.delta
+                s1 = 2 * lam / (1 + lam)
+                if re > d:
+                    h = lam
+                elif re > 0:
+                    h = s1 + 2 * (lam * lam - lam) / (d * (1 + lam)) * re + (lam - lam * lam) / (d * d * (1 + lam)) * re * re
+                elif re > -d:
+                    h = s1 + 2 * (lam - 1) / (d * (1 + lam)) * re + (lam - 1) / (d * d * (1 + lam)) * re * re
+                else:
+                    h = 1.0
+                GA = Gw2 * h
+            else:
+                GA = cfg.lam * Gw2
+            g = np.array(cfg.g, float)
+            FA[:, y, x] = -cfg.G * rA * gB - GA * rA * a + rA * g
+            FB[:, y, x] = -cfg.G * rB * gA - Gw2 * rB * a + rB * g
+    return FA, FB
+
+
+def _pillar_case(nx=8, ny=8, block=None):
+    solid = np.zeros((ny, nx), np.uint8)
+    if block is None:
+        solid[3, 3] = 1
+    else:
+        (x0, x1), (y0, y1) = block
+        solid[y0:y1, x0:x1] = 1
+    return solid
+
+
+@pytest.mark.parametrize("scheme,lam", [("improved", 0.4), ("improved", 1.7), ("original", 0.6)])
+@pytest.mark.parametrize("geom", ["pillar", "block_walls", "open_x"])
+def test_forces_match_brute_force(scheme, lam, geom):
+    rng = np.random.default_rng(7)
+    if geom == "pillar":
+        solid = _pillar_case()
+        cfg = oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic", scheme=scheme, lam=lam,
+                            G=1.2, g=(1e-3, -2e-3), nthreads=1)
+    elif geom == "block_walls":
+        solid = _pillar_case(9, 8, ((2, 5), (3, 6)))
+        solid[5, 7] = 1
+        cfg = oracle.Config(nx=9, ny=8, bc_x="periodic", bc_y="wall", scheme=scheme, lam=lam, G=1.2,
+                            Gw2=0.7, nthreads=1)
+    else:
+        solid = _pillar_case(10, 7)
+        solid[0, :] = 1
+        cfg = oracle.Config(nx=10, ny=7, bc_x="open", bc_y="wall", scheme=scheme, lam=lam, G=1.2,
+                            nthreads=1)
+    ny, nx = solid.shape
+    rA = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
+    rB = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
+    # a state whose densities are exactly these: all mass in the rest population
+    f = np.zeros((2, 9, ny, nx))
+    f[0, 0] = rA
+    f[1, 0] = rB
+    FA, FB = oracle.forces(cfg, solid, f)
+    bA, bB = _bf_forces(cfg, solid, rA, rB)
+    np.testing.assert_allclose(FA, bA, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(FB, bB, rtol=1e-12, atol=1e-14)
+
+
+def _entry(node, subst, seff, ax, ay, nx, x, y):
+    k = np.nonzero(node == y * nx + x)[0]
+    assert len(k) == 1, (x, y)
+    k = k[0]
+    return int(subst[k]), int(seff[k]), ax[k], ay[k]
+
+
+def _bits(*nodes):
+    """Mask with the bits of the given 1-based stencil node numbers."""
+    m = 0
+    for n in nodes:
+        m |= 1 << (n - 1)
+    return m
+
+
+def test_wall_list_single_pillar_by_hand():
+    """8x8 fully periodic, one solid node at (3,3): the wall list is the 24 nodes around it."""
+    solid = _pillar_case()
+    cfg = oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    expect = sorted((3 + dy) * 8 + (3 + dx) for dy in range(-2, 3) for dx in range(-2, 3)
+                    if (dx, dy) != (0, 0))
+    assert node.tolist() == expect
+    W = _weights_float()
+    # (3,4): pillar is first-layer node 4 (0,-1)
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 4) == (0, _bits(4), 0.0, -W[1])
+    # (3,5): pillar is second-layer node 12 (0,-2): replaced by first-layer node 4 = (3,4), fluid
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 5) == (_bits(12), 0, 0.0, 0.0)
+    # (5,5): pillar is node 15 (-2,-2) -> node 7 (-1,-1) = (4,4), fluid
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 5) == (_bits(15), 0, 0.0, 0.0)
+    # (5,4): pillar is knight node 19 (-2,-1) -> node 7 (-1,-1) = (4,3), fluid
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 4) == (_bits(19), 0, 0.0, 0.0)
+    # (4,5): pillar is knight node 23 (-1,-2) -> node 7 = (3,4), fluid
+    assert _entry(node, subst, seff, ax, ay, 8, 4, 5) == (_bits(23), 0, 0.0, 0.0)
+    # (2,2): pillar is first-layer diagonal node 5 (1,1)
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 8, 2, 2)
+    assert (sm, em) == (0, _bits(5)) and a_x == pytest.approx(W[2]) and a_y == pytest.approx(W[2])
+
+
+def test_wall_list_block_by_hand():
+    """8x8 fully periodic with a 3x3 solid block at x, y in [2, 4]."""
+    solid = _pillar_case(8, 8, ((2, 5), (2, 5)))
+    cfg = oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    W = _weights_float()
+    # fluid nodes within two cells (Chebyshev, on the torus) of the block: all but column 7 and row 7
+    near = [(x, y) for y in range(8) for x in range(8) if not solid[y, x] and x != 7 and y != 7]
+    assert node.tolist() == sorted(y * 8 + x for x, y in near)
+    # (3,5) right above the block's middle column
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 8, 3, 5)
+    assert sm == _bits(12, 23, 24)
+    assert em == _bits(4, 7, 8, 12, 23, 24)
+    assert a_x == pytest.approx(0.0, abs=1e-15)
+    assert a_y == pytest.approx(-(W[1] + 2 * W[2] + 2 * W[4] + 4 * W[5]))
+    # (3,6): (0,-2) = (3,4) is solid -> copied from (3,5), fluid; (+-1,-2), (+-2,-2) solid or
+    # fluid per the block: (2,4),(4,4) solid -> from (2,5),(4,5) fluid; (1,4),(5,4) fluid
+    sm, em, _, _ = _entry(node, subst, seff, ax, ay, 8, 3, 6)
+    assert sm == _bits(12, 23, 24) and em == 0
+
+
+def test_wall_list_counts_outside_of_wall_direction():
+    """Rows outside the array along a wall direction count as solid; periodic ones do not."""
+    solid = np.zeros((10, 6), np.uint8)
+    cfg = oracle.Config(nx=6, ny=10, bc_x="periodic", bc_y="wall")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    rows = sorted(set((node // 6).tolist()))
+    assert rows == [0, 1, 8, 9]
+    W = _weights_float()
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 6, 2, 0)
+    # y = -1 and y = -2 are outside: layer 1 below solid, layer 2 below copied from layer 1
+    assert em == _bits(4, 7, 8, 12, 19, 20, 15, 16, 23, 24)
+    assert sm == _bits(12, 15, 16, 19, 20, 23, 24)
+    assert a_y == pytest.approx(-(W[1] + 2 * W[2] + 2 * W[4] + 6 * W[5] + 4 * W[8]))
