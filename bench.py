@@ -1,0 +1,376 @@
+"""Throughput benchmark of the fused two-component pseudopotential LBM step on GB300.
+
+Workload (one GPU): the cylinder contact-angle case scaled to 1024x1024 (cylinder radius 160,
+droplet radius 200), seven adhesion values lambda targeting theta = 30..150 degrees, FP32 compute
+and FP32 SoA storage, run as one seven-case ensemble.  One bench step is one pass of the whole hot
+path over that batch: 100 time steps (fused collide-stream-force kernel, one launch per time step,
+replayed from a captured CUDA graph), then the FP64 diagnostics reduction and the contact-angle
+measurement of every case.
+
+Metric: MLUPS = lattice nodes x time steps / second over all nodes of all cases (whole job).
+Timed region: W warm-up steps, then exactly K steps between a barrier + synchronize on both sides,
+CUDA events on the library's stream; the populations (1.06 GB per buffer) are far larger than L2.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun each rank runs its own seven cases (weak scaling, no collective on the data path);
+rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (2-comp D2Q9) & % of GB300 HBM peak; FP32/FP16-store vs FP64 at stated error"
+UNIT = "MLUPS"
+INNER = 100            # time steps per bench step
+BYTES_PER_NODE = {"f32": 144, "f16": 72, "bf16": 72, "f64": 288}
+KERNEL_SOURCES = ("paper_2505_22256_gb300/csrc/lbm_step.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--n", type=int, default=1024, help="lattice side of each case")
+    ap.add_argument("--cases", type=int, default=7, help="number of lambda values (1..7)")
+    ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2505_22256_gb300 import scenarios as S
+
+    angles = (30, 50, 70, 90, 110, 130, 150)[: args.cases]
+    return S.lambda_sweep_cylinder(n=args.n, seed=2 + 1000 * rank, angles=angles)
+
+
+def config_dict(args, cases, world):
+    nodes = sum(c.nx * c.ny for c in cases)
+    fluid = sum(int((c.solid == 0).sum()) for c in cases)
+    return {
+        "workload": f"cylinder contact-angle sweep, {len(cases)} cases of {args.n}x{args.n} per GPU "
+                    f"(R={160 * args.n // 1024}, r={200 * args.n // 1024}, lambda for theta=30..150 deg), "
+                    f"{args.inner} time steps + diagnostics + contact angle per step",
+        "storage": args.storage, "cases_per_gpu": len(cases), "nodes_per_gpu": nodes,
+        "fluid_nodes_per_gpu": fluid, "inner_steps": args.inner, "parallelism": f"ensemble x{world} (no collective)",
+        "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE[args.storage] / 2 / 1e9),
+    }
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 6:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, p[2:6]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# measured peaks and the committed ncu counters
+# ------------------------------------------------------------------------------------------------
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(storage: str, nodes_per_launch: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch's nodes; None when
+    the summary is missing or was taken on a different version of the kernel source."""
+    p = os.path.join(ROOT, "profiles", f"k_step_{storage}_counters.txt")
+    try:
+        kv = {}
+        with open(p) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
+        return per_node * nodes_per_launch
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------------
+def cpu_baseline(args, seconds: float) -> dict:
+    import oracle
+
+    cases = workload(args)
+    sc = cases[len(cases) // 2]
+    cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+    f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        f = oracle.run(cfg, sc.solid, f, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 10000:
+            break
+    mlups = sc.nx * sc.ny * n / el / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, lambda={sc.lam:.4f}), {n} FP64 time steps "
+                      f"in {el:.1f} s on {cfg.nthreads} host threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cases = workload(args)
+    # each step: a bounded sample of the workload (time steps of one case), sized so that the whole
+    # --steps/--warmup run stays within a few minutes
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    base = None
+    vals = []
+    for k in range(args.warmup + args.steps):
+        b = cpu_baseline(args, per_step)
+        if k >= args.warmup:
+            vals.append(b["value"])
+            base = b
+    value = statistics.mean(vals)
+    ms_per_step = len(cases) * args.n * args.n * args.inner / (value * 1e6) * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, cases, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_22256_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cases = workload(args, rank)
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(cases, storage=args.storage, cuda_stream=stream.cuda_stream)
+    info = lat.info()
+    nodes = info["nodes"]
+    fluid = info["fluid_nodes"]
+
+    def contact_angle(i):
+        try:
+            return lat.contact_angle(i)[0]
+        except lbm.LbmError:  # no interface left to measure: reported as null
+            return None
+
+    def bench_step(ev_pairs=None):
+        if ev_pairs is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        lat.step(args.inner)
+        if ev_pairs is not None:
+            b.record(stream)
+            ev_pairs.append((a, b))
+        for i in range(len(cases)):
+            lat.diagnostics(i, allow_unstable=True)
+            contact_angle(i)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    pairs = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        bench_step(pairs)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = sum(a.elapsed_time(b) for a, b in pairs)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nodes * args.inner * args.steps / (total_ms / 1e3) / 1e6
+    launch_ms = step_ms / (args.inner * args.steps)
+    algo_bytes = BYTES_PER_NODE[args.storage] * fluid
+    achieved = algo_bytes / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = committed_traffic(args.storage, nodes)
+    d = lat.diagnostics(0, allow_unstable=True)
+    theta = [contact_angle(i) for i in range(len(cases))]
+
+    # e2e through the public API with host buffers: densities in (H2D), 100 steps, fields out (D2H)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        hin = [(pin(c.rhoA0.shape), pin(c.rhoB0.shape)) for c in cases]
+        for (a, b), c in zip(hin, cases):
+            a[...] = c.rhoA0
+            b[...] = c.rhoB0
+        hout = [[pin(c.rhoA0.shape) for _ in range(4)] for c in cases]
+        ksteps = max(2, args.steps // 4)
+
+        def e2e_step():
+            for i, (a, b) in enumerate(hin):
+                lbm.lbm_set_densities(lat.ctx, i, a, b, False)
+            lat.step(args.inner)
+            for i, o in enumerate(hout):
+                lbm.lbm_fields(lat.ctx, i, *o)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        s0 = time.perf_counter()
+        for _ in range(ksteps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        el = time.perf_counter() - s0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = sum(2 * c.nx * c.ny * 8 for c in cases)
+        d2h = sum(4 * c.nx * c.ny * 8 for c in cases)
+        e2e = {"value": world * nodes * args.inner * ksteps / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "step": "lbm_set_densities (host) for every case, lbm_step(%d), lbm_fields (host) for every case" % args.inner}
+
+    launches = args.inner + len(cases) * (2 + 1 + 8)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage, "data": "synthetic", "config": config_dict(args, cases, world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_step",
+                     "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
+        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
+        "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
+        "sample_diagnostics": {"theta_deg": theta, "case0_umax": d["umax"], "case0_unstable": d["unstable"]},
+    }
+    lat.close()
+    if rank == 0:
+        if not args.no_cpu and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+        elif not args.no_cpu:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

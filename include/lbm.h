@@ -1,0 +1,267 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-component pseudopotential lattice Boltzmann library.
+ *
+ * The library advances the time-step loop of the two-component immiscible pseudopotential
+ * (Shan-Chen-type) lattice Boltzmann model with the improved solid-fluid interaction scheme of
+ * Chen, Wang, Tao, Yang and Chen, "Improvement of Solid-Fluid Interaction Scheme in Lattice
+ * Boltzmann Immiscible Pseudopotential Models" (arXiv 2505.22256):
+ *   per-component densities (Eq. 3), inter-component cohesion force on the eighth-order isotropic
+ *   24-node stencil (Eq. 8, Sec. 2.4), solid-fluid adhesion force (Eq. 9) with the local adhesion
+ *   parameter of the improved scheme (Eqs. 10-12), second-layer reconstruction at walls (Sec. 2.4,
+ *   Table 1), SRT collision with Guo forcing (Eqs. 1, 2, 6, 7) and streaming with halfway
+ *   bounce-back (Sec. 3.5), plus the open inlet/outlet of Sec. 3.3.
+ *
+ * Conventions shared by every call
+ *   - Lattice: D2Q9, e_0 = (0,0), e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1), e_5..e_8 = (1,1),(-1,1),
+ *     (-1,-1),(1,-1); c_s^2 = 1/3; lattice units (dx = dt = 1).  Component 0 = "A" (the paper's
+ *     fluid 1), component 1 = "B" (fluid 2).
+ *   - 2-D arrays are row-major [ny][nx] with x fastest; populations are [2][9][ny][nx].
+ *   - Every call returns an lbm_status and never throws; lbm_last_error() gives a message for the
+ *     last failing call on the calling thread.
+ *   - Host inputs are copied before the call returns; the caller keeps ownership of every buffer
+ *     it passes.  The library does not retain caller pointers.
+ *   - All device work is issued on the context's CUDA stream (the one given at creation, or a
+ *     non-blocking stream the library creates when NULL is given).  lbm_step is asynchronous;
+ *     calls that return data to the host synchronise that stream first.  A device-side error of
+ *     an asynchronous call surfaces as LBM_ECUDA from the next call that synchronises.
+ *   - Not thread-safe per context: one host thread at a time may use a given context.
+ *   - There is no CPU fallback: every call that computes runs CUDA kernels for sm_103a and fails
+ *     with LBM_ECUDA when no such device is present.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; created by lbm_create / lbm_ensemble_create */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* invalid argument: sizes, parameters, NULL pointer, case index */
+    LBM_ENOMEM = 2,    /* device or host allocation failed */
+    LBM_ECUDA = 3,     /* a CUDA call or kernel failed (also: no usable sm_103a device) */
+    LBM_EUNSTABLE = 4, /* a non-finite or non-positive density was found (lbm_diagnostics) */
+    LBM_ETIMEOUT = 5,  /* lbm_synchronize gave up after its time limit */
+    LBM_ESTATE = 6,    /* call not valid in the context's current state */
+    LBM_EIO = 7        /* file error in lbm_save / lbm_load, or a file that does not match */
+} lbm_status;
+
+/* Boundary treatment along one axis. */
+typedef enum {
+    LBM_BC_PERIODIC = 0, /* wrap around */
+    LBM_BC_WALL = 1,     /* outside the array is solid: halfway bounce-back, s = 1 for adhesion */
+    LBM_BC_OPEN = 2      /* x only: velocity inlet at x = 0, outflow at x = nx-1 (Sec. 3.3) */
+} lbm_bc;
+
+typedef struct {
+    int32_t nx, ny; /* lattice size; each >= 5 */
+    int32_t bc_x;   /* lbm_bc */
+    int32_t bc_y;   /* LBM_BC_PERIODIC or LBM_BC_WALL */
+} lbm_grid;
+
+/* Solid-fluid interaction scheme (Sec. 2.3). */
+typedef enum {
+    LBM_ADS_ORIGINAL = 0, /* Eq. 9 with constant G_w1 = lambda * G_w2 */
+    LBM_ADS_IMPROVED = 1  /* Eq. 9 with G_w1(x) from the effective density, Eqs. 10-12 */
+} lbm_ads_mode;
+
+typedef struct {
+    double tau[2];        /* relaxation times tau_A, tau_B (Eq. 2); each > 0.5 */
+    double G_AB;          /* inter-component strength G_12 (Eq. 8), stencil weights with
+                             sum_e w(|e|^2) e_x^2 = 1 */
+    int32_t mode;         /* lbm_ads_mode */
+    double lambda;        /* strength coefficient lambda = G_w1 / G_w2 (Sec. 2.3.2); > 0 */
+    double G_w2;          /* adhesion parameter of component B; the paper sets G_w2 = G_12 */
+    double delta;         /* half-width delta of the interpolation in Eqs. 11-12, in (0, 1] */
+    double g[2];          /* body acceleration (force per unit density), F_k += rho_k g */
+    double u_in;          /* inlet x-velocity (LBM_BC_OPEN) */
+    double rho_in[2];     /* component densities imposed at the inlet (LBM_BC_OPEN) */
+    double rho0_store[2]; /* reference densities of the shifted 16-bit storage modes: populations
+                             are stored as f_i^k - w_i rho0_store[k]; ignored for FP32/FP64 */
+} lbm_params;
+
+/* Storage and arithmetic precision of the populations. */
+typedef enum {
+    LBM_STORE_F64 = 0,         /* FP64 storage, FP64 arithmetic */
+    LBM_STORE_F32 = 1,         /* FP32 storage, FP32 arithmetic */
+    LBM_STORE_F16_SHIFTED = 2, /* FP16 storage of f - w rho0, FP32 arithmetic */
+    LBM_STORE_BF16_SHIFTED = 3 /* BF16 storage of f - w rho0, FP32 arithmetic */
+} lbm_storage;
+
+/* Global diagnostics of one case over its fluid nodes, accumulated in FP64 (Sec. 3.2 measures:
+ * maximum spurious velocity, Fig. 10; density extrema, Fig. 11). */
+typedef struct {
+    double mass_A, mass_B;       /* sum of rho_A, rho_B */
+    double mom_x, mom_y;         /* sum of (rho_A + rho_B) u, u with the half-force shift */
+    double umax;                 /* max |u| */
+    double rhoA_min, rhoA_max;
+    double rhoB_min, rhoB_max;
+    int64_t n_fluid;             /* number of fluid nodes */
+    int32_t unstable;            /* 1 when a density was non-finite or <= 0, or u non-finite */
+    int32_t pad_;
+} lbm_diag;
+
+/* Solid surface a droplet rests on, for the contact angle. */
+typedef enum { LBM_SURFACE_FLAT = 0, LBM_SURFACE_CIRCLE = 1 } lbm_surface_kind;
+typedef struct {
+    int32_t kind;   /* lbm_surface_kind */
+    int32_t normal; /* flat: +1 when the fluid lies at y > y_w, -1 when at y < y_w */
+    double y_w;     /* flat: wall plane (halfway bounce-back: half a cell beyond the last fluid row) */
+    double cx, cy;  /* circle: centre of the solid disk */
+    double R;       /* circle: effective radius (disk radius + 0.5 for halfway bounce-back) */
+} lbm_surface;
+
+/* One case of an ensemble. */
+typedef struct {
+    lbm_grid grid;
+    const uint8_t* solid;  /* host, [ny][nx], nonzero = solid */
+    const double* rho_A0;  /* host, [ny][nx], initial density of A (ignored at solid nodes) */
+    const double* rho_B0;  /* host, [ny][nx], initial density of B */
+    lbm_params params;
+} lbm_case;
+
+typedef struct {
+    int32_t ncases;
+    int32_t storage;         /* lbm_storage */
+    int64_t nodes;           /* sum of nx*ny over cases */
+    int64_t fluid_nodes;     /* sum of fluid nodes */
+    int64_t wall_nodes;      /* sum of wall-list entries */
+    int64_t steps;           /* time steps taken since creation or the last state load */
+    int64_t state_bytes;     /* bytes of one population buffer (all cases) */
+    int64_t device_bytes;    /* device memory held by the context */
+    int32_t block_threads;   /* launch shape of the step kernel: threads per block */
+    int32_t block_rows;      /* rows per work item */
+    int32_t grid_blocks;     /* blocks per launch */
+    int32_t work_items;      /* work items per step */
+} lbm_info_t;
+
+/* ---------------------------------------------------------------------------------------------
+ * Creation and destruction
+ * ------------------------------------------------------------------------------------------- */
+
+/* Create a single-case context.
+ *   grid: lattice size and axis boundary types.  solid: host [ny][nx] mask, nonzero = solid; must
+ *   contain at least one fluid node.  params: model parameters (Eqs. 2, 8, 9, 11-12; invalid values
+ *   give LBM_EINVAL: tau <= 0.5, lambda <= 0, delta outside (0, 1], non-finite numbers, bc_y open).
+ *   rho_A0, rho_B0: host [ny][nx] initial densities (> 0 at fluid nodes); the populations start at
+ *   f = f^eq(rho_k, u = 0) (Eq. 6).  storage: lbm_storage.  cuda_stream: a cudaStream_t to issue
+ *   all work on, or NULL for a library-owned non-blocking stream.  *out receives the context.
+ * Builds the node flags and the wall list (Sec. 2.4 second-layer reconstruction) on the device. */
+lbm_status lbm_create(const lbm_grid* grid, const uint8_t* solid, const lbm_params* params,
+                      const double* rho_A0, const double* rho_B0, int32_t storage,
+                      void* cuda_stream, lbm_ctx** out);
+
+/* Create a context holding ncases independent cases of any sizes, stepped together by one launch
+ * per time step.  Each case is validated as in lbm_create.  All cases share one storage mode. */
+lbm_status lbm_ensemble_create(int32_t ncases, const lbm_case* cases, int32_t storage,
+                               void* cuda_stream, lbm_ctx** out);
+
+/* Release every device and host resource of the context (synchronises its stream).  NULL is a
+ * no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------------
+ * Time stepping
+ * ------------------------------------------------------------------------------------------- */
+
+/* Advance every case by n >= 0 time steps (Eq. 1: collide, force, stream; Sec. 2.2-2.4).
+ * Asynchronous on the context's stream.  Repeated calls replay a captured CUDA graph of the step
+ * launches. */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream, giving up after timeout_s seconds (<= 0: wait without limit)
+ * with LBM_ETIMEOUT.  Reports LBM_ECUDA for a device error of earlier asynchronous work. */
+lbm_status lbm_synchronize(lbm_ctx* ctx, double timeout_s);
+
+/* Re-initialise one case from new densities: f = f^eq(rho_k, 0).  rho_A0 / rho_B0 are [ny][nx]
+ * doubles on the host (on_device = 0) or on the device (on_device = 1); host buffers are copied
+ * before return, device buffers are read on the context's stream. */
+lbm_status lbm_set_densities(lbm_ctx* ctx, int32_t case_index, const double* rho_A0,
+                             const double* rho_B0, int32_t on_device);
+
+/* ---------------------------------------------------------------------------------------------
+ * Outputs
+ * ------------------------------------------------------------------------------------------- */
+
+/* Macroscopic fields of one case at the current state: rho_A, rho_B (Eq. 3) and the equilibrium
+ * velocity u = (sum_k sum_i f e + F/2) / (rho_A + rho_B) (Eqs. 4-5 with Guo's half-force shift);
+ * 0 at solid nodes.  Each output is [ny][nx] doubles, on the host (on_device = 0; the call
+ * synchronises) or on the device (on_device = 1; written asynchronously on the stream).  Any
+ * output pointer may be NULL. */
+lbm_status lbm_fields(lbm_ctx* ctx, int32_t case_index, double* rho_A, double* rho_B, double* ux,
+                      double* uy, int32_t on_device);
+
+/* Global FP64 diagnostics of one case (host output; synchronises).  Returns LBM_EUNSTABLE, with
+ * *out filled, when the state holds a non-finite or non-positive density. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t case_index, lbm_diag* out);
+
+/* Contact angle of the droplet of component A in one case (Sec. 3.2): interface points are the
+ * linear-interpolated zeros of the effective density rho^e (Eq. 10) along lattice rows and columns,
+ * away (> 3 cells) from non-fluid sites; an algebraic circle fit in FP64 refined by one
+ * Gauss-Newton step gives the droplet circle, and theta follows from its geometry relative to
+ * *surface (cos theta = (R^2 + r^2 - d^2) / (2 r R) on a circle, -normal (c_y - y_w) / r on a flat
+ * wall).  Host outputs; synchronises.  theta_deg, fit_rms (rms distance of the points from the
+ * fitted circle) and npoints may be NULL.  LBM_ESTATE when fewer than 8 interface points exist. */
+lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t case_index, const lbm_surface* surface,
+                             double* theta_deg, double* fit_rms, int64_t* npoints);
+
+/* Wall list of one case (host outputs; synchronises): fluid nodes whose 24-node stencil reaches a
+ * non-fluid site, in increasing node order y*nx + x.  Per entry: node index; subst = bit n-1 set
+ * when second-layer stencil node n (numbering of Table 1: 1-8 first layer in the D2Q9 order, 9-16
+ * = 2 e_(n-8), 17-20 and 21-24 the knight moves whose first-layer partner is n-12 and n-16) is
+ * replaced by its first-layer partner; seff = bit n-1 set when stencil node n counts as solid in
+ * the adhesion sum; a = sum_n w(|e_n|^2) seff_n e_n.  Call first with node = NULL to get *n; the
+ * arrays must then hold *n entries (any of them may be NULL). */
+lbm_status lbm_wall_list(lbm_ctx* ctx, int32_t case_index, int32_t* node, uint32_t* subst,
+                         uint32_t* seff, double* ax, double* ay, int64_t* n);
+
+/* Populations f_i^k(x, t) of one case after streaming (the state collision acts on), as host
+ * doubles [2][9][ny][nx]; 0 at solid nodes.  Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t case_index, double* f);
+
+/* Replace the state of one case by the post-streaming populations f (host doubles [2][9][ny][nx]),
+ * rounded to the storage type.  For LBM_BC_OPEN the populations that enter through the boundary
+ * columns are recomputed by the boundary rule at the next step. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t case_index, const double* f);
+
+/* Size and launch information. */
+lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
+
+/* ---------------------------------------------------------------------------------------------
+ * Launch shape
+ * ------------------------------------------------------------------------------------------- */
+
+/* Set the step kernel's launch shape: threads per block (64, 128 or 256) and rows per work
+ * item (>= 1, or 0 to size the work list at about two waves of resident blocks).  Rebuilds the
+ * work list and drops the captured graph. */
+lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
+
+/* Time candidate launch shapes on the live state (each for `steps` steps, after one warm-up
+ * launch) and keep the fastest.  The state advances by the steps taken; best_ms (may be NULL)
+ * receives the best time per step.  Synchronises. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms);
+
+/* ---------------------------------------------------------------------------------------------
+ * Checkpoints
+ * ------------------------------------------------------------------------------------------- */
+
+/* Write / read the raw populations of every case with a header (sizes, storage, step count and a
+ * hash of the parameters).  lbm_load requires a context built with the same cases and storage
+ * (LBM_EIO otherwise) and restores the state bit for bit. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* ---------------------------------------------------------------------------------------------
+ * Errors
+ * ------------------------------------------------------------------------------------------- */
+const char* lbm_status_str(int32_t status);
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -253,6 +253,8 @@ int64_t oracle_wall_list(const oracle_cfg* c, const uint8_t* solid, int32_t* nod
     return count;
 }
 
+static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f);
+
 /* ---------------------------------------------------------------------------------------------
  * Initial state: f = f^eq(rho_k, u = 0) at fluid nodes, 0 at solid nodes.
  * ------------------------------------------------------------------------------------------- */
@@ -267,6 +269,9 @@ void oracle_init(const oracle_cfg* c, const uint8_t* solid, const double* rhoA0,
             for (int i = 0; i < 9; i++) f[((size_t)k * 9 + i) * N + s] = solid[s] ? 0.0 : fe[i];
         }
     }
+    /* With open boundaries the entering populations of the boundary columns are, in every
+     * post-streaming state, the ones the boundary rule gives -- the initial state included. */
+    open_boundaries(c, solid, f, f);
 }
 
 /* Step (1): component densities rho_k = sum_i f_i^k (Eq. 3); 0 at solid nodes. */
@@ -373,34 +378,14 @@ int oracle_collide(const oracle_cfg* c, const uint8_t* solid, const double* f, d
     return 0;
 }
 
-/* Step (8): streaming with halfway bounce-back.
- * f_i(x, t+1) = f*_i(x - e_i) when x - e_i is a fluid node (periodic wrap), otherwise
- * f*_{opp(i)}(x) (halfway bounce-back, Sec. 3.5: the wall sits half a link from the fluid node).
- * Open x boundaries (Sec. 3.3): populations entering through x = 0 are given by non-equilibrium
- * bounce-back about f^eq(rho_in,k, (u_in, 0)) (the reading of the two-component Zou-He inlet);
- * populations entering through x = nx-1 are copied from column nx-2 (outflow). */
-int oracle_stream(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
+/* Open x boundaries (Sec. 3.3), applied to a post-streaming state f whose pre-streaming state was
+ * fstar.  Populations entering through x = 0 are given by non-equilibrium bounce-back about
+ * f^eq(rho_in,k, (u_in, 0)) (the reading of the two-component Zou-He inlet); populations entering
+ * through x = nx-1 are copied from column nx-2 (outflow), or bounced back if that node is solid. */
+static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
     size_t N = (size_t)c->nx * (size_t)c->ny;
-#pragma omp parallel for num_threads(c->nthreads) schedule(static)
-    for (int y = 0; y < c->ny; y++)
-        for (int x = 0; x < c->nx; x++) {
-            size_t s0 = idx(c, x, y);
-            for (int k = 0; k < 2; k++)
-                for (int i = 0; i < 9; i++) {
-                    size_t q = ((size_t)k * 9 + i) * N + s0;
-                    if (solid[s0]) { f[q] = 0.0; continue; }
-                    int X = x - CX[i], Y = y - CY[i];
-                    if (c->bc_x == BC_OPEN && (X < 0 || X >= c->nx)) {
-                        f[q] = NAN; /* unknown: set by the boundary rule below */
-                        continue;
-                    }
-                    if (wrap_site(c, &X, &Y) && !solid[idx(c, X, Y)])
-                        f[q] = fstar[((size_t)k * 9 + i) * N + idx(c, X, Y)];
-                    else
-                        f[q] = fstar[((size_t)k * 9 + OPP[i]) * N + s0];
-                }
-        }
-    if (c->bc_x == BC_OPEN) {
+    if (c->bc_x != BC_OPEN) return;
+    {
         for (int y = 0; y < c->ny; y++) {
             /* inlet, x = 0 */
             size_t s0 = idx(c, 0, y);
@@ -426,6 +411,34 @@ int oracle_stream(const oracle_cfg* c, const uint8_t* solid, const double* fstar
                         }
         }
     }
+}
+
+/* Step (8): streaming with halfway bounce-back.
+ * f_i(x, t+1) = f*_i(x - e_i) when x - e_i is a fluid node (periodic wrap), otherwise
+ * f*_{opp(i)}(x) (halfway bounce-back, Sec. 3.5: the wall sits half a link from the fluid node).
+ * Open x boundaries: see open_boundaries(). */
+int oracle_stream(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
+    size_t N = (size_t)c->nx * (size_t)c->ny;
+#pragma omp parallel for num_threads(c->nthreads) schedule(static)
+    for (int y = 0; y < c->ny; y++)
+        for (int x = 0; x < c->nx; x++) {
+            size_t s0 = idx(c, x, y);
+            for (int k = 0; k < 2; k++)
+                for (int i = 0; i < 9; i++) {
+                    size_t q = ((size_t)k * 9 + i) * N + s0;
+                    if (solid[s0]) { f[q] = 0.0; continue; }
+                    int X = x - CX[i], Y = y - CY[i];
+                    if (c->bc_x == BC_OPEN && (X < 0 || X >= c->nx)) {
+                        f[q] = NAN; /* unknown: set by the boundary rule below */
+                        continue;
+                    }
+                    if (wrap_site(c, &X, &Y) && !solid[idx(c, X, Y)])
+                        f[q] = fstar[((size_t)k * 9 + i) * N + idx(c, X, Y)];
+                    else
+                        f[q] = fstar[((size_t)k * 9 + OPP[i]) * N + s0];
+                }
+        }
+    open_boundaries(c, solid, fstar, f);
     return 0;
 }
 

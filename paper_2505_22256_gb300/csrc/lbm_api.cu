@@ -1,0 +1,698 @@
+// C ABI of the library (include/lbm.h): validation, device layout, graph-captured stepping and the
+// output calls.  All numerical work is done by the kernels in lbm_step.cu, lbm_geometry.cu and
+// lbm_contact.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+int contact_work_doubles();
+}
+
+using namespace lbm;
+
+struct lbm_ctx {
+    Ctx c;
+};
+
+namespace {
+
+thread_local std::string g_err;
+constexpr int kGraphSteps = 16;  // step launches per captured graph (even: ends on the same buffer)
+
+lbm_status fail(lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(Ctx& c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaSuccess) c.device_bytes += count * sizeof(T);
+    return e;
+}
+
+bool finite(double v) { return isfinite(v) != 0; }
+
+lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_params* p, const double* rA,
+                         const double* rB, int idx, int64_t* nfluid) {
+    if (!g || !solid || !p || !rA || !rB) return fail(LBM_EINVAL, "case %d: NULL argument", idx);
+    if (g->nx < 5 || g->ny < 5) return fail(LBM_EINVAL, "case %d: nx, ny must be >= 5 (got %d, %d)", idx, g->nx, g->ny);
+    if ((long long)g->nx * g->ny > (1LL << 31) - 1) return fail(LBM_EINVAL, "case %d: lattice too large", idx);
+    if (g->bc_x < 0 || g->bc_x > 2) return fail(LBM_EINVAL, "case %d: bad bc_x %d", idx, g->bc_x);
+    if (g->bc_y < 0 || g->bc_y > 1) return fail(LBM_EINVAL, "case %d: bc_y must be periodic or wall", idx);
+    for (int k = 0; k < 2; ++k) {
+        if (!finite(p->tau[k]) || p->tau[k] <= 0.5) return fail(LBM_EINVAL, "case %d: tau[%d] must be > 0.5", idx, k);
+        if (!finite(p->g[k]) || !finite(p->rho_in[k]) || !finite(p->rho0_store[k]))
+            return fail(LBM_EINVAL, "case %d: non-finite parameter", idx);
+    }
+    if (!finite(p->G_AB) || !finite(p->G_w2) || !finite(p->u_in)) return fail(LBM_EINVAL, "case %d: non-finite parameter", idx);
+    if (!finite(p->lambda) || p->lambda <= 0.0) return fail(LBM_EINVAL, "case %d: lambda must be > 0", idx);
+    if (!finite(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return fail(LBM_EINVAL, "case %d: delta must lie in (0, 1]", idx);
+    if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return fail(LBM_EINVAL, "case %d: bad mode", idx);
+    if (g->bc_x == LBM_BC_OPEN && (p->rho_in[0] <= 0.0 || p->rho_in[1] <= 0.0))
+        return fail(LBM_EINVAL, "case %d: inlet densities must be > 0", idx);
+    const long long N = (long long)g->nx * g->ny;
+    int64_t nf = 0;
+    for (long long s = 0; s < N; ++s) {
+        if (solid[s]) continue;
+        ++nf;
+        if (!finite(rA[s]) || !finite(rB[s]) || rA[s] <= 0.0 || rB[s] <= 0.0)
+            return fail(LBM_EINVAL, "case %d: initial densities must be finite and > 0 at fluid node %lld", idx, s);
+    }
+    if (nf == 0) return fail(LBM_EINVAL, "case %d: the mask has no fluid node", idx);
+    *nfluid = nf;
+    return LBM_OK;
+}
+
+DevCase make_desc(const lbm_grid& g, const lbm_params& p) {
+    DevCase d;
+    memset(&d, 0, sizeof d);
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.pitch = (g.nx + 31) / 32 * 32;
+    d.bc_x = g.bc_x;
+    d.bc_y = g.bc_y;
+    d.mode = p.mode;
+    for (int k = 0; k < 2; ++k) {
+        d.omega[k] = 1.0 / p.tau[k];
+        d.cF[k] = 1.0 - 0.5 / p.tau[k];
+        d.g[k] = p.g[k];
+        d.rho_in[k] = p.rho_in[k];
+        d.rho0[k] = p.rho0_store[k];
+    }
+    d.G = p.G_AB;
+    d.Gw2 = p.G_w2;
+    d.lam = p.lambda;
+    d.delta = p.delta;
+    const double l = p.lambda, dl = p.delta;
+    d.s1 = 2.0 * l / (1.0 + l);                          // s'_1 = t'_1
+    d.s2 = 2.0 * (l * l - l) / (dl * (1.0 + l));          // s'_2
+    d.s3 = (l - l * l) / (dl * dl * (1.0 + l));           // s'_3
+    d.t2 = 2.0 * (l - 1.0) / (dl * (1.0 + l));            // t'_2
+    d.t3 = (l - 1.0) / (dl * dl * (1.0 + l));             // t'_3
+    d.u_in = p.u_in;
+    return d;
+}
+
+size_t elem_size(int storage) {
+    switch (storage) {
+        case LBM_STORE_F64: return 8;
+        case LBM_STORE_F32: return 4;
+        default: return 2;
+    }
+}
+
+void drop_graphs(Ctx& c) {
+    if (c.graph) cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+    c.graph_steps = 0;
+}
+
+// Work list: per case, row chunks by column windows of block_threads (interior block_threads - 4).
+// Cases are laid out one after the other.  block_rows = 0 picks the chunk height so that the list
+// holds about two waves of resident blocks (at least 16 rows, at most 128).
+lbm_status build_items(Ctx& c) {
+    const int W = c.block_threads, Wi = W - 4;
+    int per_sm = 0;
+    CUDA_TRY(step_occupancy(c.storage, W, &per_sm));
+    if (per_sm < 1) return fail(LBM_ECUDA, "step kernel cannot be resident with %d threads", W);
+    const long long resident = (long long)per_sm * c.num_sms;
+    int H = c.block_rows;
+    if (H <= 0) {
+        long long strip_rows = 0;
+        for (const DevCase& d : c.hcases) strip_rows += (long long)((d.nx + Wi - 1) / Wi) * d.ny;
+        H = (int)std::min<long long>(128, std::max<long long>(16, (strip_rows + 2 * resident - 1) / (2 * resident)));
+    }
+    c.rows_used = H;
+    std::vector<int4> items;
+    for (size_t ci = 0; ci < c.hcases.size(); ++ci) {
+        DevCase& d = c.hcases[ci];
+        d.item_begin = (int)items.size();
+        const int nstrip = (d.nx + Wi - 1) / Wi;
+        for (int y0 = 0; y0 < d.ny; y0 += H)
+            for (int s = 0; s < nstrip; ++s) items.push_back(make_int4((int)ci, s * Wi - 2, y0, std::min(d.ny, y0 + H)));
+        d.item_end = (int)items.size();
+    }
+    if (c.items) {
+        cudaFree(c.items);
+        c.items = nullptr;
+    }
+    if (c.diag_part) {
+        cudaFree(c.diag_part);
+        c.diag_part = nullptr;
+    }
+    c.nitems = (int)items.size();
+    CUDA_TRY(cudaMalloc(&c.items, items.size() * sizeof(int4)));
+    CUDA_TRY(cudaMemcpy(c.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&c.diag_part, items.size() * kDiagN * sizeof(double)));
+    CUDA_TRY(cudaMemcpy(c.dcases, c.hcases.data(), c.hcases.size() * sizeof(DevCase), cudaMemcpyHostToDevice));
+    c.grid_blocks = (int)std::min<long long>(c.nitems, resident);
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status check_case(lbm_ctx* ctx, int ci) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (ci < 0 || ci >= (int)ctx->c.cases.size()) return fail(LBM_EINVAL, "case index %d out of range", ci);
+    return LBM_OK;
+}
+
+void free_ctx(Ctx& c) {
+    drop_graphs(c);
+    void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.widx, c.solid, c.wl_node, c.wl_subst, c.wl_seff, c.wl_a,
+                    c.wl_ar, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+}
+
+lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream, lbm_ctx** out) {
+    if (!out) return fail(LBM_EINVAL, "NULL output pointer");
+    *out = nullptr;
+    if (ncases < 1 || !cs) return fail(LBM_EINVAL, "need at least one case");
+    if (storage < LBM_STORE_F64 || storage > LBM_STORE_BF16_SHIFTED) return fail(LBM_EINVAL, "bad storage %d", storage);
+    std::vector<int64_t> nfluid(ncases);
+    for (int i = 0; i < ncases; ++i) {
+        lbm_status s = validate_case(&cs[i].grid, cs[i].solid, &cs[i].params, cs[i].rho_A0, cs[i].rho_B0, i, &nfluid[i]);
+        if (s != LBM_OK) return s;
+    }
+    int dev = 0, ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (ndev < 1) return fail(LBM_ECUDA, "no CUDA device");
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(LBM_ECUDA, "this library is built for sm_103a (GB300); device %d is sm_%d%d", dev, prop.major, prop.minor);
+
+    lbm_ctx* h = new (std::nothrow) lbm_ctx();
+    if (!h) return fail(LBM_ENOMEM, "host allocation");
+    Ctx& c = h->c;
+    c.storage = storage;
+    c.elem = elem_size(storage);
+    c.device = dev;
+    c.num_sms = prop.multiProcessorCount;
+    auto bail = [&](lbm_status s) {
+        free_ctx(c);
+        delete h;
+        return s;
+    };
+    if (stream) {
+        c.stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(LBM_ECUDA, "cudaStreamCreate failed"));
+        c.own_stream = true;
+    }
+
+    long long max_nodes = 0;
+    for (int i = 0; i < ncases; ++i) {
+        HostCase hc;
+        hc.grid = cs[i].grid;
+        hc.params = cs[i].params;
+        hc.nfluid = nfluid[i];
+        c.cases.push_back(hc);
+        DevCase d = make_desc(cs[i].grid, cs[i].params);
+        d.f_off = c.pop_elems;
+        d.n_off = c.node_elems;
+        d.d_off = c.dense_elems;
+        c.pop_elems += 18LL * d.ny * d.pitch;
+        c.node_elems += (long long)d.ny * d.pitch;
+        c.dense_elems += (long long)d.nx * d.ny;
+        max_nodes = std::max(max_nodes, (long long)d.nx * d.ny);
+        c.hcases.push_back(d);
+    }
+    auto cu = [&](cudaError_t e, const char* what) -> lbm_status {
+        if (e == cudaErrorMemoryAllocation) return fail(LBM_ENOMEM, "%s: out of device memory", what);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+        return LBM_OK;
+    };
+#define STEP(expr, what)                        \
+    do {                                        \
+        lbm_status s_ = cu((expr), what);       \
+        if (s_ != LBM_OK) return bail(s_);      \
+    } while (0)
+
+    STEP(dalloc(c, (unsigned char**)&c.f[0], c.pop_elems * c.elem), "population buffer");
+    STEP(dalloc(c, (unsigned char**)&c.f[1], c.pop_elems * c.elem), "population buffer");
+    STEP(cudaMemsetAsync(c.f[0], 0, c.pop_elems * c.elem, c.stream), "memset");
+    STEP(cudaMemsetAsync(c.f[1], 0, c.pop_elems * c.elem, c.stream), "memset");
+    STEP(dalloc(c, &c.flags, c.node_elems), "flags");
+    STEP(dalloc(c, &c.widx, c.node_elems), "wall index");
+    STEP(cudaMemsetAsync(c.flags, 0, c.node_elems * sizeof(uint16_t), c.stream), "memset");
+    STEP(cudaMemsetAsync(c.widx, 0xff, c.node_elems * sizeof(int32_t), c.stream), "memset");
+    STEP(dalloc(c, &c.solid, c.dense_elems), "masks");
+    STEP(dalloc(c, &c.dcases, ncases), "descriptors");
+    STEP(dalloc(c, &c.dense, 18 * max_nodes), "transfer scratch");
+    c.dense_cap = 18 * max_nodes;
+    STEP(dalloc(c, &c.fields, 4 * max_nodes), "field scratch");
+    STEP(dalloc(c, &c.diag_out, (size_t)ncases * kDiagN), "diagnostics");
+    STEP(dalloc(c, &c.ca_work, (size_t)contact_work_doubles()), "contact-angle scratch");
+    for (int i = 0; i < ncases; ++i) {
+        std::vector<uint8_t> m((size_t)c.hcases[i].nx * c.hcases[i].ny);
+        for (size_t s = 0; s < m.size(); ++s) m[s] = cs[i].solid[s] ? 1 : 0;
+        STEP(cudaMemcpy(c.solid + c.hcases[i].d_off, m.data(), m.size(), cudaMemcpyHostToDevice), "mask upload");
+    }
+    STEP(cudaMemcpy(c.dcases, c.hcases.data(), ncases * sizeof(DevCase), cudaMemcpyHostToDevice), "descriptors");
+
+    // flags and per-row wall counts, then the wall list
+    std::vector<int32_t*> offs(ncases, nullptr);
+    int32_t* counts = nullptr;
+    int max_ny = 0;
+    for (auto& d : c.hcases) max_ny = std::max(max_ny, d.ny);
+    STEP(cudaMalloc(&counts, (size_t)max_ny * sizeof(int32_t)), "row counts");
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < ncases && st == LBM_OK; ++i) {
+        const int ny = c.hcases[i].ny;
+        st = cu(cudaMalloc(&offs[i], (size_t)(ny + 1) * sizeof(int32_t)), "row offsets");
+        if (st == LBM_OK) st = cu(cudaMemsetAsync(counts, 0, (size_t)ny * sizeof(int32_t), c.stream), "memset");
+        if (st == LBM_OK) st = cu(launch_flags(c, i, counts), "flags kernel");
+        if (st == LBM_OK) st = cu(launch_scan_rows(counts, offs[i], ny, c.stream), "scan kernel");
+        int32_t tot = 0;
+        if (st == LBM_OK) st = cu(cudaMemcpyAsync(&tot, offs[i] + ny, sizeof tot, cudaMemcpyDeviceToHost, c.stream), "count");
+        if (st == LBM_OK) st = cu(cudaStreamSynchronize(c.stream), "flags");
+        c.hcases[i].w_off = c.nwall;
+        c.hcases[i].nwall = tot;
+        c.nwall += tot;
+    }
+    cudaFree(counts);
+    if (st == LBM_OK) st = cu(cudaMemcpy(c.dcases, c.hcases.data(), ncases * sizeof(DevCase), cudaMemcpyHostToDevice), "descriptors");
+    if (st == LBM_OK) st = cu(dalloc(c, &c.wl_node, c.nwall), "wall list");
+    if (st == LBM_OK) st = cu(dalloc(c, &c.wl_subst, c.nwall), "wall list");
+    if (st == LBM_OK) st = cu(dalloc(c, &c.wl_seff, c.nwall), "wall list");
+    if (st == LBM_OK) st = cu(dalloc(c, &c.wl_a, 2 * c.nwall), "wall list");
+    if (st == LBM_OK) st = cu(dalloc(c, (unsigned char**)&c.wl_ar, 2 * c.nwall * (storage == LBM_STORE_F64 ? 8 : 4)), "wall list");
+    for (int i = 0; i < ncases && st == LBM_OK; ++i) st = cu(launch_wall_fill(c, i, offs[i]), "wall-list kernel");
+    if (st == LBM_OK) st = cu(launch_wall_cast(c), "wall-list cast");
+    if (st == LBM_OK) st = cu(cudaStreamSynchronize(c.stream), "wall list");
+    for (auto p : offs)
+        if (p) cudaFree(p);
+    if (st != LBM_OK) return bail(st);
+
+    // work list and launch shape
+    c.block_threads = 128;
+    c.block_rows = 0;
+    st = build_items(c);
+    if (st != LBM_OK) return bail(st);
+
+    // initial state f = f^eq(rho_k, 0)
+    for (int i = 0; i < ncases; ++i) {
+        const long long N = (long long)c.hcases[i].nx * c.hcases[i].ny;
+        STEP(cudaMemcpyAsync(c.fields, cs[i].rho_A0, N * sizeof(double), cudaMemcpyHostToDevice, c.stream), "density upload");
+        STEP(cudaMemcpyAsync(c.fields + N, cs[i].rho_B0, N * sizeof(double), cudaMemcpyHostToDevice, c.stream), "density upload");
+        STEP(launch_feq_rest(c, i, c.fields, c.fields + N, c.dense), "init kernel");
+        STEP(launch_set_state(c, i, c.dense), "init kernel");
+    }
+    STEP(cudaStreamSynchronize(c.stream), "initialisation");
+#undef STEP
+    *out = h;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid* grid, const uint8_t* solid, const lbm_params* params, const double* rho_A0,
+                      const double* rho_B0, int32_t storage, void* cuda_stream, lbm_ctx** out) {
+    if (!grid || !params) return fail(LBM_EINVAL, "NULL argument");
+    lbm_case cs;
+    cs.grid = *grid;
+    cs.solid = solid;
+    cs.rho_A0 = rho_A0;
+    cs.rho_B0 = rho_B0;
+    cs.params = *params;
+    return create_impl(1, &cs, storage, cuda_stream, out);
+}
+
+lbm_status lbm_ensemble_create(int32_t ncases, const lbm_case* cases, int32_t storage, void* cuda_stream,
+                               lbm_ctx** out) {
+    return create_impl(ncases, cases, storage, cuda_stream, out);
+}
+
+void lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->c.stream);
+    free_ctx(ctx->c);
+    delete ctx;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (n < 0) return fail(LBM_EINVAL, "negative step count");
+    Ctx& c = ctx->c;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(c.stream, &cap));
+    const bool may_graph = cap == cudaStreamCaptureStatusNone;
+    while (n > 0) {
+        if (may_graph && n >= kGraphSteps && c.cur == 0) {
+            if (!c.graph) {
+                cudaGraph_t g = nullptr;
+                CUDA_TRY(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t le = cudaSuccess;
+                for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) le = launch_step(c, c.f[k & 1], c.f[(k & 1) ^ 1], c.stream);
+                cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
+                if (le != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return fail(LBM_ECUDA, "step launch during capture: %s", cudaGetErrorString(le));
+                }
+                if (ee != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
+                cudaError_t ie = cudaGraphInstantiate(&c.graph, g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+                c.graph_steps = kGraphSteps;
+            }
+            CUDA_TRY(cudaGraphLaunch(c.graph, c.stream));
+            n -= kGraphSteps;
+            c.steps += kGraphSteps;
+        } else {
+            CUDA_TRY(launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream));
+            c.cur ^= 1;
+            --n;
+            ++c.steps;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx* ctx, double timeout_s) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    Ctx& c = ctx->c;
+    if (timeout_s <= 0) {
+        CUDA_TRY(cudaStreamSynchronize(c.stream));
+        return LBM_OK;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c.stream);
+        if (e == cudaSuccess) return LBM_OK;
+        if (e != cudaErrorNotReady) return fail(LBM_ECUDA, "stream: %s", cudaGetErrorString(e));
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(LBM_ETIMEOUT, "stream still busy after %.3f s", el);
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+lbm_status lbm_set_densities(lbm_ctx* ctx, int32_t ci, const double* rho_A0, const double* rho_B0, int32_t on_device) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!rho_A0 || !rho_B0) return fail(LBM_EINVAL, "NULL density");
+    Ctx& c = ctx->c;
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    const double *a = rho_A0, *b = rho_B0;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(c.fields, rho_A0, N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        CUDA_TRY(cudaMemcpyAsync(c.fields + N, rho_B0, N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        a = c.fields;
+        b = c.fields + N;
+    }
+    CUDA_TRY(launch_feq_rest(c, ci, a, b, c.dense));
+    CUDA_TRY(launch_set_state(c, ci, c.dense));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_ctx* ctx, int32_t ci, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    Ctx& c = ctx->c;
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    if (on_device) {
+        CUDA_TRY(launch_fields(c, ci, rho_A, rho_B, ux, uy, false));
+        return LBM_OK;
+    }
+    CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, false));
+    double* outs[4] = {rho_A, rho_B, ux, uy};
+    for (int q = 0; q < 4; ++q)
+        if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], c.fields + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!out) return fail(LBM_EINVAL, "NULL output");
+    Ctx& c = ctx->c;
+    CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, true));
+    CUDA_TRY(launch_diag_reduce(c, ci));
+    double v[kDiagN];
+    CUDA_TRY(cudaMemcpyAsync(v, c.diag_out + (size_t)ci * kDiagN, sizeof v, cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    out->mass_A = v[0];
+    out->mass_B = v[1];
+    out->mom_x = v[2];
+    out->mom_y = v[3];
+    out->umax = v[4];
+    out->rhoA_min = v[5];
+    out->rhoA_max = v[6];
+    out->rhoB_min = v[7];
+    out->rhoB_max = v[8];
+    out->n_fluid = (int64_t)llround(v[9]);
+    out->unstable = v[10] != 0.0;
+    out->pad_ = 0;
+    if (out->unstable) return fail(LBM_EUNSTABLE, "case %d: non-finite or non-positive density", ci);
+    return LBM_OK;
+}
+
+lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surface, double* theta_deg, double* fit_rms,
+                             int64_t* npoints) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!surface) return fail(LBM_EINVAL, "NULL surface");
+    if (surface->kind == LBM_SURFACE_CIRCLE && !(surface->R > 0)) return fail(LBM_EINVAL, "surface radius must be > 0");
+    if (surface->kind != LBM_SURFACE_CIRCLE && surface->kind != LBM_SURFACE_FLAT) return fail(LBM_EINVAL, "bad surface kind");
+    Ctx& c = ctx->c;
+    CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, false));
+    double o[4];
+    CUDA_TRY(launch_contact_angle(c, ci, *surface, o));
+    if (npoints) *npoints = (int64_t)llround(o[2]);
+    if (o[3] != 0.0) return fail(LBM_ESTATE, "case %d: only %.0f interface points", ci, o[2]);
+    if (theta_deg) *theta_deg = o[0];
+    if (fit_rms) *fit_rms = o[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_wall_list(lbm_ctx* ctx, int32_t ci, int32_t* node, uint32_t* subst, uint32_t* seff, double* ax,
+                         double* ay, int64_t* n) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!n) return fail(LBM_EINVAL, "NULL count");
+    Ctx& c = ctx->c;
+    const DevCase& d = c.hcases[ci];
+    *n = d.nwall;
+    if (d.nwall == 0) return LBM_OK;
+    if (node) CUDA_TRY(cudaMemcpyAsync(node, c.wl_node + d.w_off, d.nwall * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    if (subst) CUDA_TRY(cudaMemcpyAsync(subst, c.wl_subst + d.w_off, d.nwall * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    if (seff) CUDA_TRY(cudaMemcpyAsync(seff, c.wl_seff + d.w_off, d.nwall * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    if (ax) CUDA_TRY(cudaMemcpyAsync(ax, c.wl_a + d.w_off, d.nwall * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (ay) CUDA_TRY(cudaMemcpyAsync(ay, c.wl_a + c.nwall + d.w_off, d.nwall * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t ci, double* f) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(LBM_EINVAL, "NULL output");
+    Ctx& c = ctx->c;
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    CUDA_TRY(launch_get_state(c, ci, c.dense));
+    CUDA_TRY(cudaMemcpyAsync(f, c.dense, 18 * N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t ci, const double* f) {
+    lbm_status s = check_case(ctx, ci);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(LBM_EINVAL, "NULL input");
+    Ctx& c = ctx->c;
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    CUDA_TRY(cudaMemcpyAsync(c.dense, f, 18 * N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(launch_set_state(c, ci, c.dense));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
+    if (!ctx || !out) return fail(LBM_EINVAL, "NULL argument");
+    const Ctx& c = ctx->c;
+    memset(out, 0, sizeof *out);
+    out->ncases = (int32_t)c.cases.size();
+    out->storage = c.storage;
+    for (size_t i = 0; i < c.cases.size(); ++i) {
+        out->nodes += (int64_t)c.cases[i].grid.nx * c.cases[i].grid.ny;
+        out->fluid_nodes += c.cases[i].nfluid;
+    }
+    out->wall_nodes = c.nwall;
+    out->steps = c.steps;
+    out->state_bytes = (int64_t)(c.pop_elems * c.elem);
+    out->device_bytes = (int64_t)c.device_bytes;
+    out->block_threads = c.block_threads;
+    out->block_rows = c.rows_used;
+    out->grid_blocks = c.grid_blocks;
+    out->work_items = c.nitems;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!(threads == 64 || threads == 128 || threads == 256)) return fail(LBM_EINVAL, "threads must be 64, 128 or 256");
+    if (rows < 0) return fail(LBM_EINVAL, "rows must be >= 0 (0 = automatic)");
+    Ctx& c = ctx->c;
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    c.block_threads = threads;
+    c.block_rows = rows;
+    return build_items(c);
+}
+
+lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
+    Ctx& c = ctx->c;
+    const int cand_t[] = {64, 128, 256};
+    const int cand_r[] = {0, 16, 32, 64, 128};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bt = c.block_threads, br = c.block_rows;
+    for (int t : cand_t)
+        for (int r : cand_r) {
+            lbm_status s = lbm_set_launch(ctx, t, r);
+            if (s != LBM_OK) continue;
+            if (launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream) != cudaSuccess) continue;
+            c.cur ^= 1;
+            ++c.steps;
+            cudaEventRecord(e0, c.stream);
+            for (int k = 0; k < steps; ++k) {
+                launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream);
+                c.cur ^= 1;
+                ++c.steps;
+            }
+            cudaEventRecord(e1, c.stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / steps < best) {
+                best = ms / steps;
+                bt = t;
+                br = r;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(cudaGetLastError());
+    lbm_status s = lbm_set_launch(ctx, bt, br);
+    if (s != LBM_OK) return s;
+    if (best_ms) *best_ms = best;
+    return LBM_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, storage, ncases, pad;
+    int64_t steps, bytes;
+    uint64_t hash;
+};
+
+uint64_t params_hash(const Ctx& c) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+    };
+    for (const auto& hc : c.cases) {
+        mix(&hc.grid, sizeof hc.grid);
+        mix(&hc.params, sizeof hc.params);
+    }
+    return h;
+}
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(LBM_EINVAL, "NULL argument");
+    Ctx& c = ctx->c;
+    std::vector<unsigned char> buf(c.pop_elems * c.elem);
+    CUDA_TRY(cudaMemcpyAsync(buf.data(), c.f[c.cur], buf.size(), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "LBMGB300", 8);
+    h.version = 1;
+    h.storage = c.storage;
+    h.ncases = (int32_t)c.cases.size();
+    h.steps = c.steps;
+    h.bytes = (int64_t)buf.size();
+    h.hash = params_hash(c);
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(LBM_EIO, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(LBM_EIO, "short write to %s", path);
+}
+
+lbm_status lbm_load(lbm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(LBM_EINVAL, "NULL argument");
+    Ctx& c = ctx->c;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(LBM_EIO, "cannot open %s", path);
+    CkptHeader h;
+    std::vector<unsigned char> buf(c.pop_elems * c.elem);
+    bool ok = fread(&h, sizeof h, 1, fp) == 1;
+    if (ok && (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1 || h.storage != c.storage ||
+               h.ncases != (int32_t)c.cases.size() || h.bytes != (int64_t)buf.size() || h.hash != params_hash(c))) {
+        fclose(fp);
+        return fail(LBM_EIO, "%s does not match this context", path);
+    }
+    ok = ok && fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    fclose(fp);
+    if (!ok) return fail(LBM_EIO, "short read from %s", path);
+    CUDA_TRY(cudaMemcpyAsync(c.f[c.cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    c.steps = h.steps;
+    return LBM_OK;
+}
+
+const char* lbm_status_str(int32_t s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_EINVAL: return "LBM_EINVAL";
+        case LBM_ENOMEM: return "LBM_ENOMEM";
+        case LBM_ECUDA: return "LBM_ECUDA";
+        case LBM_EUNSTABLE: return "LBM_EUNSTABLE";
+        case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
+        case LBM_ESTATE: return "LBM_ESTATE";
+        case LBM_EIO: return "LBM_EIO";
+        default: return "LBM_UNKNOWN";
+    }
+}
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Device-side definitions shared by the library's kernels: lattice tables, the per-case
+// descriptor, node flags and the storage-type traits.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ------------------------------------------------------------------------------------------------
+// Boundary kinds (mirror lbm_bc) and node flags.
+// ------------------------------------------------------------------------------------------------
+enum : int { kPeriodic = 0, kWall = 1, kOpen = 2 };
+
+// uint16 per node:
+//   bits 0-7  link i = bit+1 is blocked: the node upstream along e_i (x - e_i) is not fluid, so
+//             f_i arrives by halfway bounce-back of f*_opp(i) at the node itself.  At an outflow
+//             node the bits of the entering populations (e_x < 0) describe the links of the
+//             node one column upstream, from which those populations are copied.
+//   bit 8     solid node
+//   bit 9     wall-list node: the 24-node stencil reaches a non-fluid site
+//   bit 10    outflow node whose upstream neighbour is solid: entering populations bounce back
+//   bit 11    a non-fluid site lies within three cells (Chebyshev) -- excluded from the interface
+//             points of the contact-angle measurement
+constexpr uint16_t kSolidBit = 1u << 8;
+constexpr uint16_t kWallBit = 1u << 9;
+constexpr uint16_t kOutletOwnBit = 1u << 10;
+constexpr uint16_t kNearSolidBit = 1u << 11;
+
+// ------------------------------------------------------------------------------------------------
+// D2Q9 (Sec. 2.1): 0 rest; 1-4 = (1,0),(0,1),(-1,0),(0,-1); 5-8 = (1,1),(-1,1),(-1,-1),(1,-1).
+// Written as functions so fully unrolled loops fold them into immediates.
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+// lattice weights 4/9, 1/9, 1/36 as exact double quotients
+__host__ __device__ __forceinline__ constexpr double wq(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// ------------------------------------------------------------------------------------------------
+// 24-node eighth-order stencil in the numbering of Table 1 (index n-1 for node n): first layer in
+// the D2Q9 order, then 2 e_(n-8) for n = 9..16, then the knight moves (2,1),(-2,1),(-2,-1),(2,-1)
+// and (1,2),(-1,2),(-1,-2),(1,-2).  Used by the wall-list builder, whose masks are reported in
+// this numbering.
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ constexpr int s24x(int n) {
+    return n < 8 ? cx(n + 1) : n < 16 ? 2 * cx(n - 7) : n < 20 ? 2 * cx(n - 11) : cx(n - 15);
+}
+__host__ __device__ __forceinline__ constexpr int s24y(int n) {
+    return n < 8 ? cy(n + 1) : n < 16 ? 2 * cy(n - 7) : n < 20 ? cy(n - 11) : 2 * cy(n - 15);
+}
+// E8 weights by squared length (normalised so that sum_e w e_x^2 = 1)
+__host__ __device__ __forceinline__ constexpr double w8(int e2) {
+    return e2 == 1 ? 4.0 / 21.0 : e2 == 2 ? 4.0 / 45.0 : e2 == 4 ? 1.0 / 60.0 : e2 == 5 ? 2.0 / 315.0 : 1.0 / 5040.0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Per-case descriptor (device copy; built on the host).
+// ------------------------------------------------------------------------------------------------
+struct DevCase {
+    int nx, ny, pitch;      // pitch: elements per stored row (multiple of 32)
+    int bc_x, bc_y;
+    int mode;               // 0 original, 1 improved
+    long long f_off;        // element offset of the case's [2][9][ny][pitch] block in a population buffer
+    long long n_off;        // element offset of the case's [ny][pitch] block in per-node arrays
+    long long d_off;        // element offset of the case's [ny][nx] block in dense node arrays
+    long long w_off;        // first wall-list entry of the case
+    long long nwall;        // wall-list entries of the case
+    int item_begin, item_end;
+    double omega[2];        // 1 / tau_k
+    double cF[2];           // 1 - 1 / (2 tau_k)
+    double G, Gw2, lam;
+    double delta;
+    double s1, s2, s3, t2, t3;   // Eq. 12 coefficients s'_1 = t'_1, s'_2, s'_3, t'_2, t'_3
+    double g[2];
+    double u_in, rho_in[2];
+    double rho0[2];         // storage shift per component
+};
+
+// ------------------------------------------------------------------------------------------------
+// Storage traits: load/store one population value of storage type S as compute type R.
+// 16-bit types hold f - w rho0; the kernels add and remove the shift around ld() and st().
+// ------------------------------------------------------------------------------------------------
+template <class S>
+struct Store;
+
+template <>
+struct Store<double> {
+    static constexpr bool kShift = false;
+    __device__ __forceinline__ static double ld(const double* p) { return __ldg(p); }
+    __device__ __forceinline__ static void st(double* p, double v) { *p = v; }
+};
+template <>
+struct Store<float> {
+    static constexpr bool kShift = false;
+    __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+    __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    static constexpr bool kShift = true;
+    __device__ __forceinline__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static constexpr bool kShift = true;
+    __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    __device__ __forceinline__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Compute type for a storage type: FP64 storage computes in FP64, everything else in FP32.
+template <class S>
+struct ComputeOf {
+    using type = float;
+};
+template <>
+struct ComputeOf<double> {
+    using type = double;
+};
+
+}  // namespace lbm

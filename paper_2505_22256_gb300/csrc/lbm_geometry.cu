@@ -1,0 +1,227 @@
+// Geometry preprocessing on the device: node flags (solid, blocked links for halfway bounce-back,
+// wall-list membership) and the wall list with the second-layer reconstruction of Sec. 2.4.
+//
+// Wall list: the fluid nodes whose 24-node eighth-order stencil reaches a site that is not an
+// in-array fluid node (solid, or outside the array along a non-periodic axis), in increasing node
+// order y*nx + x.  For each entry:
+//   subst  bit n-1 set when second-layer stencil node n (Table 1 numbering) is not a fluid node and
+//          therefore takes the information of its first-layer partner x + sign(e_n)
+//   seff   bit n-1 set when stencil node n counts as solid in the adhesion sum (Eq. 9): a solid or
+//          outside first-layer site, or a replaced second-layer node whose partner is one
+//   a      sum_n w(|e_n|^2) seff_n e_n  (FP64)
+// Along an open axis a first-layer site beyond the boundary column is the boundary column itself.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+struct Geo {
+    int nx, ny, bc_x, bc_y;
+    const uint8_t* solid;  // dense [ny][nx]
+};
+
+// Is (X, Y) a fluid node after the periodic wrap?  Outside a non-periodic axis: no.
+__device__ __forceinline__ bool fluid_at(const Geo& g, int X, int Y) {
+    if (X < 0 || X >= g.nx) {
+        if (g.bc_x != kPeriodic) return false;
+        X = ((X % g.nx) + g.nx) % g.nx;
+    }
+    if (Y < 0 || Y >= g.ny) {
+        if (g.bc_y != kPeriodic) return false;
+        Y = ((Y % g.ny) + g.ny) % g.ny;
+    }
+    return g.solid[(long long)Y * g.nx + X] == 0;
+}
+
+// Solid switch of a first-layer site (dx, dy in {-1, 0, 1}).
+__device__ __forceinline__ bool first_layer_solid(const Geo& g, int X, int Y, int dx, int dy) {
+    int Xs = X + dx;
+    if (g.bc_x == kOpen) Xs = Xs < 0 ? 0 : (Xs > g.nx - 1 ? g.nx - 1 : Xs);
+    return !fluid_at(g, Xs, Y + dy);
+}
+
+__global__ void k_flags(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
+                        uint16_t* __restrict__ flags_all, int32_t* __restrict__ widx_all,
+                        int32_t* __restrict__ row_counts) {
+    const DevCase C = cases[c];
+    const Geo g{C.nx, C.ny, C.bc_x, C.bc_y, solid_all + C.d_off};
+    const long long N = (long long)C.nx * C.ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
+        const long long o = C.n_off + (long long)Y * C.pitch + X;
+        widx_all[o] = -1;
+        if (g.solid[s]) {
+            flags_all[o] = kSolidBit;
+            continue;
+        }
+        uint16_t fl = 0;
+        for (int i = 1; i < 9; ++i) {
+            const int sx = X - cx(i), sy = Y - cy(i);
+            bool blocked;
+            if (C.bc_x == kOpen && (sx < 0 || sx >= C.nx)) blocked = false;  // enters through the open boundary
+            else blocked = !fluid_at(g, sx, sy);
+            if (blocked) fl |= (uint16_t)(1u << (i - 1));
+        }
+        if (C.bc_x == kOpen && X == C.nx - 1) {
+            // outflow: entering populations are those of the node one column upstream
+            const bool base_fluid = fluid_at(g, X - 1, Y);
+            if (!base_fluid) fl |= kOutletOwnBit;
+            for (int i = 1; i < 9; ++i) {
+                if (cx(i) >= 0) continue;
+                const bool blocked = !base_fluid || !fluid_at(g, X, Y - cy(i));
+                fl = blocked ? (uint16_t)(fl | (1u << (i - 1))) : (uint16_t)(fl & ~(1u << (i - 1)));
+            }
+        }
+        bool near = false;
+        for (int dy = -3; dy <= 3 && !near; ++dy)
+            for (int dx = -3; dx <= 3 && !near; ++dx) near = !fluid_at(g, X + dx, Y + dy);
+        if (near) fl |= kNearSolidBit;
+        bool touches = false;
+        for (int n = 0; n < 24 && !touches; ++n) touches = !fluid_at(g, X + s24x(n), Y + s24y(n));
+        if (touches) {
+            fl |= kWallBit;
+            atomicAdd(row_counts + Y, 1);
+        }
+        flags_all[o] = fl;
+    }
+}
+
+// Exclusive scan of n counts by one block; offsets[n] receives the total.
+__global__ void k_scan(const int32_t* __restrict__ counts, int32_t* __restrict__ offsets, int n) {
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        const int v = i < n ? counts[i] : 0;
+        int incl = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int ws = lane < nw ? warp_sums[lane] : 0;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, ws, off);
+                if (lane >= off) ws += t;
+            }
+            if (lane < nw) warp_sums[lane] = ws;  // inclusive warp prefix
+        }
+        __syncthreads();
+        const int before = carry + (warp > 0 ? warp_sums[warp - 1] : 0);
+        if (i < n) offsets[i] = before + incl - v;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (tid == 0) offsets[n] = carry;
+}
+
+// One block per row: wall nodes of the row in increasing x get consecutive entries.
+__global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
+                            const uint16_t* __restrict__ flags_all, int32_t* __restrict__ widx_all,
+                            const int32_t* __restrict__ row_off, int32_t* __restrict__ wl_node,
+                            uint32_t* __restrict__ wl_subst, uint32_t* __restrict__ wl_seff,
+                            double* __restrict__ wl_a, long long nwall_total) {
+    const DevCase C = cases[c];
+    const Geo g{C.nx, C.ny, C.bc_x, C.bc_y, solid_all + C.d_off};
+    const int Y = blockIdx.x;
+    __shared__ int32_t warp_cnt[32];
+    __shared__ int32_t running;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) running = 0;
+    __syncthreads();
+    for (int base = 0; base < C.nx; base += blockDim.x) {
+        const int X = base + tid;
+        bool is_wall = false;
+        if (X < C.nx) is_wall = (flags_all[C.n_off + (long long)Y * C.pitch + X] & kWallBit) != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, is_wall);
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = running;
+        for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+        before += __popc(bal & ((1u << lane) - 1u));
+        if (is_wall) {
+            const long long e = C.w_off + row_off[Y] + before;
+            uint32_t sm = 0, em = 0;
+            for (int n = 0; n < 24; ++n) {
+                const int ex = s24x(n), ey = s24y(n);
+                bool s;
+                if (ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1) {
+                    s = first_layer_solid(g, X, Y, ex, ey);
+                } else if (fluid_at(g, X + ex, Y + ey)) {
+                    s = false;
+                } else {
+                    sm |= 1u << n;
+                    s = first_layer_solid(g, X, Y, (ex > 0) - (ex < 0), (ey > 0) - (ey < 0));
+                }
+                if (s) em |= 1u << n;
+            }
+            double ax = 0.0, ay = 0.0;
+            for (int p = 0; p < 12; ++p) {  // pairs (n, n+2): e_(n+2) = -e_n within each group of four
+                const int n = (p / 2) * 4 + (p % 2), m = n + 2;
+                const int ex = s24x(n), ey = s24y(n);
+                const double w = w8(ex * ex + ey * ey);
+                const double ds = (double)((em >> n) & 1u) - (double)((em >> m) & 1u);
+                ax += w * ds * ex;
+                ay += w * ds * ey;
+            }
+            wl_node[e] = Y * C.nx + X;
+            wl_subst[e] = sm;
+            wl_seff[e] = em;
+            wl_a[e] = ax;
+            wl_a[nwall_total + e] = ay;
+            widx_all[C.n_off + (long long)Y * C.pitch + X] = (int32_t)e;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < nw; ++w) tot += warp_cnt[w];
+            running += tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_cast(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+}  // namespace
+
+cudaError_t launch_flags(Ctx& c, int ci, int32_t* row_counts) {
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    const int g = (int)((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
+    k_flags<<<g, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.widx, row_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(counts, offsets, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_fill(Ctx& c, int ci, const int32_t* row_offsets) {
+    k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.widx, row_offsets,
+                                                        c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_cast(Ctx& c) {
+    if (c.nwall == 0) return cudaSuccess;
+    if (c.storage == LBM_STORE_F64)
+        return cudaMemcpyAsync(c.wl_ar, c.wl_a, 2 * c.nwall * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    const long long n = 2 * c.nwall;
+    const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_cast<<<g, 256, 0, c.stream>>>(c.wl_a, (float*)c.wl_ar, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

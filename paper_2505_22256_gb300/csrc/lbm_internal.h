@@ -1,0 +1,97 @@
+// Host-side internals of the library: the context and the kernel launch entry points that the
+// C-ABI layer (lbm_api.cu) calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kDiagN = 12;  // per-item partial record: see diag_partial layout in lbm_step.cu
+
+struct HostCase {
+    lbm_grid grid;
+    lbm_params params;
+    int64_t nfluid = 0;
+};
+
+struct Ctx {
+    int storage = LBM_STORE_F32;
+    size_t elem = 4;                 // bytes per stored population value
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+
+    std::vector<HostCase> cases;
+    std::vector<DevCase> hcases;     // host copy of the descriptors
+    DevCase* dcases = nullptr;
+
+    long long pop_elems = 0;         // elements in one population buffer
+    long long node_elems = 0;        // elements in per-node (pitched) arrays
+    long long dense_elems = 0;       // sum of nx*ny
+    long long nwall = 0;
+
+    void* f[2] = {nullptr, nullptr}; // ping-pong population buffers (post-collision f*)
+    int cur = 0;                     // f[cur] holds the current state
+    uint16_t* flags = nullptr;       // [node_elems]
+    int32_t* widx = nullptr;         // [node_elems] wall-list index of a wall node, -1 otherwise
+    uint8_t* solid = nullptr;        // [dense_elems] copy of the masks
+    int32_t* wl_node = nullptr;      // wall list, all cases back to back
+    uint32_t* wl_subst = nullptr;
+    uint32_t* wl_seff = nullptr;
+    double* wl_a = nullptr;          // [2][nwall] adhesion vectors in FP64
+    void* wl_ar = nullptr;           // [2][nwall] the same in the compute type
+
+    // work list of the step kernel
+    int block_threads = 128;
+    int block_rows = 0;              // 0: automatic
+    int rows_used = 0;
+    int grid_blocks = 0;
+    int4* items = nullptr;
+    int nitems = 0;
+
+    // scratch
+    double* dense = nullptr;         // [18 * max case nodes] doubles for population transfers
+    long long dense_cap = 0;
+    double* fields = nullptr;        // [4][max case nodes]
+    double* diag_part = nullptr;     // [nitems][kDiagN]
+    double* diag_out = nullptr;      // [ncases][kDiagN]
+    double* ca_work = nullptr;       // contact-angle reductions
+    int ca_cap = 0;
+
+    // CUDA graph of kGraphSteps step launches
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+
+    int64_t steps = 0;
+    size_t device_bytes = 0;
+};
+
+// lbm_step.cu
+cudaError_t launch_step(Ctx& c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_fields(Ctx& c, int case_index, double* rhoA, double* rhoB, double* ux, double* uy,
+                          bool diag);
+cudaError_t launch_diag_reduce(Ctx& c, int case_index);
+cudaError_t launch_set_state(Ctx& c, int case_index, const double* dense_f);
+cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);
+cudaError_t launch_feq_rest(Ctx& c, int case_index, const double* rhoA, const double* rhoB, double* dense_f);
+int step_smem_bytes(int storage, int threads);
+cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm);
+
+// lbm_geometry.cu
+cudaError_t launch_flags(Ctx& c, int case_index, int32_t* row_counts);
+cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cudaStream_t s);
+cudaError_t launch_wall_fill(Ctx& c, int case_index, const int32_t* row_offsets);
+cudaError_t launch_wall_cast(Ctx& c);
+
+// lbm_contact.cu
+cudaError_t launch_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* host_out4);
+
+}  // namespace lbm

@@ -34,6 +34,12 @@ def mean_field_G(rho_m: float = RHO_M, rho_d: float = RHO_D, cs2: float = 1.0 / 
 # steps on the 96x96 cylinder case.)
 G_DEFAULT = round(mean_field_G(), 3)
 
+# Default adhesion parameter of component B for the synthetic workloads.  With both forces on the
+# same normalised stencil, G_w2 = G_AB puts a wall force of about 0.53 lambda per unit density on
+# the main phase and cases with lambda >= 1.7 diverge; G_w2 = 0.3 keeps the whole lambda range of
+# the sweep (0.22 .. 2.17) stable with theta increasing in lambda.
+GW2_DEFAULT = 0.3
+
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -78,7 +84,7 @@ class Scenario:
     tau: tuple = (1.0, 1.0)
     G: float = G_DEFAULT
     lam: float = 1.0
-    Gw2: float | None = None
+    Gw2: float | None = GW2_DEFAULT
     delta: float = 0.8
     g: tuple = (0.0, 0.0)
     u_in: float = 0.0

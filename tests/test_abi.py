@@ -1,0 +1,115 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point that include/lbm.h
+declares, rejects invalid arguments with LBM_EINVAL before touching the device, and reports the
+absence of a GB300 as LBM_ECUDA (there is no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2505_22256_gb300 import build, lbm as binding
+
+    build.build()
+    binding.load_library()
+    return binding
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_documented_calls():
+    names = _declared_functions()
+    for must in ("lbm_create", "lbm_step", "lbm_fields", "lbm_contact_angle", "lbm_diagnostics",
+                 "lbm_wall_list", "lbm_ensemble_create", "lbm_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    lib = ctypes.CDLL(lbm.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(lbm.SYMBOLS) == _declared_functions()
+
+
+def test_struct_layouts_match_header(lbm):
+    assert ctypes.sizeof(lbm.lbm_grid) == 16
+    assert ctypes.sizeof(lbm.lbm_params) == 8 * 13 + 8   # int32 mode padded to 8
+    assert lbm.lbm_params.lambda_.offset == 32
+    assert ctypes.sizeof(lbm.lbm_diag) == 9 * 8 + 8 + 8
+    assert ctypes.sizeof(lbm.lbm_surface) == 8 + 4 * 8
+    assert ctypes.sizeof(lbm.lbm_info_t) == 8 + 6 * 8 + 16
+
+
+def _case(n=16):
+    solid = np.zeros((n, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    r = np.full((n, n), 0.5)
+    return solid, r, r.copy()
+
+
+@pytest.mark.parametrize("field,value", [("tau", (0.5, 1.0)), ("lambda_", 0.0), ("delta", 1.5),
+                                         ("delta", 0.0), ("G_AB", float("nan")), ("mode", 7)])
+def test_invalid_parameters_are_rejected(lbm, field, value):
+    solid, a, b = _case()
+    p = lbm.make_params()
+    if field == "tau":
+        p.tau[0], p.tau[1] = value
+    else:
+        setattr(p, field, value)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16), solid, p, a, b)
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_invalid_grids_and_fields_are_rejected(lbm):
+    solid, a, b = _case()
+    p = lbm.make_params()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(4, 16), solid[:, :4], p, a[:, :4], b[:, :4])
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16, "periodic", "open"), solid, p, a, b)
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16), np.ones((16, 16), np.uint8), p, a, b)
+    assert e.value.status == lbm.LBM_EINVAL and "no fluid" in str(e.value)
+    bad = a.copy()
+    bad[5, 5] = -1.0
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16), solid, p, bad, b)
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_ensemble_create([], lbm.LBM_STORE_F32)
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_null_context_is_rejected(lbm):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step(None, 1)
+    assert e.value.status == lbm.LBM_EINVAL
+    lbm.lbm_destroy(None)  # no-op
+
+
+def test_no_cpu_fallback_without_a_gb300(lbm):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    solid, a, b = _case()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16), solid, lbm.make_params(), a, b)
+    assert e.value.status == lbm.LBM_ECUDA
+
+
+def test_status_strings(lbm):
+    assert lbm.status_name(0) == "LBM_OK"
+    assert lbm.status_name(4) == "LBM_EUNSTABLE"
+    assert lbm.status_name(99) == "LBM_UNKNOWN"

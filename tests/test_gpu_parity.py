@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle on the same seeded
+inputs.  Integer structures (wall list, masks) must match bit for bit; FP64 storage to ~1e-10;
+FP32 storage to max relative |d rho| <= 1e-5 after 100 steps (the stated tolerance); 16-bit shifted
+storage reports its error against the oracle."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_22256_gb300 import lbm, scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2505_22256_gb300 import build
+
+    build.build()
+    oracle.build()
+    lbm.load_library()
+
+
+def ocfg(sc):
+    return oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+
+
+def orun(sc, n):
+    cfg = ocfg(sc)
+    f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    return cfg, oracle.run(cfg, sc.solid, f, n)
+
+
+def rel_rho(g, o, solid):
+    fl = solid == 0
+    return max(float(np.max(np.abs(g[0] - o[0])[fl] / o[0][fl])), float(np.max(np.abs(g[1] - o[1])[fl] / o[1][fl])))
+
+
+def pillar_case():
+    solid = np.zeros((8, 8), np.uint8)
+    solid[3, 3] = 1
+    r = np.where(solid == 1, 0.0, 0.6)
+    return S.Scenario("pillar8", solid, r, r * 0.5, bc_x="periodic", bc_y="periodic", lam=0.5)
+
+
+def small_porous():
+    return S.porous_disks(nx=192, ny=96, rmin=5, rmax=11, keep_out=(12, 12), seed=9, porosity=0.7)
+
+
+SCENARIOS = {
+    "cylinder96": lambda: S.cylinder_droplet(96, lam=0.6),
+    "ragged131x77": lambda: S.cylinder_droplet(77, nx=131, R=12, r=15, lam=1.4),
+    "flat64x48": lambda: S.flat_droplet(64, 48, r=12, lam=0.4),
+    "free64": lambda: S.free_droplet(64, R=14),
+    "throat256x96": lambda: S.throat_channel(256, 96, R=34, r=22, g=1e-5),
+    "porous_open": small_porous,
+    "original_cyl": lambda: S.cylinder_droplet(96, lam=0.5, scheme="original"),
+    "pillar8": pillar_case,
+    "gw2_equals_G": lambda: S.Scenario(**{**S.cylinder_droplet(64, lam=0.7).__dict__, "Gw2": None}),
+}
+
+
+# ---------------------------------------------------------------------------------------------
+# geometry: bit-exact wall list
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(SCENARIOS))
+def test_wall_list_bit_exact(name):
+    sc = SCENARIOS[name]()
+    lat = lbm.Lattice(sc, "f64")
+    g = lat.wall_list()
+    o = oracle.wall_list(ocfg(sc), sc.solid)
+    assert len(g[0]) == len(o[0])
+    assert len(o[0]) > 0 or (sc.solid.sum() == 0 and sc.bc_x == sc.bc_y == "periodic")
+    for a, b in zip(g[:3], o[:3]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(g[3], o[3])
+    np.testing.assert_array_equal(g[4], o[4])
+    info = lat.info()
+    assert info["wall_nodes"] == len(o[0])
+    assert info["fluid_nodes"] == int((sc.solid == 0).sum())
+    lat.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# state transfer
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "pillar8"])
+def test_initial_state_and_roundtrip(name):
+    sc = SCENARIOS[name]()
+    cfg = ocfg(sc)
+    f0 = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    lat = lbm.Lattice(sc, "f64")
+    np.testing.assert_allclose(lat.populations(), f0, rtol=1e-15, atol=1e-17)
+    f30 = oracle.run(cfg, sc.solid, f0, 30)
+    lat.set_populations(f30)
+    np.testing.assert_allclose(lat.populations(), f30, rtol=1e-14, atol=1e-17)
+    lat.close()
+    lat = lbm.Lattice(sc, "f32")
+    np.testing.assert_allclose(lat.populations(), f0, rtol=1e-7, atol=1e-9)
+    lat.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# multi-step parity
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(SCENARIOS))
+def test_f64_matches_oracle_after_100_steps(name):
+    sc = SCENARIOS[name]()
+    cfg, f = orun(sc, 100)
+    o = oracle.fields(cfg, sc.solid, f)
+    lat = lbm.Lattice(sc, "f64")
+    lat.step(100)
+    g = lat.fields()
+    assert rel_rho(g, o, sc.solid) <= 1e-10
+    assert max(np.max(np.abs(g[2] - o[2])), np.max(np.abs(g[3] - o[3]))) <= 1e-11
+    np.testing.assert_allclose(lat.populations(), f, rtol=1e-9, atol=1e-13)
+    lat.close()
+
+
+@pytest.mark.parametrize("name", list(SCENARIOS))
+def test_f32_matches_oracle_after_100_steps(name):
+    """The stated FP32 bar: max relative |d rho| <= 1e-5 after 100 steps."""
+    sc = SCENARIOS[name]()
+    cfg, f = orun(sc, 100)
+    o = oracle.fields(cfg, sc.solid, f)
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(100)
+    g = lat.fields()
+    err = rel_rho(g, o, sc.solid)
+    du = max(np.max(np.abs(g[2] - o[2])), np.max(np.abs(g[3] - o[3])))
+    lat.close()
+    assert err <= 1e-5, err
+    assert du <= 1e-6, du
+
+
+@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "throat256x96", "flat64x48"])
+def test_f32_one_step_from_developed_state(name):
+    """Every node's single update from an oracle state (rounded to FP32) matches the oracle's
+    update of the same rounded state to FP32 rounding."""
+    sc = SCENARIOS[name]()
+    cfg, f = orun(sc, 150)
+    f32 = f.astype(np.float32).astype(np.float64)
+    lat = lbm.Lattice(sc, "f32")
+    lat.set_populations(f32)
+    lat.step(1)
+    g = lat.populations()
+    o = oracle.run(cfg, sc.solid, f32, 1)
+    scale = np.abs(o).max(axis=(2, 3), keepdims=True)
+    assert np.max(np.abs(g - o) / scale) <= 2e-6
+    lat.close()
+
+
+def test_fields_and_diagnostics_match_oracle():
+    sc = SCENARIOS["cylinder96"]()
+    cfg, f = orun(sc, 60)
+    lat = lbm.Lattice(sc, "f64")
+    lat.step(60)
+    d = lat.diagnostics()
+    od = oracle.diagnostics(cfg, sc.solid, f)
+    for k in ("mass_A", "mass_B", "rhoA_min", "rhoA_max", "rhoB_min", "rhoB_max", "umax"):
+        assert d[k] == pytest.approx(od[k], rel=1e-10), k
+    for k in ("mom_x", "mom_y"):
+        assert d[k] == pytest.approx(od[k], rel=1e-8, abs=1e-12), k
+    assert d["n_fluid"] == int((sc.solid == 0).sum()) and d["unstable"] == 0
+    lat.close()
+
+
+def test_mass_conservation_f32():
+    sc = SCENARIOS["cylinder96"]()
+    lat = lbm.Lattice(sc, "f32")
+    m0 = lat.diagnostics()
+    lat.step(500)
+    m1 = lat.diagnostics()
+    for k in ("mass_A", "mass_B"):
+        assert abs(m1[k] / m0[k] - 1) < 2e-5, (k, m0[k], m1[k])
+    lat.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# launch shapes, ensembles, checkpoints
+# ---------------------------------------------------------------------------------------------
+def test_launch_shapes_give_identical_results():
+    sc = SCENARIOS["ragged131x77"]()
+    ref = None
+    for threads, rows in ((128, 64), (64, 7), (256, 16), (128, 1)):
+        lat = lbm.Lattice(sc, "f32")
+        lbm.lbm_set_launch(lat.ctx, threads, rows)
+        lat.step(37)
+        f = lat.populations()
+        lat.close()
+        if ref is None:
+            ref = f
+        else:
+            np.testing.assert_array_equal(f, ref)
+
+
+def test_ensemble_equals_single_cases():
+    cases = [SCENARIOS["cylinder96"](), SCENARIOS["flat64x48"](), SCENARIOS["porous_open"](), SCENARIOS["free64"]()]
+    ens = lbm.Lattice(cases, "f32")
+    ens.step(41)
+    for i, sc in enumerate(cases):
+        one = lbm.Lattice(sc, "f32")
+        one.step(41)
+        np.testing.assert_array_equal(ens.populations(i), one.populations())
+        one.close()
+    assert ens.info()["ncases"] == 4
+    ens.close()
+
+
+def test_checkpoint_roundtrip_is_bit_exact():
+    sc = SCENARIOS["cylinder96"]()
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(20)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "state.lbm")
+        lbm.lbm_save(lat.ctx, p)
+        lat.step(13)
+        a = lat.populations()
+        lbm.lbm_load(lat.ctx, p)
+        assert lat.info()["steps"] == 20
+        lat.step(13)
+        np.testing.assert_array_equal(lat.populations(), a)
+        other = lbm.Lattice(SCENARIOS["flat64x48"](), "f32")
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_load(other.ctx, p)
+        assert e.value.status == lbm.LBM_EIO
+        other.close()
+    lat.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# 16-bit shifted storage: error against the oracle is reported, not hidden
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,bound", [("f16", 5e-3), ("bf16", 5e-2)])
+def test_shifted_16bit_storage_error(storage, bound):
+    sc = SCENARIOS["cylinder96"]()
+    cfg, f = orun(sc, 100)
+    o = oracle.fields(cfg, sc.solid, f)
+    lat = lbm.Lattice(sc, storage, rho0_store=(0.0, 0.0))
+    lat.step(100)
+    g = lat.fields()
+    err = rel_rho(g, o, sc.solid)
+    print(f"{storage}: max rel |d rho| after 100 steps = {err:.3e}")
+    assert np.isfinite(err) and err <= bound
+    lat.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# contact angle
+# ---------------------------------------------------------------------------------------------
+def test_contact_angle_routine_matches_oracle_on_the_same_state():
+    sc = SCENARIOS["cylinder96"]()
+    cfg, f = orun(sc, 600)
+    lat = lbm.Lattice(sc, "f64")
+    lat.set_populations(f)
+    th, rms, n = lat.contact_angle()
+    oth, orms, on = oracle.contact_angle(cfg, sc.solid, f, sc.surface)
+    assert n == on
+    assert th == pytest.approx(oth, abs=1e-8)
+    assert rms == pytest.approx(orms, rel=1e-6, abs=1e-10)
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_contact_angle_after_2000_steps(storage):
+    """The 96x96 droplet-on-cylinder case: 2,000 steps, then theta within 0.5 degrees."""
+    sc = SCENARIOS["cylinder96"]()
+    cfg, f = orun(sc, 2000)
+    oth, _, _ = oracle.contact_angle(cfg, sc.solid, f, sc.surface)
+    lat = lbm.Lattice(sc, storage)
+    lat.step(2000)
+    th, _, _ = lat.contact_angle()
+    lat.close()
+    assert abs(th - oth) <= 0.5, (th, oth)
+
+
+def test_flat_wall_contact_angle_matches_oracle():
+    sc = S.flat_droplet(96, 64, r=20, lam=0.5)
+    cfg, f = orun(sc, 1500)
+    oth, _, _ = oracle.contact_angle(cfg, sc.solid, f, sc.surface)
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(1500)
+    th, _, _ = lat.contact_angle()
+    lat.close()
+    assert abs(th - oth) <= 0.5, (th, oth)
+
+
+# ---------------------------------------------------------------------------------------------
+# failure reporting without faulting the GPU
+# ---------------------------------------------------------------------------------------------
+def test_divergent_run_is_flagged_unstable():
+    sc = S.cylinder_droplet(48, G=3.5)  # diverges within a few steps in this weight normalisation
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(20)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.diagnostics()
+    assert e.value.status == lbm.LBM_EUNSTABLE
+    d = lat.diagnostics(allow_unstable=True)
+    assert d["unstable"] == 1
+    lat.close()
+
+
+def test_synchronize_gives_up_after_its_time_limit():
+    sc = S.cylinder_droplet(1024, lam=1.0)
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(3000)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.sync(1e-4)
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    lat.sync(0)
+    lat.close()
