@@ -43,7 +43,8 @@ typedef enum {
     LBM_OK = 0,
     LBM_EINVAL = 1,    /* invalid argument: sizes, parameters, NULL pointer, case index */
     LBM_ENOMEM = 2,    /* device or host allocation failed */
-    LBM_ECUDA = 3,     /* a CUDA call or kernel failed (also: no usable sm_103a device) */
+    LBM_ECUDA = 3,     /* a CUDA call or kernel failed (also: no usable sm_103a device, or a
+                          bounded wait for a tensor load inside a kernel gave up) */
     LBM_EUNSTABLE = 4, /* a non-finite or non-positive density was found (lbm_diagnostics) */
     LBM_ETIMEOUT = 5,  /* lbm_synchronize gave up after its time limit */
     LBM_ESTATE = 6,    /* call not valid in the context's current state */
@@ -235,7 +236,7 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * Launch shape
  * ------------------------------------------------------------------------------------------- */
 
-/* Set the step kernel's launch shape: threads per block (64, 128 or 256) and rows per work
+/* Set the step kernel's launch shape: threads per block (64 or 128) and rows per work
  * item (>= 1, or 0 to size the work list at about two waves of resident blocks).  Rebuilds the
  * work list and drops the captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);

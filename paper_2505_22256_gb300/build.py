@@ -33,8 +33,13 @@ def _stale(obj: str, deps: list) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, out_dir: str | None = None, defines: dict | None = None) -> str:
+    """Compile (when stale) and link the library; returns its path.  ``out_dir`` and ``defines``
+    (e.g. {"LBM_SLOTS": 6}) build a variant of the step kernel's compile-time shape elsewhere."""
+    build_dir = out_dir or BUILD
+    lib = os.path.join(build_dir, "liblbm_gb300.so")
+    os.makedirs(build_dir, exist_ok=True)
+    extra = [f"-D{k}={v}" for k, v in (defines or {}).items()]
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "lbm.h"))
     nvcc = _nvcc()
@@ -42,10 +47,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -59,12 +64,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(f"--- {src} ---\n{text}")
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    if force or procs or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs]
+    if force or procs or _stale(lib, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

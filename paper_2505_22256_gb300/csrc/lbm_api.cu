@@ -12,6 +12,8 @@
 #include <thread>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -92,7 +94,6 @@ DevCase make_desc(const lbm_grid& g, const lbm_params& p) {
     memset(&d, 0, sizeof d);
     d.nx = g.nx;
     d.ny = g.ny;
-    d.pitch = (g.nx + 31) / 32 * 32;
     d.bc_x = g.bc_x;
     d.bc_y = g.bc_y;
     d.mode = p.mode;
@@ -131,11 +132,56 @@ void drop_graphs(Ctx& c) {
     c.graph_steps = 0;
 }
 
-// Work list: per case, row chunks by column windows of block_threads (interior block_threads - 4).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Two tensor maps per case: one row of all 18 planes of each population buffer, T [+8] columns from
+// column x - G (the ghost columns included), as the step kernel loads it.
+lbm_status build_tmaps(Ctx& c) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int T = c.block_threads, G = ghost_cols(c.storage), XB = box_extra_cols(c.storage);
+    if (T + XB > 256) return fail(LBM_EINVAL, "block of %d threads needs a tensor box wider than 256 columns", T);
+    CUtensorMapDataType dt = c.storage == LBM_STORE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : c.storage == LBM_STORE_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : c.storage == LBM_STORE_F16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    std::vector<CUtensorMap> maps(2 * c.hcases.size());
+    for (size_t ci = 0; ci < c.hcases.size(); ++ci) {
+        const DevCase& d = c.hcases[ci];
+        for (int buf = 0; buf < 2; ++buf) {
+            void* base = (char*)c.f[buf] + (size_t)d.f_off * c.elem;
+            cuuint64_t dims[3] = {(cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 18};
+            cuuint64_t strides[2] = {(cuuint64_t)d.pitch * c.elem, (cuuint64_t)d.pitch * d.ny * c.elem};
+            cuuint32_t box[3] = {(cuuint32_t)(T + XB), 1, 18};
+            cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = enc(&maps[2 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "tensor map of case %zu rejected (CUresult %d)", ci, (int)r);
+        }
+    }
+    if (!c.tmaps) CUDA_TRY(cudaMalloc(&c.tmaps, maps.size() * sizeof(CUtensorMap)));
+    CUDA_TRY(cudaMemcpy(c.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+// Work list: per case, row chunks by column windows of block_threads (interior block_threads - 8).
 // Cases are laid out one after the other.  block_rows = 0 picks the chunk height so that the list
 // holds about two waves of resident blocks (at least 16 rows, at most 128).
 lbm_status build_items(Ctx& c) {
-    const int W = c.block_threads, Wi = W - 4;
+    const int W = c.block_threads, Wi = W - 8;
+    lbm_status ts = build_tmaps(c);
+    if (ts != LBM_OK) return ts;
     int per_sm = 0;
     CUDA_TRY(step_occupancy(c.storage, W, &per_sm));
     if (per_sm < 1) return fail(LBM_ECUDA, "step kernel cannot be resident with %d threads", W);
@@ -153,7 +199,7 @@ lbm_status build_items(Ctx& c) {
         d.item_begin = (int)items.size();
         const int nstrip = (d.nx + Wi - 1) / Wi;
         for (int y0 = 0; y0 < d.ny; y0 += H)
-            for (int s = 0; s < nstrip; ++s) items.push_back(make_int4((int)ci, s * Wi - 2, y0, std::min(d.ny, y0 + H)));
+            for (int s = 0; s < nstrip; ++s) items.push_back(make_int4((int)ci, s * Wi, y0, std::min(d.ny, y0 + H)));
         d.item_end = (int)items.size();
     }
     if (c.items) {
@@ -174,6 +220,15 @@ lbm_status build_items(Ctx& c) {
     return LBM_OK;
 }
 
+// After a synchronisation: report a pipeline wait inside a kernel that gave up.
+lbm_status check_device_error(Ctx& c) {
+    int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, c.err, sizeof e, cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    if (e) return fail(LBM_ECUDA, "a tensor-load wait inside the step kernel gave up (device error word %d)", e);
+    return LBM_OK;
+}
+
 lbm_status check_case(lbm_ctx* ctx, int ci) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (ci < 0 || ci >= (int)ctx->c.cases.size()) return fail(LBM_EINVAL, "case index %d out of range", ci);
@@ -182,8 +237,8 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 
 void free_ctx(Ctx& c) {
     drop_graphs(c);
-    void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.widx, c.solid, c.wl_node, c.wl_subst, c.wl_seff, c.wl_a,
-                    c.wl_ar, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work};
+    void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -236,11 +291,11 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         hc.nfluid = nfluid[i];
         c.cases.push_back(hc);
         DevCase d = make_desc(cs[i].grid, cs[i].params);
+        const int per_line = (int)(128 / c.elem);  // rows start on 128-byte boundaries
+        d.pitch = (d.nx + 2 * ghost_cols(storage) + per_line - 1) / per_line * per_line;
         d.f_off = c.pop_elems;
-        d.n_off = c.node_elems;
         d.d_off = c.dense_elems;
         c.pop_elems += 18LL * d.ny * d.pitch;
-        c.node_elems += (long long)d.ny * d.pitch;
         c.dense_elems += (long long)d.nx * d.ny;
         max_nodes = std::max(max_nodes, (long long)d.nx * d.ny);
         c.hcases.push_back(d);
@@ -260,10 +315,15 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
     STEP(dalloc(c, (unsigned char**)&c.f[1], c.pop_elems * c.elem), "population buffer");
     STEP(cudaMemsetAsync(c.f[0], 0, c.pop_elems * c.elem, c.stream), "memset");
     STEP(cudaMemsetAsync(c.f[1], 0, c.pop_elems * c.elem, c.stream), "memset");
-    STEP(dalloc(c, &c.flags, c.node_elems), "flags");
-    STEP(dalloc(c, &c.widx, c.node_elems), "wall index");
-    STEP(cudaMemsetAsync(c.flags, 0, c.node_elems * sizeof(uint16_t), c.stream), "memset");
-    STEP(cudaMemsetAsync(c.widx, 0xff, c.node_elems * sizeof(int32_t), c.stream), "memset");
+    const size_t rsize = storage == LBM_STORE_F64 ? 8 : 4;
+    STEP(dalloc(c, &c.flags, c.dense_elems), "flags");
+    STEP(dalloc(c, &c.wsub, c.dense_elems), "wall masks");
+    STEP(dalloc(c, (unsigned char**)&c.wa, 2 * c.dense_elems * rsize), "wall vectors");
+    STEP(dalloc(c, &c.err, 1), "error word");
+    STEP(cudaMemsetAsync(c.flags, 0, c.dense_elems * sizeof(uint16_t), c.stream), "memset");
+    STEP(cudaMemsetAsync(c.wsub, 0, c.dense_elems * sizeof(uint32_t), c.stream), "memset");
+    STEP(cudaMemsetAsync(c.wa, 0, 2 * c.dense_elems * rsize, c.stream), "memset");
+    STEP(cudaMemsetAsync(c.err, 0, sizeof(int), c.stream), "memset");
     STEP(dalloc(c, &c.solid, c.dense_elems), "masks");
     STEP(dalloc(c, &c.dcases, ncases), "descriptors");
     STEP(dalloc(c, &c.dense, 18 * max_nodes), "transfer scratch");
@@ -304,9 +364,8 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
     if (st == LBM_OK) st = cu(dalloc(c, &c.wl_subst, c.nwall), "wall list");
     if (st == LBM_OK) st = cu(dalloc(c, &c.wl_seff, c.nwall), "wall list");
     if (st == LBM_OK) st = cu(dalloc(c, &c.wl_a, 2 * c.nwall), "wall list");
-    if (st == LBM_OK) st = cu(dalloc(c, (unsigned char**)&c.wl_ar, 2 * c.nwall * (storage == LBM_STORE_F64 ? 8 : 4)), "wall list");
     for (int i = 0; i < ncases && st == LBM_OK; ++i) st = cu(launch_wall_fill(c, i, offs[i]), "wall-list kernel");
-    if (st == LBM_OK) st = cu(launch_wall_cast(c), "wall-list cast");
+    for (int i = 0; i < ncases && st == LBM_OK; ++i) st = cu(launch_wall_cast(c, i), "wall-list scatter");
     if (st == LBM_OK) st = cu(cudaStreamSynchronize(c.stream), "wall list");
     for (auto p : offs)
         if (p) cudaFree(p);
@@ -373,7 +432,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
                 cudaGraph_t g = nullptr;
                 CUDA_TRY(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t le = cudaSuccess;
-                for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) le = launch_step(c, c.f[k & 1], c.f[(k & 1) ^ 1], c.stream);
+                for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) le = launch_step(c, k & 1, c.stream);
                 cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
                 if (le != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -389,7 +448,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
             n -= kGraphSteps;
             c.steps += kGraphSteps;
         } else {
-            CUDA_TRY(launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream));
+            CUDA_TRY(launch_step(c, c.cur, c.stream));
             c.cur ^= 1;
             --n;
             ++c.steps;
@@ -403,12 +462,12 @@ lbm_status lbm_synchronize(lbm_ctx* ctx, double timeout_s) {
     Ctx& c = ctx->c;
     if (timeout_s <= 0) {
         CUDA_TRY(cudaStreamSynchronize(c.stream));
-        return LBM_OK;
+        return check_device_error(c);
     }
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(c.stream);
-        if (e == cudaSuccess) return LBM_OK;
+        if (e == cudaSuccess) return check_device_error(c);
         if (e != cudaErrorNotReady) return fail(LBM_ECUDA, "stream: %s", cudaGetErrorString(e));
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return fail(LBM_ETIMEOUT, "stream still busy after %.3f s", el);
@@ -449,7 +508,7 @@ lbm_status lbm_fields(lbm_ctx* ctx, int32_t ci, double* rho_A, double* rho_B, do
     for (int q = 0; q < 4; ++q)
         if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], c.fields + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
@@ -462,6 +521,10 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
     double v[kDiagN];
     CUDA_TRY(cudaMemcpyAsync(v, c.diag_out + (size_t)ci * kDiagN, sizeof v, cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
+    {
+        lbm_status es = check_device_error(c);
+        if (es != LBM_OK) return es;
+    }
     out->mass_A = v[0];
     out->mass_B = v[1];
     out->mom_x = v[2];
@@ -523,7 +586,7 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t ci, double* f) {
     CUDA_TRY(launch_get_state(c, ci, c.dense));
     CUDA_TRY(cudaMemcpyAsync(f, c.dense, 18 * N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t ci, const double* f) {
@@ -561,7 +624,7 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
 
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
-    if (!(threads == 64 || threads == 128 || threads == 256)) return fail(LBM_EINVAL, "threads must be 64, 128 or 256");
+    if (!(threads == 64 || threads == 128)) return fail(LBM_EINVAL, "threads must be 64 or 128");
     if (rows < 0) return fail(LBM_EINVAL, "rows must be >= 0 (0 = automatic)");
     Ctx& c = ctx->c;
     CUDA_TRY(cudaStreamSynchronize(c.stream));
@@ -574,7 +637,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
     Ctx& c = ctx->c;
-    const int cand_t[] = {64, 128, 256};
+    const int cand_t[] = {64, 128};
     const int cand_r[] = {0, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -585,12 +648,12 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
         for (int r : cand_r) {
             lbm_status s = lbm_set_launch(ctx, t, r);
             if (s != LBM_OK) continue;
-            if (launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream) != cudaSuccess) continue;
+            if (launch_step(c, c.cur, c.stream) != cudaSuccess) continue;
             c.cur ^= 1;
             ++c.steps;
             cudaEventRecord(e0, c.stream);
             for (int k = 0; k < steps; ++k) {
-                launch_step(c, c.f[c.cur], c.f[1 - c.cur], c.stream);
+                launch_step(c, c.cur, c.stream);
                 c.cur ^= 1;
                 ++c.steps;
             }

@@ -23,15 +23,15 @@ constexpr int kCaBlocks = 256;
 constexpr int kCaVals = 9;
 
 struct CaGeo {
-    int nx, ny, pitch;
-    const uint16_t* flags;  // pitched node flags of the case
+    int nx, ny;
+    const uint16_t* flags;  // node flags of the case
     const double* rA;
     const double* rB;
 };
 
 // fluid and more than three cells from any non-fluid site (precomputed by the flags kernel)
 __device__ bool usable(const CaGeo& g, int X, int Y) {
-    return (g.flags[(long long)Y * g.pitch + X] & (kSolidBit | kNearSolidBit)) == 0;
+    return (g.flags[(long long)Y * g.nx + X] & (kSolidBit | kNearSolidBit)) == 0;
 }
 
 __device__ double phi_at(const CaGeo& g, int X, int Y) {
@@ -209,7 +209,7 @@ __global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ par
 cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* host_out4) {
     const DevCase& C = c.hcases[ci];
     const long long N = (long long)C.nx * C.ny;
-    CaGeo g{C.nx, C.ny, C.pitch, c.flags + C.n_off, c.fields, c.fields + N};
+    CaGeo g{C.nx, C.ny, c.flags + C.d_off, c.fields, c.fields + N};
     double* st = c.ca_work;
     double* part = c.ca_work + 16;
     cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c.stream);

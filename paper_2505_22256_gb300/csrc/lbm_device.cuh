@@ -68,12 +68,11 @@ __host__ __device__ __forceinline__ constexpr double w8(int e2) {
 // Per-case descriptor (device copy; built on the host).
 // ------------------------------------------------------------------------------------------------
 struct DevCase {
-    int nx, ny, pitch;      // pitch: elements per stored row (multiple of 32)
+    int nx, ny, pitch;      // pitch: elements per stored population row (ghost columns included)
     int bc_x, bc_y;
     int mode;               // 0 original, 1 improved
-    long long f_off;        // element offset of the case's [2][9][ny][pitch] block in a population buffer
-    long long n_off;        // element offset of the case's [ny][pitch] block in per-node arrays
-    long long d_off;        // element offset of the case's [ny][nx] block in dense node arrays
+    long long f_off;        // element offset of the case's [18][ny][pitch] block in a population buffer
+    long long d_off;        // element offset of the case's [ny][nx] block in per-node arrays
     long long w_off;        // first wall-list entry of the case
     long long nwall;        // wall-list entries of the case
     int item_begin, item_end;

@@ -42,15 +42,13 @@ __device__ __forceinline__ bool first_layer_solid(const Geo& g, int X, int Y, in
 }
 
 __global__ void k_flags(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
-                        uint16_t* __restrict__ flags_all, int32_t* __restrict__ widx_all,
-                        int32_t* __restrict__ row_counts) {
+                        uint16_t* __restrict__ flags_all, int32_t* __restrict__ row_counts) {
     const DevCase C = cases[c];
     const Geo g{C.nx, C.ny, C.bc_x, C.bc_y, solid_all + C.d_off};
     const long long N = (long long)C.nx * C.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
-        const long long o = C.n_off + (long long)Y * C.pitch + X;
-        widx_all[o] = -1;
+        const long long o = C.d_off + s;
         if (g.solid[s]) {
             flags_all[o] = kSolidBit;
             continue;
@@ -125,7 +123,7 @@ __global__ void k_scan(const int32_t* __restrict__ counts, int32_t* __restrict__
 
 // One block per row: wall nodes of the row in increasing x get consecutive entries.
 __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
-                            const uint16_t* __restrict__ flags_all, int32_t* __restrict__ widx_all,
+                            const uint16_t* __restrict__ flags_all, uint32_t* __restrict__ wsub_all,
                             const int32_t* __restrict__ row_off, int32_t* __restrict__ wl_node,
                             uint32_t* __restrict__ wl_subst, uint32_t* __restrict__ wl_seff,
                             double* __restrict__ wl_a, long long nwall_total) {
@@ -140,7 +138,7 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
     for (int base = 0; base < C.nx; base += blockDim.x) {
         const int X = base + tid;
         bool is_wall = false;
-        if (X < C.nx) is_wall = (flags_all[C.n_off + (long long)Y * C.pitch + X] & kWallBit) != 0;
+        if (X < C.nx) is_wall = (flags_all[C.d_off + (long long)Y * C.nx + X] & kWallBit) != 0;
         const unsigned bal = __ballot_sync(0xffffffffu, is_wall);
         if (lane == 0) warp_cnt[warp] = __popc(bal);
         __syncthreads();
@@ -177,7 +175,7 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
             wl_seff[e] = em;
             wl_a[e] = ax;
             wl_a[nwall_total + e] = ay;
-            widx_all[C.n_off + (long long)Y * C.pitch + X] = (int32_t)e;
+            wsub_all[C.d_off + (long long)Y * C.nx + X] = sm;
         }
         __syncthreads();
         if (tid == 0) {
@@ -189,9 +187,18 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
     }
 }
 
-__global__ void k_cast(const double* __restrict__ a, float* __restrict__ b, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
+// Per-node copy of the adhesion vectors of one case's wall-list entries, in the compute type.
+template <class R>
+__global__ void k_wall_scatter(const DevCase* __restrict__ cases, int c, const int32_t* __restrict__ wl_node,
+                               const double* __restrict__ wl_a, long long nwall_total, long long dense_total,
+                               R* __restrict__ wa) {
+    const DevCase C = cases[c];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < C.nwall; i += (long long)gridDim.x * blockDim.x) {
+        const long long e = C.w_off + i;
+        const long long o = C.d_off + wl_node[e];
+        wa[o] = (R)wl_a[e];
+        wa[dense_total + o] = (R)wl_a[nwall_total + e];
+    }
 }
 
 }  // namespace
@@ -199,7 +206,7 @@ __global__ void k_cast(const double* __restrict__ a, float* __restrict__ b, long
 cudaError_t launch_flags(Ctx& c, int ci, int32_t* row_counts) {
     const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
     const int g = (int)((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
-    k_flags<<<g, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.widx, row_counts);
+    k_flags<<<g, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, row_counts);
     return cudaGetLastError();
 }
 
@@ -209,18 +216,19 @@ cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cud
 }
 
 cudaError_t launch_wall_fill(Ctx& c, int ci, const int32_t* row_offsets) {
-    k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.widx, row_offsets,
+    k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.wsub, row_offsets,
                                                         c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wall_cast(Ctx& c) {
-    if (c.nwall == 0) return cudaSuccess;
-    if (c.storage == LBM_STORE_F64)
-        return cudaMemcpyAsync(c.wl_ar, c.wl_a, 2 * c.nwall * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
-    const long long n = 2 * c.nwall;
+cudaError_t launch_wall_cast(Ctx& c, int ci) {
+    const long long n = c.hcases[ci].nwall;
+    if (n == 0) return cudaSuccess;
     const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_cast<<<g, 256, 0, c.stream>>>(c.wl_a, (float*)c.wl_ar, n);
+    if (c.storage == LBM_STORE_F64)
+        k_wall_scatter<double><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.wl_node, c.wl_a, c.nwall, c.dense_elems, (double*)c.wa);
+    else
+        k_wall_scatter<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.wl_node, c.wl_a, c.nwall, c.dense_elems, (float*)c.wa);
     return cudaGetLastError();
 }
 

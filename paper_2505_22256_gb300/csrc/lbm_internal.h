@@ -2,6 +2,7 @@
 // C-ABI layer (lbm_api.cu) calls.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,20 +35,21 @@ struct Ctx {
     DevCase* dcases = nullptr;
 
     long long pop_elems = 0;         // elements in one population buffer
-    long long node_elems = 0;        // elements in per-node (pitched) arrays
-    long long dense_elems = 0;       // sum of nx*ny
+    long long dense_elems = 0;       // sum of nx*ny (per-node arrays)
     long long nwall = 0;
 
     void* f[2] = {nullptr, nullptr}; // ping-pong population buffers (post-collision f*)
     int cur = 0;                     // f[cur] holds the current state
-    uint16_t* flags = nullptr;       // [node_elems]
-    int32_t* widx = nullptr;         // [node_elems] wall-list index of a wall node, -1 otherwise
+    uint16_t* flags = nullptr;       // [dense_elems] node flags
+    uint32_t* wsub = nullptr;        // [dense_elems] substitution mask of wall-list nodes
+    void* wa = nullptr;              // [2][dense_elems] adhesion vectors of wall-list nodes, compute type
     uint8_t* solid = nullptr;        // [dense_elems] copy of the masks
+    CUtensorMap* tmaps = nullptr;    // [ncases][2] tensor maps of the population buffers
+    int* err = nullptr;              // device error word (pipeline wait gave up)
     int32_t* wl_node = nullptr;      // wall list, all cases back to back
     uint32_t* wl_subst = nullptr;
     uint32_t* wl_seff = nullptr;
     double* wl_a = nullptr;          // [2][nwall] adhesion vectors in FP64
-    void* wl_ar = nullptr;           // [2][nwall] the same in the compute type
 
     // work list of the step kernel
     int block_threads = 128;
@@ -75,7 +77,7 @@ struct Ctx {
 };
 
 // lbm_step.cu
-cudaError_t launch_step(Ctx& c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s);
 cudaError_t launch_fields(Ctx& c, int case_index, double* rhoA, double* rhoB, double* ux, double* uy,
                           bool diag);
 cudaError_t launch_diag_reduce(Ctx& c, int case_index);
@@ -84,12 +86,14 @@ cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);
 cudaError_t launch_feq_rest(Ctx& c, int case_index, const double* rhoA, const double* rhoB, double* dense_f);
 int step_smem_bytes(int storage, int threads);
 cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm);
+int ghost_cols(int storage);      // ghost columns on each side of a stored population row
+int box_extra_cols(int storage);  // tensor-box columns beyond the block width
 
 // lbm_geometry.cu
 cudaError_t launch_flags(Ctx& c, int case_index, int32_t* row_counts);
 cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cudaStream_t s);
 cudaError_t launch_wall_fill(Ctx& c, int case_index, const int32_t* row_offsets);
-cudaError_t launch_wall_cast(Ctx& c);
+cudaError_t launch_wall_cast(Ctx& c, int case_index);
 
 // lbm_contact.cu
 cudaError_t launch_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* host_out4);

@@ -1,35 +1,51 @@
 // Fused time-step kernel of the two-component pseudopotential LBM (arXiv 2505.22256) and the
 // kernels that read and write its state.
 //
-// State: one buffer per time level holds the post-collision populations f*_i^k of every case,
-// [2][9][ny][pitch] per case, of the storage type S.  One launch of k_step performs, for every
-// fluid node x:
+// State: one buffer per time level holds the post-collision populations f*_i^k of every case as
+// [18][ny][pitch] planes of the storage type S (plane q = 9k + i).  Column x of a row lives at
+// element x + G; the G ghost columns on each side repeat the opposite edge when x is periodic, so
+// a tensor box never has to wrap.
+//
+// One launch of k_step performs, for every fluid node x:
 //   pull    f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link (halfway bounce-back,
 //           Sec. 3.5); open columns complete the entering populations (Sec. 3.3)
 //   moments rho_k = sum_i f_i (Eq. 3), momentum sum_k sum_i f_i e_i (Eq. 4)
-//   forces  cohesion on the eighth-order 24-node stencil (Eq. 8, Sec. 2.4) from a shared-memory
-//           ring of densities; wall-list nodes take second-layer values from their first-layer
-//           partner (Table 1) and add the adhesion force of Eq. 9 with the local parameter of
-//           Eqs. 10-12; body force
+//   forces  cohesion on the eighth-order 24-node stencil (Eq. 8, Sec. 2.4); wall-list nodes take
+//           second-layer values from their first-layer partner (Table 1) and add the adhesion
+//           force of Eq. 9 with the local parameter of Eqs. 10-12; body force
 //   collide u = (momentum + F/2) / rho (Eq. 5 with Guo's shift); f* = f + (f^eq - f)/tau +
 //           (1 - 1/(2 tau)) F_i (Eqs. 1, 2, 6, 7), written to the other buffer.
 //
-// Work decomposition: a work item is a window of blockDim.x columns by a chunk of rows of one
-// case.  Every thread owns one window column and marches down the rows: for row y+2 it pulls the
-// populations and stores rho_A, rho_B in a six-row ring in shared memory, keeps the populations
-// of rows y..y+2 in registers, and after one barrier collides row y with the 5x5 neighbourhood of
-// densities it needs.  The two outermost columns on each side only supply densities (the window's
-// halo); interior columns collide.  Densities of halo rows and columns are recomputed by the
-// neighbouring items, so one launch needs no grid-wide synchronisation.
+// Work decomposition.  A work item is a column window of one case (T - 8 interior columns) by a
+// chunk of rows.  One thread per window column marches down the rows.  Data path per row:
+//   * the tensor engine loads the whole row of f* (all 18 planes, T [+8] columns) into a ring of
+//     kSlots shared-memory slots, about four rows ahead, each slot completing on its mbarrier;
+//   * every thread pulls its 18 populations from the three slots around the row, sums rho_A,
+//     rho_B into a six-row density ring and keeps the populations in registers;
+//   * after one barrier, each interior thread forms the row sums of the density gradient
+//     (D1 = rho(x+1) - rho(x-1), D2, and the |dy| = 1, 2 weighted sums) and adds them into a
+//     five-row window of partial gradients; the row two rows up is then complete, is collided and
+//     written straight to global memory (one coalesced store per plane and warp).
+// Densities of halo rows and columns are recomputed by neighbouring items; one launch needs no
+// grid-wide synchronisation.
 #include <math.h>
 
 #include "lbm_internal.h"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
 namespace {
 
 constexpr int kRing = 6;  // rows of densities kept in shared memory
+#ifndef LBM_SLOTS
+#define LBM_SLOTS 5
+#endif
+#ifndef LBM_MIN_BLOCKS
+#define LBM_MIN_BLOCKS 3
+#endif
+constexpr int kSlots = LBM_SLOTS;  // rows of f* resident or in flight in shared memory (>= 4)
+static_assert(kSlots >= 4, "the pull of a row needs three resident rows plus one in flight");
 
 template <class R>
 struct Params {
@@ -38,7 +54,7 @@ struct Params {
     R omega[2], cF[2];
     R G, Gw2, lam, delta, s1, s2, s3, t2, t3;
     R gx, gy;
-    R d1[2], d5[2];   // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
+    R d1[2], d5[2];            // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
     R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
 };
 
@@ -67,44 +83,59 @@ __device__ __forceinline__ R shift_of(const Params<R>& P, int k, int i) {
     return i == 0 ? P.sh0[k] : (i <= 4 ? P.sh1[k] : P.sh5[k]);
 }
 
-// Pull the 18 post-streaming populations of fluid node (X, Y) from the post-collision buffer.
+// storage <-> compute conversions
 template <class S, class R>
-__device__ __forceinline__ void pull_node(const S* __restrict__ fin, const Params<R>& P, int X, int Y,
-                                          uint16_t fl, R (&f)[18]) {
-    const bool open = P.bc_x == kOpen;
-    const bool inlet = open && X == 0;
-    const bool outlet = open && X == P.nx - 1;
+__device__ __forceinline__ R sload(const S* p) { return (R)*p; }
+template <>
+__device__ __forceinline__ float sload<__half, float>(const __half* p) { return __half2float(*p); }
+template <>
+__device__ __forceinline__ float sload<__nv_bfloat16, float>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <class S, class R>
+__device__ __forceinline__ S to_store(R v) { return (S)v; }
+template <>
+__device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+// ------------------------------------------------------------------------------------------------
+// Pull of one node's 18 populations.  rm / r0 / rp point at the rows y-1, y, y+1 (plane stride ps,
+// column c of the node); used with the shared-memory row slots (step kernel) and with global
+// memory (state read-back).  The plain form assumes no blocked link and no open column.
+// ------------------------------------------------------------------------------------------------
+template <bool kGeneral, class S, class R>
+__device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restrict__ r0, const S* __restrict__ rp,
+                                     long long ps, int c, uint16_t fl, bool inlet, bool outlet, const Params<R>& P,
+                                     R (&f)[18]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        int sx = X, sy = Y, si = i;
-        if (i != 0) {
+        const S* src;
+        long long off;
+        if (i == 0) {
+            src = r0;
+            off = c;
+        } else if (!kGeneral) {
+            src = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+            off = (long long)i * ps + c - cx(i);
+        } else {
+            if (cx(i) > 0 && inlet) continue;  // entering through the inlet: set below
             const bool blocked = (fl >> (i - 1)) & 1u;
-            int bx = X;
-            if (cx(i) < 0 && outlet) bx = (fl & kOutletOwnBit) ? X : X - 1;  // copied from upstream
-            if (blocked) {
-                sx = bx;
-                si = opp(i);
-            } else {
-                sx = bx - cx(i);
-                sy = Y - cy(i);
-                sx += (sx < 0) ? P.nx : 0;
-                sx -= (sx >= P.nx) ? P.nx : 0;
-                sy += (sy < 0) ? P.ny : 0;
-                sy -= (sy >= P.ny) ? P.ny : 0;
-            }
+            int b = c;
+            if (cx(i) < 0 && outlet) b = (fl & kOutletOwnBit) ? c : c - 1;  // copied from upstream
+            const S* nsrc = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+            src = blocked ? r0 : nsrc;
+            off = blocked ? (long long)opp(i) * ps + b : (long long)i * ps + b - cx(i);
         }
-        if (cx(i) > 0 && inlet) continue;  // entering through the inlet: set below
-        const long long o = (long long)sy * P.pitch + sx;
-        R a = (R)Store<S>::ld(fin + (long long)si * P.plane + o);
-        R b = (R)Store<S>::ld(fin + (long long)(9 + si) * P.plane + o);
+        R va = sload<S, R>(src + off);
+        R vb = sload<S, R>(src + off + 9 * ps);
         if constexpr (Store<S>::kShift) {
-            a += shift_of(P, 0, i);  // w_si = w_i
-            b += shift_of(P, 1, i);
+            va += shift_of(P, 0, i);
+            vb += shift_of(P, 1, i);
         }
-        f[i] = a;
-        f[9 + i] = b;
+        f[i] = va;
+        f[9 + i] = vb;
     }
-    if (inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in, 0))
+    if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in, 0))
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             f[9 * k + 1] = f[9 * k + 3] + P.d1[k];
@@ -114,7 +145,7 @@ __device__ __forceinline__ void pull_node(const S* __restrict__ fin, const Param
     }
 }
 
-// Window column -> lattice column for density lookups; -1 when it lies outside a wall boundary.
+// Window column -> lattice column; -1 when it lies outside a wall boundary.
 template <class R>
 __device__ __forceinline__ int map_col(const Params<R>& P, int x) {
     if (x >= 0 && x < P.nx) return x;
@@ -123,9 +154,8 @@ __device__ __forceinline__ int map_col(const Params<R>& P, int x) {
     return -1;
 }
 
-__device__ __forceinline__ int ring_slot(int r) { return (r + kRing) % kRing; }
+__device__ __forceinline__ int ring_slot(int r) { return (r + 2 * kRing) % kRing; }
 
-template <class R>
 struct Diag {
     double v[kDiagN];
     __device__ void init() {
@@ -135,33 +165,69 @@ struct Diag {
     }
 };
 
-// Collide (or, in fields mode, evaluate) one interior fluid node.
-template <class S, class R, bool kFields>
-__device__ __forceinline__ void node_update(const Params<R>& P, const R* __restrict__ ringA,
-                                            const R* __restrict__ ringB, int W, int tid, int y,
-                                            int x, uint16_t fl, const R (&f)[18], long long w_entry,
-                                            const uint32_t* __restrict__ wl_subst,
-                                            const R* __restrict__ wl_a, long long nwall_total,
-                                            S* __restrict__ fout, double* __restrict__ o_rA,
-                                            double* __restrict__ o_rB, double* __restrict__ o_ux,
-                                            double* __restrict__ o_uy, Diag<R>& dg) {
-    int sb[5];
+template <class R>
+struct RowState {
+    R f[18];
+    uint16_t fl;
+    uint32_t sub;
+    R ax, ay;
+};
+
+// five-row window of partial gradients per component (index 0 = the row being collided)
+template <class R>
+struct Grad {
+    R x[2][5], y[2][5];
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int d = 0; d < 5; ++d) sb[d] = ring_slot(y + d - 2) * W + tid;
-    const R rA = ringA[sb[2]];
-    const R rB = ringB[sb[2]];
-
-    uint32_t sub = 0;
-    R ax = (R)0, ay = (R)0;
-    const bool wall = (fl & kWallBit) != 0;
-    if (wall) {
-        sub = __ldg(wl_subst + w_entry);
-        ax = __ldg(wl_a + w_entry);
-        ay = __ldg(wl_a + nwall_total + w_entry);
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[k][j] = y[k][j] = (R)0;
     }
+    __device__ __forceinline__ void shift() {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                x[k][j] = x[k][j + 1];
+                y[k][j] = y[k][j + 1];
+            }
+            x[k][4] = (R)0;
+            y[k][4] = (R)0;
+        }
+    }
+};
 
-    // 24 stencil values psi~ of each component.  v[dy+2][dx+2]; second-layer sites flagged in
-    // the substitution mask read their first-layer partner x + sign(e) (Table 1).
+// Row sums of row r at this thread's column, added into the gradient window (targets r-2..r+2):
+// Gx(T) = sum_dy [w(1+dy^2) D1(T+dy) + 2 w(4+dy^2) D2(T+dy)],
+// Gy(T) = R1(T+1) - R1(T-1) + 2 (R2(T+2) - R2(T-2)),
+// D1 = rho(x+1) - rho(x-1), D2 = rho(x+2) - rho(x-2), R_k = w(k^2) rho + w(1+k^2) S1 + w(4+k^2) S2
+// with S1, S2 the sums of the same pairs.
+template <class R>
+__device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Grad<R>& g, int k) {
+    const R m2 = ring[base - 2], m1 = ring[base - 1], c0 = ring[base], p1 = ring[base + 1], p2 = ring[base + 2];
+    const R D1 = p1 - m1, D2 = p2 - m2, S1 = p1 + m1, S2 = p2 + m2;
+    const R w1 = (R)w8(1), w2 = (R)w8(2), w4 = (R)w8(4), w5 = (R)w8(5), w8v = (R)w8(8);
+    const R X0 = w1 * D1 + (R)2 * w4 * D2;
+    const R X1 = w2 * D1 + (R)2 * w5 * D2;
+    const R X2 = w5 * D1 + (R)2 * w8v * D2;
+    const R R1 = w1 * c0 + w2 * S1 + w5 * S2;
+    const R R2 = (R)2 * (w4 * c0 + w5 * S1 + w8v * S2);
+    g.x[k][0] += X2;
+    g.y[k][0] += R2;
+    g.x[k][1] += X1;
+    g.y[k][1] += R1;
+    g.x[k][2] += X0;
+    g.x[k][3] += X1;
+    g.y[k][3] -= R1;
+    g.x[k][4] += X2;
+    g.y[k][4] -= R2;
+}
+
+// Explicit 24-node gradient of a wall-list node with the second-layer substitution of Table 1:
+// a second-layer site whose bit is set in `sub` reads its first-layer partner x + sign(e).
+template <class R>
+__device__ __forceinline__ void wall_gradient(const R* __restrict__ ringA, const R* __restrict__ ringB,
+                                              const int (&sb)[5], uint32_t sub, R& gAx, R& gAy, R& gBx, R& gBy) {
     R vA[5][5], vB[5][5];
 #pragma unroll
     for (int dy = -2; dy <= 2; ++dy) {
@@ -170,11 +236,9 @@ __device__ __forceinline__ void node_update(const Params<R>& P, const R* __restr
             if (dx == 0 && dy == 0) continue;
             int addr = sb[dy + 2] + dx;
             if (dx == 2 || dx == -2 || dy == 2 || dy == -2) {
-                // Table 1 node number of (dx, dy) minus one
                 const int sx = (dx > 0) - (dx < 0), sy = (dy > 0) - (dy < 0);
-                int n;
+                int n;  // Table 1 number of (dx, dy), minus one
                 if (dx == 2 * sx && dy == 2 * sy) {
-                    // (+-2, 0), (0, +-2), (+-2, +-2): 2 e_m, m = first-layer partner
                     const int m = (sx == 1 && sy == 0) ? 1 : (sx == 0 && sy == 1) ? 2 : (sx == -1 && sy == 0) ? 3
                                 : (sx == 0 && sy == -1) ? 4 : (sx == 1 && sy == 1) ? 5 : (sx == -1 && sy == 1) ? 6
                                 : (sx == -1 && sy == -1) ? 7 : 8;
@@ -190,239 +254,382 @@ __device__ __forceinline__ void node_update(const Params<R>& P, const R* __restr
             vB[dy + 2][dx + 2] = ringB[addr];
         }
     }
-
-    // sum_e w(|e|^2) psi~(x + e) e, grouping mirror images so a uniform field gives exactly 0
-    R gAx = 0, gAy = 0, gBx = 0, gBy = 0;
+    gAx = gAy = gBx = gBy = (R)0;
 #pragma unroll
-    for (int dy = -2; dy <= 2; ++dy) {
+    for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
         for (int dx = 1; dx <= 2; ++dx) {
             const R w = (R)(w8(dx * dx + dy * dy) * dx);
             gAx += w * (vA[dy + 2][2 + dx] - vA[dy + 2][2 - dx]);
             gBx += w * (vB[dy + 2][2 + dx] - vB[dy + 2][2 - dx]);
         }
-    }
 #pragma unroll
-    for (int dx = -2; dx <= 2; ++dx) {
+    for (int dx = -2; dx <= 2; ++dx)
 #pragma unroll
         for (int dy = 1; dy <= 2; ++dy) {
             const R w = (R)(w8(dx * dx + dy * dy) * dy);
             gAy += w * (vA[2 + dy][dx + 2] - vA[2 - dy][dx + 2]);
             gBy += w * (vB[2 + dy][dx + 2] - vB[2 - dy][dx + 2]);
         }
-    }
+}
 
-    // cohesion: each component is pushed by the other's pseudopotential gradient (Eq. 8)
-    R FAx = -P.G * rA * gBx, FAy = -P.G * rA * gBy;
-    R FBx = -P.G * rB * gAx, FBy = -P.G * rB * gAy;
-    // adhesion (Eq. 9); G_w1 local in the improved scheme (Eqs. 10, 12)
-    if (wall) {
-        R GA;
-        if (P.mode == 1) {
-            const R re = (rA - rB) / (rA + rB);
-            R h;
-            if (re > P.delta) h = P.lam;
-            else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
-            else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
-            else h = (R)1;
-            GA = P.Gw2 * h;
-        } else {
-            GA = P.lam * P.Gw2;
-        }
-        FAx -= GA * rA * ax;
-        FAy -= GA * rA * ay;
-        FBx -= P.Gw2 * rB * ax;
-        FBy -= P.Gw2 * rB * ay;
+// SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e):
+// f*_+- = (1 - w) f_+- + [w sym(f^eq) + c sym(F)] +- [w anti(f^eq) + c anti(F)], with
+// sym / anti the parts of f^eq and F_i that are even / odd in e.
+template <class R>
+__device__ __forceinline__ void collide_comp(const R* f, int k, R rho, R ux, R uy, R Fx, R Fy, R om, R cf,
+                                             R (&out)[18]) {
+    const R om1 = (R)1 - om;
+    const R A0 = rho * ((R)1 - (R)1.5 * (ux * ux + uy * uy));
+    const R uF = ux * Fx + uy * Fy;
+    out[9 * k] = om1 * f[9 * k] + (R)(4.0 / 9.0) * (om * A0 - cf * (R)3 * uF);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {  // axis pairs (1,3) and (2,4)
+        const R av = p == 0 ? ux : uy, bv = p == 0 ? Fx : Fy;
+        const R ra = rho * av;
+        const R sym = om * (R)(1.0 / 9.0) * (A0 + (R)4.5 * ra * av) + cf * (av * bv - uF * (R)(1.0 / 3.0));
+        const R anti = (om * ra + cf * bv) * (R)(1.0 / 3.0);
+        const int ip = 1 + p, im = 3 + p;
+        out[9 * k + ip] = om1 * f[9 * k + ip] + (sym + anti);
+        out[9 * k + im] = om1 * f[9 * k + im] + (sym - anti);
     }
-    // body force
-    FAx += rA * P.gx; FAy += rA * P.gy;
-    FBx += rB * P.gx; FBy += rB * P.gy;
-
-    // equilibrium velocity with the half-force shift
-    R mx = 0, my = 0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const R s = f[i] + f[9 + i];
-        if (cx(i) != 0) mx += cx(i) > 0 ? s : -s;
-        if (cy(i) != 0) my += cy(i) > 0 ? s : -s;
-    }
-    const R rho = rA + rB;
-    const R inv = (R)1 / rho;
-    const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
-    const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
-
-    if constexpr (kFields) {
-        const long long o = (long long)y * P.nx + x;
-        o_rA[o] = (double)rA;
-        o_rB[o] = (double)rB;
-        o_ux[o] = (double)ux;
-        o_uy[o] = (double)uy;
-        const double dux = ux, duy = uy, drho = (double)rho;
-        dg.v[0] += (double)rA;
-        dg.v[1] += (double)rB;
-        dg.v[2] += drho * dux;
-        dg.v[3] += drho * duy;
-        const double um = sqrt(dux * dux + duy * duy);
-        dg.v[4] = fmax(dg.v[4], um);
-        dg.v[5] = fmin(dg.v[5], (double)rA);
-        dg.v[6] = fmax(dg.v[6], (double)rA);
-        dg.v[7] = fmin(dg.v[7], (double)rB);
-        dg.v[8] = fmax(dg.v[8], (double)rB);
-        dg.v[9] += 1.0;
-        if (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB))
-            dg.v[10] = 1.0;
-    } else {
-        // SRT collision with Guo forcing for each component (Eqs. 1, 2, 6, 7)
-        const R usq15 = (R)1.5 * (ux * ux + uy * uy);
-        const long long o = (long long)y * P.pitch + x;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const R rk = k == 0 ? rA : rB;
-            const R Fx = k == 0 ? FAx : FBx, Fy = k == 0 ? FAy : FBy;
-            const R om = P.omega[k], cf = P.cF[k];
-            const R uF3 = (R)3 * (ux * Fx + uy * Fy);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                R eu = 0, eF = 0;
-                if (cx(i) != 0) { eu += cx(i) > 0 ? ux : -ux; eF += cx(i) > 0 ? Fx : -Fx; }
-                if (cy(i) != 0) { eu += cy(i) > 0 ? uy : -uy; eF += cy(i) > 0 ? Fy : -Fy; }
-                const R w = (R)wq(i);
-                const R feq = w * rk * ((R)1 - usq15 + eu * ((R)3 + (R)4.5 * eu));
-                const R Fi = w * ((R)3 * eF - uF3 + (R)9 * eu * eF);
-                const R fi = f[9 * k + i];
-                R fo = fi + om * (feq - fi) + cf * Fi;
-                if constexpr (Store<S>::kShift) fo -= shift_of(P, k, i);
-                Store<S>::st(fout + (long long)(9 * k + i) * P.plane + o, fo);
-            }
-        }
+    for (int p = 0; p < 2; ++p) {  // diagonal pairs (5,7): e = (1,1);  (6,8): e = (-1,1)
+        const R av = p == 0 ? ux + uy : uy - ux, bv = p == 0 ? Fx + Fy : Fy - Fx;
+        const R ra = rho * av;
+        const R sym = om * (R)(1.0 / 36.0) * (A0 + (R)4.5 * ra * av) + cf * (av * bv * (R)0.25 - uF * (R)(1.0 / 12.0));
+        const R anti = (om * ra + cf * bv) * (R)(1.0 / 12.0);
+        const int ip = 5 + p, im = 7 + p;
+        out[9 * k + ip] = om1 * f[9 * k + ip] + (sym + anti);
+        out[9 * k + im] = om1 * f[9 * k + im] + (sym - anti);
     }
 }
 
+template <class S>
+struct Layout {
+    static constexpr int G = sizeof(S) == 2 ? 8 : 4;   // ghost columns per side (16 B multiple, >= 3)
+    static constexpr int XB = sizeof(S) == 2 ? 8 : 0;  // box columns beyond the block width
+};
+
+template <class S, class R>
+struct SmemPlan {
+    size_t slot_bytes, ring_off, bar_off, total;
+    __host__ __device__ explicit SmemPlan(int T) {
+        slot_bytes = ((size_t)(T + Layout<S>::XB) * 18 * sizeof(S) + 127) / 128 * 128;
+        ring_off = kSlots * slot_bytes;
+        bar_off = (ring_off + 2 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
+        total = bar_off + kSlots * 8;
+    }
+};
+
+struct StepArgs {
+    const DevCase* cases;
+    const int4* items;
+    int item_begin, item_end;
+    const CUtensorMap* tmaps;  // [case][2]: row loads from buffer 0, from buffer 1
+    int in_buf;                // buffer holding the current state
+    void* fout;                // the other buffer
+    const uint16_t* flags;     // dense per case
+    const uint32_t* wsub;      // dense: substitution mask of wall-list nodes
+    const void* wa;            // dense: adhesion vectors [2][nodes] in the compute type
+    long long dense_total;
+    int* err;
+    double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
+};
+
 template <class S, class R, bool kFields>
-__global__ void __launch_bounds__(256) k_step(const DevCase* __restrict__ cases, const int4* __restrict__ items,
-                                              int item_begin, int item_end, const S* __restrict__ fin_all,
-                                              S* __restrict__ fout_all, const uint16_t* __restrict__ flags_all,
-                                              const int32_t* __restrict__ widx_all,
-                                              const uint32_t* __restrict__ wl_subst,
-                                              const R* __restrict__ wl_a, long long nwall_total,
-                                              double* __restrict__ o_rA, double* __restrict__ o_rB,
-                                              double* __restrict__ o_ux, double* __restrict__ o_uy,
-                                              double* __restrict__ diag_part) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x, tid = threadIdx.x;
-    R* ringA = reinterpret_cast<R*>(smem_raw);
-    R* ringB = ringA + kRing * W;
+__global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int T = blockDim.x, t = threadIdx.x, Wi = T - 8;
+    constexpr int G = Layout<S>::G;
+    const int BX = T + Layout<S>::XB;
+    const SmemPlan<S, R> plan(T);
+    R* ringA = reinterpret_cast<R*>(smem + plan.ring_off);
+    R* ringB = ringA + kRing * T;
+    const uint32_t bar0 = smem_u32(smem + plan.bar_off);
+    const uint32_t slot0 = smem_u32(smem);
+    const uint32_t box_bytes = (uint32_t)((size_t)BX * 18 * sizeof(S));
+    const R* wax = reinterpret_cast<const R*>(a.wa);
+    const R* way = wax + a.dense_total;
 
-    for (int it = item_begin + blockIdx.x; it < item_end; it += gridDim.x) {
-        const int4 item = items[it];
-        const DevCase& C = cases[item.x];
+    if (t == 0) {
+        for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8 * s, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+
+    // Row loads are numbered per block: load n goes to slot n % kSlots and completes phase
+    // n / kSlots of that slot's barrier.  (slot, parity) of the next load to issue and of the next
+    // load to wait for advance incrementally.
+    int issue_slot = 0, wait_slot = 0;
+    uint32_t issue_par = 0, wait_par = 0;
+    bool failed = false;
+
+    for (int it = a.item_begin + blockIdx.x; it < a.item_end; it += gridDim.x) {
+        const int4 item = a.items[it];
+        const DevCase& C = a.cases[item.x];
         const Params<R> P = load_params<R>(C);
-        const S* __restrict__ fin = fin_all + C.f_off;
-        S* __restrict__ fout = fout_all + C.f_off;
-        const uint16_t* __restrict__ flags = flags_all + C.n_off;
-        const int32_t* __restrict__ widx = widx_all + C.n_off;
-        const int x = item.y + tid;               // window column of this thread
-        const int X = map_col(P, x);              // lattice column for the density ring
-        const bool interior = tid >= 2 && tid < W - 2 && x < P.nx;
-        const int y0 = item.z, y1 = item.w;
+        const int xs = item.y, y0 = item.z, y1 = item.w;
+        const CUtensorMap* lmap = a.tmaps + 2 * item.x + a.in_buf;
+        const uint16_t* flags = a.flags + C.d_off;
+        const int x = xs - 2 + t;                 // this thread's window column
+        const bool rcol = t < Wi + 4;             // computes densities
+        const int X = rcol ? map_col(P, x) : -1;  // lattice column
+        const int sc = (P.bc_x == kPeriodic ? x : X) - (xs - G);  // column inside a row slot
+        const bool interior = t >= 2 && t < Wi + 2 && x < P.nx;
+        const bool inlet = P.bc_x == kOpen && X == 0;
+        const bool outlet = P.bc_x == kOpen && X == P.nx - 1;
+        const int nload = (y1 + 2) - (y0 - 3) + 1;  // f* rows y0-3 .. y1+2
+        S* fo = reinterpret_cast<S*>(a.fout) + C.f_off;
 
-        Diag<R> dg;
-        if constexpr (kFields) dg.init();
-
-        // densities of row r into the ring; populations of row r kept in f, flags in fl
-        auto rho_row = [&](int r, R(&f)[18], uint16_t& fl) {
-            int Y = r;
-            bool ok = X >= 0;
-            if (Y < 0 || Y >= P.ny) {
-                if (P.bc_y == kPeriodic) Y = (Y + P.ny) % P.ny;
-                else ok = false;
+        auto wrap_row = [&](int r) -> int {
+            if (P.bc_y == kPeriodic) r += r < 0 ? P.ny : (r >= P.ny ? -P.ny : 0);
+            return r;
+        };
+        int next_row = y0 - 3;  // next f* row to load (thread 0 only)
+        auto issue = [&]() {  // load the next f* row into the next slot (outside a wall: zeros)
+            mbar_expect_tx(bar0 + 8 * issue_slot, box_bytes);
+            tma_load_3d(slot0 + issue_slot * (uint32_t)plan.slot_bytes, lmap, xs, wrap_row(next_row), 0,
+                        bar0 + 8 * issue_slot);
+            ++next_row;
+            if (++issue_slot == kSlots) {
+                issue_slot = 0;
+                issue_par ^= 1u;
             }
-            R a = 0, b = 0;
-            fl = kSolidBit;
-            if (ok) {
-                fl = __ldg(flags + (long long)Y * P.pitch + X);
-                if (!(fl & kSolidBit)) {
-                    pull_node<S, R>(fin, P, X, Y, fl, f);
+        };
+        auto wait_next = [&]() -> bool {  // wait for the oldest load not yet waited for
+            const bool okw = mbar_wait_bounded(bar0 + 8 * wait_slot, wait_par);
+            if (++wait_slot == kSlots) {
+                wait_slot = 0;
+                wait_par ^= 1u;
+            }
+            return okw;
+        };
+        // slot holding f* row r+1 is the one just waited for; rows r and r-1 sit in the two before
+        auto slot_back = [&](int back) -> const S* {
+            int sidx = wait_slot - 1 - back;
+            sidx += sidx < 0 ? kSlots : 0;
+            sidx += sidx < 0 ? kSlots : 0;
+            return reinterpret_cast<const S*>(smem + sidx * plan.slot_bytes);
+        };
+        auto flags_of = [&](int r) -> uint16_t {
+            const int Y = wrap_row(r);
+            if (X < 0 || Y < 0 || Y >= P.ny) return kSolidBit;
+            return __ldg(flags + (long long)Y * P.nx + X);
+        };
+
+        // densities of row r into the ring, populations of row r into st
+        auto rho_row = [&](int r, RowState<R>& st) -> bool {
+            const bool ok = wait_next();  // f* row r+1
+            R ra = 0, rb = 0;
+            const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
+            if (!(st.fl & kSolidBit)) {
+                const S* rm = slot_back(2);
+                const S* r0 = slot_back(1);
+                const S* rp = slot_back(0);
+                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
+                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) { a += f[i]; b += f[9 + i]; }
+                for (int i = 0; i < 9; ++i) {
+                    ra += st.f[i];
+                    rb += st.f[9 + i];
+                }
+                if (st.fl & kWallBit) {
+                    const long long o = C.d_off + (long long)wrap_row(r) * P.nx + X;
+                    st.sub = __ldg(a.wsub + o);
+                    st.ax = __ldg(wax + o);
+                    st.ay = __ldg(way + o);
                 }
             }
-            const int s = ring_slot(r) * W + tid;
-            ringA[s] = a;
-            ringB[s] = b;
+            const int s = ring_slot(r) * T + t;
+            ringA[s] = ra;
+            ringB[s] = rb;
+            return ok;
         };
-        auto update_row = [&](int y, const R(&f)[18], uint16_t fl) {
-            if (!interior) return;
-            if (fl & kSolidBit) {
-                if constexpr (kFields) {  // fields are 0 at solid nodes
-                    const long long o = (long long)y * P.nx + x;
-                    o_rA[o] = 0.0;
-                    o_rB[o] = 0.0;
-                    o_ux[o] = 0.0;
-                    o_uy[o] = 0.0;
+
+        // collide row y (state st, complete gradient g[0]) and store it
+        auto update_row = [&](int y, const RowState<R>& st, const Grad<R>& g, Diag& dg) {
+            if (!interior || (st.fl & kSolidBit)) {
+                if constexpr (kFields) {
+                    if (interior) {
+                        const long long o = (long long)y * P.nx + x;
+                        a.o_rA[o] = 0.0;
+                        a.o_rB[o] = 0.0;
+                        a.o_ux[o] = 0.0;
+                        a.o_uy[o] = 0.0;
+                    }
                 }
                 return;
             }
-            long long we = 0;
-            if (fl & kWallBit) {
-                we = __ldg(widx + (long long)y * P.pitch + x);
-                we = we < 0 ? 0 : (we >= nwall_total ? nwall_total - 1 : we);  // never read outside the list
+            int sb[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) sb[d] = ring_slot(y + d - 2) * T + t;
+            const R rA = ringA[sb[2]], rB = ringB[sb[2]];
+            R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
+            const bool wall = (st.fl & kWallBit) != 0;
+            if (wall) wall_gradient<R>(ringA, ringB, sb, st.sub, gAx, gAy, gBx, gBy);
+            // cohesion: each component is pushed by the other's pseudopotential gradient (Eq. 8)
+            R FAx = -P.G * rA * gBx, FAy = -P.G * rA * gBy;
+            R FBx = -P.G * rB * gAx, FBy = -P.G * rB * gAy;
+            if (wall) {  // adhesion (Eq. 9), G_w1 local in the improved scheme (Eqs. 10, 12)
+                R GA;
+                if (P.mode == 1) {
+                    const R re = (rA - rB) / (rA + rB);
+                    R h;
+                    if (re > P.delta) h = P.lam;
+                    else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
+                    else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
+                    else h = (R)1;
+                    GA = P.Gw2 * h;
+                } else {
+                    GA = P.lam * P.Gw2;
+                }
+                FAx -= GA * rA * st.ax;
+                FAy -= GA * rA * st.ay;
+                FBx -= P.Gw2 * rB * st.ax;
+                FBy -= P.Gw2 * rB * st.ay;
             }
-            node_update<S, R, kFields>(P, ringA, ringB, W, tid, y, x, fl, f, we, wl_subst, wl_a, nwall_total,
-                                       fout, o_rA, o_rB, o_ux, o_uy, dg);
+            FAx += rA * P.gx;
+            FAy += rA * P.gy;
+            FBx += rB * P.gx;
+            FBy += rB * P.gy;
+            const R* f = st.f;
+            const R s1 = f[1] + f[10], s2 = f[2] + f[11], s3 = f[3] + f[12], s4 = f[4] + f[13];
+            const R s5 = f[5] + f[14], s6 = f[6] + f[15], s7 = f[7] + f[16], s8 = f[8] + f[17];
+            const R mx = (s1 - s3) + ((s5 - s7) + (s8 - s6));
+            const R my = (s2 - s4) + ((s5 - s7) + (s6 - s8));
+            const R rho = rA + rB;
+            const R inv = (R)1 / rho;
+            const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
+            const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
+            if constexpr (kFields) {
+                const long long o = (long long)y * P.nx + x;
+                a.o_rA[o] = (double)rA;
+                a.o_rB[o] = (double)rB;
+                a.o_ux[o] = (double)ux;
+                a.o_uy[o] = (double)uy;
+                const double dux = ux, duy = uy, drho = (double)rho;
+                dg.v[0] += (double)rA;
+                dg.v[1] += (double)rB;
+                dg.v[2] += drho * dux;
+                dg.v[3] += drho * duy;
+                const double um = sqrt(dux * dux + duy * duy);
+                dg.v[4] = fmax(dg.v[4], um);
+                dg.v[5] = fmin(dg.v[5], (double)rA);
+                dg.v[6] = fmax(dg.v[6], (double)rA);
+                dg.v[7] = fmin(dg.v[7], (double)rB);
+                dg.v[8] = fmax(dg.v[8], (double)rB);
+                dg.v[9] += 1.0;
+                if (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB))
+                    dg.v[10] = 1.0;
+            } else {
+                R o[18];
+                collide_comp<R>(f, 0, rA, ux, uy, FAx, FAy, P.omega[0], P.cF[0], o);
+                collide_comp<R>(f, 1, rB, ux, uy, FBx, FBy, P.omega[1], P.cF[1], o);
+                const bool ghost = P.bc_x == kPeriodic && (x < G || x >= P.nx - G);
+                const int gcol = x < G ? x + P.nx + G : x - P.nx + G;
+                S* out = fo + (long long)y * P.pitch + x + G;
+#pragma unroll
+                for (int q = 0; q < 18; ++q) {
+                    R v = o[q];
+                    if constexpr (Store<S>::kShift) v -= shift_of(P, q / 9, q % 9);
+                    const S sv = to_store<S, R>(v);
+                    out[(long long)q * P.plane] = sv;
+                    if (ghost) out[(long long)q * P.plane + gcol - (x + G)] = sv;  // copy for the periodic wrap
+                }
+            }
         };
 
-        R fa[18], fb[18], fc[18];
-        uint16_t la, lb, lc;
-        __syncthreads();  // the previous item's readers are done with the ring
-        rho_row(y0 - 2, fa, la);
-        rho_row(y0 - 1, fa, la);
-        rho_row(y0, fa, la);
-        rho_row(y0 + 1, fb, lb);
-        for (int y = y0; y < y1; y += 3) {
-            rho_row(y + 2, fc, lc);
-            __syncthreads();
-            update_row(y, fa, la);
-            if (y + 1 >= y1) break;
-            rho_row(y + 3, fa, la);
-            __syncthreads();
-            update_row(y + 1, fb, lb);
-            if (y + 2 >= y1) break;
-            rho_row(y + 4, fb, lb);
-            __syncthreads();
-            update_row(y + 2, fc, lc);
+        Diag dg;
+        if constexpr (kFields) dg.init();
+        Grad<R> g;
+        g.zero();
+        RowState<R> s0, s1, s2;
+        s0.sub = s1.sub = s2.sub = 0;
+        s0.ax = s0.ay = s1.ax = s1.ay = s2.ax = s2.ay = (R)0;
+        uint16_t fl_next = flags_of(y0 - 2);
+
+        if (t == 0) {
+            const int n0 = nload < kSlots ? nload : kSlots;
+            for (int k = 0; k < n0; ++k) issue();
         }
+        bool ok = wait_next();  // f* row y0-3
+        ok = wait_next() && ok; // f* row y0-2
+
+        // One row of the march: densities of row q into `cur`, barrier, refill of the slot that
+        // held f* row q-1, gradient row sums of row q, collision of row q-2 (`old`).
+        auto iter = [&](int q, RowState<R>& old, RowState<R>& cur) -> bool {
+            cur.fl = fl_next;
+            fl_next = flags_of(q + 1);
+            const bool mine = rho_row(q, cur);
+            if (__syncthreads_or(!mine)) return false;
+            if (t == 0 && next_row <= y1 + 2) issue();  // the slot of f* row q-1 is free now
+            if (interior) {
+                const int base = ring_slot(q) * T + t;
+                add_row<R>(ringA, base, g, 0);
+                add_row<R>(ringB, base, g, 1);
+            }
+            if (q - 2 >= y0) update_row(q - 2, old, g, dg);
+            g.shift();
+            return true;
+        };
+
+        // row states rotate with period three: row q goes into cur, row q-2 is old
+        int q = y0 - 2;
+        while (ok) {
+            if (q > y1 + 1) break;
+            ok = iter(q++, s0, s2);
+            if (!ok || q > y1 + 1) break;
+            ok = iter(q++, s1, s0);
+            if (!ok || q > y1 + 1) break;
+            ok = iter(q++, s2, s1);
+        }
+        if (!ok) {
+            failed = true;
+            break;
+        }
+        __syncthreads();  // every thread is done with the slots before the next item refills them
 
         if constexpr (kFields) {
-            // block reduction of the item's partial diagnostics (sums, max, min), in FP64
-            __shared__ double red[16][kDiagN];
-            const int lane = tid & 31, warp = tid >> 5;
+            __shared__ double red[8][kDiagN];
+            const int lane = t & 31, warp = t >> 5;
 #pragma unroll
-            for (int q = 0; q < kDiagN; ++q) {
-                double v = dg.v[q];
+            for (int qq = 0; qq < kDiagN; ++qq) {
+                double v = dg.v[qq];
                 for (int off = 16; off > 0; off >>= 1) {
                     const double o = __shfl_xor_sync(0xffffffffu, v, off);
-                    v = (q == 4 || q == 6 || q == 8 || q == 10) ? fmax(v, o) : (q == 5 || q == 7) ? fmin(v, o) : v + o;
+                    v = (qq == 4 || qq == 6 || qq == 8 || qq == 10) ? fmax(v, o) : (qq == 5 || qq == 7) ? fmin(v, o) : v + o;
                 }
-                if (lane == 0) red[warp][q] = v;
+                if (lane == 0) red[warp][qq] = v;
             }
             __syncthreads();
-            if (tid == 0) {
-                const int nw = (W + 31) >> 5;
-                for (int q = 0; q < kDiagN; ++q) {
-                    double v = red[0][q];
+            if (t == 0) {
+                const int nw = (T + 31) >> 5;
+                for (int qq = 0; qq < kDiagN; ++qq) {
+                    double v = red[0][qq];
                     for (int w2 = 1; w2 < nw; ++w2) {
-                        const double o = red[w2][q];
-                        v = (q == 4 || q == 6 || q == 8 || q == 10) ? fmax(v, o) : (q == 5 || q == 7) ? fmin(v, o) : v + o;
+                        const double o = red[w2][qq];
+                        v = (qq == 4 || qq == 6 || qq == 8 || qq == 10) ? fmax(v, o) : (qq == 5 || qq == 7) ? fmin(v, o) : v + o;
                     }
-                    diag_part[(long long)it * kDiagN + q] = v;
+                    a.diag_part[(long long)it * kDiagN + qq] = v;
                 }
             }
+            __syncthreads();
+        }
+    }
+    if (failed && t == 0) {
+        atomicOr(a.err, 1);
+        // give loads still in flight a bounded time to land before the block leaves
+        const unsigned long long t0 = clock64();
+        while (clock64() - t0 < 200000000ULL) {
         }
     }
 }
 
-// f = f^eq(rho_k, 0) = w_i rho_k at fluid nodes (dense doubles [2][9][ny][nx]).
+// ------------------------------------------------------------------------------------------------
+// State transfer kernels (dense doubles [2][9][ny][nx] <-> the post-collision buffer)
+// ------------------------------------------------------------------------------------------------
 __global__ void k_feq_rest(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
                            const double* __restrict__ rhoA, const double* __restrict__ rhoB,
                            double* __restrict__ f) {
@@ -439,20 +646,21 @@ __global__ void k_feq_rest(const DevCase* __restrict__ cases, int c, const uint8
     }
 }
 
-// Post-streaming populations (dense doubles) -> post-collision buffer: the inverse of the pull, so
-// that the next pull reproduces f exactly (up to the storage rounding).
+// Post-streaming populations -> post-collision buffer: the inverse of the pull, so that the next
+// pull reproduces f exactly (up to the storage rounding).  Ghost columns are filled as well.
 template <class S>
 __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint16_t* __restrict__ flags_all,
                             const double* __restrict__ f, S* __restrict__ out_all) {
-    const DevCase C = cases[c];
     using R = typename ComputeOf<S>::type;
+    constexpr int G = Layout<S>::G;
+    const DevCase C = cases[c];
     const long long N = (long long)C.nx * C.ny;
     const long long plane = (long long)C.ny * C.pitch;
     S* out = out_all + C.f_off;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
-        const long long o = (long long)Y * C.pitch + X;
-        const uint16_t fl = flags_all[C.n_off + o];
+        const uint16_t fl = flags_all[C.d_off + s];
+        const long long o = (long long)Y * C.pitch + X + G;
         for (int k = 0; k < 2; ++k) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -473,7 +681,11 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
                     }
                     if constexpr (Store<S>::kShift) v -= wq(i) * C.rho0[k];
                 }
-                Store<S>::st(out + (long long)(9 * k + i) * plane + o, (R)v);
+                const S sv = to_store<S, R>((R)v);
+                S* p = out + (long long)(9 * k + i) * plane;
+                p[o] = sv;
+                if (C.bc_x == kPeriodic && X < G) p[o + C.nx] = sv;
+                if (C.bc_x == kPeriodic && X >= C.nx - G) p[o - C.nx] = sv;
             }
         }
     }
@@ -484,37 +696,52 @@ template <class S>
 __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint16_t* __restrict__ flags_all,
                             const S* __restrict__ fin_all, double* __restrict__ f) {
     using R = typename ComputeOf<S>::type;
+    constexpr int G = Layout<S>::G;
     const DevCase C = cases[c];
     const Params<R> P = load_params<R>(C);
     const long long N = (long long)C.nx * C.ny;
+    const S* fin = fin_all + C.f_off;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
-        const uint16_t fl = flags_all[C.n_off + (long long)Y * C.pitch + X];
+        const uint16_t fl = flags_all[C.d_off + s];
         R v[18];
         if (fl & kSolidBit) {
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = 0;
         } else {
-            pull_node<S, R>(fin_all + C.f_off, P, X, Y, fl, v);
+            // rows beyond a wall are reached only through blocked links; clamping keeps the unused
+            // row pointer inside the buffer
+            const int ym = Y - 1 < 0 ? (C.bc_y == kPeriodic ? C.ny - 1 : 0) : Y - 1;
+            const int yp = Y + 1 >= C.ny ? (C.bc_y == kPeriodic ? 0 : C.ny - 1) : Y + 1;
+            const bool inlet = C.bc_x == kOpen && X == 0, outlet = C.bc_x == kOpen && X == C.nx - 1;
+            pull<true, S, R>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch, fin + (long long)yp * C.pitch,
+                             P.plane, X + G, fl, inlet, outlet, P, v);
         }
 #pragma unroll
         for (int q = 0; q < 18; ++q) f[(long long)q * N + s] = (double)v[q];
     }
 }
 
-// Per-case reduction of the per-item partials, in item order (deterministic).
+// Per-case reduction of the per-item partials in item order (one warp; deterministic).
 __global__ void k_diag_reduce(const DevCase* __restrict__ cases, int c, const double* __restrict__ part,
                               double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const DevCase C = cases[c];
+    const int lane = threadIdx.x;
     double v[kDiagN];
-    for (int q = 0; q < kDiagN; ++q) v[q] = part[(long long)C.item_begin * kDiagN + q];
-    for (int it = C.item_begin + 1; it < C.item_end; ++it)
+    for (int q = 0; q < kDiagN; ++q) v[q] = (q == 5 || q == 7) ? INFINITY : (q == 4 || q == 6 || q == 8) ? -INFINITY : 0.0;
+    for (int it = C.item_begin + lane; it < C.item_end; it += 32)
         for (int q = 0; q < kDiagN; ++q) {
             const double o = part[(long long)it * kDiagN + q];
             v[q] = (q == 4 || q == 6 || q == 8 || q == 10) ? fmax(v[q], o) : (q == 5 || q == 7) ? fmin(v[q], o) : v[q] + o;
         }
-    for (int q = 0; q < kDiagN; ++q) out[(long long)c * kDiagN + q] = v[q];
+    for (int q = 0; q < kDiagN; ++q) {
+        double xv = v[q];
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, xv, off);
+            xv = (q == 4 || q == 6 || q == 8 || q == 10) ? fmax(xv, o) : (q == 5 || q == 7) ? fmin(xv, o) : xv + o;
+        }
+        if (lane == 0) out[(long long)c * kDiagN + q] = xv;
+    }
 }
 
 template <class S>
@@ -532,31 +759,49 @@ void* step_kernel(int storage, bool fields) {
     }
 }
 
-size_t compute_size(int storage) { return storage == LBM_STORE_F64 ? 8 : 4; }
+template <class S>
+size_t smem_for(int threads) {
+    using R = typename ComputeOf<S>::type;
+    return SmemPlan<S, R>(threads).total;
+}
+
+StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
+    StepArgs a;
+    a.cases = c.dcases;
+    a.items = c.items;
+    a.item_begin = ib;
+    a.item_end = ie;
+    a.tmaps = c.tmaps;
+    a.in_buf = c.cur;
+    a.fout = c.f[1 - c.cur];
+    a.flags = c.flags;
+    a.wsub = c.wsub;
+    a.wa = c.wa;
+    a.dense_total = c.dense_elems;
+    a.err = c.err;
+    a.o_rA = o4[0];
+    a.o_rB = o4[1];
+    a.o_ux = o4[2];
+    a.o_uy = o4[3];
+    a.diag_part = part;
+    return a;
+}
 
 template <class S>
-cudaError_t launch_step_t(Ctx& c, const void* fin, void* fout, cudaStream_t s, bool fields, int ib, int ie,
-                          int grid, double* o4[4], double* part) {
+cudaError_t launch_step_t(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
     using R = typename ComputeOf<S>::type;
-    const size_t smem = 2 * kRing * (size_t)c.block_threads * sizeof(R);
-    if (fields)
-        k_step<S, R, true><<<grid, c.block_threads, smem, s>>>(
-            c.dcases, c.items, ib, ie, (const S*)fin, (S*)fout, c.flags, c.widx, c.wl_subst, (const R*)c.wl_ar,
-            c.nwall, o4[0], o4[1], o4[2], o4[3], part);
-    else
-        k_step<S, R, false><<<grid, c.block_threads, smem, s>>>(
-            c.dcases, c.items, ib, ie, (const S*)fin, (S*)fout, c.flags, c.widx, c.wl_subst, (const R*)c.wl_ar,
-            c.nwall, nullptr, nullptr, nullptr, nullptr, nullptr);
+    const size_t smem = smem_for<S>(c.block_threads);
+    if (fields) k_step<S, R, true><<<grid, c.block_threads, smem, s>>>(a);
+    else k_step<S, R, false><<<grid, c.block_threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch(Ctx& c, const void* fin, void* fout, cudaStream_t s, bool fields, int ib, int ie, int grid,
-                     double* o4[4], double* part) {
+cudaError_t dispatch(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
     switch (c.storage) {
-        case LBM_STORE_F64: return launch_step_t<double>(c, fin, fout, s, fields, ib, ie, grid, o4, part);
-        case LBM_STORE_F32: return launch_step_t<float>(c, fin, fout, s, fields, ib, ie, grid, o4, part);
-        case LBM_STORE_F16_SHIFTED: return launch_step_t<__half>(c, fin, fout, s, fields, ib, ie, grid, o4, part);
-        default: return launch_step_t<__nv_bfloat16>(c, fin, fout, s, fields, ib, ie, grid, o4, part);
+        case LBM_STORE_F64: return launch_step_t<double>(c, a, s, fields, grid);
+        case LBM_STORE_F32: return launch_step_t<float>(c, a, s, fields, grid);
+        case LBM_STORE_F16_SHIFTED: return launch_step_t<__half>(c, a, s, fields, grid);
+        default: return launch_step_t<__nv_bfloat16>(c, a, s, fields, grid);
     }
 }
 
@@ -564,16 +809,33 @@ int blocks_for(long long n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 
 
 }  // namespace
 
-int step_smem_bytes(int storage, int threads) { return (int)(2 * kRing * (size_t)threads * compute_size(storage)); }
+int ghost_cols(int storage) { return (storage == LBM_STORE_F16_SHIFTED || storage == LBM_STORE_BF16_SHIFTED) ? 8 : 4; }
+int box_extra_cols(int storage) { return (storage == LBM_STORE_F16_SHIFTED || storage == LBM_STORE_BF16_SHIFTED) ? 8 : 0; }
 
-cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel(storage, false), threads,
-                                                         step_smem_bytes(storage, threads));
+int step_smem_bytes(int storage, int threads) {
+    switch (storage) {
+        case LBM_STORE_F64: return (int)smem_for<double>(threads);
+        case LBM_STORE_F32: return (int)smem_for<float>(threads);
+        case LBM_STORE_F16_SHIFTED: return (int)smem_for<__half>(threads);
+        default: return (int)smem_for<__nv_bfloat16>(threads);
+    }
 }
 
-cudaError_t launch_step(Ctx& c, const void* fin, void* fout, cudaStream_t s) {
+cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm) {
+    const int bytes = step_smem_bytes(storage, threads);
+    for (int f = 0; f < 2; ++f) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel(storage, f != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel(storage, false), threads, bytes);
+}
+
+cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s) {
     double* o4[4] = {nullptr, nullptr, nullptr, nullptr};
-    return dispatch(c, fin, fout, s, false, 0, c.nitems, c.grid_blocks, o4, nullptr);
+    StepArgs a = make_args(c, 0, c.nitems, o4, nullptr);
+    a.in_buf = in_buf;
+    a.fout = c.f[1 - in_buf];
+    return dispatch(c, a, s, false, c.grid_blocks);
 }
 
 cudaError_t launch_fields(Ctx& c, int ci, double* rhoA, double* rhoB, double* ux, double* uy, bool diag) {
@@ -584,7 +846,8 @@ cudaError_t launch_fields(Ctx& c, int ci, double* rhoA, double* rhoB, double* ux
     const int n = C.item_end - C.item_begin;
     const int grid = n < c.grid_blocks ? n : c.grid_blocks;
     (void)diag;
-    return dispatch(c, c.f[c.cur], c.f[1 - c.cur], c.stream, true, C.item_begin, C.item_end, grid, o4, c.diag_part);
+    StepArgs a = make_args(c, C.item_begin, C.item_end, o4, c.diag_part);
+    return dispatch(c, a, c.stream, true, grid);
 }
 
 cudaError_t launch_diag_reduce(Ctx& c, int ci) {

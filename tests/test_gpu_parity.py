@@ -184,7 +184,7 @@ def test_mass_conservation_f32():
 def test_launch_shapes_give_identical_results():
     sc = SCENARIOS["ragged131x77"]()
     ref = None
-    for threads, rows in ((128, 64), (64, 7), (256, 16), (128, 1)):
+    for threads, rows in ((128, 64), (64, 7), (128, 16), (128, 1)):
         lat = lbm.Lattice(sc, "f32")
         lbm.lbm_set_launch(lat.ctx, threads, rows)
         lat.step(37)
