@@ -237,8 +237,8 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * ------------------------------------------------------------------------------------------- */
 
 /* Set the step kernel's launch shape: threads per block (64 or 128) and rows per work
- * item (>= 1, or 0 to size the work list at about two waves of resident blocks).  Rebuilds the
- * work list and drops the captured graph. */
+ * item (>= 1, or 0 to choose the height that balances the work list over the resident blocks).
+ * Rebuilds the work list and drops the captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
 
 /* Time candidate launch shapes on the live state (each for `steps` steps, after one warm-up

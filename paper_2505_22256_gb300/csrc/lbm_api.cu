@@ -176,8 +176,8 @@ lbm_status build_tmaps(Ctx& c) {
 }
 
 // Work list: per case, row chunks by column windows of block_threads (interior block_threads - 8).
-// Cases are laid out one after the other.  block_rows = 0 picks the chunk height so that the list
-// holds about two waves of resident blocks (at least 16 rows, at most 128).
+// Cases are laid out one after the other.  block_rows = 0 picks the chunk height (16..128 rows)
+// that minimises the number of waves of resident blocks times the rows each item marches.
 lbm_status build_items(Ctx& c) {
     const int W = c.block_threads, Wi = W - 8;
     lbm_status ts = build_tmaps(c);
@@ -188,9 +188,17 @@ lbm_status build_items(Ctx& c) {
     const long long resident = (long long)per_sm * c.num_sms;
     int H = c.block_rows;
     if (H <= 0) {
-        long long strip_rows = 0;
-        for (const DevCase& d : c.hcases) strip_rows += (long long)((d.nx + Wi - 1) / Wi) * d.ny;
-        H = (int)std::min<long long>(128, std::max<long long>(16, (strip_rows + 2 * resident - 1) / (2 * resident)));
+        // pick the chunk height that minimises (waves of resident blocks) x (rows per item + halo)
+        long long best = -1;
+        for (int h = 16; h <= 128; ++h) {
+            long long items = 0;
+            for (const DevCase& d : c.hcases) items += (long long)((d.nx + Wi - 1) / Wi) * ((d.ny + h - 1) / h);
+            const long long cost = ((items + resident - 1) / resident) * (h + 5);
+            if (best < 0 || cost < best || (cost == best && h > H)) {
+                best = cost;
+                H = h;
+            }
+        }
     }
     c.rows_used = H;
     std::vector<int4> items;
@@ -447,11 +455,13 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
             CUDA_TRY(cudaGraphLaunch(c.graph, c.stream));
             n -= kGraphSteps;
             c.steps += kGraphSteps;
+            ++c.version;
         } else {
             CUDA_TRY(launch_step(c, c.cur, c.stream));
             c.cur ^= 1;
             --n;
             ++c.steps;
+            ++c.version;
         }
     }
     return LBM_OK;
@@ -490,6 +500,7 @@ lbm_status lbm_set_densities(lbm_ctx* ctx, int32_t ci, const double* rho_A0, con
     }
     CUDA_TRY(launch_feq_rest(c, ci, a, b, c.dense));
     CUDA_TRY(launch_set_state(c, ci, c.dense));
+    ++c.version;
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c.stream));
     return LBM_OK;
 }
@@ -500,10 +511,13 @@ lbm_status lbm_fields(lbm_ctx* ctx, int32_t ci, double* rho_A, double* rho_B, do
     Ctx& c = ctx->c;
     const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
     if (on_device) {
+        c.fields_case = -1;  // NULL outputs land in the scratch
         CUDA_TRY(launch_fields(c, ci, rho_A, rho_B, ux, uy, false));
         return LBM_OK;
     }
     CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, false));
+    c.fields_case = ci;
+    c.fields_version = c.version;
     double* outs[4] = {rho_A, rho_B, ux, uy};
     for (int q = 0; q < 4; ++q)
         if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], c.fields + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -517,6 +531,8 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
     if (!out) return fail(LBM_EINVAL, "NULL output");
     Ctx& c = ctx->c;
     CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, true));
+    c.fields_case = ci;
+    c.fields_version = c.version;
     CUDA_TRY(launch_diag_reduce(c, ci));
     double v[kDiagN];
     CUDA_TRY(cudaMemcpyAsync(v, c.diag_out + (size_t)ci * kDiagN, sizeof v, cudaMemcpyDeviceToHost, c.stream));
@@ -549,7 +565,11 @@ lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surfac
     if (surface->kind == LBM_SURFACE_CIRCLE && !(surface->R > 0)) return fail(LBM_EINVAL, "surface radius must be > 0");
     if (surface->kind != LBM_SURFACE_CIRCLE && surface->kind != LBM_SURFACE_FLAT) return fail(LBM_EINVAL, "bad surface kind");
     Ctx& c = ctx->c;
-    CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, false));
+    if (!(c.fields_case == ci && c.fields_version == c.version)) {  // reuse fields of this very state
+        CUDA_TRY(launch_fields(c, ci, nullptr, nullptr, nullptr, nullptr, false));
+        c.fields_case = ci;
+        c.fields_version = c.version;
+    }
     double o[4];
     CUDA_TRY(launch_contact_angle(c, ci, *surface, o));
     if (npoints) *npoints = (int64_t)llround(o[2]);
@@ -597,6 +617,7 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t ci, const double* f) {
     const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
     CUDA_TRY(cudaMemcpyAsync(c.dense, f, 18 * N * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     CUDA_TRY(launch_set_state(c, ci, c.dense));
+    ++c.version;
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     return LBM_OK;
 }
@@ -651,11 +672,13 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
             if (launch_step(c, c.cur, c.stream) != cudaSuccess) continue;
             c.cur ^= 1;
             ++c.steps;
+            ++c.version;
             cudaEventRecord(e0, c.stream);
             for (int k = 0; k < steps; ++k) {
                 launch_step(c, c.cur, c.stream);
                 c.cur ^= 1;
                 ++c.steps;
+                ++c.version;
             }
             cudaEventRecord(e1, c.stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -739,6 +762,7 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path) {
     CUDA_TRY(cudaMemcpyAsync(c.f[c.cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     c.steps = h.steps;
+    ++c.version;
     return LBM_OK;
 }
 

@@ -124,10 +124,16 @@ __global__ void k_ca_pass(CaGeo g, int pass, const double* __restrict__ st, doub
         }
 }
 
+// Sum of the per-block partial records by one warp: lane l adds blocks l, l+32, ... in order, then
+// a fixed butterfly combines the lanes (deterministic).
 __device__ void sum_parts(const double* part, int nblocks, double* out) {
-    for (int q = 0; q < kCaVals; ++q) out[q] = 0.0;
-    for (int b = 0; b < nblocks; ++b)
-        for (int q = 0; q < kCaVals; ++q) out[q] += part[b * kCaVals + q];
+    const int lane = threadIdx.x & 31;
+    for (int q = 0; q < kCaVals; ++q) {
+        double v = 0.0;
+        for (int b = lane; b < nblocks; b += 32) v += part[b * kCaVals + q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        out[q] = v;
+    }
 }
 
 // 3x3 solve by Gaussian elimination with partial pivoting.
@@ -159,9 +165,9 @@ __device__ void solve3(double A[3][3], double b[3], double x[3]) {
 
 __global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
                            lbm_surface surf) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double S[kCaVals];
-    sum_parts(part, nblocks, S);
+    sum_parts(part, nblocks, S);  // the whole warp
+    if (threadIdx.x != 0) return;
     if (pass == 0) {
         st[0] = S[0];
         st[8] = S[0] < 8.0 ? 1.0 : 0.0;

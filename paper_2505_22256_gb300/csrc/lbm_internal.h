@@ -74,6 +74,9 @@ struct Ctx {
 
     int64_t steps = 0;
     size_t device_bytes = 0;
+    uint64_t version = 1;            // bumped by every change of the state
+    int fields_case = -1;            // case whose fields the scratch holds ...
+    uint64_t fields_version = 0;     // ... computed at this state version
 };
 
 // lbm_step.cu
