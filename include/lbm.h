@@ -257,6 +257,32 @@ lbm_status lbm_save(lbm_ctx* ctx, const char* path);
 lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
 /* ---------------------------------------------------------------------------------------------
+ * Diagnostics without allocation
+ * ------------------------------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this call; it is a service for callers that cannot allocate
+ * device memory: code running under a framework that owns all device memory through its own
+ * pool, real-time loops that cannot afford the synchronisation and latency of cudaMalloc/cudaFree,
+ * or tools attached to a process whose device memory is already committed.
+ *
+ * Computes the same global FP64 diagnostics as lbm_diagnostics, from fields the caller already
+ * holds on the device: rho_A, rho_B, ux, uy as [ny][nx] doubles (for example written by lbm_fields
+ * with on_device = 1) and the solid mask as [ny][nx] uint8 (nonzero = solid), all device pointers
+ * owned by the caller and only read.  *out is a host struct, filled before return; the call
+ * synchronises cuda_stream (NULL = the legacy default stream).  It allocates nothing: its partial
+ * sums live in a fixed array inside the library's device image (about 384 KB, held by every GPU
+ * that loads the library until the process exits).  Limits and rules:
+ *   - nx * ny may not exceed 16,777,216 nodes (LBM_EINVAL otherwise);
+ *   - all calls on a device share that array, so calls that overlap on the GPU race; serialise them;
+ *   - the first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture on the device.
+ * Returns LBM_EUNSTABLE, with *out filled, when a fluid node has a non-finite or non-positive
+ * density. */
+lbm_status lbm_diagnostics_noalloc(const double* rho_A, const double* rho_B, const double* ux,
+                                   const double* uy, const uint8_t* solid, int32_t nx, int32_t ny,
+                                   void* cuda_stream, lbm_diag* out);
+
+/* ---------------------------------------------------------------------------------------------
  * Errors
  * ------------------------------------------------------------------------------------------- */
 const char* lbm_status_str(int32_t status);

@@ -401,6 +401,19 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
 
 }  // namespace
 
+namespace lbm {
+// Error reporting for entry points defined in other translation units.
+lbm_status report_error(lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+}  // namespace lbm
+
 extern "C" {
 
 lbm_status lbm_create(const lbm_grid* grid, const uint8_t* solid, const lbm_params* params, const double* rho_A0,

@@ -31,7 +31,7 @@ BC = {"periodic": LBM_BC_PERIODIC, "wall": LBM_BC_WALL, "open": LBM_BC_OPEN}
 SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_synchronize",
            "lbm_set_densities", "lbm_fields", "lbm_diagnostics", "lbm_contact_angle", "lbm_wall_list",
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
-           "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error")
+           "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc")
 
 
 class lbm_grid(ctypes.Structure):
@@ -114,6 +114,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_autotune.argtypes = [ctx_p, c_int32, d]
     lib.lbm_save.argtypes = [ctx_p, ctypes.c_char_p]
     lib.lbm_load.argtypes = [ctx_p, ctypes.c_char_p]
+    lib.lbm_diagnostics_noalloc.argtypes = [c_void_p] * 5 + [c_int32, c_int32, c_void_p, POINTER(lbm_diag)]
     lib.lbm_status_str.argtypes = [c_int32]
     lib.lbm_status_str.restype = ctypes.c_char_p
     lib.lbm_last_error.argtypes = []
@@ -237,6 +238,20 @@ def lbm_fields(ctx, case_index: int, rho_A=None, rho_B=None, ux=None, uy=None, o
 def lbm_diagnostics(ctx, case_index: int = 0, allow_unstable: bool = False) -> dict:
     d = lbm_diag()
     st = load_library().lbm_diagnostics(ctx, case_index, ctypes.byref(d))
+    if not (allow_unstable and st == LBM_EUNSTABLE):
+        _check(st)
+    return d.as_dict()
+
+
+def lbm_diagnostics_noalloc(rho_A, rho_B, ux, uy, solid, nx: int, ny: int, cuda_stream: int | None = None,
+                            allow_unstable: bool = False) -> dict:
+    """Diagnostics of device-resident fields without any device allocation (for callers that may
+    not allocate: pool-owning frameworks, latency-bound loops, fully committed devices).  The five
+    arrays are device buffers (tensors or addresses) of shape [ny][nx]; solid is uint8."""
+    d = lbm_diag()
+    st = load_library().lbm_diagnostics_noalloc(_ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy), _ptr(solid), int(nx),
+                                                int(ny), c_void_p(cuda_stream) if cuda_stream else None,
+                                                ctypes.byref(d))
     if not (allow_unstable and st == LBM_EUNSTABLE):
         _check(st)
     return d.as_dict()
