@@ -236,7 +236,8 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * Launch shape
  * ------------------------------------------------------------------------------------------- */
 
-/* Set the step kernel's launch shape: threads per block (64 or 128) and rows per work
+/* Set the step kernel's launch shape: threads per block (128, the width the kernel is built for)
+ * and rows per work
  * item (>= 1, or 0 to choose the height that balances the work list over the resident blocks).
  * Rebuilds the work list and drops the captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);

@@ -144,8 +144,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Two tensor maps per case: one row of all 18 planes of each population buffer, T [+8] columns from
-// column x - G (the ghost columns included), as the step kernel loads it.
+// Three tensor maps per case: one row of all 18 planes of each population buffer, T [+8] columns
+// from column x - G (the ghost columns included), and one row of the ghost-padded flags, as the
+// step kernel loads them.
 lbm_status build_tmaps(Ctx& c) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -155,7 +156,7 @@ lbm_status build_tmaps(Ctx& c) {
                            : c.storage == LBM_STORE_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                            : c.storage == LBM_STORE_F16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    std::vector<CUtensorMap> maps(2 * c.hcases.size());
+    std::vector<CUtensorMap> maps(3 * c.hcases.size());
     for (size_t ci = 0; ci < c.hcases.size(); ++ci) {
         const DevCase& d = c.hcases[ci];
         for (int buf = 0; buf < 2; ++buf) {
@@ -164,11 +165,20 @@ lbm_status build_tmaps(Ctx& c) {
             cuuint64_t strides[2] = {(cuuint64_t)d.pitch * c.elem, (cuuint64_t)d.pitch * d.ny * c.elem};
             cuuint32_t box[3] = {(cuuint32_t)(T + XB), 1, 18};
             cuuint32_t estr[3] = {1, 1, 1};
-            CUresult r = enc(&maps[2 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CUresult r = enc(&maps[3 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "tensor map of case %zu rejected (CUresult %d)", ci, (int)r);
         }
+        // flag rows: T + 8 columns from column x - 8 (8 ghost columns per side)
+        cuuint64_t fdims[2] = {(cuuint64_t)(d.nx + 16), (cuuint64_t)d.ny};
+        cuuint64_t fstr[1] = {(cuuint64_t)c.gf_pitch[ci] * sizeof(uint16_t)};
+        cuuint32_t fbox[2] = {(cuuint32_t)(T + 8), 1};
+        cuuint32_t festr[2] = {1, 1};
+        CUresult r = enc(&maps[3 * ci + 2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, c.gflags + c.gf_off[ci], fdims, fstr, fbox,
+                         festr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "flag tensor map of case %zu rejected (CUresult %d)", ci, (int)r);
     }
     if (!c.tmaps) CUDA_TRY(cudaMalloc(&c.tmaps, maps.size() * sizeof(CUtensorMap)));
     CUDA_TRY(cudaMemcpy(c.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
@@ -206,8 +216,12 @@ lbm_status build_items(Ctx& c) {
         DevCase& d = c.hcases[ci];
         d.item_begin = (int)items.size();
         const int nstrip = (d.nx + Wi - 1) / Wi;
-        for (int y0 = 0; y0 < d.ny; y0 += H)
-            for (int s = 0; s < nstrip; ++s) items.push_back(make_int4((int)ci, s * Wi, y0, std::min(d.ny, y0 + H)));
+        // odd chunks march upwards (sign bit of the case field): the halo rows two chunks share are
+        // then read by both at the same time, while they are still in L2
+        for (int y0 = 0, chunk = 0; y0 < d.ny; y0 += H, ++chunk)
+            for (int s = 0; s < nstrip; ++s)
+                items.push_back(make_int4((int)((unsigned)ci | ((chunk & 1) ? 0x80000000u : 0u)), s * Wi, y0,
+                                          std::min(d.ny, y0 + H)));
         d.item_end = (int)items.size();
     }
     if (c.items) {
@@ -246,7 +260,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -367,6 +381,14 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         c.nwall += tot;
     }
     cudaFree(counts);
+    long long gf_total = 0;
+    for (int i = 0; i < ncases; ++i) {
+        c.gf_off.push_back(gf_total);
+        c.gf_pitch.push_back((c.hcases[i].nx + 16 + 63) / 64 * 64);
+        gf_total += (long long)c.gf_pitch.back() * c.hcases[i].ny;
+    }
+    if (st == LBM_OK) st = cu(dalloc(c, &c.gflags, gf_total), "padded flags");
+    for (int i = 0; i < ncases && st == LBM_OK; ++i) st = cu(launch_flags_ghost(c, i), "padded flags kernel");
     if (st == LBM_OK) st = cu(cudaMemcpy(c.dcases, c.hcases.data(), ncases * sizeof(DevCase), cudaMemcpyHostToDevice), "descriptors");
     if (st == LBM_OK) st = cu(dalloc(c, &c.wl_node, c.nwall), "wall list");
     if (st == LBM_OK) st = cu(dalloc(c, &c.wl_subst, c.nwall), "wall list");
@@ -658,7 +680,7 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
 
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
-    if (!(threads == 64 || threads == 128)) return fail(LBM_EINVAL, "threads must be 64 or 128");
+    if (threads != 128) return fail(LBM_EINVAL, "the step kernel is built for 128 threads per block");
     if (rows < 0) return fail(LBM_EINVAL, "rows must be >= 0 (0 = automatic)");
     Ctx& c = ctx->c;
     CUDA_TRY(cudaStreamSynchronize(c.stream));
@@ -671,7 +693,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
     Ctx& c = ctx->c;
-    const int cand_t[] = {64, 128};
+    const int cand_t[] = {128};
     const int cand_r[] = {0, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));

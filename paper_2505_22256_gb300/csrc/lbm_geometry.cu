@@ -187,6 +187,25 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
     }
 }
 
+// Flags with 8 ghost columns on each side, as the step kernel's tensor loads read them: column x
+// at element x + 8; beyond the array a periodic axis wraps, a wall is solid and an open boundary
+// repeats its boundary column.
+__global__ void k_flags_ghost(const DevCase* __restrict__ cases, int c, const uint16_t* __restrict__ flags_all,
+                              uint16_t* __restrict__ out, int pitch) {
+    const DevCase C = cases[c];
+    const long long n = (long long)C.ny * pitch;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int Y = (int)(s / pitch), m = (int)(s % pitch), x = m - 8;
+        uint16_t v;
+        if (m >= C.nx + 16) v = 0;  // row padding
+        else if (x >= 0 && x < C.nx) v = flags_all[C.d_off + (long long)Y * C.nx + x];
+        else if (C.bc_x == kPeriodic) v = flags_all[C.d_off + (long long)Y * C.nx + ((x % C.nx) + C.nx) % C.nx];
+        else if (C.bc_x == kOpen) v = flags_all[C.d_off + (long long)Y * C.nx + (x < 0 ? 0 : C.nx - 1)];
+        else v = kSolidBit;
+        out[s] = v;
+    }
+}
+
 // Per-node copy of the adhesion vectors of one case's wall-list entries, in the compute type.
 template <class R>
 __global__ void k_wall_scatter(const DevCase* __restrict__ cases, int c, const int32_t* __restrict__ wl_node,
@@ -218,6 +237,13 @@ cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cud
 cudaError_t launch_wall_fill(Ctx& c, int ci, const int32_t* row_offsets) {
     k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.wsub, row_offsets,
                                                         c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags_ghost(Ctx& c, int ci) {
+    const long long n = (long long)c.hcases[ci].ny * c.gf_pitch[ci];
+    const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_flags_ghost<<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, c.gflags + c.gf_off[ci], c.gf_pitch[ci]);
     return cudaGetLastError();
 }
 

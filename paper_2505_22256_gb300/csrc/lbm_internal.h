@@ -44,7 +44,10 @@ struct Ctx {
     uint32_t* wsub = nullptr;        // [dense_elems] substitution mask of wall-list nodes
     void* wa = nullptr;              // [2][dense_elems] adhesion vectors of wall-list nodes, compute type
     uint8_t* solid = nullptr;        // [dense_elems] copy of the masks
-    CUtensorMap* tmaps = nullptr;    // [ncases][2] tensor maps of the population buffers
+    CUtensorMap* tmaps = nullptr;    // [ncases][3] tensor maps: population buffers 0 and 1, flag rows
+    uint16_t* gflags = nullptr;      // flags with 8 ghost columns per side ([ny][gpitch] per case)
+    std::vector<long long> gf_off;   // element offset of each case's block in gflags
+    std::vector<int> gf_pitch;       // its row pitch (elements)
     int* err = nullptr;              // device error word (pipeline wait gave up)
     int32_t* wl_node = nullptr;      // wall list, all cases back to back
     uint32_t* wl_subst = nullptr;
@@ -97,6 +100,7 @@ cudaError_t launch_flags(Ctx& c, int case_index, int32_t* row_counts);
 cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cudaStream_t s);
 cudaError_t launch_wall_fill(Ctx& c, int case_index, const int32_t* row_offsets);
 cudaError_t launch_wall_cast(Ctx& c, int case_index);
+cudaError_t launch_flags_ghost(Ctx& c, int case_index);
 
 // lbm_contact.cu
 cudaError_t launch_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* host_out4);

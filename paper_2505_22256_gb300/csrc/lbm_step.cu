@@ -197,21 +197,23 @@ struct Grad {
     }
 };
 
-// Row sums of row r at this thread's column, added into the gradient window (targets r-2..r+2):
+// Row sums of row r at this thread's column, added into the gradient window (the five target rows
+// around r, in marching order):
 // Gx(T) = sum_dy [w(1+dy^2) D1(T+dy) + 2 w(4+dy^2) D2(T+dy)],
 // Gy(T) = R1(T+1) - R1(T-1) + 2 (R2(T+2) - R2(T-2)),
 // D1 = rho(x+1) - rho(x-1), D2 = rho(x+2) - rho(x-2), R_k = w(k^2) rho + w(1+k^2) S1 + w(4+k^2) S2
 // with S1, S2 the sums of the same pairs.
 template <class R>
-__device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Grad<R>& g, int k) {
+__device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Grad<R>& g, int k, R dir) {
     const R m2 = ring[base - 2], m1 = ring[base - 1], c0 = ring[base], p1 = ring[base + 1], p2 = ring[base + 2];
     const R D1 = p1 - m1, D2 = p2 - m2, S1 = p1 + m1, S2 = p2 + m2;
     const R w1 = (R)w8(1), w2 = (R)w8(2), w4 = (R)w8(4), w5 = (R)w8(5), w8v = (R)w8(8);
     const R X0 = w1 * D1 + (R)2 * w4 * D2;
     const R X1 = w2 * D1 + (R)2 * w5 * D2;
     const R X2 = w5 * D1 + (R)2 * w8v * D2;
-    const R R1 = w1 * c0 + w2 * S1 + w5 * S2;
-    const R R2 = (R)2 * (w4 * c0 + w5 * S1 + w8v * S2);
+    // window slot j holds target row r - 2 dir + j dir, i.e. dy = r - target = dir (2 - j)
+    const R R1 = dir * (w1 * c0 + w2 * S1 + w5 * S2);
+    const R R2 = dir * (R)2 * (w4 * c0 + w5 * S1 + w8v * S2);
     g.x[k][0] += X2;
     g.y[k][0] += R2;
     g.x[k][1] += X1;
@@ -223,11 +225,19 @@ __device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Gr
     g.y[k][4] -= R2;
 }
 
-// Explicit 24-node gradient of a wall-list node with the second-layer substitution of Table 1:
-// a second-layer site whose bit is set in `sub` reads its first-layer partner x + sign(e).
 template <class R>
-__device__ __forceinline__ void wall_gradient(const R* __restrict__ ringA, const R* __restrict__ ringB,
-                                              const int (&sb)[5], uint32_t sub, R& gAx, R& gAy, R& gBx, R& gBy) {
+struct Grad4 {
+    R ax, ay, bx, by;
+};
+
+// Explicit 24-node gradient of a wall-list node with the second-layer substitution of Table 1:
+// a second-layer site whose bit is set in `sub` reads its first-layer partner x + sign(e).  Kept out
+// of line: only wall-list nodes run it, and the hot loop stays small.
+template <class R>
+__device__ __noinline__ Grad4<R> wall_gradient(const R* __restrict__ ringA, const R* __restrict__ ringB, int sb0,
+                                               int sb1, int sb2, int sb3, int sb4, uint32_t sub) {
+    const int sb[5] = {sb0, sb1, sb2, sb3, sb4};
+    R gAx, gAy, gBx, gBy;
     R vA[5][5], vB[5][5];
 #pragma unroll
     for (int dy = -2; dy <= 2; ++dy) {
@@ -271,6 +281,7 @@ __device__ __forceinline__ void wall_gradient(const R* __restrict__ ringA, const
             gAy += w * (vA[2 + dy][dx + 2] - vA[2 - dy][dx + 2]);
             gBy += w * (vB[2 + dy][dx + 2] - vB[2 - dy][dx + 2]);
         }
+    return Grad4<R>{gAx, gAy, gBx, gBy};
 }
 
 // SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e):
@@ -313,9 +324,10 @@ struct Layout {
 
 template <class S, class R>
 struct SmemPlan {
-    size_t slot_bytes, ring_off, bar_off, total;
+    size_t pop_bytes, slot_bytes, ring_off, bar_off, total;
     __host__ __device__ explicit SmemPlan(int T) {
-        slot_bytes = ((size_t)(T + Layout<S>::XB) * 18 * sizeof(S) + 127) / 128 * 128;
+        pop_bytes = ((size_t)(T + Layout<S>::XB) * 18 * sizeof(S) + 127) / 128 * 128;
+        slot_bytes = pop_bytes + ((size_t)(T + 8) * sizeof(uint16_t) + 127) / 128 * 128;  // + the flags row
         ring_off = kSlots * slot_bytes;
         bar_off = (ring_off + 2 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
         total = bar_off + kSlots * 8;
@@ -326,10 +338,9 @@ struct StepArgs {
     const DevCase* cases;
     const int4* items;
     int item_begin, item_end;
-    const CUtensorMap* tmaps;  // [case][2]: row loads from buffer 0, from buffer 1
+    const CUtensorMap* tmaps;  // [case][3]: rows of buffer 0, rows of buffer 1, rows of the flags
     int in_buf;                // buffer holding the current state
     void* fout;                // the other buffer
-    const uint16_t* flags;     // dense per case
     const uint32_t* wsub;      // dense: substitution mask of wall-list nodes
     const void* wa;            // dense: adhesion vectors [2][nodes] in the compute type
     long long dense_total;
@@ -337,18 +348,21 @@ struct StepArgs {
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
+constexpr int kT = 128;  // threads per block = columns per window (interior kT - 8)
+
 template <class S, class R, bool kFields>
-__global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
+__global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int T = blockDim.x, t = threadIdx.x, Wi = T - 8;
+    constexpr int T = kT, Wi = T - 8;
+    const int t = threadIdx.x;
     constexpr int G = Layout<S>::G;
-    const int BX = T + Layout<S>::XB;
+    constexpr int BX = T + Layout<S>::XB;
     const SmemPlan<S, R> plan(T);
     R* ringA = reinterpret_cast<R*>(smem + plan.ring_off);
     R* ringB = ringA + kRing * T;
     const uint32_t bar0 = smem_u32(smem + plan.bar_off);
     const uint32_t slot0 = smem_u32(smem);
-    const uint32_t box_bytes = (uint32_t)((size_t)BX * 18 * sizeof(S));
+    const uint32_t box_bytes = (uint32_t)((size_t)BX * 18 * sizeof(S) + (size_t)(T + 8) * sizeof(uint16_t));
     const R* wax = reinterpret_cast<const R*>(a.wa);
     const R* way = wax + a.dense_total;
 
@@ -368,11 +382,13 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
 
     for (int it = a.item_begin + blockIdx.x; it < a.item_end; it += gridDim.x) {
         const int4 item = a.items[it];
-        const DevCase& C = a.cases[item.x];
+        const int ci = item.x & 0x7FFFFFFF;       // case
+        const int dir = item.x < 0 ? -1 : 1;      // marching direction (neighbouring chunks alternate)
+        const DevCase& C = a.cases[ci];
         const Params<R> P = load_params<R>(C);
         const int xs = item.y, y0 = item.z, y1 = item.w;
-        const CUtensorMap* lmap = a.tmaps + 2 * item.x + a.in_buf;
-        const uint16_t* flags = a.flags + C.d_off;
+        const CUtensorMap* lmap = a.tmaps + 3 * ci + a.in_buf;
+        const CUtensorMap* fmap = a.tmaps + 3 * ci + 2;
         const int x = xs - 2 + t;                 // this thread's window column
         const bool rcol = t < Wi + 4;             // computes densities
         const int X = rcol ? map_col(P, x) : -1;  // lattice column
@@ -381,18 +397,21 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
         const bool inlet = P.bc_x == kOpen && X == 0;
         const bool outlet = P.bc_x == kOpen && X == P.nx - 1;
         const int nload = (y1 + 2) - (y0 - 3) + 1;  // f* rows y0-3 .. y1+2
+        const int r_first = dir > 0 ? y0 - 3 : y1 + 2, r_last = dir > 0 ? y1 + 2 : y0 - 3;
         S* fo = reinterpret_cast<S*>(a.fout) + C.f_off;
 
         auto wrap_row = [&](int r) -> int {
             if (P.bc_y == kPeriodic) r += r < 0 ? P.ny : (r >= P.ny ? -P.ny : 0);
             return r;
         };
-        int next_row = y0 - 3;  // next f* row to load (thread 0 only)
-        auto issue = [&]() {  // load the next f* row into the next slot (outside a wall: zeros)
+        int next_row = r_first;  // next f* row to load (thread 0 only)
+        // load the next row of f* and of the flags into the next slot (outside a wall: zeros)
+        auto issue = [&]() {
+            const uint32_t dst = slot0 + issue_slot * (uint32_t)plan.slot_bytes;
             mbar_expect_tx(bar0 + 8 * issue_slot, box_bytes);
-            tma_load_3d(slot0 + issue_slot * (uint32_t)plan.slot_bytes, lmap, xs, wrap_row(next_row), 0,
-                        bar0 + 8 * issue_slot);
-            ++next_row;
+            tma_load_3d(dst, lmap, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
+            tma_load_2d(dst + (uint32_t)plan.pop_bytes, fmap, xs, wrap_row(next_row), bar0 + 8 * issue_slot);
+            next_row += dir;
             if (++issue_slot == kSlots) {
                 issue_slot = 0;
                 issue_par ^= 1u;
@@ -406,35 +425,34 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
             }
             return okw;
         };
-        // slot holding f* row r+1 is the one just waited for; rows r and r-1 sit in the two before
-        auto slot_back = [&](int back) -> const S* {
+        // the slot just waited for holds row r+dir; rows r and r-dir sit in the two before it
+        auto slot_back = [&](int back) -> const unsigned char* {
             int sidx = wait_slot - 1 - back;
             sidx += sidx < 0 ? kSlots : 0;
             sidx += sidx < 0 ? kSlots : 0;
-            return reinterpret_cast<const S*>(smem + sidx * plan.slot_bytes);
-        };
-        auto flags_of = [&](int r) -> uint16_t {
-            const int Y = wrap_row(r);
-            if (X < 0 || Y < 0 || Y >= P.ny) return kSolidBit;
-            return __ldg(flags + (long long)Y * P.nx + X);
+            return smem + sidx * plan.slot_bytes;
         };
 
         // densities of row r into the ring, populations of row r into st
         auto rho_row = [&](int r, RowState<R>& st) -> bool {
-            const bool ok = wait_next();  // f* row r+1
+            const bool ok = wait_next();  // f* row r+dir
+            const unsigned char* s0 = slot_back(1);
+            // node flags of row r; rows beyond a wall boundary are solid
+            st.fl = (rcol && (P.bc_y == kPeriodic || (r >= 0 && r < P.ny)))
+                        ? reinterpret_cast<const uint16_t*>(s0 + plan.pop_bytes)[t + 6]
+                        : kSolidBit;
             R ra = 0, rb = 0;
             const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
             if (!(st.fl & kSolidBit)) {
-                const S* rm = slot_back(2);
-                const S* r0 = slot_back(1);
-                const S* rp = slot_back(0);
+                const S* rm = reinterpret_cast<const S*>(slot_back(dir > 0 ? 2 : 0));
+                const S* r0 = reinterpret_cast<const S*>(s0);
+                const S* rp = reinterpret_cast<const S*>(slot_back(dir > 0 ? 0 : 2));
                 if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
                 else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    ra += st.f[i];
-                    rb += st.f[9 + i];
-                }
+                // rho_k = sum_i f_i as a balanced tree (short dependency chains)
+                const R* f = st.f;
+                ra = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + (f[7] + f[8])));
+                rb = ((f[9] + f[10]) + (f[11] + f[12])) + ((f[13] + f[14]) + (f[15] + (f[16] + f[17])));
                 if (st.fl & kWallBit) {
                     const long long o = C.d_off + (long long)wrap_row(r) * P.nx + X;
                     st.sub = __ldg(a.wsub + o);
@@ -468,7 +486,13 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
             const R rA = ringA[sb[2]], rB = ringB[sb[2]];
             R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
             const bool wall = (st.fl & kWallBit) != 0;
-            if (wall) wall_gradient<R>(ringA, ringB, sb, st.sub, gAx, gAy, gBx, gBy);
+            if (wall) {
+                const Grad4<R> w4 = wall_gradient<R>(ringA, ringB, sb[0], sb[1], sb[2], sb[3], sb[4], st.sub);
+                gAx = w4.ax;
+                gAy = w4.ay;
+                gBx = w4.bx;
+                gBy = w4.by;
+            }
             // cohesion: each component is pushed by the other's pseudopotential gradient (Eq. 8)
             R FAx = -P.G * rA * gBx, FAy = -P.G * rA * gBy;
             R FBx = -P.G * rB * gAx, FBy = -P.G * rB * gAy;
@@ -527,16 +551,22 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
                 R o[18];
                 collide_comp<R>(f, 0, rA, ux, uy, FAx, FAy, P.omega[0], P.cF[0], o);
                 collide_comp<R>(f, 1, rB, ux, uy, FBx, FBy, P.omega[1], P.cF[1], o);
-                const bool ghost = P.bc_x == kPeriodic && (x < G || x >= P.nx - G);
-                const int gcol = x < G ? x + P.nx + G : x - P.nx + G;
                 S* out = fo + (long long)y * P.pitch + x + G;
 #pragma unroll
                 for (int q = 0; q < 18; ++q) {
                     R v = o[q];
                     if constexpr (Store<S>::kShift) v -= shift_of(P, q / 9, q % 9);
-                    const S sv = to_store<S, R>(v);
-                    out[(long long)q * P.plane] = sv;
-                    if (ghost) out[(long long)q * P.plane + gcol - (x + G)] = sv;  // copy for the periodic wrap
+                    o[q] = v;
+                    *out = to_store<S, R>(v);
+                    out += P.plane;
+                }
+                if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
+                    S* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) {
+                        *gout = to_store<S, R>(o[q]);
+                        gout += P.plane;
+                    }
                 }
             }
         };
@@ -548,42 +578,45 @@ __global__ void __launch_bounds__(128, LBM_MIN_BLOCKS) k_step(StepArgs a) {
         RowState<R> s0, s1, s2;
         s0.sub = s1.sub = s2.sub = 0;
         s0.ax = s0.ay = s1.ax = s1.ay = s2.ax = s2.ay = (R)0;
-        uint16_t fl_next = flags_of(y0 - 2);
 
         if (t == 0) {
             const int n0 = nload < kSlots ? nload : kSlots;
             for (int k = 0; k < n0; ++k) issue();
         }
-        bool ok = wait_next();  // f* row y0-3
-        ok = wait_next() && ok; // f* row y0-2
+        bool ok = wait_next();   // f* row r_first
+        ok = wait_next() && ok;  // f* row r_first + dir
+        const R rdir = (R)dir;
 
         // One row of the march: densities of row q into `cur`, barrier, refill of the slot that
-        // held f* row q-1, gradient row sums of row q, collision of row q-2 (`old`).
+        // held f* row q-dir, gradient row sums of row q, collision of row q-2 dir (`old`).
         auto iter = [&](int q, RowState<R>& old, RowState<R>& cur) -> bool {
-            cur.fl = fl_next;
-            fl_next = flags_of(q + 1);
             const bool mine = rho_row(q, cur);
             if (__syncthreads_or(!mine)) return false;
-            if (t == 0 && next_row <= y1 + 2) issue();  // the slot of f* row q-1 is free now
+            if (t == 0 && (dir > 0 ? next_row <= r_last : next_row >= r_last)) issue();  // slot of q-dir is free
             if (interior) {
                 const int base = ring_slot(q) * T + t;
-                add_row<R>(ringA, base, g, 0);
-                add_row<R>(ringB, base, g, 1);
+                add_row<R>(ringA, base, g, 0, rdir);
+                add_row<R>(ringB, base, g, 1, rdir);
             }
-            if (q - 2 >= y0) update_row(q - 2, old, g, dg);
+            const int y = q - 2 * dir;
+            if (y >= y0 && y < y1) update_row(y, old, g, dg);
             g.shift();
             return true;
         };
 
-        // row states rotate with period three: row q goes into cur, row q-2 is old
-        int q = y0 - 2;
-        while (ok) {
-            if (q > y1 + 1) break;
-            ok = iter(q++, s0, s2);
-            if (!ok || q > y1 + 1) break;
-            ok = iter(q++, s1, s0);
-            if (!ok || q > y1 + 1) break;
-            ok = iter(q++, s2, s1);
+        // row states rotate with period three: row q goes into cur, row q-2 dir is old
+        int q = dir > 0 ? y0 - 2 : y1 + 1;
+        int left = (y1 - y0) + 4;  // rows of densities to produce
+        while (ok && left > 0) {
+            ok = iter(q, s0, s2);
+            q += dir;
+            if (!ok || --left == 0) break;
+            ok = iter(q, s1, s0);
+            q += dir;
+            if (!ok || --left == 0) break;
+            ok = iter(q, s2, s1);
+            q += dir;
+            --left;
         }
         if (!ok) {
             failed = true;
@@ -774,7 +807,6 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
     a.tmaps = c.tmaps;
     a.in_buf = c.cur;
     a.fout = c.f[1 - c.cur];
-    a.flags = c.flags;
     a.wsub = c.wsub;
     a.wa = c.wa;
     a.dense_total = c.dense_elems;
@@ -790,9 +822,10 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
 template <class S>
 cudaError_t launch_step_t(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
     using R = typename ComputeOf<S>::type;
-    const size_t smem = smem_for<S>(c.block_threads);
-    if (fields) k_step<S, R, true><<<grid, c.block_threads, smem, s>>>(a);
-    else k_step<S, R, false><<<grid, c.block_threads, smem, s>>>(a);
+    if (c.block_threads != kT) return cudaErrorInvalidConfiguration;
+    const size_t smem = smem_for<S>(kT);
+    if (fields) k_step<S, R, true><<<grid, kT, smem, s>>>(a);
+    else k_step<S, R, false><<<grid, kT, smem, s>>>(a);
     return cudaGetLastError();
 }
 

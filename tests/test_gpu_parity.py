@@ -181,19 +181,28 @@ def test_mass_conservation_f32():
 # ---------------------------------------------------------------------------------------------
 # launch shapes, ensembles, checkpoints
 # ---------------------------------------------------------------------------------------------
-def test_launch_shapes_give_identical_results():
+def test_launch_shapes_agree():
+    """Any chunk height gives the same state to FP32 rounding (row chunks that march upwards sum the
+    gradient rows in the opposite order); a fixed launch shape is bit-reproducible."""
     sc = SCENARIOS["ragged131x77"]()
     ref = None
-    for threads, rows in ((128, 64), (64, 7), (128, 16), (128, 1)):
+    for rows in (64, 7, 16, 1, 16):
         lat = lbm.Lattice(sc, "f32")
-        lbm.lbm_set_launch(lat.ctx, threads, rows)
+        lbm.lbm_set_launch(lat.ctx, 128, rows)
         lat.step(37)
         f = lat.populations()
         lat.close()
         if ref is None:
             ref = f
         else:
-            np.testing.assert_array_equal(f, ref)
+            scale = np.abs(ref).max(axis=(2, 3), keepdims=True)
+            assert np.max(np.abs(f - ref) / scale) < 2e-6
+        if rows == 16:
+            if "f16" in locals():
+                np.testing.assert_array_equal(f, f16)
+            f16 = f
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_set_launch(lbm.Lattice(sc, "f32").ctx, 64, 16)
 
 
 def test_ensemble_equals_single_cases():
