@@ -198,12 +198,13 @@ lbm_status build_items(Ctx& c) {
     const long long resident = (long long)per_sm * c.num_sms;
     int H = c.block_rows;
     if (H <= 0) {
-        // pick the chunk height that minimises (waves of resident blocks) x (rows per item + halo)
+        // Blocks claim items dynamically, so a launch lasts about (all rows marched, halo included) /
+        // (resident blocks) plus the tail of one item: minimise (items + resident) x (h + 5).
         long long best = -1;
         for (int h = 16; h <= 128; ++h) {
             long long items = 0;
             for (const DevCase& d : c.hcases) items += (long long)((d.nx + Wi - 1) / Wi) * ((d.ny + h - 1) / h);
-            const long long cost = ((items + resident - 1) / resident) * (h + 5);
+            const long long cost = (items + resident) * (h + 5);
             if (best < 0 || cost < best || (cost == best && h > H)) {
                 best = cost;
                 H = h;
@@ -260,7 +261,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -317,6 +318,7 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         d.pitch = (d.nx + 2 * ghost_cols(storage) + per_line - 1) / per_line * per_line;
         d.f_off = c.pop_elems;
         d.d_off = c.dense_elems;
+        fill_case_params(d);
         c.pop_elems += 18LL * d.ny * d.pitch;
         c.dense_elems += (long long)d.nx * d.ny;
         max_nodes = std::max(max_nodes, (long long)d.nx * d.ny);
@@ -342,10 +344,12 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
     STEP(dalloc(c, &c.wsub, c.dense_elems), "wall masks");
     STEP(dalloc(c, (unsigned char**)&c.wa, 2 * c.dense_elems * rsize), "wall vectors");
     STEP(dalloc(c, &c.err, 1), "error word");
+    STEP(dalloc(c, &c.sched, 2), "work counters");
     STEP(cudaMemsetAsync(c.flags, 0, c.dense_elems * sizeof(uint16_t), c.stream), "memset");
     STEP(cudaMemsetAsync(c.wsub, 0, c.dense_elems * sizeof(uint32_t), c.stream), "memset");
     STEP(cudaMemsetAsync(c.wa, 0, 2 * c.dense_elems * rsize, c.stream), "memset");
     STEP(cudaMemsetAsync(c.err, 0, sizeof(int), c.stream), "memset");
+    STEP(cudaMemsetAsync(c.sched, 0, 2 * sizeof(int), c.stream), "memset");
     STEP(dalloc(c, &c.solid, c.dense_elems), "masks");
     STEP(dalloc(c, &c.dcases, ncases), "descriptors");
     STEP(dalloc(c, &c.dense, 18 * max_nodes), "transfer scratch");

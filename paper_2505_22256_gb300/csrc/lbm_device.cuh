@@ -65,6 +65,21 @@ __host__ __device__ __forceinline__ constexpr double w8(int e2) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// Per-case parameters in the compute type R, derived on the host once per case so that a kernel
+// starting a work item only loads them.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+struct CaseParams {
+    int nx, ny, pitch, bc_x, bc_y, mode;
+    long long plane;  // ny * pitch
+    R omega[2], cF[2];
+    R G, Gw2, lam, delta, s1, s2, s3, t2, t3;
+    R gx, gy;
+    R d1[2], d5[2];            // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
+    R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
+};
+
+// ------------------------------------------------------------------------------------------------
 // Per-case descriptor (device copy; built on the host).
 // ------------------------------------------------------------------------------------------------
 struct DevCase {
@@ -84,7 +99,40 @@ struct DevCase {
     double g[2];
     double u_in, rho_in[2];
     double rho0[2];         // storage shift per component
+    CaseParams<float> pf;   // the above in FP32 and FP64 (filled by fill_case_params)
+    CaseParams<double> pd;
 };
+
+// Derive pf / pd from the double fields above (host side, after pitch is known).
+template <class R>
+inline void fill_case_params_as(const DevCase& d, CaseParams<R>& P) {
+    P.nx = d.nx; P.ny = d.ny; P.pitch = d.pitch; P.bc_x = d.bc_x; P.bc_y = d.bc_y; P.mode = d.mode;
+    P.plane = (long long)d.ny * d.pitch;
+    for (int k = 0; k < 2; ++k) {
+        P.omega[k] = (R)d.omega[k];
+        P.cF[k] = (R)d.cF[k];
+        P.d1[k] = (R)(6.0 * wq(1) * d.rho_in[k] * d.u_in);
+        P.d5[k] = (R)(6.0 * wq(5) * d.rho_in[k] * d.u_in);
+        P.sh0[k] = (R)(wq(0) * d.rho0[k]);
+        P.sh1[k] = (R)(wq(1) * d.rho0[k]);
+        P.sh5[k] = (R)(wq(5) * d.rho0[k]);
+    }
+    P.G = (R)d.G; P.Gw2 = (R)d.Gw2; P.lam = (R)d.lam; P.delta = (R)d.delta;
+    P.s1 = (R)d.s1; P.s2 = (R)d.s2; P.s3 = (R)d.s3; P.t2 = (R)d.t2; P.t3 = (R)d.t3;
+    P.gx = (R)d.g[0]; P.gy = (R)d.g[1];
+}
+
+inline void fill_case_params(DevCase& d) {
+    fill_case_params_as<float>(d, d.pf);
+    fill_case_params_as<double>(d, d.pd);
+}
+
+template <class R>
+__device__ __forceinline__ const CaseParams<R>& case_params(const DevCase& C);
+template <>
+__device__ __forceinline__ const CaseParams<float>& case_params<float>(const DevCase& C) { return C.pf; }
+template <>
+__device__ __forceinline__ const CaseParams<double>& case_params<double>(const DevCase& C) { return C.pd; }
 
 // ------------------------------------------------------------------------------------------------
 // Storage traits: load/store one population value of storage type S as compute type R.

@@ -49,6 +49,7 @@ struct Ctx {
     std::vector<long long> gf_off;   // element offset of each case's block in gflags
     std::vector<int> gf_pitch;       // its row pitch (elements)
     int* err = nullptr;              // device error word (pipeline wait gave up)
+    int* sched = nullptr;            // step kernel's work-item and finished-block counters
     int32_t* wl_node = nullptr;      // wall list, all cases back to back
     uint32_t* wl_subst = nullptr;
     uint32_t* wl_seff = nullptr;

@@ -37,7 +37,9 @@ namespace lbm {
 
 namespace {
 
-constexpr int kRing = 6;  // rows of densities kept in shared memory
+// Rows of densities kept in shared memory.  Each row is written twice, at ring slot m and m + kRing,
+// so the five consecutive rows a collision reads sit at consecutive slots from one base.
+constexpr int kRing = 6;
 #ifndef LBM_SLOTS
 #define LBM_SLOTS 5
 #endif
@@ -48,34 +50,11 @@ constexpr int kSlots = LBM_SLOTS;  // rows of f* resident or in flight in shared
 static_assert(kSlots >= 4, "the pull of a row needs three resident rows plus one in flight");
 
 template <class R>
-struct Params {
-    int nx, ny, pitch, bc_x, bc_y, mode;
-    long long plane;  // ny * pitch
-    R omega[2], cF[2];
-    R G, Gw2, lam, delta, s1, s2, s3, t2, t3;
-    R gx, gy;
-    R d1[2], d5[2];            // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
-    R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
-};
+using Params = CaseParams<R>;
 
 template <class R>
 __device__ __forceinline__ Params<R> load_params(const DevCase& C) {
-    Params<R> P;
-    P.nx = C.nx; P.ny = C.ny; P.pitch = C.pitch; P.bc_x = C.bc_x; P.bc_y = C.bc_y; P.mode = C.mode;
-    P.plane = (long long)C.ny * C.pitch;
-    for (int k = 0; k < 2; ++k) {
-        P.omega[k] = (R)C.omega[k];
-        P.cF[k] = (R)C.cF[k];
-        P.d1[k] = (R)(6.0 * wq(1) * C.rho_in[k] * C.u_in);
-        P.d5[k] = (R)(6.0 * wq(5) * C.rho_in[k] * C.u_in);
-        P.sh0[k] = (R)(wq(0) * C.rho0[k]);
-        P.sh1[k] = (R)(wq(1) * C.rho0[k]);
-        P.sh5[k] = (R)(wq(5) * C.rho0[k]);
-    }
-    P.G = (R)C.G; P.Gw2 = (R)C.Gw2; P.lam = (R)C.lam; P.delta = (R)C.delta;
-    P.s1 = (R)C.s1; P.s2 = (R)C.s2; P.s3 = (R)C.s3; P.t2 = (R)C.t2; P.t3 = (R)C.t3;
-    P.gx = (R)C.g[0]; P.gy = (R)C.g[1];
-    return P;
+    return case_params<R>(C);
 }
 
 template <class R>
@@ -329,7 +308,7 @@ struct SmemPlan {
         pop_bytes = ((size_t)(T + Layout<S>::XB) * 18 * sizeof(S) + 127) / 128 * 128;
         slot_bytes = pop_bytes + ((size_t)(T + 8) * sizeof(uint16_t) + 127) / 128 * 128;  // + the flags row
         ring_off = kSlots * slot_bytes;
-        bar_off = (ring_off + 2 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
+        bar_off = (ring_off + 4 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
         total = bar_off + kSlots * 8;
     }
 };
@@ -345,13 +324,14 @@ struct StepArgs {
     const void* wa;            // dense: adhesion vectors [2][nodes] in the compute type
     long long dense_total;
     int* err;
+    int* sched;                // [0] next work item, [1] blocks finished; both back to 0 at exit
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
 constexpr int kT = 128;  // threads per block = columns per window (interior kT - 8)
 
 template <class S, class R, bool kFields>
-__global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
+__global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_step(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int T = kT, Wi = T - 8;
     const int t = threadIdx.x;
@@ -359,7 +339,7 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
     constexpr int BX = T + Layout<S>::XB;
     const SmemPlan<S, R> plan(T);
     R* ringA = reinterpret_cast<R*>(smem + plan.ring_off);
-    R* ringB = ringA + kRing * T;
+    R* ringB = ringA + 2 * kRing * T;
     const uint32_t bar0 = smem_u32(smem + plan.bar_off);
     const uint32_t slot0 = smem_u32(smem);
     const uint32_t box_bytes = (uint32_t)((size_t)BX * 18 * sizeof(S) + (size_t)(T + 8) * sizeof(uint16_t));
@@ -380,7 +360,12 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
     uint32_t issue_par = 0, wait_par = 0;
     bool failed = false;
 
-    for (int it = a.item_begin + blockIdx.x; it < a.item_end; it += gridDim.x) {
+    // Work items are claimed from a counter, so blocks that share a busy SM take fewer of them.
+    __shared__ int s_claim;
+    if (t == 0) s_claim = atomicAdd(a.sched, 1);
+    __syncthreads();
+    int it = a.item_begin + s_claim;
+    while (it < a.item_end) {
         const int4 item = a.items[it];
         const int ci = item.x & 0x7FFFFFFF;       // case
         const int dir = item.x < 0 ? -1 : 1;      // marching direction (neighbouring chunks alternate)
@@ -434,7 +419,7 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
         };
 
         // densities of row r into the ring, populations of row r into st
-        auto rho_row = [&](int r, RowState<R>& st) -> bool {
+        auto rho_row = [&](int r, int m, RowState<R>& st) -> bool {
             const bool ok = wait_next();  // f* row r+dir
             const unsigned char* s0 = slot_back(1);
             // node flags of row r; rows beyond a wall boundary are solid
@@ -460,14 +445,17 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
                     st.ay = __ldg(way + o);
                 }
             }
-            const int s = ring_slot(r) * T + t;
+            const int s = m * T + t;
             ringA[s] = ra;
             ringB[s] = rb;
+            ringA[s + kRing * T] = ra;
+            ringB[s + kRing * T] = rb;
             return ok;
         };
 
         // collide row y (state st, complete gradient g[0]) and store it
-        auto update_row = [&](int y, const RowState<R>& st, const Grad<R>& g, Diag& dg) {
+        // lo: ring slot of row y - 2 (rows y-2 .. y+2 sit at slots lo .. lo+4)
+        auto update_row = [&](int y, int lo, const RowState<R>& st, const Grad<R>& g, Diag& dg) {
             if (!interior || (st.fl & kSolidBit)) {
                 if constexpr (kFields) {
                     if (interior) {
@@ -480,14 +468,12 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
                 }
                 return;
             }
-            int sb[5];
-#pragma unroll
-            for (int d = 0; d < 5; ++d) sb[d] = ring_slot(y + d - 2) * T + t;
-            const R rA = ringA[sb[2]], rB = ringB[sb[2]];
+            const int sb0 = lo * T + t;
+            const R rA = ringA[sb0 + 2 * T], rB = ringB[sb0 + 2 * T];
             R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
             const bool wall = (st.fl & kWallBit) != 0;
             if (wall) {
-                const Grad4<R> w4 = wall_gradient<R>(ringA, ringB, sb[0], sb[1], sb[2], sb[3], sb[4], st.sub);
+                const Grad4<R> w4 = wall_gradient<R>(ringA, ringB, sb0, sb0 + T, sb0 + 2 * T, sb0 + 3 * T, sb0 + 4 * T, st.sub);
                 gAx = w4.ax;
                 gAy = w4.ay;
                 gBx = w4.bx;
@@ -590,16 +576,18 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
         // One row of the march: densities of row q into `cur`, barrier, refill of the slot that
         // held f* row q-dir, gradient row sums of row q, collision of row q-2 dir (`old`).
         auto iter = [&](int q, RowState<R>& old, RowState<R>& cur) -> bool {
-            const bool mine = rho_row(q, cur);
+            const int mq = ring_slot(q);
+            const bool mine = rho_row(q, mq, cur);
             if (__syncthreads_or(!mine)) return false;
             if (t == 0 && (dir > 0 ? next_row <= r_last : next_row >= r_last)) issue();  // slot of q-dir is free
             if (interior) {
-                const int base = ring_slot(q) * T + t;
+                const int base = mq * T + t;
                 add_row<R>(ringA, base, g, 0, rdir);
                 add_row<R>(ringB, base, g, 1, rdir);
             }
             const int y = q - 2 * dir;
-            if (y >= y0 && y < y1) update_row(y, old, g, dg);
+            // slot of row y - 2: q - 4 when marching up (= mq + 2 mod kRing), q itself marching down
+            if (y >= y0 && y < y1) update_row(y, dir > 0 ? (mq + 2 < kRing ? mq + 2 : mq + 2 - kRing) : mq, old, g, dg);
             g.shift();
             return true;
         };
@@ -649,6 +637,17 @@ __global__ void __launch_bounds__(kT, LBM_MIN_BLOCKS) k_step(StepArgs a) {
                 }
             }
             __syncthreads();
+        }
+        if (t == 0) s_claim = atomicAdd(a.sched, 1);  // every thread has read the previous claim
+        __syncthreads();
+        it = a.item_begin + s_claim;
+    }
+    if (t == 0) {
+        // the last block to finish sees every claim made and resets the counters for the next launch
+        __threadfence();
+        if (atomicAdd(a.sched + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(a.sched, 0);
+            atomicExch(a.sched + 1, 0);
         }
     }
     if (failed && t == 0) {
@@ -811,6 +810,7 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
     a.wa = c.wa;
     a.dense_total = c.dense_elems;
     a.err = c.err;
+    a.sched = c.sched;
     a.o_rA = o4[0];
     a.o_rB = o4[1];
     a.o_ux = o4[2];
