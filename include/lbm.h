@@ -135,7 +135,7 @@ typedef struct {
     int64_t state_bytes;     /* bytes of one population buffer (all cases) */
     int64_t device_bytes;    /* device memory held by the context */
     int32_t block_threads;   /* launch shape of the step kernel: threads per block */
-    int32_t block_rows;      /* rows per work item */
+    int32_t block_rows;      /* rows per work item (guided list: rows of its long items) */
     int32_t grid_blocks;     /* blocks per launch */
     int32_t work_items;      /* work items per step */
 } lbm_info_t;
@@ -237,9 +237,10 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * ------------------------------------------------------------------------------------------- */
 
 /* Set the step kernel's launch shape: threads per block (128, the width the kernel is built for)
- * and rows per work
- * item (>= 1, or 0 to choose the height that balances the work list over the resident blocks).
- * Rebuilds the work list and drops the captured graph. */
+ * and rows per work item: >= 1 for uniform items of that height, or 0 (the default) for a guided
+ * list -- long items first, then 16-row items that even out the end of the launch, the long height
+ * chosen to balance the list over the resident blocks.  Rebuilds the work list and drops the
+ * captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
 
 /* Time candidate launch shapes on the live state (each for `steps` steps, after one warm-up

@@ -185,9 +185,33 @@ lbm_status build_tmaps(Ctx& c) {
     return LBM_OK;
 }
 
-// Work list: per case, row chunks by column windows of block_threads (interior block_threads - 8).
-// Cases are laid out one after the other.  block_rows = 0 picks the chunk height (16..128 rows)
-// that minimises the number of waves of resident blocks times the rows each item marches.
+#ifndef LBM_TAIL_ROWS
+#define LBM_TAIL_ROWS 16  // height of the short items that end a launch
+#endif
+
+// Row chunks [y0, y1) of one case's column strips, chunk-major; odd chunks march upwards (sign bit
+// of the case field), so the halo rows two neighbouring chunks share are read at about the same
+// time, while they are still in L2.
+void push_chunks(std::vector<int4>& out, int ci, int nstrip, int Wi, int y_begin, int y_end, int h) {
+    const int n = (y_end - y_begin + h - 1) / h;
+    for (int k = 0; k < n; ++k) {
+        // balanced heights: the first (rows % n) chunks take one row more
+        const int rows = y_end - y_begin, base = rows / n, extra = rows % n;
+        const int y0 = y_begin + k * base + std::min(k, extra), y1 = y0 + base + (k < extra ? 1 : 0);
+        for (int s = 0; s < nstrip; ++s)
+            out.push_back(make_int4((int)((unsigned)ci | ((k & 1) ? 0x80000000u : 0u)), s * Wi, y0, y1));
+    }
+}
+
+// Work lists.  A work item is a column window of block_threads - 8 interior columns by a chunk of
+// rows of one case; blocks of the step kernel claim items in list order from a counter.
+//  * Step list.  With block_rows > 0, uniform chunks of that height.  With block_rows = 0 (the
+//    default), a guided list: long chunks of height Hb first, then short chunks of LBM_TAIL_ROWS
+//    rows, enough of them to absorb the ragged end of the long ones, so that a launch lasts about
+//    (rows marched, 5 halo rows per item included) / (resident blocks) + one short item.  Hb
+//    minimises that estimate.
+//  * Per-case list (after the step list): uniform chunks, contiguous per case, used by the fields
+//    pass, whose per-item partial sums are reduced per case in item order.
 lbm_status build_items(Ctx& c) {
     const int W = c.block_threads, Wi = W - 8;
     lbm_status ts = build_tmaps(c);
@@ -196,33 +220,65 @@ lbm_status build_items(Ctx& c) {
     CUDA_TRY(step_occupancy(c.storage, W, &per_sm));
     if (per_sm < 1) return fail(LBM_ECUDA, "step kernel cannot be resident with %d threads", W);
     const long long resident = (long long)per_sm * c.num_sms;
-    int H = c.block_rows;
-    if (H <= 0) {
-        // Blocks claim items dynamically, so a launch lasts about (all rows marched, halo included) /
-        // (resident blocks) plus the tail of one item: minimise (items + resident) x (h + 5).
-        long long best = -1;
-        for (int h = 16; h <= 128; ++h) {
-            long long items = 0;
-            for (const DevCase& d : c.hcases) items += (long long)((d.nx + Wi - 1) / Wi) * ((d.ny + h - 1) / h);
-            const long long cost = (items + resident) * (h + 5);
-            if (best < 0 || cost < best || (cost == best && h > H)) {
+    const int ncases = (int)c.hcases.size();
+    std::vector<int> nstrip(ncases);
+    long long strips = 0;
+    for (int i = 0; i < ncases; ++i) {
+        nstrip[i] = (c.hcases[i].nx + Wi - 1) / Wi;
+        strips += nstrip[i];
+    }
+    std::vector<int4> items;
+    if (c.block_rows > 0) {
+        const int H = c.block_rows;
+        for (int i = 0; i < ncases; ++i) push_chunks(items, i, nstrip[i], Wi, 0, c.hcases[i].ny, H);
+        c.rows_used = H;
+    } else {
+        const int Hs = LBM_TAIL_ROWS;
+        // rows of short chunks per strip of case i for a given long height hb
+        auto tail_chunks = [&](int i, int hb) -> int {
+            const long long need = (resident * (hb + 5) + strips * (Hs + 5) - 1) / (strips * (Hs + 5));
+            return (int)std::min<long long>(need, c.hcases[i].ny / Hs);
+        };
+        double best = -1.0;
+        int Hb = 32;
+        for (int hb = 16; hb <= 256; ++hb) {
+            double work = 0.0, tail = 0.0;
+            for (int i = 0; i < ncases; ++i) {
+                const int ns = tail_chunks(i, hb), bulk = c.hcases[i].ny - ns * Hs;
+                const int nb = (bulk + hb - 1) / hb;
+                work += (double)nstrip[i] * (bulk + 5.0 * nb + ns * (Hs + 5.0));
+                tail += (double)nstrip[i] * ns * (Hs + 5.0);
+            }
+            const double cost = work / resident + (Hs + 5) + std::max(0.0, (hb + 5) - tail / resident);
+            if (best < 0 || cost < best) {
                 best = cost;
-                H = h;
+                Hb = hb;
             }
         }
+        std::vector<int> ns(ncases);
+        for (int i = 0; i < ncases; ++i) {
+            ns[i] = tail_chunks(i, Hb);
+            push_chunks(items, i, nstrip[i], Wi, 0, c.hcases[i].ny - ns[i] * Hs, Hb);
+        }
+        for (int i = 0; i < ncases; ++i)
+            if (ns[i] > 0) push_chunks(items, i, nstrip[i], Wi, c.hcases[i].ny - ns[i] * Hs, c.hcases[i].ny, Hs);
+        c.rows_used = Hb;
     }
-    c.rows_used = H;
-    std::vector<int4> items;
-    for (size_t ci = 0; ci < c.hcases.size(); ++ci) {
-        DevCase& d = c.hcases[ci];
+    c.nitems = (int)items.size();
+    for (int i = 0; i < ncases; ++i) {
+        DevCase& d = c.hcases[i];
+        // per-case chunk height: minimise (items + resident) x (h + 5) for this case alone
+        long long bestc = -1;
+        int Hf = 16;
+        for (int h = 16; h <= 128; ++h) {
+            const long long cost = ((long long)nstrip[i] * ((d.ny + h - 1) / h) + resident) * (h + 5);
+            if (bestc < 0 || cost < bestc) {
+                bestc = cost;
+                Hf = h;
+            }
+        }
         d.item_begin = (int)items.size();
-        const int nstrip = (d.nx + Wi - 1) / Wi;
-        // odd chunks march upwards (sign bit of the case field): the halo rows two chunks share are
-        // then read by both at the same time, while they are still in L2
-        for (int y0 = 0, chunk = 0; y0 < d.ny; y0 += H, ++chunk)
-            for (int s = 0; s < nstrip; ++s)
-                items.push_back(make_int4((int)((unsigned)ci | ((chunk & 1) ? 0x80000000u : 0u)), s * Wi, y0,
-                                          std::min(d.ny, y0 + H)));
+        push_chunks(items, i, nstrip[i], Wi, 0, d.ny, Hf);
         d.item_end = (int)items.size();
     }
     if (c.items) {
@@ -233,7 +289,6 @@ lbm_status build_items(Ctx& c) {
         cudaFree(c.diag_part);
         c.diag_part = nullptr;
     }
-    c.nitems = (int)items.size();
     CUDA_TRY(cudaMalloc(&c.items, items.size() * sizeof(int4)));
     CUDA_TRY(cudaMemcpy(c.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&c.diag_part, items.size() * kDiagN * sizeof(double)));
