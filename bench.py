@@ -12,6 +12,11 @@ Timed region: W warm-up steps, then exactly K steps between a barrier + synchron
 CUDA events on the library's stream; the populations (1.06 GB per buffer) are far larger than L2.
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                    [--workload sweep|throat|porous|ensemble] [--storage f32|f16|bf16|f64]
+
+The other workloads measure the remaining configurations the same way (one JSON line each): the
+2048x512 throat channel as 8 replicas (so that even 16-bit state exceeds L2), the 4096x2048 porous
+medium with inlet and outflow, and the 256-case uneven ensemble plus the co-current channel.
 
 Under torchrun each rank runs its own seven cases (weak scaling, no collective on the data path);
 rank 0 prints the JSON line with the max time over ranks.
@@ -46,8 +51,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
-    ap.add_argument("--n", type=int, default=1024, help="lattice side of each case")
-    ap.add_argument("--cases", type=int, default=7, help="number of lambda values (1..7)")
+    ap.add_argument("--workload", default="sweep", choices=list(WORKLOADS),
+                    help="sweep: 7 cylinder cases of 1024^2 (the headline); throat: 8 replicas of the "
+                         "2048x512 throat channel; porous: 4096x2048 porous medium with inlet/outflow; "
+                         "ensemble: 256 uneven cases + the 4096x256 co-current channel")
+    ap.add_argument("--n", type=int, default=1024, help="sweep: lattice side of each case")
+    ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -55,20 +64,35 @@ def parse():
     return ap.parse_args()
 
 
+WORKLOADS = ("sweep", "throat", "porous", "ensemble")
+
+
 def workload(args, rank=0):
+    """(cases, description) of the chosen workload; rank offsets the seeds (weak scaling)."""
     from paper_2505_22256_gb300 import scenarios as S
 
+    if args.workload == "throat":
+        cases = [S.throat_channel(seed=3 + 100 * k + 1000 * rank) for k in range(8)]
+        return cases, ("throat channel, 8 replicas of 2048x512 per GPU (half-disks R=180, droplet r=120, "
+                       "g=1e-6, lambda for theta=90 deg)")
+    if args.workload == "porous":
+        return [S.porous_disks(seed=4 + 1000 * rank)], \
+            "porous medium 4096x2048 per GPU (disks r=12..40, porosity 0.6, inlet u=0.005 at x=0, outflow)"
+    if args.workload == "ensemble":
+        return S.ensemble_cases(256, seed=5 + 1000 * rank) + [S.cocurrent_channel(seed=6 + 1000 * rank)], \
+            ("uneven ensemble per GPU: 256 square cases n=64..512 (flat wall / cylinder, lambda 0.22..2.17) "
+             "+ the 4096x256 co-current channel")
     angles = (30, 50, 70, 90, 110, 130, 150)[: args.cases]
-    return S.lambda_sweep_cylinder(n=args.n, seed=2 + 1000 * rank, angles=angles)
+    return S.lambda_sweep_cylinder(n=args.n, seed=2 + 1000 * rank, angles=angles), \
+        (f"cylinder contact-angle sweep, {len(angles)} cases of {args.n}x{args.n} per GPU "
+         f"(R={160 * args.n // 1024}, r={200 * args.n // 1024}, lambda for theta=30..150 deg)")
 
 
-def config_dict(args, cases, world):
+def config_dict(args, cases, desc, world):
     nodes = sum(c.nx * c.ny for c in cases)
     fluid = sum(int((c.solid == 0).sum()) for c in cases)
     return {
-        "workload": f"cylinder contact-angle sweep, {len(cases)} cases of {args.n}x{args.n} per GPU "
-                    f"(R={160 * args.n // 1024}, r={200 * args.n // 1024}, lambda for theta=30..150 deg), "
-                    f"{args.inner} time steps + diagnostics + contact angle per step",
+        "workload": f"{desc}, {args.inner} time steps + diagnostics + contact angle per step",
         "storage": args.storage, "cases_per_gpu": len(cases), "nodes_per_gpu": nodes,
         "fluid_nodes_per_gpu": fluid, "inner_steps": args.inner, "parallelism": f"ensemble x{world} (no collective)",
         "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE[args.storage] / 2 / 1e9),
@@ -175,8 +199,8 @@ def committed_traffic(storage: str, nodes_per_launch: int):
 def cpu_baseline(args, seconds: float) -> dict:
     import oracle
 
-    cases = workload(args)
-    sc = cases[len(cases) // 2]
+    cases, _ = workload(args)
+    sc = max(cases, key=lambda c: c.nx * c.ny) if args.workload != "sweep" else cases[len(cases) // 2]
     cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
     f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
     n = 0
@@ -189,7 +213,7 @@ def cpu_baseline(args, seconds: float) -> dict:
             break
     mlups = sc.nx * sc.ny * n / el / 1e6
     return {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
-            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, lambda={sc.lam:.4f}), {n} FP64 time steps "
+            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, {sc.name}), {n} FP64 time steps "
                       f"in {el:.1f} s on {cfg.nthreads} host threads"}
 
 
@@ -197,7 +221,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cases = workload(args)
+    cases, desc = workload(args)
     # each step: a bounded sample of the workload (time steps of one case), sized so that the whole
     # --steps/--warmup run stays within a few minutes
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
@@ -209,11 +233,11 @@ def run_reference(args):
             vals.append(b["value"])
             base = b
     value = statistics.mean(vals)
-    ms_per_step = len(cases) * args.n * args.n * args.inner / (value * 1e6) * 1e3
+    ms_per_step = sum(c.nx * c.ny for c in cases) * args.inner / (value * 1e6) * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(args, cases, 1),
+            "config": config_dict(args, cases, desc, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -245,18 +269,16 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    cases = workload(args, rank)
+    cases, desc = workload(args, rank)
+    surfaces = [c.surface for c in cases]
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(cases, storage=args.storage, cuda_stream=stream.cuda_stream)
     info = lat.info()
     nodes = info["nodes"]
     fluid = info["fluid_nodes"]
 
-    def contact_angle(i):
-        try:
-            return lat.contact_angle(i)[0]
-        except lbm.LbmError:  # no interface left to measure: reported as null
-            return None
+    def contact_angles():  # theta per case; NaN (reported as null) without a surface or an interface
+        return lat.contact_angle_all(surfaces)[0]
 
     def bench_step(ev_pairs=None):
         if ev_pairs is not None:
@@ -266,9 +288,8 @@ def run_ours(args):
         if ev_pairs is not None:
             b.record(stream)
             ev_pairs.append((a, b))
-        for i in range(len(cases)):
-            lat.diagnostics(i, allow_unstable=True)
-            contact_angle(i)
+        lat.diagnostics_all(allow_unstable=True)
+        contact_angles()
 
     for _ in range(args.warmup):
         bench_step()
@@ -301,8 +322,9 @@ def run_ours(args):
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     peak, peak_kind = hbm_peak()
     traffic = committed_traffic(args.storage, nodes)
-    d = lat.diagnostics(0, allow_unstable=True)
-    theta = [contact_angle(i) for i in range(len(cases))]
+    dall = lat.diagnostics_all(allow_unstable=True)
+    d = dall[0]
+    theta = [None if th != th else float(th) for th in contact_angles()]
 
     # e2e through the public API with host buffers: densities in (H2D), 100 steps, fields out (D2H)
     e2e = None
@@ -341,17 +363,22 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h,
                "step": "lbm_set_densities (host) for every case, lbm_step(%d), lbm_fields (host) for every case" % args.inner}
 
-    launches = args.inner + len(cases) * (2 + 1 + 8)
+    # step kernels + (fields pass + per-case reduction) + per measured case (fields pass + 4 x 2 passes)
+    launches = args.inner + 2 + 9 * sum(1 for sf in surfaces if sf is not None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.storage, "data": "synthetic", "config": config_dict(args, cases, world),
+        "dtype": args.storage, "data": "synthetic", "config": config_dict(args, cases, desc, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_step",
                      "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
         "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
-        "sample_diagnostics": {"theta_deg": theta, "case0_umax": d["umax"], "case0_unstable": d["unstable"]},
+        "sample_diagnostics": {"theta_deg": theta if len(theta) <= 8 else
+                               {"measured": sum(t is not None for t in theta),
+                                "min": min((t for t in theta if t is not None), default=None),
+                                "max": max((t for t in theta if t is not None), default=None)},
+                               "case0_umax": d["umax"], "unstable_cases": sum(x["unstable"] for x in dall)},
     }
     lat.close()
     if rank == 0:

@@ -107,7 +107,7 @@ typedef struct {
 } lbm_diag;
 
 /* Solid surface a droplet rests on, for the contact angle. */
-typedef enum { LBM_SURFACE_FLAT = 0, LBM_SURFACE_CIRCLE = 1 } lbm_surface_kind;
+typedef enum { LBM_SURFACE_FLAT = 0, LBM_SURFACE_CIRCLE = 1, LBM_SURFACE_NONE = 2 } lbm_surface_kind;
 typedef struct {
     int32_t kind;   /* lbm_surface_kind */
     int32_t normal; /* flat: +1 when the fluid lies at y > y_w, -1 when at y < y_w */
@@ -209,6 +209,21 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t case_index, lbm_diag* out);
  * fitted circle) and npoints may be NULL.  LBM_ESTATE when fewer than 8 interface points exist. */
 lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t case_index, const lbm_surface* surface,
                              double* theta_deg, double* fit_rms, int64_t* npoints);
+
+/* Diagnostics of every case of the context (the reductions of lbm_diagnostics over an ensemble) in
+ * one launch over the state plus one reduction per case; the same per-item partial sums, reduced
+ * in the same order, so each record equals lbm_diagnostics of that case bit for bit.  out: host,
+ * one lbm_diag per case.  Synchronises once.  LBM_EUNSTABLE when any case is unstable (every record
+ * is written; the message names the first such case). */
+lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out);
+
+/* Contact angle of every case (the measurement of lbm_contact_angle over an ensemble), enqueued case
+ * after case with one synchronisation at the end.  surfaces: host, one per case; kind
+ * LBM_SURFACE_NONE skips a case.  Host outputs, one per case, each may be NULL: theta_deg and
+ * fit_rms (NaN for a skipped case or one with fewer than 8 interface points), npoints (0 when
+ * skipped).  LBM_EINVAL for a bad surface, before any work. */
+lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, double* theta_deg,
+                                 double* fit_rms, int64_t* npoints);
 
 /* Wall list of one case (host outputs; synchronises): fluid nodes whose 24-node stencil reaches a
  * non-fluid site, in increasing node order y*nx + x.  Per entry: node index; subst = bit n-1 set

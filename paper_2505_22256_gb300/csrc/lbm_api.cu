@@ -281,6 +281,7 @@ lbm_status build_items(Ctx& c) {
         push_chunks(items, i, nstrip[i], Wi, 0, d.ny, Hf);
         d.item_end = (int)items.size();
     }
+    c.nitems_all = (int)items.size();
     if (c.items) {
         cudaFree(c.items);
         c.items = nullptr;
@@ -316,7 +317,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.tmaps, c.err, c.sched, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -412,6 +413,7 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
     STEP(dalloc(c, &c.fields, 4 * max_nodes), "field scratch");
     STEP(dalloc(c, &c.diag_out, (size_t)ncases * kDiagN), "diagnostics");
     STEP(dalloc(c, &c.ca_work, (size_t)contact_work_doubles()), "contact-angle scratch");
+    STEP(dalloc(c, &c.ca_all, (size_t)16 * ncases), "contact-angle records");
     for (int i = 0; i < ncases; ++i) {
         std::vector<uint8_t> m((size_t)c.hcases[i].nx * c.hcases[i].ny);
         for (size_t s = 0; s < m.size(); ++s) m[s] = cs[i].solid[s] ? 1 : 0;
@@ -670,6 +672,79 @@ lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surfac
     if (o[3] != 0.0) return fail(LBM_ESTATE, "case %d: only %.0f interface points", ci, o[2]);
     if (theta_deg) *theta_deg = o[0];
     if (fit_rms) *fit_rms = o[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!out) return fail(LBM_EINVAL, "NULL output");
+    Ctx& c = ctx->c;
+    const int n = (int)c.hcases.size();
+    CUDA_TRY(launch_diag_all(c));
+    std::vector<double> v((size_t)n * kDiagN);
+    CUDA_TRY(cudaMemcpyAsync(v.data(), c.diag_out, v.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    {
+        lbm_status es = check_device_error(c);
+        if (es != LBM_OK) return es;
+    }
+    int first_bad = -1;
+    for (int i = 0; i < n; ++i) {
+        const double* r = v.data() + (size_t)i * kDiagN;
+        lbm_diag& o = out[i];
+        o.mass_A = r[0];
+        o.mass_B = r[1];
+        o.mom_x = r[2];
+        o.mom_y = r[3];
+        o.umax = r[4];
+        o.rhoA_min = r[5];
+        o.rhoA_max = r[6];
+        o.rhoB_min = r[7];
+        o.rhoB_max = r[8];
+        o.n_fluid = (int64_t)llround(r[9]);
+        o.unstable = r[10] != 0.0;
+        o.pad_ = 0;
+        if (o.unstable && first_bad < 0) first_bad = i;
+    }
+    if (first_bad >= 0) return fail(LBM_EUNSTABLE, "case %d: non-finite or non-positive density", first_bad);
+    return LBM_OK;
+}
+
+lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, double* theta_deg, double* fit_rms,
+                                 int64_t* npoints) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!surfaces) return fail(LBM_EINVAL, "NULL surfaces");
+    Ctx& c = ctx->c;
+    const int n = (int)c.hcases.size();
+    for (int i = 0; i < n; ++i) {
+        const lbm_surface& s = surfaces[i];
+        if (s.kind != LBM_SURFACE_CIRCLE && s.kind != LBM_SURFACE_FLAT && s.kind != LBM_SURFACE_NONE)
+            return fail(LBM_EINVAL, "case %d: bad surface kind", i);
+        if (s.kind == LBM_SURFACE_CIRCLE && !(s.R > 0)) return fail(LBM_EINVAL, "case %d: surface radius must be > 0", i);
+    }
+    int last = -1;
+    for (int i = 0; i < n; ++i) {
+        if (surfaces[i].kind == LBM_SURFACE_NONE) continue;
+        c.fields_case = -1;
+        CUDA_TRY(launch_fields(c, i, nullptr, nullptr, nullptr, nullptr, false));
+        CUDA_TRY(enqueue_contact_angle(c, i, surfaces[i], c.ca_all + (size_t)16 * i));
+        last = i;
+    }
+    if (last >= 0) {  // the scratch fields hold the last case measured
+        c.fields_case = last;
+        c.fields_version = c.version;
+    }
+    std::vector<double> h((size_t)16 * n);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), c.ca_all, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int i = 0; i < n; ++i) {
+        const double* r = h.data() + (size_t)16 * i;
+        const bool skip = surfaces[i].kind == LBM_SURFACE_NONE;
+        const bool few = !skip && r[8] != 0.0;
+        if (theta_deg) theta_deg[i] = (skip || few) ? NAN : r[7];
+        if (fit_rms) fit_rms[i] = (skip || few) ? NAN : r[6];
+        if (npoints) npoints[i] = skip ? 0 : (int64_t)llround(r[0]);
+    }
     return LBM_OK;
 }
 

@@ -212,11 +212,10 @@ __global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ par
 
 // ctx->fields must already hold rho_A, rho_B of the case (dense).  host_out4 <- theta, rms, npoints,
 // status.
-cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* host_out4) {
+cudaError_t enqueue_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* st) {
     const DevCase& C = c.hcases[ci];
     const long long N = (long long)C.nx * C.ny;
     CaGeo g{C.nx, C.ny, c.flags + C.d_off, c.fields, c.fields + N};
-    double* st = c.ca_work;
     double* part = c.ca_work + 16;
     cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
@@ -224,7 +223,12 @@ cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double
         k_ca_pass<<<kCaBlocks, kCaThreads, 0, c.stream>>>(g, pass, st, part);
         k_ca_solve<<<1, 32, 0, c.stream>>>(pass, kCaBlocks, part, st, surf);
     }
-    e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* host_out4) {
+    double* st = c.ca_work;
+    cudaError_t e = enqueue_contact_angle(c, ci, surf, st);
     if (e != cudaSuccess) return e;
     double h[16];
     e = cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, c.stream);

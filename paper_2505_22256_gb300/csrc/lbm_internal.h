@@ -61,7 +61,8 @@ struct Ctx {
     int rows_used = 0;
     int grid_blocks = 0;
     int4* items = nullptr;
-    int nitems = 0;
+    int nitems = 0;                  // step list: items [0, nitems)
+    int nitems_all = 0;              // per-case lists follow: items [nitems, nitems_all)
 
     // scratch
     double* dense = nullptr;         // [18 * max case nodes] doubles for population transfers
@@ -70,6 +71,7 @@ struct Ctx {
     double* diag_part = nullptr;     // [nitems][kDiagN]
     double* diag_out = nullptr;      // [ncases][kDiagN]
     double* ca_work = nullptr;       // contact-angle reductions
+    double* ca_all = nullptr;        // [ncases][16] contact-angle status records of the batched call
     int ca_cap = 0;
 
     // CUDA graph of kGraphSteps step launches
@@ -88,6 +90,8 @@ cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s);
 cudaError_t launch_fields(Ctx& c, int case_index, double* rhoA, double* rhoB, double* ux, double* uy,
                           bool diag);
 cudaError_t launch_diag_reduce(Ctx& c, int case_index);
+// partial sums of every case in one launch over the per-case lists, then one reduction per case
+cudaError_t launch_diag_all(Ctx& c);
 cudaError_t launch_set_state(Ctx& c, int case_index, const double* dense_f);
 cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);
 cudaError_t launch_feq_rest(Ctx& c, int case_index, const double* rhoA, const double* rhoB, double* dense_f);
@@ -105,5 +109,9 @@ cudaError_t launch_flags_ghost(Ctx& c, int case_index);
 
 // lbm_contact.cu
 cudaError_t launch_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* host_out4);
+// Enqueue the contact-angle passes of one case (ctx->fields must hold its densities by then); the
+// 16-double status record st (device) receives theta at [7], rms at [6], points at [0], the
+// too-few-points flag at [8].  No synchronisation.
+cudaError_t enqueue_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* st);
 
 }  // namespace lbm

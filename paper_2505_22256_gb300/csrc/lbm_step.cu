@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
         auto update_row = [&](int y, int lo, const RowState<R>& st, const Grad<R>& g, Diag& dg) {
             if (!interior || (st.fl & kSolidBit)) {
                 if constexpr (kFields) {
-                    if (interior) {
+                    if (interior && a.o_rA) {
                         const long long o = (long long)y * P.nx + x;
                         a.o_rA[o] = 0.0;
                         a.o_rB[o] = 0.0;
@@ -514,11 +514,13 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
             const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
             if constexpr (kFields) {
-                const long long o = (long long)y * P.nx + x;
-                a.o_rA[o] = (double)rA;
-                a.o_rB[o] = (double)rB;
-                a.o_ux[o] = (double)ux;
-                a.o_uy[o] = (double)uy;
+                if (a.o_rA) {  // null outputs: partial sums only
+                    const long long o = (long long)y * P.nx + x;
+                    a.o_rA[o] = (double)rA;
+                    a.o_rB[o] = (double)rB;
+                    a.o_ux[o] = (double)ux;
+                    a.o_uy[o] = (double)uy;
+                }
                 const double dux = ux, duy = uy, drho = (double)rho;
                 dg.v[0] += (double)rA;
                 dg.v[1] += (double)rB;
@@ -754,9 +756,11 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
     }
 }
 
-// Per-case reduction of the per-item partials in item order (one warp; deterministic).
+// Per-case reduction of the per-item partials in item order (one warp; deterministic).  c < 0:
+// block b reduces case b.
 __global__ void k_diag_reduce(const DevCase* __restrict__ cases, int c, const double* __restrict__ part,
                               double* __restrict__ out) {
+    if (c < 0) c = blockIdx.x;
     const DevCase C = cases[c];
     const int lane = threadIdx.x;
     double v[kDiagN];
@@ -885,6 +889,17 @@ cudaError_t launch_fields(Ctx& c, int ci, double* rhoA, double* rhoB, double* ux
 
 cudaError_t launch_diag_reduce(Ctx& c, int ci) {
     k_diag_reduce<<<1, 32, 0, c.stream>>>(c.dcases, ci, c.diag_part, c.diag_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_all(Ctx& c) {
+    double* o4[4] = {nullptr, nullptr, nullptr, nullptr};
+    const int n = c.nitems_all - c.nitems;
+    const int grid = n < c.grid_blocks ? n : c.grid_blocks;
+    StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, c.diag_part);
+    cudaError_t e = dispatch(c, a, c.stream, true, grid);
+    if (e != cudaSuccess) return e;
+    k_diag_reduce<<<(unsigned)c.hcases.size(), 32, 0, c.stream>>>(c.dcases, -1, c.diag_part, c.diag_out);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OPEN = 0, 1, 2
 LBM_ADS_ORIGINAL, LBM_ADS_IMPROVED = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16_SHIFTED, LBM_STORE_BF16_SHIFTED = 0, 1, 2, 3
-LBM_SURFACE_FLAT, LBM_SURFACE_CIRCLE = 0, 1
+LBM_SURFACE_FLAT, LBM_SURFACE_CIRCLE, LBM_SURFACE_NONE = 0, 1, 2
 
 STORAGE = {"f64": LBM_STORE_F64, "f32": LBM_STORE_F32, "f16": LBM_STORE_F16_SHIFTED,
            "bf16": LBM_STORE_BF16_SHIFTED}
@@ -31,7 +31,8 @@ BC = {"periodic": LBM_BC_PERIODIC, "wall": LBM_BC_WALL, "open": LBM_BC_OPEN}
 SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_synchronize",
            "lbm_set_densities", "lbm_fields", "lbm_diagnostics", "lbm_contact_angle", "lbm_wall_list",
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
-           "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc")
+           "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc",
+           "lbm_diagnostics_all", "lbm_contact_angle_all")
 
 
 class lbm_grid(ctypes.Structure):
@@ -115,6 +116,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_save.argtypes = [ctx_p, ctypes.c_char_p]
     lib.lbm_load.argtypes = [ctx_p, ctypes.c_char_p]
     lib.lbm_diagnostics_noalloc.argtypes = [c_void_p] * 5 + [c_int32, c_int32, c_void_p, POINTER(lbm_diag)]
+    lib.lbm_diagnostics_all.argtypes = [ctx_p, POINTER(lbm_diag)]
+    lib.lbm_contact_angle_all.argtypes = [ctx_p, POINTER(lbm_surface), c_void_p, c_void_p, c_void_p]
     lib.lbm_status_str.argtypes = [c_int32]
     lib.lbm_status_str.restype = ctypes.c_char_p
     lib.lbm_last_error.argtypes = []
@@ -257,13 +260,40 @@ def lbm_diagnostics_noalloc(rho_A, rho_B, ux, uy, solid, nx: int, ny: int, cuda_
     return d.as_dict()
 
 
-def lbm_contact_angle(ctx, case_index: int, surface: dict):
-    s = lbm_surface()
-    if surface["kind"] == "flat":
+def _fill_surface(s, surface: dict | None) -> None:
+    if surface is None:
+        s.kind, s.normal = LBM_SURFACE_NONE, 1
+    elif surface["kind"] == "flat":
         s.kind, s.normal, s.y_w = LBM_SURFACE_FLAT, int(surface.get("normal", 1)), float(surface["y_w"])
     else:
         s.kind, s.normal = LBM_SURFACE_CIRCLE, 1
         s.cx, s.cy, s.R = float(surface["cx"]), float(surface["cy"]), float(surface["R"])
+
+
+def lbm_diagnostics_all(ctx, ncases: int, allow_unstable: bool = False) -> list:
+    """Diagnostics of every case in one pass (one dict per case)."""
+    d = (lbm_diag * ncases)()
+    st = load_library().lbm_diagnostics_all(ctx, d)
+    if not (allow_unstable and st == LBM_EUNSTABLE):
+        _check(st)
+    return [x.as_dict() for x in d]
+
+
+def lbm_contact_angle_all(ctx, surfaces: list):
+    """Contact angle of every case; a None surface skips its case.  Returns (theta_deg, fit_rms,
+    npoints) as arrays, NaN where a case was skipped or had too few interface points."""
+    n = len(surfaces)
+    s = (lbm_surface * n)()
+    for i, sf in enumerate(surfaces):
+        _fill_surface(s[i], sf)
+    th, rms, npts = np.zeros(n), np.zeros(n), np.zeros(n, np.int64)
+    _check(load_library().lbm_contact_angle_all(ctx, s, th.ctypes.data, rms.ctypes.data, npts.ctypes.data))
+    return th, rms, npts
+
+
+def lbm_contact_angle(ctx, case_index: int, surface: dict):
+    s = lbm_surface()
+    _fill_surface(s, surface)
     th, rms, n = c_double(), c_double(), c_int64()
     _check(load_library().lbm_contact_angle(ctx, case_index, ctypes.byref(s), ctypes.byref(th), ctypes.byref(rms),
                                             ctypes.byref(n)))
@@ -380,6 +410,12 @@ class Lattice:
 
     def contact_angle(self, case: int = 0, surface: dict | None = None):
         return lbm_contact_angle(self.ctx, case, surface or self.scenarios[case].surface)
+
+    def diagnostics_all(self, allow_unstable: bool = False) -> list:
+        return lbm_diagnostics_all(self.ctx, len(self.scenarios), allow_unstable)
+
+    def contact_angle_all(self, surfaces: list | None = None):
+        return lbm_contact_angle_all(self.ctx, surfaces or [sc.surface for sc in self.scenarios])
 
     def info(self) -> dict:
         return lbm_info(self.ctx)

@@ -218,6 +218,41 @@ def test_ensemble_equals_single_cases():
     ens.close()
 
 
+def test_batched_diagnostics_and_contact_angles_equal_per_case_calls():
+    """lbm_diagnostics_all / lbm_contact_angle_all over an uneven ensemble give each case's
+    lbm_diagnostics / lbm_contact_angle result bit for bit; a case without a surface is skipped."""
+    cases = [SCENARIOS["cylinder96"](), SCENARIOS["flat64x48"](), SCENARIOS["porous_open"](),
+             S.cylinder_droplet(77, nx=131, R=12, r=15, lam=1.4)]
+    ens = lbm.Lattice(cases, "f32")
+    ens.step(300)
+    batch = ens.diagnostics_all()
+    surfaces = [sc.surface for sc in cases]
+    surfaces[2] = None
+    th, rms, npts = ens.contact_angle_all(surfaces)
+    for i, sc in enumerate(cases):
+        assert batch[i] == ens.diagnostics(i), i
+        if surfaces[i] is None:
+            assert np.isnan(th[i]) and np.isnan(rms[i]) and npts[i] == 0
+        else:
+            t1, r1, n1 = ens.contact_angle(i)
+            assert (th[i], rms[i], npts[i]) == (t1, r1, n1), i
+    ens.close()
+
+
+def test_batched_diagnostics_match_oracle_f64():
+    cases = [SCENARIOS["cylinder96"](), SCENARIOS["free64"]()]
+    ens = lbm.Lattice(cases, "f64")
+    ens.step(40)
+    batch = ens.diagnostics_all()
+    for i, sc in enumerate(cases):
+        cfg, f = orun(sc, 40)
+        od = oracle.diagnostics(cfg, sc.solid, f)
+        for k in ("mass_A", "mass_B", "rhoA_min", "rhoA_max", "rhoB_min", "rhoB_max", "umax"):
+            assert batch[i][k] == pytest.approx(od[k], rel=1e-10), (i, k)
+        assert batch[i]["n_fluid"] == int((sc.solid == 0).sum())
+    ens.close()
+
+
 def test_checkpoint_roundtrip_is_bit_exact():
     sc = SCENARIOS["cylinder96"]()
     lat = lbm.Lattice(sc, "f32")
