@@ -40,6 +40,7 @@ namespace {
 // Rows of densities kept in shared memory.  Each row is written twice, at ring slot m and m + kRing,
 // so the five consecutive rows a collision reads sit at consecutive slots from one base.
 constexpr int kRing = 6;
+constexpr int kTc = 128;  // threads per block of the step kernel = window columns (ring row length)
 #ifndef LBM_SLOTS
 #define LBM_SLOTS 5
 #endif
@@ -204,63 +205,86 @@ __device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Gr
     g.y[k][4] -= R2;
 }
 
+// Second-layer substitution of Table 1 on top of the bulk gradient.  The row sums give
+// sum_e w e rho(x+e) with rho = 0 at every non-fluid site; a substituted second-layer site x+e
+// (non-fluid) takes rho(x + sign e) instead, i.e. adds w e rho(x + sign e).  Grouped by the
+// first-layer partner p = sign e: an axis partner has one second-layer site (2 e_p), a diagonal
+// partner three (2 e_p and the two knight moves), so the correction is sum_p c_p rho(x + e_p) with
+// c_p built from the substitution bits (bit n-1 for stencil node n: 2 e_p is n = p + 8, the
+// knights are n = p + 12 and n = p + 16).
+template <class R>
+struct SubCoef {
+    R x[8], y[8];
+};
+
+template <class R>
+__device__ __forceinline__ void substitution_coefficients(uint32_t sub, SubCoef<R>& c) {
+#pragma unroll
+    for (int p = 1; p <= 8; ++p) {
+        const R ex = (R)cx(p), ey = (R)cy(p);
+        const bool b1 = (sub >> (p + 7)) & 1u;
+        if (p <= 4) {
+            const R w = (R)(2.0 * w8(4));
+            c.x[p - 1] = b1 ? w * ex : (R)0;
+            c.y[p - 1] = b1 ? w * ey : (R)0;
+        } else {
+            const bool b2 = (sub >> (p + 11)) & 1u, b3 = (sub >> (p + 15)) & 1u;
+            const R wd = (R)(2.0 * w8(8)), wk = (R)w8(5);
+            const R a = b1 ? wd : (R)0, kx = b2 ? wk : (R)0, ky = b3 ? wk : (R)0;
+            // 2 e_p w8(8) + (2 ex, ey) w8(5) + (ex, 2 ey) w8(5)
+            c.x[p - 1] = ex * (a + (R)2 * kx + ky);
+            c.y[p - 1] = ey * (a + kx + (R)2 * ky);
+        }
+    }
+}
+
 template <class R>
 struct Grad4 {
     R ax, ay, bx, by;
 };
 
-// Explicit 24-node gradient of a wall-list node with the second-layer substitution of Table 1:
-// a second-layer site whose bit is set in `sub` reads its first-layer partner x + sign(e).  Kept out
-// of line: only wall-list nodes run it, and the hot loop stays small.
+// Gradient correction of a wall-list node (ring slots from sb0 = row y-2 at this column), kept out
+// of line so that only warps holding wall-list nodes carry it.  open_edge: the node lies within two
+// columns of an open boundary, where the ring holds clamped densities beyond the edge.
+#ifndef LBM_WALL_INLINE
+#define LBM_WALL_INLINE 0
+#endif
+#if LBM_WALL_INLINE
+#define LBM_WALL_FN __forceinline__
+#else
+#define LBM_WALL_FN __noinline__
+#endif
 template <class R>
-__device__ __noinline__ Grad4<R> wall_gradient(const R* __restrict__ ringA, const R* __restrict__ ringB, int sb0,
-                                               int sb1, int sb2, int sb3, int sb4, uint32_t sub) {
-    const int sb[5] = {sb0, sb1, sb2, sb3, sb4};
-    R gAx, gAy, gBx, gBy;
-    R vA[5][5], vB[5][5];
+__device__ LBM_WALL_FN Grad4<R> substitution_correction(const R* __restrict__ ringA, const R* __restrict__ ringB,
+                                                        int sb0, uint32_t sub, bool open_edge) {
+    SubCoef<R> sc;
+    substitution_coefficients<R>(sub, sc);
+    Grad4<R> g{(R)0, (R)0, (R)0, (R)0};
 #pragma unroll
-    for (int dy = -2; dy <= 2; ++dy) {
+    for (int p = 1; p <= 8; ++p) {
+        const int o = sb0 + (cy(p) + 2) * kTc + cx(p);
+        const R nA = ringA[o], nB = ringB[o];
+        g.ax += sc.x[p - 1] * nA;
+        g.ay += sc.y[p - 1] * nA;
+        g.bx += sc.x[p - 1] * nB;
+        g.by += sc.y[p - 1] * nB;
+    }
+    if (open_edge) {
+        // beyond an open column a second-layer site is not fluid, but the ring holds the clamped
+        // boundary-column density there: take it out again
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            int addr = sb[dy + 2] + dx;
-            if (dx == 2 || dx == -2 || dy == 2 || dy == -2) {
-                const int sx = (dx > 0) - (dx < 0), sy = (dy > 0) - (dy < 0);
-                int n;  // Table 1 number of (dx, dy), minus one
-                if (dx == 2 * sx && dy == 2 * sy) {
-                    const int m = (sx == 1 && sy == 0) ? 1 : (sx == 0 && sy == 1) ? 2 : (sx == -1 && sy == 0) ? 3
-                                : (sx == 0 && sy == -1) ? 4 : (sx == 1 && sy == 1) ? 5 : (sx == -1 && sy == 1) ? 6
-                                : (sx == -1 && sy == -1) ? 7 : 8;
-                    n = m + 7;
-                } else {
-                    const int m = (sx == 1 && sy == 1) ? 5 : (sx == -1 && sy == 1) ? 6 : (sx == -1 && sy == -1) ? 7 : 8;
-                    n = (dx == 2 || dx == -2) ? m + 11 : m + 15;
-                }
-                const int alt = sb[sy + 2] + sx;
-                addr = ((sub >> n) & 1u) ? alt : addr;
+        for (int n = 8; n < 24; ++n) {
+            if ((sub >> n) & 1u) {
+                const int o = sb0 + (s24y(n) + 2) * kTc + s24x(n);
+                const R w = (R)w8(s24x(n) * s24x(n) + s24y(n) * s24y(n));
+                g.ax -= w * (R)s24x(n) * ringA[o];
+                g.ay -= w * (R)s24y(n) * ringA[o];
+                g.bx -= w * (R)s24x(n) * ringB[o];
+                g.by -= w * (R)s24y(n) * ringB[o];
             }
-            vA[dy + 2][dx + 2] = ringA[addr];
-            vB[dy + 2][dx + 2] = ringB[addr];
         }
     }
-    gAx = gAy = gBx = gBy = (R)0;
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-        for (int dx = 1; dx <= 2; ++dx) {
-            const R w = (R)(w8(dx * dx + dy * dy) * dx);
-            gAx += w * (vA[dy + 2][2 + dx] - vA[dy + 2][2 - dx]);
-            gBx += w * (vB[dy + 2][2 + dx] - vB[dy + 2][2 - dx]);
-        }
-#pragma unroll
-    for (int dx = -2; dx <= 2; ++dx)
-#pragma unroll
-        for (int dy = 1; dy <= 2; ++dy) {
-            const R w = (R)(w8(dx * dx + dy * dy) * dy);
-            gAy += w * (vA[2 + dy][dx + 2] - vA[2 - dy][dx + 2]);
-            gBy += w * (vB[2 + dy][dx + 2] - vB[2 - dy][dx + 2]);
-        }
-    return Grad4<R>{gAx, gAy, gBx, gBy};
+    return g;
 }
 
 // SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e):
@@ -328,7 +352,7 @@ struct StepArgs {
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
-constexpr int kT = 128;  // threads per block = columns per window (interior kT - 8)
+constexpr int kT = kTc;  // threads per block = columns per window (interior kT - 8)
 
 template <class S, class R, bool kFields>
 __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_step(StepArgs a) {
@@ -473,11 +497,12 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
             const bool wall = (st.fl & kWallBit) != 0;
             if (wall) {
-                const Grad4<R> w4 = wall_gradient<R>(ringA, ringB, sb0, sb0 + T, sb0 + 2 * T, sb0 + 3 * T, sb0 + 4 * T, st.sub);
-                gAx = w4.ax;
-                gAy = w4.ay;
-                gBx = w4.bx;
-                gBy = w4.by;
+                const Grad4<R> c4 = substitution_correction<R>(ringA, ringB, sb0, st.sub,
+                                                               P.bc_x == kOpen && (X < 2 || X >= P.nx - 2));
+                gAx += c4.ax;
+                gAy += c4.ay;
+                gBx += c4.bx;
+                gBy += c4.by;
             }
             // cohesion: each component is pushed by the other's pseudopotential gradient (Eq. 8)
             R FAx = -P.G * rA * gBx, FAy = -P.G * rA * gBy;
