@@ -217,11 +217,14 @@ lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t case_index, const lbm_surface
  * is written; the message names the first such case). */
 lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out);
 
-/* Contact angle of every case (the measurement of lbm_contact_angle over an ensemble), enqueued case
- * after case with one synchronisation at the end.  surfaces: host, one per case; kind
- * LBM_SURFACE_NONE skips a case.  Host outputs, one per case, each may be NULL: theta_deg and
- * fit_rms (NaN for a skipped case or one with fewer than 8 interface points), npoints (0 when
- * skipped).  LBM_EINVAL for a bad surface, before any work. */
+/* Contact angle of every case (the measurement of lbm_contact_angle over an ensemble): one density
+ * pass over all cases, then each fit pass as one launch over all cases, one synchronisation at the
+ * end.  Per-case partial sums are formed and combined as in lbm_contact_angle, so each angle equals
+ * the single-case result bit for bit.  surfaces: host, one per case; kind LBM_SURFACE_NONE skips a
+ * case.  Host outputs, one per case, each may be NULL: theta_deg and fit_rms (NaN for a skipped case
+ * or one with fewer than 8 interface points), npoints (0 when skipped).  The first call allocates
+ * 16 bytes per lattice node of all cases (FP64 densities) plus small tables, held until
+ * lbm_destroy (LBM_ENOMEM when that fails).  LBM_EINVAL for a bad surface, before any work. */
 lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, double* theta_deg,
                                  double* fit_rms, int64_t* npoints);
 

@@ -317,7 +317,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.tmaps, c.err, c.sched, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -722,19 +722,25 @@ lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, doub
             return fail(LBM_EINVAL, "case %d: bad surface kind", i);
         if (s.kind == LBM_SURFACE_CIRCLE && !(s.R > 0)) return fail(LBM_EINVAL, "case %d: surface radius must be > 0", i);
     }
-    int last = -1;
-    for (int i = 0; i < n; ++i) {
-        if (surfaces[i].kind == LBM_SURFACE_NONE) continue;
-        c.fields_case = -1;
-        CUDA_TRY(launch_fields(c, i, nullptr, nullptr, nullptr, nullptr, false));
-        CUDA_TRY(enqueue_contact_angle(c, i, surfaces[i], c.ca_all + (size_t)16 * i));
-        last = i;
+    bool any = false;
+    for (int i = 0; i < n; ++i) any = any || surfaces[i].kind != LBM_SURFACE_NONE;
+    std::vector<double> h((size_t)16 * n, 0.0);
+    if (!any) {
+        for (int i = 0; i < n; ++i) {
+            if (theta_deg) theta_deg[i] = NAN;
+            if (fit_rms) fit_rms[i] = NAN;
+            if (npoints) npoints[i] = 0;
+        }
+        return LBM_OK;
     }
-    if (last >= 0) {  // the scratch fields hold the last case measured
-        c.fields_case = last;
-        c.fields_version = c.version;
+    {
+        const cudaError_t e = enqueue_contact_angle_all(c, surfaces);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();  // clear the (non-sticky) allocation error
+            return fail(LBM_ENOMEM, "batched contact angle: out of device memory for the densities of all cases");
+        }
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "batched contact angle: %s", cudaGetErrorString(e));
     }
-    std::vector<double> h((size_t)16 * n);
     CUDA_TRY(cudaMemcpyAsync(h.data(), c.ca_all, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     for (int i = 0; i < n; ++i) {

@@ -12,6 +12,8 @@
 // block order, so results do not depend on scheduling.
 #include <math.h>
 
+#include <vector>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -19,8 +21,16 @@ namespace lbm {
 namespace {
 
 constexpr int kCaThreads = 256;
-constexpr int kCaBlocks = 256;
+constexpr int kCaBlocks = 256;             // most blocks per case
+constexpr int kCaNodesPerBlock = 4096;
 constexpr int kCaVals = 9;
+
+// blocks of one case's passes: one per 4,096 nodes, 1..256 (the same in the single-case and the
+// batched call, so both sum the same partial records in the same order)
+int ca_blocks(long long n) {
+    const long long b = (n + kCaNodesPerBlock - 1) / kCaNodesPerBlock;
+    return (int)(b < 1 ? 1 : (b > kCaBlocks ? kCaBlocks : b));
+}
 
 struct CaGeo {
     int nx, ny;
@@ -64,12 +74,15 @@ __device__ int node_points(const CaGeo& g, int X, int Y, double* px, double* py)
 }
 
 // st: 0 N, 1 xm, 2 ym, 3 cx, 4 cy, 5 r, 6 rms, 7 theta, 8 status (0 ok, 1 too few points)
-__global__ void k_ca_pass(CaGeo g, int pass, const double* __restrict__ st, double* __restrict__ part) {
+// Block lb of nb of one case: nodes lb * threads + tid, strided by nb * threads; its partial record
+// goes to out[0 .. kCaVals).
+__device__ void ca_pass_block(const CaGeo& g, int lb, int nb, int pass, const double* __restrict__ st,
+                              double* __restrict__ out) {
     double acc[kCaVals];
     for (int q = 0; q < kCaVals; ++q) acc[q] = 0.0;
     const long long N = (long long)g.nx * g.ny;
     const double xm = st[1], ym = st[2], cxv = st[3], cyv = st[4], r = st[5];
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+    for (long long s = lb * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)nb * blockDim.x) {
         const int X = (int)(s % g.nx), Y = (int)(s / g.nx);
         double px[2], py[2];
         const int n = node_points(g, X, Y, px, py);
@@ -120,8 +133,30 @@ __global__ void k_ca_pass(CaGeo g, int pass, const double* __restrict__ st, doub
         for (int q = 0; q < kCaVals; ++q) {
             double v = 0.0;
             for (int w = 0; w < kCaThreads / 32; ++w) v += red[w][q];
-            part[blockIdx.x * kCaVals + q] = v;
+            out[q] = v;
         }
+}
+
+__global__ void k_ca_pass(CaGeo g, int pass, const double* __restrict__ st, double* __restrict__ part) {
+    ca_pass_block(g, blockIdx.x, gridDim.x, pass, st, part + (long long)blockIdx.x * kCaVals);
+}
+
+// Batched passes: block b belongs to case blk_case[b], whose blocks are [blk0[case], blk0[case+1]).
+struct CaBatch {
+    const CaGeo* geo;          // per case
+    const int* blk_case;       // per block
+    const int* blk0;           // per case + 1
+    const lbm_surface* surf;   // per case
+    double* st;                // per case: 16-double status record
+    double* part;              // per block: kCaVals partial sums
+};
+
+__global__ void k_ca_pass_all(CaBatch b, int pass) {
+    const int ci = b.blk_case[blockIdx.x];
+    if (b.surf[ci].kind == LBM_SURFACE_NONE) return;  // skipped: its partials are never read
+    const int b0 = b.blk0[ci];
+    ca_pass_block(b.geo[ci], blockIdx.x - b0, b.blk0[ci + 1] - b0, pass, b.st + 16 * (long long)ci,
+                  b.part + (long long)blockIdx.x * kCaVals);
 }
 
 // Sum of the per-block partial records by one warp: lane l adds blocks l, l+32, ... in order, then
@@ -163,8 +198,8 @@ __device__ void solve3(double A[3][3], double b[3], double x[3]) {
     }
 }
 
-__global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
-                           lbm_surface surf) {
+__device__ void ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
+                         const lbm_surface& surf) {
     double S[kCaVals];
     sum_parts(part, nblocks, S);  // the whole warp
     if (threadIdx.x != 0) return;
@@ -208,6 +243,20 @@ __global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ par
     }
 }
 
+__global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
+                           lbm_surface surf) {
+    ca_solve(pass, nblocks, part, st, surf);
+}
+
+// one warp per case
+__global__ void k_ca_solve_all(CaBatch b, int pass) {
+    const int ci = blockIdx.x;
+    const lbm_surface surf = b.surf[ci];
+    if (surf.kind == LBM_SURFACE_NONE) return;
+    const int b0 = b.blk0[ci];
+    ca_solve(pass, b.blk0[ci + 1] - b0, b.part + (long long)b0 * kCaVals, b.st + 16 * (long long)ci, surf);
+}
+
 }  // namespace
 
 // ctx->fields must already hold rho_A, rho_B of the case (dense).  host_out4 <- theta, rms, npoints,
@@ -217,11 +266,63 @@ cudaError_t enqueue_contact_angle(Ctx& c, int ci, const lbm_surface& surf, doubl
     const long long N = (long long)C.nx * C.ny;
     CaGeo g{C.nx, C.ny, c.flags + C.d_off, c.fields, c.fields + N};
     double* part = c.ca_work + 16;
+    const int nb = ca_blocks(N);
     cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < 4; ++pass) {
-        k_ca_pass<<<kCaBlocks, kCaThreads, 0, c.stream>>>(g, pass, st, part);
-        k_ca_solve<<<1, 32, 0, c.stream>>>(pass, kCaBlocks, part, st, surf);
+        k_ca_pass<<<nb, kCaThreads, 0, c.stream>>>(g, pass, st, part);
+        k_ca_solve<<<1, 32, 0, c.stream>>>(pass, nb, part, st, surf);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_contact_angle_all(Ctx& c, const lbm_surface* surf) {
+    const int n = (int)c.hcases.size();
+    // block tables
+    std::vector<int> blk0(n + 1), blk_case;
+    for (int i = 0; i < n; ++i) {
+        blk0[i] = (int)blk_case.size();
+        const int nb = ca_blocks((long long)c.hcases[i].nx * c.hcases[i].ny);
+        blk_case.insert(blk_case.end(), nb, i);
+    }
+    blk0[n] = (int)blk_case.size();
+    const int nblk = blk0[n];
+    // one allocation: densities [2][dense_elems], geometry, tables, partials, surfaces
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_rho = 0, o_geo = al(2 * (size_t)c.dense_elems * sizeof(double));
+    const size_t o_bc = o_geo + al(n * sizeof(CaGeo)), o_b0 = o_bc + al(nblk * sizeof(int));
+    const size_t o_part = o_b0 + al((n + 1) * sizeof(int)), o_surf = o_part + al((size_t)nblk * kCaVals * sizeof(double));
+    const size_t total = o_surf + al(n * sizeof(lbm_surface));
+    cudaError_t e;
+    if (!c.ca_batch) {
+        e = cudaMalloc(&c.ca_batch, total);
+        if (e != cudaSuccess) return e;
+        c.ca_batch_bytes = total;
+        c.device_bytes += (long long)total;
+        double* rho = reinterpret_cast<double*>(c.ca_batch + o_rho);
+        std::vector<CaGeo> geo(n);
+        for (int i = 0; i < n; ++i) {
+            const DevCase& d = c.hcases[i];
+            geo[i] = CaGeo{d.nx, d.ny, c.flags + d.d_off, rho + d.d_off, rho + c.dense_elems + d.d_off};
+        }
+        e = cudaMemcpy(c.ca_batch + o_geo, geo.data(), n * sizeof(CaGeo), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c.ca_batch + o_bc, blk_case.data(), nblk * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c.ca_batch + o_b0, blk0.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemcpyAsync(c.ca_batch + o_surf, surf, n * sizeof(lbm_surface), cudaMemcpyHostToDevice, c.stream);
+    if (e != cudaSuccess) return e;
+    double* rho = reinterpret_cast<double*>(c.ca_batch + o_rho);
+    e = launch_densities_all(c, rho, rho + c.dense_elems);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.ca_all, 0, (size_t)16 * n * sizeof(double), c.stream);
+    if (e != cudaSuccess) return e;
+    CaBatch b{reinterpret_cast<const CaGeo*>(c.ca_batch + o_geo), reinterpret_cast<const int*>(c.ca_batch + o_bc),
+              reinterpret_cast<const int*>(c.ca_batch + o_b0), reinterpret_cast<const lbm_surface*>(c.ca_batch + o_surf),
+              c.ca_all, reinterpret_cast<double*>(c.ca_batch + o_part)};
+    for (int pass = 0; pass < 4; ++pass) {
+        k_ca_pass_all<<<nblk, kCaThreads, 0, c.stream>>>(b, pass);
+        k_ca_solve_all<<<n, 32, 0, c.stream>>>(b, pass);
     }
     return cudaGetLastError();
 }

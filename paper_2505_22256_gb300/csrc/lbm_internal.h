@@ -72,6 +72,8 @@ struct Ctx {
     double* diag_out = nullptr;      // [ncases][kDiagN]
     double* ca_work = nullptr;       // contact-angle reductions
     double* ca_all = nullptr;        // [ncases][16] contact-angle status records of the batched call
+    unsigned char* ca_batch = nullptr;  // batched contact angle: densities of all cases, block tables,
+    size_t ca_batch_bytes = 0;          // partial sums, surfaces (allocated by its first call)
     int ca_cap = 0;
 
     // CUDA graph of kGraphSteps step launches
@@ -92,6 +94,8 @@ cudaError_t launch_fields(Ctx& c, int case_index, double* rhoA, double* rhoB, do
 cudaError_t launch_diag_reduce(Ctx& c, int case_index);
 // partial sums of every case in one launch over the per-case lists, then one reduction per case
 cudaError_t launch_diag_all(Ctx& c);
+// densities of every case into [dense_elems] arrays indexed d_off + y nx + x (zero at solid nodes)
+cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all);
 cudaError_t launch_set_state(Ctx& c, int case_index, const double* dense_f);
 cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);
 cudaError_t launch_feq_rest(Ctx& c, int case_index, const double* rhoA, const double* rhoB, double* dense_f);
@@ -113,5 +117,10 @@ cudaError_t launch_contact_angle(Ctx& c, int case_index, const lbm_surface& surf
 // 16-double status record st (device) receives theta at [7], rms at [6], points at [0], the
 // too-few-points flag at [8].  No synchronisation.
 cudaError_t enqueue_contact_angle(Ctx& c, int case_index, const lbm_surface& surf, double* st);
+// Contact angles of every case: densities of all cases, then each fit pass as one launch over all
+// cases' blocks (per-case block counts as in the single-case call, so results agree bit for bit).
+// surf: host, one per case (LBM_SURFACE_NONE skips).  Records land in ctx->ca_all; no
+// synchronisation.
+cudaError_t enqueue_contact_angle_all(Ctx& c, const lbm_surface* surf);
 
 }  // namespace lbm

@@ -349,6 +349,7 @@ struct StepArgs {
     long long dense_total;
     int* err;
     int* sched;                // [0] next work item, [1] blocks finished; both back to 0 at exit
+    int fields_global;         // fields mode: outputs indexed over all cases (d_off + y nx + x)
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
@@ -483,11 +484,13 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             if (!interior || (st.fl & kSolidBit)) {
                 if constexpr (kFields) {
                     if (interior && a.o_rA) {
-                        const long long o = (long long)y * P.nx + x;
+                        const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
                         a.o_rA[o] = 0.0;
                         a.o_rB[o] = 0.0;
-                        a.o_ux[o] = 0.0;
-                        a.o_uy[o] = 0.0;
+                        if (a.o_ux) {
+                            a.o_ux[o] = 0.0;
+                            a.o_uy[o] = 0.0;
+                        }
                     }
                 }
                 return;
@@ -540,11 +543,13 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
             if constexpr (kFields) {
                 if (a.o_rA) {  // null outputs: partial sums only
-                    const long long o = (long long)y * P.nx + x;
+                    const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
                     a.o_rA[o] = (double)rA;
                     a.o_rB[o] = (double)rB;
-                    a.o_ux[o] = (double)ux;
-                    a.o_uy[o] = (double)uy;
+                    if (a.o_ux) {  // null velocity outputs: densities only
+                        a.o_ux[o] = (double)ux;
+                        a.o_uy[o] = (double)uy;
+                    }
                 }
                 const double dux = ux, duy = uy, drho = (double)rho;
                 dg.v[0] += (double)rA;
@@ -840,6 +845,7 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
     a.dense_total = c.dense_elems;
     a.err = c.err;
     a.sched = c.sched;
+    a.fields_global = 0;
     a.o_rA = o4[0];
     a.o_rB = o4[1];
     a.o_ux = o4[2];
@@ -915,6 +921,15 @@ cudaError_t launch_fields(Ctx& c, int ci, double* rhoA, double* rhoB, double* ux
 cudaError_t launch_diag_reduce(Ctx& c, int ci) {
     k_diag_reduce<<<1, 32, 0, c.stream>>>(c.dcases, ci, c.diag_part, c.diag_out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
+    double* o4[4] = {rhoA_all, rhoB_all, nullptr, nullptr};
+    const int n = c.nitems_all - c.nitems;
+    const int grid = n < c.grid_blocks ? n : c.grid_blocks;
+    StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, c.diag_part);
+    a.fields_global = 1;
+    return dispatch(c, a, c.stream, true, grid);
 }
 
 cudaError_t launch_diag_all(Ctx& c) {
