@@ -138,6 +138,8 @@ typedef struct {
     int32_t block_rows;      /* rows per work item (guided list: rows of its long items) */
     int32_t grid_blocks;     /* blocks per launch */
     int32_t work_items;      /* work items per step */
+    int32_t wall_inline;     /* 1: the wall-list correction is inlined in the step kernel, 0: called */
+    int32_t pad_;
 } lbm_info_t;
 
 /* ---------------------------------------------------------------------------------------------
@@ -260,6 +262,13 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * chosen to balance the list over the resident blocks.  Rebuilds the work list and drops the
  * captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
+
+/* Choose the step kernel's form for wall-list nodes (the second-layer correction of Table 1): 1
+ * inlines it (faster where wall-list nodes are common, e.g. porous media), 0 calls an out-of-line
+ * copy (keeps the loop of warps without wall-list nodes small).  lbm_create picks 1 when wall-list
+ * nodes exceed 4 % of the fluid nodes; lbm_autotune tries both.  Results agree to FP rounding.
+ * Drops the captured graph.  LBM_EINVAL for other values. */
+lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction);
 
 /* Time candidate launch shapes on the live state (each for `steps` steps, after one warm-up
  * launch) and keep the fastest.  The state advances by the steps taken; best_ms (may be NULL)

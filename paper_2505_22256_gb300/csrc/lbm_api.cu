@@ -462,9 +462,15 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         if (p) cudaFree(p);
     if (st != LBM_OK) return bail(st);
 
-    // work list and launch shape
+    // work list and launch shape; the wall-list correction is inlined where wall-list nodes are
+    // common (more than 4 % of the fluid nodes), called out of line otherwise
     c.block_threads = 128;
     c.block_rows = 0;
+    {
+        long long fl = 0;
+        for (const HostCase& h : c.cases) fl += h.nfluid;
+        c.wall_inline = (double)c.nwall > 0.04 * (double)fl ? 1 : 0;
+    }
     st = build_items(c);
     if (st != LBM_OK) return bail(st);
 
@@ -815,6 +821,8 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
     out->block_rows = c.rows_used;
     out->grid_blocks = c.grid_blocks;
     out->work_items = c.nitems;
+    out->wall_inline = c.wall_inline;
+    out->pad_ = 0;
     return LBM_OK;
 }
 
@@ -829,6 +837,14 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     return build_items(c);
 }
 
+lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (inline_correction != 0 && inline_correction != 1) return fail(LBM_EINVAL, "inline_correction must be 0 or 1");
+    ctx->c.wall_inline = inline_correction;
+    drop_graphs(ctx->c);
+    return LBM_OK;
+}
+
 lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
@@ -839,9 +855,11 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     double best = 1e300;
-    int bt = c.block_threads, br = c.block_rows;
+    int bt = c.block_threads, br = c.block_rows, bw = c.wall_inline;
+    for (int w = 0; w < 2; ++w)
     for (int t : cand_t)
         for (int r : cand_r) {
+            c.wall_inline = w;
             lbm_status s = lbm_set_launch(ctx, t, r);
             if (s != LBM_OK) continue;
             if (launch_step(c, c.cur, c.stream) != cudaSuccess) continue;
@@ -863,11 +881,13 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
                 best = ms / steps;
                 bt = t;
                 br = r;
+                bw = w;
             }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CUDA_TRY(cudaGetLastError());
+    c.wall_inline = bw;
     lbm_status s = lbm_set_launch(ctx, bt, br);
     if (s != LBM_OK) return s;
     if (best_ms) *best_ms = best;

@@ -58,6 +58,7 @@ struct Ctx {
     // work list of the step kernel
     int block_threads = 128;
     int block_rows = 0;              // 0: automatic
+    int wall_inline = 0;             // step kernel variant: wall-list correction inline (1) or called (0)
     int rows_used = 0;
     int grid_blocks = 0;
     int4* items = nullptr;

@@ -86,7 +86,7 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v)
 template <bool kGeneral, class S, class R>
 __device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restrict__ r0, const S* __restrict__ rp,
                                      long long ps, int c, uint16_t fl, bool inlet, bool outlet, const Params<R>& P,
-                                     R (&f)[18]) {
+                                     const Params<R>& Pin, R (&f)[18]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const S* src;
@@ -118,9 +118,9 @@ __device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restri
     if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in, 0))
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            f[9 * k + 1] = f[9 * k + 3] + P.d1[k];
-            f[9 * k + 5] = f[9 * k + 7] + P.d5[k];
-            f[9 * k + 8] = f[9 * k + 6] + P.d5[k];
+            f[9 * k + 1] = f[9 * k + 3] + Pin.d1[k];
+            f[9 * k + 5] = f[9 * k + 7] + Pin.d5[k];
+            f[9 * k + 8] = f[9 * k + 6] + Pin.d5[k];
         }
     }
 }
@@ -243,20 +243,13 @@ struct Grad4 {
     R ax, ay, bx, by;
 };
 
-// Gradient correction of a wall-list node (ring slots from sb0 = row y-2 at this column), kept out
-// of line so that only warps holding wall-list nodes carry it.  open_edge: the node lies within two
-// columns of an open boundary, where the ring holds clamped densities beyond the edge.
-#ifndef LBM_WALL_INLINE
-#define LBM_WALL_INLINE 0
-#endif
-#if LBM_WALL_INLINE
-#define LBM_WALL_FN __forceinline__
-#else
-#define LBM_WALL_FN __noinline__
-#endif
+// Gradient correction of a wall-list node (ring slots from sb0 = row y-2 at this column).
+// open_edge: the node lies within two columns of an open boundary, where the ring holds clamped
+// densities beyond the edge.  The step kernel inlines it where wall-list nodes are common and calls
+// the out-of-line copy otherwise, so that warps without wall-list nodes keep a small loop.
 template <class R>
-__device__ LBM_WALL_FN Grad4<R> substitution_correction(const R* __restrict__ ringA, const R* __restrict__ ringB,
-                                                        int sb0, uint32_t sub, bool open_edge) {
+__device__ __forceinline__ Grad4<R> substitution_correction(const R* __restrict__ ringA, const R* __restrict__ ringB,
+                                                            int sb0, uint32_t sub, bool open_edge) {
     SubCoef<R> sc;
     substitution_coefficients<R>(sub, sc);
     Grad4<R> g{(R)0, (R)0, (R)0, (R)0};
@@ -287,33 +280,37 @@ __device__ LBM_WALL_FN Grad4<R> substitution_correction(const R* __restrict__ ri
     return g;
 }
 
-// SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e):
-// f*_+- = (1 - w) f_+- + [w sym(f^eq) + c sym(F)] +- [w anti(f^eq) + c anti(F)], with
-// sym / anti the parts of f^eq and F_i that are even / odd in e.
+template <class R>
+__device__ __noinline__ Grad4<R> substitution_correction_call(const R* __restrict__ ringA, const R* __restrict__ ringB,
+                                                              int sb0, uint32_t sub, bool open_edge) {
+    return substitution_correction<R>(ringA, ringB, sb0, sub, open_edge);
+}
+
+// SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e).
+// With a = e.u, b = e.F, c_s^2 = 1/3:
+//   f^eq_i = w rho (1 + 3a + 4.5a^2 - 1.5u^2),   F_i = w (3b - 3 u.F + 9ab)   (Guo's term, Eq. 7)
+// and f*_i = (1 - om) f_i + om f^eq_i + cF F_i splits into the part even in e,
+//   w [C0 + 4.5 a (om rho a + 2 cF b)],   C0 = om rho (1 - 1.5u^2) - 3 cF u.F,
+// and the odd part 3 w (om rho a + cF b).  With P = om rho a + cF b:
+//   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,   f*_0 = (1 - om) f_0 + w_0 C0.
 template <class R>
 __device__ __forceinline__ void collide_comp(const R* f, int k, R rho, R ux, R uy, R Fx, R Fy, R om, R cf,
                                              R (&out)[18]) {
     const R om1 = (R)1 - om;
-    const R A0 = rho * ((R)1 - (R)1.5 * (ux * ux + uy * uy));
-    const R uF = ux * Fx + uy * Fy;
-    out[9 * k] = om1 * f[9 * k] + (R)(4.0 / 9.0) * (om * A0 - cf * (R)3 * uF);
+    const R wr = om * rho;
+    const R C0 = wr * ((R)1 - (R)1.5 * (ux * ux + uy * uy)) - (R)3 * cf * (ux * Fx + uy * Fy);
+    out[9 * k] = om1 * f[9 * k] + (R)(4.0 / 9.0) * C0;
+    const R s1 = (R)(1.0 / 9.0) * C0, s5 = (R)(1.0 / 36.0) * C0;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {  // axis pairs (1,3) and (2,4)
-        const R av = p == 0 ? ux : uy, bv = p == 0 ? Fx : Fy;
-        const R ra = rho * av;
-        const R sym = om * (R)(1.0 / 9.0) * (A0 + (R)4.5 * ra * av) + cf * (av * bv - uF * (R)(1.0 / 3.0));
-        const R anti = (om * ra + cf * bv) * (R)(1.0 / 3.0);
-        const int ip = 1 + p, im = 3 + p;
-        out[9 * k + ip] = om1 * f[9 * k + ip] + (sym + anti);
-        out[9 * k + im] = om1 * f[9 * k + im] + (sym - anti);
-    }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {  // diagonal pairs (5,7): e = (1,1);  (6,8): e = (-1,1)
-        const R av = p == 0 ? ux + uy : uy - ux, bv = p == 0 ? Fx + Fy : Fy - Fx;
-        const R ra = rho * av;
-        const R sym = om * (R)(1.0 / 36.0) * (A0 + (R)4.5 * ra * av) + cf * (av * bv * (R)0.25 - uF * (R)(1.0 / 12.0));
-        const R anti = (om * ra + cf * bv) * (R)(1.0 / 12.0);
-        const int ip = 5 + p, im = 7 + p;
+    for (int p = 0; p < 4; ++p) {  // pairs (1,3): e = (1,0); (2,4): (0,1); (5,7): (1,1); (6,8): (-1,1)
+        const R a = p == 0 ? ux : p == 1 ? uy : p == 2 ? ux + uy : uy - ux;
+        const R b = p == 0 ? Fx : p == 1 ? Fy : p == 2 ? Fx + Fy : Fy - Fx;
+        const double w = p < 2 ? 1.0 / 9.0 : 1.0 / 36.0;
+        const R cb = cf * b;
+        const R P = wr * a + cb;
+        const R sym = (p < 2 ? s1 : s5) + (R)(4.5 * w) * (a * (P + cb));
+        const R anti = (R)(3.0 * w) * P;
+        const int ip = p < 2 ? 1 + p : 3 + p, im = p < 2 ? 3 + p : 5 + p;
         out[9 * k + ip] = om1 * f[9 * k + ip] + (sym + anti);
         out[9 * k + im] = om1 * f[9 * k + im] + (sym - anti);
     }
@@ -355,7 +352,7 @@ struct StepArgs {
 
 constexpr int kT = kTc;  // threads per block = columns per window (interior kT - 8)
 
-template <class S, class R, bool kFields>
+template <class S, class R, bool kFields, bool kWallInline>
 __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_step(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int T = kT, Wi = T - 8;
@@ -385,9 +382,17 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
     uint32_t issue_par = 0, wait_par = 0;
     bool failed = false;
 
-    // Work items are claimed from a counter, so blocks that share a busy SM take fewer of them.
+    // Work items are claimed from a counter, so blocks that share a busy SM take fewer of them.  The
+    // claiming thread also copies the item's case parameters to shared memory: the rarely used ones
+    // (adhesion, inlet) are read from there where needed instead of occupying registers.
     __shared__ int s_claim;
-    if (t == 0) s_claim = atomicAdd(a.sched, 1);
+    __shared__ Params<R> s_par;
+    auto claim = [&]() {
+        const int k = atomicAdd(a.sched, 1);
+        s_claim = k;
+        if (a.item_begin + k < a.item_end) s_par = load_params<R>(a.cases[a.items[a.item_begin + k].x & 0x7FFFFFFF]);
+    };
+    if (t == 0) claim();
     __syncthreads();
     int it = a.item_begin + s_claim;
     while (it < a.item_end) {
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
         const int ci = item.x & 0x7FFFFFFF;       // case
         const int dir = item.x < 0 ? -1 : 1;      // marching direction (neighbouring chunks alternate)
         const DevCase& C = a.cases[ci];
-        const Params<R> P = load_params<R>(C);
+        const Params<R> P = s_par;
         const int xs = item.y, y0 = item.z, y1 = item.w;
         const CUtensorMap* lmap = a.tmaps + 3 * ci + a.in_buf;
         const CUtensorMap* fmap = a.tmaps + 3 * ci + 2;
@@ -457,8 +462,8 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 const S* rm = reinterpret_cast<const S*>(slot_back(dir > 0 ? 2 : 0));
                 const S* r0 = reinterpret_cast<const S*>(s0);
                 const S* rp = reinterpret_cast<const S*>(slot_back(dir > 0 ? 0 : 2));
-                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
-                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, st.f);
+                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, st.f);
+                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, st.f);
                 // rho_k = sum_i f_i as a balanced tree (short dependency chains)
                 const R* f = st.f;
                 ra = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + (f[7] + f[8])));
@@ -500,8 +505,10 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
             const bool wall = (st.fl & kWallBit) != 0;
             if (wall) {
-                const Grad4<R> c4 = substitution_correction<R>(ringA, ringB, sb0, st.sub,
-                                                               P.bc_x == kOpen && (X < 2 || X >= P.nx - 2));
+                const bool open_edge = P.bc_x == kOpen && (X < 2 || X >= P.nx - 2);
+                Grad4<R> c4;
+                if constexpr (kWallInline) c4 = substitution_correction<R>(ringA, ringB, sb0, st.sub, open_edge);
+                else c4 = substitution_correction_call<R>(ringA, ringB, sb0, st.sub, open_edge);
                 gAx += c4.ax;
                 gAy += c4.ay;
                 gBx += c4.bx;
@@ -512,21 +519,22 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             R FBx = -P.G * rB * gAx, FBy = -P.G * rB * gAy;
             if (wall) {  // adhesion (Eq. 9), G_w1 local in the improved scheme (Eqs. 10, 12)
                 R GA;
-                if (P.mode == 1) {
+                const Params<R>& Q = s_par;
+                if (Q.mode == 1) {
                     const R re = (rA - rB) / (rA + rB);
                     R h;
-                    if (re > P.delta) h = P.lam;
-                    else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
-                    else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
+                    if (re > Q.delta) h = Q.lam;
+                    else if (re > (R)0) h = Q.s1 + re * (Q.s2 + re * Q.s3);
+                    else if (re > -Q.delta) h = Q.s1 + re * (Q.t2 + re * Q.t3);
                     else h = (R)1;
-                    GA = P.Gw2 * h;
+                    GA = Q.Gw2 * h;
                 } else {
-                    GA = P.lam * P.Gw2;
+                    GA = Q.lam * Q.Gw2;
                 }
                 FAx -= GA * rA * st.ax;
                 FAy -= GA * rA * st.ay;
-                FBx -= P.Gw2 * rB * st.ax;
-                FBy -= P.Gw2 * rB * st.ay;
+                FBx -= s_par.Gw2 * rB * st.ax;
+                FBy -= s_par.Gw2 * rB * st.ay;
             }
             FAx += rA * P.gx;
             FAy += rA * P.gy;
@@ -670,7 +678,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             }
             __syncthreads();
         }
-        if (t == 0) s_claim = atomicAdd(a.sched, 1);  // every thread has read the previous claim
+        if (t == 0) claim();  // every thread is past the previous claim and its parameters
         __syncthreads();
         it = a.item_begin + s_claim;
     }
@@ -779,7 +787,7 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
             const int yp = Y + 1 >= C.ny ? (C.bc_y == kPeriodic ? 0 : C.ny - 1) : Y + 1;
             const bool inlet = C.bc_x == kOpen && X == 0, outlet = C.bc_x == kOpen && X == C.nx - 1;
             pull<true, S, R>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch, fin + (long long)yp * C.pitch,
-                             P.plane, X + G, fl, inlet, outlet, P, v);
+                             P.plane, X + G, fl, inlet, outlet, P, P, v);
         }
 #pragma unroll
         for (int q = 0; q < 18; ++q) f[(long long)q * N + s] = (double)v[q];
@@ -811,17 +819,19 @@ __global__ void k_diag_reduce(const DevCase* __restrict__ cases, int c, const do
 }
 
 template <class S>
-void* kernel_ptr(bool fields) {
+void* kernel_ptr(int variant) {
     using R = typename ComputeOf<S>::type;
-    return fields ? (void*)k_step<S, R, true> : (void*)k_step<S, R, false>;
+    return variant == 2 ? (void*)k_step<S, R, true, false>
+                        : (variant == 1 ? (void*)k_step<S, R, false, true> : (void*)k_step<S, R, false, false>);
 }
 
-void* step_kernel(int storage, bool fields) {
+// variant 0: step, wall path out of line; 1: step, wall path inline; 2: fields pass
+void* step_kernel(int storage, int variant) {
     switch (storage) {
-        case LBM_STORE_F64: return kernel_ptr<double>(fields);
-        case LBM_STORE_F32: return kernel_ptr<float>(fields);
-        case LBM_STORE_F16_SHIFTED: return kernel_ptr<__half>(fields);
-        default: return kernel_ptr<__nv_bfloat16>(fields);
+        case LBM_STORE_F64: return kernel_ptr<double>(variant);
+        case LBM_STORE_F32: return kernel_ptr<float>(variant);
+        case LBM_STORE_F16_SHIFTED: return kernel_ptr<__half>(variant);
+        default: return kernel_ptr<__nv_bfloat16>(variant);
     }
 }
 
@@ -859,8 +869,9 @@ cudaError_t launch_step_t(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields
     using R = typename ComputeOf<S>::type;
     if (c.block_threads != kT) return cudaErrorInvalidConfiguration;
     const size_t smem = smem_for<S>(kT);
-    if (fields) k_step<S, R, true><<<grid, kT, smem, s>>>(a);
-    else k_step<S, R, false><<<grid, kT, smem, s>>>(a);
+    if (fields) k_step<S, R, true, false><<<grid, kT, smem, s>>>(a);
+    else if (c.wall_inline) k_step<S, R, false, true><<<grid, kT, smem, s>>>(a);
+    else k_step<S, R, false, false><<<grid, kT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -891,11 +902,20 @@ int step_smem_bytes(int storage, int threads) {
 
 cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm) {
     const int bytes = step_smem_bytes(storage, threads);
-    for (int f = 0; f < 2; ++f) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel(storage, f != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    for (int v = 0; v < 3; ++v) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel(storage, v), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel(storage, false), threads, bytes);
+    // the most restrictive of the three variants sets the resident blocks
+    int m = 1 << 30;
+    for (int v = 0; v < 3; ++v) {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel(storage, v), threads, bytes);
+        if (e != cudaSuccess) return e;
+        m = b < m ? b : m;
+    }
+    *blocks_per_sm = m;
+    return cudaSuccess;
 }
 
 cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s) {

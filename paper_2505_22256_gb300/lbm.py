@@ -32,7 +32,7 @@ SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_
            "lbm_set_densities", "lbm_fields", "lbm_diagnostics", "lbm_contact_angle", "lbm_wall_list",
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
            "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc",
-           "lbm_diagnostics_all", "lbm_contact_angle_all")
+           "lbm_diagnostics_all", "lbm_contact_angle_all", "lbm_set_wall_path")
 
 
 class lbm_grid(ctypes.Structure):
@@ -69,10 +69,10 @@ class lbm_info_t(ctypes.Structure):
     _fields_ = [("ncases", c_int32), ("storage", c_int32), ("nodes", c_int64), ("fluid_nodes", c_int64),
                 ("wall_nodes", c_int64), ("steps", c_int64), ("state_bytes", c_int64),
                 ("device_bytes", c_int64), ("block_threads", c_int32), ("block_rows", c_int32),
-                ("grid_blocks", c_int32), ("work_items", c_int32)]
+                ("grid_blocks", c_int32), ("work_items", c_int32), ("wall_inline", c_int32), ("pad_", c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 class LbmError(RuntimeError):
@@ -112,6 +112,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_set_populations.argtypes = [ctx_p, c_int32, c_void_p]
     lib.lbm_info.argtypes = [ctx_p, POINTER(lbm_info_t)]
     lib.lbm_set_launch.argtypes = [ctx_p, c_int32, c_int32]
+    lib.lbm_set_wall_path.argtypes = [ctx_p, c_int32]
     lib.lbm_autotune.argtypes = [ctx_p, c_int32, d]
     lib.lbm_save.argtypes = [ctx_p, ctypes.c_char_p]
     lib.lbm_load.argtypes = [ctx_p, ctypes.c_char_p]
@@ -333,6 +334,10 @@ def lbm_info(ctx) -> dict:
 
 def lbm_set_launch(ctx, block_threads: int, block_rows: int) -> None:
     _check(load_library().lbm_set_launch(ctx, int(block_threads), int(block_rows)))
+
+
+def lbm_set_wall_path(ctx, inline_correction: int) -> None:
+    _check(load_library().lbm_set_wall_path(ctx, int(inline_correction)))
 
 
 def lbm_autotune(ctx, steps: int = 5) -> float:

@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(lbm):
     assert lbm.lbm_params.lambda_.offset == 32
     assert ctypes.sizeof(lbm.lbm_diag) == 9 * 8 + 8 + 8
     assert ctypes.sizeof(lbm.lbm_surface) == 8 + 4 * 8
-    assert ctypes.sizeof(lbm.lbm_info_t) == 8 + 6 * 8 + 16
+    assert ctypes.sizeof(lbm.lbm_info_t) == 8 + 6 * 8 + 24
 
 
 def _case(n=16):

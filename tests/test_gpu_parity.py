@@ -205,6 +205,31 @@ def test_launch_shapes_agree():
         lbm.lbm_set_launch(lbm.Lattice(sc, "f32").ctx, 64, 16)
 
 
+def test_wall_paths_agree_and_default_choice():
+    """Both forms of the wall-list correction give the same state to FP32 rounding; the default
+    inlines it in the porous medium (wall-list nodes ~15 % of the fluid) and calls it for a 256^2
+    cylinder case (~2.5 %)."""
+    cases = {"porous_open": SCENARIOS["porous_open"], "cylinder256": lambda: S.cylinder_droplet(256, lam=0.6)}
+    for name, expect in (("porous_open", 1), ("cylinder256", 0)):
+        sc = cases[name]()
+        out = []
+        for w in (None, 1 - expect):
+            lat = lbm.Lattice(sc, "f32")
+            if w is None:
+                assert lat.info()["wall_inline"] == expect, name
+            else:
+                lbm.lbm_set_wall_path(lat.ctx, w)
+                assert lat.info()["wall_inline"] == w
+            lat.step(60)
+            out.append(lat.populations())
+            lat.close()
+        scale = np.abs(out[0]).max(axis=(2, 3), keepdims=True)
+        assert np.max(np.abs(out[1] - out[0]) / scale) < 2e-6, name
+    with pytest.raises(lbm.LbmError):
+        lat = lbm.Lattice(SCENARIOS["free64"](), "f32")
+        lbm.lbm_set_wall_path(lat.ctx, 2)
+
+
 def test_ensemble_equals_single_cases():
     cases = [SCENARIOS["cylinder96"](), SCENARIOS["flat64x48"](), SCENARIOS["porous_open"](), SCENARIOS["free64"]()]
     ens = lbm.Lattice(cases, "f32")
