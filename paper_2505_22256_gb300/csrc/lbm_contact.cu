@@ -44,27 +44,36 @@ __device__ bool usable(const CaGeo& g, int X, int Y) {
     return (g.flags[(long long)Y * g.nx + X] & (kSolidBit | kNearSolidBit)) == 0;
 }
 
-__device__ double phi_at(const CaGeo& g, int X, int Y) {
-    const long long s = (long long)Y * g.nx + X;
-    return (g.rA[s] - g.rB[s]) / (g.rA[s] + g.rB[s]);
+__device__ double phi_of(double ra, double rb) { return (ra - rb) / (ra + rb); }
+
+// phi > 0 without the division where 0 < rho_A + rho_B < inf: the quotient then has the sign of
+// the difference, which is at least an ulp of the larger density and cannot underflow to zero.
+__device__ bool phi_positive(double ra, double rb) {
+    const double sum = ra + rb;
+    return (sum > 0.0 && sum < INFINITY) ? ra > rb : phi_of(ra, rb) > 0.0;
 }
 
-// Up to two crossing points owned by node (X, Y): towards (X+1, Y) and towards (X, Y+1).
+// Up to two crossing points owned by node (X, Y): towards (X+1, Y) and towards (X, Y+1).  phi is
+// formed only at the two ends of a crossing.
 __device__ int node_points(const CaGeo& g, int X, int Y, double* px, double* py) {
     int n = 0;
     if (!usable(g, X, Y)) return 0;
-    const double a = phi_at(g, X, Y);
+    const long long s = (long long)Y * g.nx + X;
+    const double ra = g.rA[s], rb = g.rB[s];
+    const bool pa = phi_positive(ra, rb);
     if (X + 1 < g.nx && usable(g, X + 1, Y)) {
-        const double b = phi_at(g, X + 1, Y);
-        if ((a > 0.0) != (b > 0.0)) {
+        const double qa = g.rA[s + 1], qb = g.rB[s + 1];
+        if (pa != phi_positive(qa, qb)) {
+            const double a = phi_of(ra, rb), b = phi_of(qa, qb);
             px[n] = X + a / (a - b);
             py[n] = (double)Y;
             ++n;
         }
     }
     if (Y + 1 < g.ny && usable(g, X, Y + 1)) {
-        const double b = phi_at(g, X, Y + 1);
-        if ((a > 0.0) != (b > 0.0)) {
+        const double qa = g.rA[s + g.nx], qb = g.rB[s + g.nx];
+        if (pa != phi_positive(qa, qb)) {
+            const double a = phi_of(ra, rb), b = phi_of(qa, qb);
             px[n] = (double)X;
             py[n] = Y + a / (a - b);
             ++n;

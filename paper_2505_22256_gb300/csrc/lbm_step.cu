@@ -136,12 +136,37 @@ __device__ __forceinline__ int map_col(const Params<R>& P, int x) {
 
 __device__ __forceinline__ int ring_slot(int r) { return (r + 2 * kRing) % kRing; }
 
+// Per-thread diagnostics of the fields pass: FP64 sums (mass, momentum); extrema and the largest
+// |u|^2 in the compute type (exact: min / max only compare), one square root at the end.
+template <class R>
 struct Diag {
-    double v[kDiagN];
+    double mA, mB, px, py;
+    R u2, aMin, aMax, bMin, bMax;
+    int n;
+    bool bad;
     __device__ void init() {
-        for (int q = 0; q < kDiagN; ++q) v[q] = 0.0;
-        v[5] = v[7] = INFINITY;
-        v[6] = v[8] = -INFINITY;
+        mA = mB = px = py = 0.0;
+        u2 = (R)0;
+        aMin = bMin = (R)INFINITY;
+        aMax = bMax = (R)-INFINITY;
+        n = 0;
+        bad = false;
+    }
+    // record layout (kDiagN doubles): mass_A, mass_B, mom_x, mom_y, umax, rhoA min/max, rhoB min/max,
+    // fluid nodes, unstable flag
+    __device__ void to_record(double* v) const {
+        v[0] = mA;
+        v[1] = mB;
+        v[2] = px;
+        v[3] = py;
+        v[4] = sqrt((double)u2);
+        v[5] = (double)aMin;
+        v[6] = (double)aMax;
+        v[7] = (double)bMin;
+        v[8] = (double)bMax;
+        v[9] = (double)n;
+        v[10] = bad ? 1.0 : 0.0;
+        for (int q = 11; q < kDiagN; ++q) v[q] = 0.0;
     }
 };
 
@@ -485,7 +510,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
 
         // collide row y (state st, complete gradient g[0]) and store it
         // lo: ring slot of row y - 2 (rows y-2 .. y+2 sit at slots lo .. lo+4)
-        auto update_row = [&](int y, int lo, const RowState<R>& st, const Grad<R>& g, Diag& dg) {
+        auto update_row = [&](int y, int lo, const RowState<R>& st, const Grad<R>& g, Diag<R>& dg) {
             if (!interior || (st.fl & kSolidBit)) {
                 if constexpr (kFields) {
                     if (interior && a.o_rA) {
@@ -559,20 +584,21 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                         a.o_uy[o] = (double)uy;
                     }
                 }
-                const double dux = ux, duy = uy, drho = (double)rho;
-                dg.v[0] += (double)rA;
-                dg.v[1] += (double)rB;
-                dg.v[2] += drho * dux;
-                dg.v[3] += drho * duy;
-                const double um = sqrt(dux * dux + duy * duy);
-                dg.v[4] = fmax(dg.v[4], um);
-                dg.v[5] = fmin(dg.v[5], (double)rA);
-                dg.v[6] = fmax(dg.v[6], (double)rA);
-                dg.v[7] = fmin(dg.v[7], (double)rB);
-                dg.v[8] = fmax(dg.v[8], (double)rB);
-                dg.v[9] += 1.0;
-                if (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB))
-                    dg.v[10] = 1.0;
+                if (a.diag_part) {  // null: densities only
+                    const double drho = (double)rho;
+                    dg.mA += (double)rA;
+                    dg.mB += (double)rB;
+                    dg.px += drho * (double)ux;
+                    dg.py += drho * (double)uy;
+                    const R u2 = ux * ux + uy * uy;
+                    dg.u2 = fmax(dg.u2, u2);
+                    dg.aMin = fmin(dg.aMin, rA);
+                    dg.aMax = fmax(dg.aMax, rA);
+                    dg.bMin = fmin(dg.bMin, rB);
+                    dg.bMax = fmax(dg.bMax, rB);
+                    ++dg.n;
+                    if (!(rA > (R)0) || !(rB > (R)0) || !isfinite(u2) || !isfinite(rA) || !isfinite(rB)) dg.bad = true;
+                }
             } else {
                 R o[18];
                 collide_comp<R>(f, 0, rA, ux, uy, FAx, FAy, P.omega[0], P.cF[0], o);
@@ -597,7 +623,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             }
         };
 
-        Diag dg;
+        Diag<R> dg;
         if constexpr (kFields) dg.init();
         Grad<R> g;
         g.zero();
@@ -652,12 +678,14 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
         }
         __syncthreads();  // every thread is done with the slots before the next item refills them
 
-        if constexpr (kFields) {
+        if (kFields && a.diag_part) {
             __shared__ double red[8][kDiagN];
             const int lane = t & 31, warp = t >> 5;
+            double rec[kDiagN];
+            dg.to_record(rec);
 #pragma unroll
             for (int qq = 0; qq < kDiagN; ++qq) {
-                double v = dg.v[qq];
+                double v = rec[qq];
                 for (int off = 16; off > 0; off >>= 1) {
                     const double o = __shfl_xor_sync(0xffffffffu, v, off);
                     v = (qq == 4 || qq == 6 || qq == 8 || qq == 10) ? fmax(v, o) : (qq == 5 || qq == 7) ? fmin(v, o) : v + o;
@@ -947,7 +975,7 @@ cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
     double* o4[4] = {rhoA_all, rhoB_all, nullptr, nullptr};
     const int n = c.nitems_all - c.nitems;
     const int grid = n < c.grid_blocks ? n : c.grid_blocks;
-    StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, c.diag_part);
+    StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, nullptr);
     a.fields_global = 1;
     return dispatch(c, a, c.stream, true, grid);
 }
