@@ -56,6 +56,7 @@ def parse():
                          "2048x512 throat channel; porous: 4096x2048 porous medium with inlet/outflow; "
                          "ensemble: 256 uneven cases + the 4096x256 co-current channel")
     ap.add_argument("--n", type=int, default=1024, help="sweep: lattice side of each case")
+    ap.add_argument("--size", default=None, help="throat / porous: lattice WxH (default 2048x512 / 4096x2048)")
     ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
@@ -72,12 +73,17 @@ def workload(args, rank=0):
     from paper_2505_22256_gb300 import scenarios as S
 
     if args.workload == "throat":
-        cases = [S.throat_channel(seed=3 + 100 * k + 1000 * rank) for k in range(8)]
-        return cases, ("throat channel, 8 replicas of 2048x512 per GPU (half-disks R=180, droplet r=120, "
-                       "g=1e-6, lambda for theta=90 deg)")
+        nx, ny = map(int, (args.size or "2048x512").split("x"))
+        k = ny / 512.0  # geometry scales with the channel height
+        cases = [S.throat_channel(nx=nx, ny=ny, R=180.0 * k, r=120.0 * k, seed=3 + 100 * j + 1000 * rank)
+                 for j in range(8)]
+        return cases, (f"throat channel, 8 replicas of {nx}x{ny} per GPU (half-disks R={180 * k:g}, "
+                       f"droplet r={120 * k:g}, g=1e-6, lambda for theta=90 deg)")
     if args.workload == "porous":
-        return [S.porous_disks(seed=4 + 1000 * rank)], \
-            "porous medium 4096x2048 per GPU (disks r=12..40, porosity 0.6, inlet u=0.005 at x=0, outflow)"
+        nx, ny = map(int, (args.size or "4096x2048").split("x"))
+        keep = max(8, 64 * nx // 4096)
+        return [S.porous_disks(nx=nx, ny=ny, keep_out=(keep, keep), seed=4 + 1000 * rank)], \
+            (f"porous medium {nx}x{ny} per GPU (disks r=12..40, porosity 0.6, inlet u=0.005 at x=0, outflow)")
     if args.workload == "ensemble":
         return S.ensemble_cases(256, seed=5 + 1000 * rank) + [S.cocurrent_channel(seed=6 + 1000 * rank)], \
             ("uneven ensemble per GPU: 256 square cases n=64..512 (flat wall / cylinder, lambda 0.22..2.17) "

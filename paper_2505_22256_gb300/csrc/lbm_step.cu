@@ -71,6 +71,23 @@ __device__ __forceinline__ float sload<__half, float>(const __half* p) { return 
 template <>
 __device__ __forceinline__ float sload<__nv_bfloat16, float>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
+// 16-bit storage holds f - w rho0: load and add the shift back in one mixed-precision add (the
+// widening is exact, so this rounds once, like a conversion followed by an FP32 add)
+template <class S, class R>
+__device__ __forceinline__ R sload_shifted(const S* p, R shift);
+template <>
+__device__ __forceinline__ float sload_shifted<__half, float>(const __half* p, float shift) {
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(__half_as_ushort(*p)), "f"(shift));
+    return r;
+}
+template <>
+__device__ __forceinline__ float sload_shifted<__nv_bfloat16, float>(const __nv_bfloat16* p, float shift) {
+    float r;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(__bfloat16_as_ushort(*p)), "f"(shift));
+    return r;
+}
+
 template <class S, class R>
 __device__ __forceinline__ S to_store(R v) { return (S)v; }
 template <>
@@ -106,11 +123,13 @@ __device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restri
             src = blocked ? r0 : nsrc;
             off = blocked ? (long long)opp(i) * ps + b : (long long)i * ps + b - cx(i);
         }
-        R va = sload<S, R>(src + off);
-        R vb = sload<S, R>(src + off + 9 * ps);
+        R va, vb;
         if constexpr (Store<S>::kShift) {
-            va += shift_of(P, 0, i);
-            vb += shift_of(P, 1, i);
+            va = sload_shifted<S, R>(src + off, shift_of(P, 0, i));
+            vb = sload_shifted<S, R>(src + off + 9 * ps, shift_of(P, 1, i));
+        } else {
+            va = sload<S, R>(src + off);
+            vb = sload<S, R>(src + off + 9 * ps);
         }
         f[i] = va;
         f[9 + i] = vb;
