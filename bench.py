@@ -102,6 +102,7 @@ def config_dict(args, cases, desc, world):
         "storage": args.storage, "cases_per_gpu": len(cases), "nodes_per_gpu": nodes,
         "fluid_nodes_per_gpu": fluid, "inner_steps": args.inner, "parallelism": f"ensemble x{world} (no collective)",
         "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE[args.storage] / 2 / 1e9),
+        **({"storage_shift_rho0": list(cases[0].rho0_store)} if args.storage in ("f16", "bf16") else {}),
     }
 
 

@@ -368,8 +368,7 @@ class Lattice:
         cases = []
         for sc in self.scenarios:
             p = sc.params()
-            if rho0_store is not None:
-                p["rho0_store"] = rho0_store
+            p["rho0_store"] = tuple(rho0_store if rho0_store is not None else getattr(sc, "rho0_store", (0.0, 0.0)))
             cases.append((make_grid(sc.nx, sc.ny, sc.bc_x, sc.bc_y), sc.solid, make_params(**p), sc.rhoA0, sc.rhoB0))
         if len(cases) == 1:
             g, s, p, a, b = cases[0]

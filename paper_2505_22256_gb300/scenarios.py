@@ -90,6 +90,9 @@ class Scenario:
     u_in: float = 0.0
     rho_in: tuple = (RHO_M, RHO_D)
     surface: dict | None = None  # for the contact angle: {"kind": "flat"|"circle", ...}
+    # 16-bit storage keeps f_i - w_i rho0 per component; the dissolved-phase density serves both
+    # phases best (ignored by FP32 / FP64 storage)
+    rho0_store: tuple = (RHO_D, RHO_D)
     extra: dict = field(default_factory=dict)
 
     @property
