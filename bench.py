@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--workload", default="sweep", choices=list(WORKLOADS),
                     help="sweep: 7 cylinder cases of 1024^2 (the headline); throat: 8 replicas of the "
                          "2048x512 throat channel; porous: 4096x2048 porous medium with inlet/outflow; "
-                         "ensemble: 256 uneven cases + the 4096x256 co-current channel")
+                         "ensemble: 256 uneven cases + the 4096x256 co-current channel; compare: the "
+                         "sweep under the improved and the original scheme (14 cases)")
     ap.add_argument("--n", type=int, default=1024, help="sweep: lattice side of each case")
     ap.add_argument("--size", default=None, help="throat / porous: lattice WxH (default 2048x512 / 4096x2048)")
     ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
@@ -65,7 +66,7 @@ def parse():
     return ap.parse_args()
 
 
-WORKLOADS = ("sweep", "throat", "porous", "ensemble")
+WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare")
 
 
 def workload(args, rank=0):
@@ -89,6 +90,10 @@ def workload(args, rank=0):
             ("uneven ensemble per GPU: 256 square cases n=64..512 (flat wall / cylinder, lambda 0.22..2.17) "
              "+ the 4096x256 co-current channel")
     angles = (30, 50, 70, 90, 110, 130, 150)[: args.cases]
+    if args.workload == "compare":
+        return S.scheme_comparison(n=args.n, seed=2 + 1000 * rank, angles=angles), \
+            (f"scheme comparison, {len(angles)} cylinder cases of {args.n}x{args.n} per GPU under the improved "
+             f"and the original scheme ({2 * len(angles)} cases)")
     return S.lambda_sweep_cylinder(n=args.n, seed=2 + 1000 * rank, angles=angles), \
         (f"cylinder contact-angle sweep, {len(angles)} cases of {args.n}x{args.n} per GPU "
          f"(R={160 * args.n // 1024}, r={200 * args.n // 1024}, lambda for theta=30..150 deg)")
@@ -381,6 +386,11 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
         "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
+        **({"scheme_comparison": [{"case": c.name, "lambda": c.lam, "scheme": c.scheme, "theta_deg": t,
+                                   "umax": x["umax"], "rhoA_min": x["rhoA_min"], "rhoA_max": x["rhoA_max"],
+                                   "rhoB_min": x["rhoB_min"], "rhoB_max": x["rhoB_max"]}
+                                  for c, t, x in zip(cases, theta, dall)]}
+           if args.workload == "compare" else {}),
         "sample_diagnostics": {"theta_deg": theta if len(theta) <= 8 else
                                {"measured": sum(t is not None for t in theta),
                                 "min": min((t for t in theta if t is not None), default=None),

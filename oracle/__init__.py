@@ -147,7 +147,8 @@ class _Cfg(ctypes.Structure):
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("lam", ctypes.c_double),
                 ("Gw2", ctypes.c_double), ("delta", ctypes.c_double), ("g", ctypes.c_double * 2),
                 ("u_in", ctypes.c_double), ("rho_in", ctypes.c_double * 2),
-                ("wE8", ctypes.c_double * 5)]
+                ("wE8", ctypes.c_double * 5), ("inlet_profile", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("u_wall", ctypes.c_double * 2)]
 
 
 @dataclass
@@ -166,6 +167,8 @@ class Config:
     g: tuple = (0.0, 0.0)
     u_in: float = 0.0
     rho_in: tuple = (1.0, 0.03)
+    inlet_profile: str = "uniform"  # uniform | poiseuille (peak u_in; Sec. 3.3)
+    u_wall: tuple = (0.0, 0.0)      # x-velocity of the lower / upper wall of a walled y (Sec. 3.1)
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
 
     def c(self) -> _Cfg:
@@ -182,6 +185,8 @@ class Config:
         s.g[0], s.g[1] = self.g
         s.u_in = self.u_in
         s.rho_in[0], s.rho_in[1] = self.rho_in
+        s.inlet_profile = {"uniform": 0, "poiseuille": 1}[self.inlet_profile]
+        s.u_wall[0], s.u_wall[1] = self.u_wall
         for i, q in enumerate(SHELLS):
             s.wE8[i] = float(w[q])
         return s

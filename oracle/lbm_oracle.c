@@ -48,6 +48,9 @@ typedef struct {
     double u_in;      /* inlet x-velocity (Sec. 3.3 velocity inlet) */
     double rho_in[2]; /* component densities imposed at the inlet */
     double wE8[5];    /* E8 weights w(|e|^2) for |e|^2 = 1, 2, 4, 5, 8 (derived in Python) */
+    int32_t inlet_profile; /* 0: uniform u_in; 1: Poiseuille profile of peak u_in (Sec. 3.3) */
+    int32_t pad_;
+    double u_wall[2]; /* x-velocity of the lower / upper wall of a walled y direction (Sec. 3.1 Couette) */
 } oracle_cfg;
 
 /* ---------------------------------------------------------------------------------------------
@@ -378,10 +381,20 @@ int oracle_collide(const oracle_cfg* c, const uint8_t* solid, const double* f, d
     return 0;
 }
 
+/* Inlet velocity of row y (Sec. 3.3).  Uniform: u_in.  Poiseuille: u_in 4 s (H - s) / H^2 with s the
+ * distance from the lower wall, the walls being the halfway bounce-back planes below row 0 and above
+ * row ny-1 (s = y + 1/2, H = ny), so u_in is the peak of the profile. */
+static double inlet_velocity(const oracle_cfg* c, int y) {
+    if (!c->inlet_profile) return c->u_in;
+    double s = y + 0.5, H = (double)c->ny;
+    return c->u_in * 4.0 * s * (H - s) / (H * H);
+}
+
 /* Open x boundaries (Sec. 3.3), applied to a post-streaming state f whose pre-streaming state was
  * fstar.  Populations entering through x = 0 are given by non-equilibrium bounce-back about
- * f^eq(rho_in,k, (u_in, 0)) (the reading of the two-component Zou-He inlet); populations entering
- * through x = nx-1 are copied from column nx-2 (outflow), or bounced back if that node is solid. */
+ * f^eq(rho_in,k, (u(y), 0)) (the reading of the two-component Zou-He inlet; u(y) from
+ * inlet_velocity); populations entering through x = nx-1 are copied from column nx-2 (outflow), or
+ * bounced back if that node is solid. */
 static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
     size_t N = (size_t)c->nx * (size_t)c->ny;
     if (c->bc_x != BC_OPEN) return;
@@ -392,7 +405,7 @@ static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const dou
             if (!solid[s0])
                 for (int k = 0; k < 2; k++) {
                     double fe[9];
-                    oracle_feq(c->rho_in[k], c->u_in, 0.0, fe);
+                    oracle_feq(c->rho_in[k], inlet_velocity(c, y), 0.0, fe);
                     for (int i = 0; i < 9; i++)
                         if (CX[i] > 0) {
                             double fo = f[((size_t)k * 9 + OPP[i]) * N + s0];
@@ -416,6 +429,10 @@ static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const dou
 /* Step (8): streaming with halfway bounce-back.
  * f_i(x, t+1) = f*_i(x - e_i) when x - e_i is a fluid node (periodic wrap), otherwise
  * f*_{opp(i)}(x) (halfway bounce-back, Sec. 3.5: the wall sits half a link from the fluid node).
+ * A link that crosses a walled y edge of the array meets the lower (y < 0) or upper (y >= ny)
+ * wall, which slides along x at u_wall (Sec. 3.1, Couette flow): the reflected population then
+ * carries the wall's momentum, f_i = f*_opp(i) + 2 w_i rho_k (e_i . u_w) / c_s^2, with rho_k the
+ * node's density sum_j f*_j(x) (the collision conserves it).
  * Open x boundaries: see open_boundaries(). */
 int oracle_stream(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
     size_t N = (size_t)c->nx * (size_t)c->ny;
@@ -432,10 +449,20 @@ int oracle_stream(const oracle_cfg* c, const uint8_t* solid, const double* fstar
                         f[q] = NAN; /* unknown: set by the boundary rule below */
                         continue;
                     }
+                    int Yraw = Y;
                     if (wrap_site(c, &X, &Y) && !solid[idx(c, X, Y)])
                         f[q] = fstar[((size_t)k * 9 + i) * N + idx(c, X, Y)];
-                    else
+                    else {
                         f[q] = fstar[((size_t)k * 9 + OPP[i]) * N + s0];
+                        if (c->bc_y == BC_WALL && (Yraw < 0 || Yraw >= c->ny)) {
+                            double uw = Yraw < 0 ? c->u_wall[0] : c->u_wall[1];
+                            if (uw != 0.0) {
+                                double rho = 0.0;
+                                for (int j = 0; j < 9; j++) rho += fstar[((size_t)k * 9 + j) * N + s0];
+                                f[q] += 6.0 * W9[i] * rho * CX[i] * uw;
+                            }
+                        }
+                    }
                 }
         }
     open_boundaries(c, solid, fstar, f);

@@ -283,13 +283,26 @@ def ensemble_cases(ncases: int = 256, nmin: int = 64, nmax: int = 512, seed: int
 
 
 def lambda_sweep_cylinder(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110, 130, 150),
-                          G: float = G_DEFAULT) -> list:
+                          G: float = G_DEFAULT, scheme: str = "improved") -> list:
     """The 1024x1024 cylinder contact-angle sweep: one case per target angle, lambda from the
     paper's correlation (Sec. 3.2), cylinder radius 160 and droplet radius 200 at n = 1024."""
     out = []
     for k, th in enumerate(angles):
         sc = cylinder_droplet(n=n, R=160.0 * n / 1024.0, r=200.0 * n / 1024.0,
-                              lam=lambda_for_angle(th), seed=seed * 100 + k, G=G)
+                              lam=lambda_for_angle(th), seed=seed * 100 + k, G=G, scheme=scheme)
         sc.name = f"sweep_theta{th}_{sc.name}"
         out.append(sc)
+    return out
+
+
+def scheme_comparison(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110, 130, 150),
+                      G: float = G_DEFAULT) -> list:
+    """The cylinder sweep under both solid-fluid schemes (Secs. 2.3, 3.2): the improved scheme's
+    cases, then the original scheme's on the same geometries and initial states (G_w1 = lambda
+    G_w2 everywhere), for the comparison of spurious currents and density extrema."""
+    out = []
+    for scheme in ("improved", "original"):
+        for sc in lambda_sweep_cylinder(n, seed, angles, G, scheme=scheme):
+            sc.name = f"{scheme}_{sc.name}"
+            out.append(sc)
     return out

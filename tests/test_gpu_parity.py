@@ -230,6 +230,29 @@ def test_wall_paths_agree_and_default_choice():
         lbm.lbm_set_wall_path(lat.ctx, 2)
 
 
+def test_lambda_one_makes_both_schemes_identical_on_the_gpu():
+    """With lambda = 1 the local parameter of Eq. 12 is G_w2 everywhere, so the improved and the
+    original scheme must give the same state bit for bit (in one ensemble launch)."""
+    cases = [S.cylinder_droplet(96, lam=1.0, scheme=s) for s in ("improved", "original")]
+    ens = lbm.Lattice(cases, "f32")
+    ens.step(200)
+    np.testing.assert_array_equal(ens.populations(0), ens.populations(1))
+    ens.close()
+
+
+def test_scheme_comparison_cases_match_oracle():
+    """The comparison workload at 128^2: each scheme's case steps like the oracle (100 steps)."""
+    cases = S.scheme_comparison(n=128, angles=(30, 150))
+    ens = lbm.Lattice(cases, "f32")
+    ens.step(100)
+    for i, sc in enumerate(cases):
+        cfg, f = orun(sc, 100)
+        o = oracle.fields(cfg, sc.solid, f)
+        g = ens.fields(i)
+        assert rel_rho(g, o, sc.solid) <= 1e-5, sc.name
+    ens.close()
+
+
 def test_ensemble_equals_single_cases():
     cases = [SCENARIOS["cylinder96"](), SCENARIOS["flat64x48"](), SCENARIOS["porous_open"](), SCENARIOS["free64"]()]
     ens = lbm.Lattice(cases, "f32")

@@ -174,6 +174,37 @@ def test_open_channel_mass_balance_per_step():
 # ---------------------------------------------------------------------------------------------
 # P13: interface points, circle fit and contact angle
 # ---------------------------------------------------------------------------------------------
+def _inlet_source(cfg, solid, rho_a, rho_b, steps=3):
+    """Per-row source of the inlet rule after one streaming step, per component:
+    sum over the entering i in {1, 5, 8} of f_i - f_opp(i) at x = 0, divided by rho_in."""
+    f = oracle.init(cfg, solid, rho_a, rho_b)
+    f = oracle.run(cfg, solid, f, steps)
+    f2 = oracle.stream(cfg, solid, oracle.collide(cfg, solid, f))
+    return np.array([[sum(f2[k, i, y, 0] - f2[k, OPP[i], y, 0] for i in (1, 5, 8)) / cfg.rho_in[k]
+                      for y in range(cfg.ny)] for k in range(2)])
+
+
+def test_poiseuille_inlet_profile_peak_symmetry_and_sum():
+    """Sec. 3.3's Poiseuille inlet: the non-equilibrium bounce-back adds rho_in u(y) per row (the
+    w-weighted odd part of f^eq sums to rho u).  With walls half a cell outside rows 0 and ny-1
+    (H = ny) the profile peaks at u_in on the centre row of an odd ny, is mirror-symmetric, and its
+    row sum is u_in (2H/3 + 1/(3H)) (sum of 4 s (H - s) / H^2 over s = 1/2, 3/2, ..., H - 1/2)."""
+    nx, ny, u = 9, 11, 0.01
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=0.5, u_in=u, rho_in=(0.6, 0.4),
+                        inlet_profile="poiseuille")
+    ra = np.full((ny, nx), 0.55)
+    src = _inlet_source(cfg, solid, ra, 1.0 - ra)
+    for k in range(2):
+        assert src[k, ny // 2] == pytest.approx(u, rel=1e-12)
+        np.testing.assert_allclose(src[k], src[k, ::-1], rtol=1e-12)
+        assert src[k].sum() / u == pytest.approx(2 * ny / 3 + 1 / (3 * ny), rel=1e-12)
+        assert np.all(np.diff(src[k, : ny // 2 + 1]) > 0)
+    # the uniform inlet adds rho_in u_in on every row
+    cfg_u = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=0.5, u_in=u, rho_in=(0.6, 0.4))
+    np.testing.assert_allclose(_inlet_source(cfg_u, solid, ra, 1.0 - ra), u, rtol=1e-12)
+
+
 def test_circle_fit_exact_points():
     t = np.linspace(0, 2 * np.pi, 37)[:-1]
     pts = np.stack([31.25 + 17.5 * np.cos(t), -4.0 + 17.5 * np.sin(t)], axis=1)

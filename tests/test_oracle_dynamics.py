@@ -223,3 +223,20 @@ def test_flat_wall_mirror_symmetry(lam):
     for a in (rA, rB, uy):
         assert np.max(np.abs(a - a[:, ::-1])) <= 1e-12
     assert np.max(np.abs(ux + ux[:, ::-1])) <= 1e-12
+
+
+@pytest.mark.parametrize("u_wall", [(-0.01, 0.01), (0.0, 0.008)])
+def test_couette_between_sliding_walls_is_exactly_linear(u_wall):
+    """Sec. 3.1's Couette flow, single phase (G = 0): halfway bounce-back walls half a cell below
+    row 0 and above row ny-1 slide at u_wall; the steady profile is the linear Couette solution
+    u(s) = u_lo + (u_hi - u_lo) s / H, s = y + 1/2, H = ny, with no wall-normal velocity."""
+    nx, ny = 4, 16
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="periodic", bc_y="wall", G=0.0, u_wall=u_wall)
+    f = oracle.init(cfg, solid, np.ones((ny, nx)), np.full((ny, nx), 1e-3))
+    f = oracle.run(cfg, solid, f, 6000)  # slowest mode decays as exp(-nu pi^2 t / H^2)
+    _, _, ux, uy = oracle.fields(cfg, solid, f)
+    s = np.arange(ny) + 0.5
+    exact = u_wall[0] + (u_wall[1] - u_wall[0]) * s / ny
+    np.testing.assert_allclose(ux, np.repeat(exact[:, None], nx, axis=1), rtol=0, atol=1e-12)
+    assert np.max(np.abs(uy)) < 1e-14
