@@ -55,7 +55,9 @@ def parse():
                     help="sweep: 7 cylinder cases of 1024^2 (the headline); throat: 8 replicas of the "
                          "2048x512 throat channel; porous: 4096x2048 porous medium with inlet/outflow; "
                          "ensemble: 256 uneven cases + the 4096x256 co-current channel; compare: the "
-                         "sweep under the improved and the original scheme (14 cases)")
+                         "sweep under the improved and the original scheme (14 cases); obstacle: 64 "
+                         "replicas of the 350x150 square-obstacle channel (Poiseuille inlet); couette: "
+                         "512 replicas of the 50x100 two-layer Couette channel (sliding walls)")
     ap.add_argument("--n", type=int, default=1024, help="sweep: lattice side of each case")
     ap.add_argument("--size", default=None, help="throat / porous: lattice WxH (default 2048x512 / 4096x2048)")
     ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
@@ -66,7 +68,7 @@ def parse():
     return ap.parse_args()
 
 
-WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare")
+WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare", "obstacle", "couette")
 
 
 def workload(args, rank=0):
@@ -89,6 +91,13 @@ def workload(args, rank=0):
         return S.ensemble_cases(256, seed=5 + 1000 * rank) + [S.cocurrent_channel(seed=6 + 1000 * rank)], \
             ("uneven ensemble per GPU: 256 square cases n=64..512 (flat wall / cylinder, lambda 0.22..2.17) "
              "+ the 4096x256 co-current channel")
+    if args.workload == "obstacle":
+        return [S.square_obstacle_channel(seed=8 + 100 * j + 1000 * rank) for j in range(64)], \
+            ("square-obstacle microchannel, 64 replicas of 350x150 per GPU (Poiseuille inlet Re=7.5, outflow, "
+             "square side 25, droplet r=25, theta 30.2 deg)")
+    if args.workload == "couette":
+        return [S.couette_channel(seed=7 + 100 * j + 1000 * rank) for j in range(512)], \
+            "two-layer Couette flow, 512 replicas of 50x100 per GPU (walls sliding at -/+0.005)"
     angles = (30, 50, 70, 90, 110, 130, 150)[: args.cases]
     if args.workload == "compare":
         return S.scheme_comparison(n=args.n, seed=2 + 1000 * rank, angles=angles), \
@@ -375,8 +384,10 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h,
                "step": "lbm_set_densities (host) for every case, lbm_step(%d), lbm_fields (host) for every case" % args.inner}
 
-    # step kernels + (fields pass + per-case reduction) + per measured case (fields pass + 4 x 2 passes)
-    launches = args.inner + 2 + 9 * sum(1 for sf in surfaces if sf is not None)
+    # step kernels (+ the sliding-wall fix-up after each step where walls slide) + (fields pass +
+    # per-case reductions) + batched contact angle (density pass + 4 x 2 passes) when any case has a surface
+    sliding = any(tuple(c.u_wall) != (0.0, 0.0) for c in cases)
+    launches = args.inner * (2 if sliding else 1) + 2 + (9 if any(sf is not None for sf in surfaces) else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -64,6 +64,13 @@ typedef struct {
     int32_t bc_y;   /* LBM_BC_PERIODIC or LBM_BC_WALL */
 } lbm_grid;
 
+/* Velocity profile of the open inlet (Sec. 3.3). */
+typedef enum {
+    LBM_INLET_UNIFORM = 0,   /* u_in on every row */
+    LBM_INLET_POISEUILLE = 1 /* u_in 4 s (ny - s) / ny^2, s = y + 1/2: peak u_in, zero at walls half a
+                                cell below row 0 and above row ny-1 (needs bc_y = LBM_BC_WALL) */
+} lbm_inlet_profile;
+
 /* Solid-fluid interaction scheme (Sec. 2.3). */
 typedef enum {
     LBM_ADS_ORIGINAL = 0, /* Eq. 9 with constant G_w1 = lambda * G_w2 */
@@ -83,6 +90,13 @@ typedef struct {
     double rho_in[2];     /* component densities imposed at the inlet (LBM_BC_OPEN) */
     double rho0_store[2]; /* reference densities of the shifted 16-bit storage modes: populations
                              are stored as f_i^k - w_i rho0_store[k]; ignored for FP32/FP64 */
+    double u_wall[2];     /* x-velocity of the lower and upper wall when bc_y = LBM_BC_WALL (the
+                             walls lie half a cell below row 0 and above row ny-1); links across
+                             them bounce back with the wall's momentum, 2 w_i rho_k (e_i . u_w) / c_s^2,
+                             rho_k the node's density (Sec. 3.1 Couette flow).  0, 0: resting walls.
+                             Nonzero needs bc_y = LBM_BC_WALL and bc_x != LBM_BC_OPEN */
+    int32_t inlet_profile; /* lbm_inlet_profile (LBM_BC_OPEN) */
+    int32_t pad_;
 } lbm_params;
 
 /* Storage and arithmetic precision of the populations. */

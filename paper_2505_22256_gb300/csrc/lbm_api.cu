@@ -74,6 +74,13 @@ lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_para
     if (!finite(p->lambda) || p->lambda <= 0.0) return fail(LBM_EINVAL, "case %d: lambda must be > 0", idx);
     if (!finite(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return fail(LBM_EINVAL, "case %d: delta must lie in (0, 1]", idx);
     if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return fail(LBM_EINVAL, "case %d: bad mode", idx);
+    if (p->inlet_profile != LBM_INLET_UNIFORM && p->inlet_profile != LBM_INLET_POISEUILLE)
+        return fail(LBM_EINVAL, "case %d: bad inlet profile", idx);
+    if (p->inlet_profile == LBM_INLET_POISEUILLE && (g->bc_x != LBM_BC_OPEN || g->bc_y != LBM_BC_WALL))
+        return fail(LBM_EINVAL, "case %d: the Poiseuille inlet needs an open x and walled y", idx);
+    if (!finite(p->u_wall[0]) || !finite(p->u_wall[1])) return fail(LBM_EINVAL, "case %d: non-finite wall velocity", idx);
+    if ((p->u_wall[0] != 0.0 || p->u_wall[1] != 0.0) && (g->bc_y != LBM_BC_WALL || g->bc_x == LBM_BC_OPEN))
+        return fail(LBM_EINVAL, "case %d: sliding walls need a walled y and a closed x", idx);
     if (g->bc_x == LBM_BC_OPEN && (p->rho_in[0] <= 0.0 || p->rho_in[1] <= 0.0))
         return fail(LBM_EINVAL, "case %d: inlet densities must be > 0", idx);
     const long long N = (long long)g->nx * g->ny;
@@ -115,6 +122,9 @@ DevCase make_desc(const lbm_grid& g, const lbm_params& p) {
     d.t2 = 2.0 * (l - 1.0) / (dl * (1.0 + l));            // t'_2
     d.t3 = (l - 1.0) / (dl * dl * (1.0 + l));             // t'_3
     d.u_in = p.u_in;
+    d.u_wall[0] = p.u_wall[0];
+    d.u_wall[1] = p.u_wall[1];
+    d.inlet_profile = p.inlet_profile;
     return d;
 }
 
@@ -317,7 +327,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.tmaps, c.err, c.sched, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -461,6 +471,21 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
     for (auto p : offs)
         if (p) cudaFree(p);
     if (st != LBM_OK) return bail(st);
+
+    // cases whose walls slide get the sliding-wall fix-up after every step
+    {
+        std::vector<int> sl;
+        for (int i = 0; i < ncases; ++i)
+            if (c.hcases[i].pf.moving) {
+                sl.push_back(i);
+                c.slide_max_nx = std::max(c.slide_max_nx, c.hcases[i].nx);
+            }
+        c.slide_n = (int)sl.size();
+        if (c.slide_n) {
+            STEP(dalloc(c, &c.slide_list, sl.size()), "sliding-wall list");
+            STEP(cudaMemcpy(c.slide_list, sl.data(), sl.size() * sizeof(int), cudaMemcpyHostToDevice), "sliding-wall list");
+        }
+    }
 
     // work list and launch shape; the wall-list correction is inlined where wall-list nodes are
     // common (more than 4 % of the fluid nodes), called out of line otherwise

@@ -77,6 +77,10 @@ struct CaseParams {
     R gx, gy;
     R d1[2], d5[2];            // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
     R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
+    int inlet_profile;         // 1: the inlet differences above scale with 4 s (ny - s) / ny^2, s = y + 1/2
+    int moving;                // 1: a walled y edge slides (u_wall nonzero)
+    R prof_c;                  // 4 / ny^2
+    R uw[2];                   // x-velocity of the lower / upper wall
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -99,6 +103,8 @@ struct DevCase {
     double g[2];
     double u_in, rho_in[2];
     double rho0[2];         // storage shift per component
+    double u_wall[2];       // x-velocity of the lower / upper wall of a walled y direction
+    int inlet_profile;      // 0 uniform, 1 Poiseuille (peak u_in)
     CaseParams<float> pf;   // the above in FP32 and FP64 (filled by fill_case_params)
     CaseParams<double> pd;
 };
@@ -120,6 +126,11 @@ inline void fill_case_params_as(const DevCase& d, CaseParams<R>& P) {
     P.G = (R)d.G; P.Gw2 = (R)d.Gw2; P.lam = (R)d.lam; P.delta = (R)d.delta;
     P.s1 = (R)d.s1; P.s2 = (R)d.s2; P.s3 = (R)d.s3; P.t2 = (R)d.t2; P.t3 = (R)d.t3;
     P.gx = (R)d.g[0]; P.gy = (R)d.g[1];
+    P.inlet_profile = d.inlet_profile;
+    P.moving = (d.bc_y == kWall && (d.u_wall[0] != 0.0 || d.u_wall[1] != 0.0)) ? 1 : 0;
+    P.prof_c = (R)(4.0 / ((double)d.ny * (double)d.ny));
+    P.uw[0] = (R)d.u_wall[0];
+    P.uw[1] = (R)d.u_wall[1];
 }
 
 inline void fill_case_params(DevCase& d) {

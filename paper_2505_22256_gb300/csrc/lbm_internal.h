@@ -59,6 +59,9 @@ struct Ctx {
     int block_threads = 128;
     int block_rows = 0;              // 0: automatic
     int wall_inline = 0;             // step kernel variant: wall-list correction inline (1) or called (0)
+    int* slide_list = nullptr;       // cases with sliding walls (device), fixed up after each step
+    int slide_n = 0;
+    int slide_max_nx = 0;
     int rows_used = 0;
     int grid_blocks = 0;
     int4* items = nullptr;

@@ -97,13 +97,14 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v)
 
 // ------------------------------------------------------------------------------------------------
 // Pull of one node's 18 populations.  rm / r0 / rp point at the rows y-1, y, y+1 (plane stride ps,
-// column c of the node); used with the shared-memory row slots (step kernel) and with global
-// memory (state read-back).  The plain form assumes no blocked link and no open column.
+// column c of the node, lattice row y); used with the shared-memory row slots (step kernel) and
+// with global memory (state read-back).  The plain form assumes no blocked link and no open column.
+// Pin: the rarely used constants (inlet, sliding walls).
 // ------------------------------------------------------------------------------------------------
 template <bool kGeneral, class S, class R>
 __device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restrict__ r0, const S* __restrict__ rp,
                                      long long ps, int c, uint16_t fl, bool inlet, bool outlet, const Params<R>& P,
-                                     const Params<R>& Pin, R (&f)[18]) {
+                                     const Params<R>& Pin, int y, R (&f)[18]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const S* src;
@@ -134,12 +135,17 @@ __device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restri
         f[i] = va;
         f[9 + i] = vb;
     }
-    if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in, 0))
+    if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in(y), 0))
+        R sc = (R)1;
+        if (Pin.inlet_profile) {  // Poiseuille profile of peak u_in (Sec. 3.3)
+            const R s = (R)y + (R)0.5;
+            sc = Pin.prof_c * s * ((R)Pin.ny - s);
+        }
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            f[9 * k + 1] = f[9 * k + 3] + Pin.d1[k];
-            f[9 * k + 5] = f[9 * k + 7] + Pin.d5[k];
-            f[9 * k + 8] = f[9 * k + 6] + Pin.d5[k];
+            f[9 * k + 1] = f[9 * k + 3] + Pin.d1[k] * sc;
+            f[9 * k + 5] = f[9 * k + 7] + Pin.d5[k] * sc;
+            f[9 * k + 8] = f[9 * k + 6] + Pin.d5[k] * sc;
         }
     }
 }
@@ -506,8 +512,8 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 const S* rm = reinterpret_cast<const S*>(slot_back(dir > 0 ? 2 : 0));
                 const S* r0 = reinterpret_cast<const S*>(s0);
                 const S* rp = reinterpret_cast<const S*>(slot_back(dir > 0 ? 0 : 2));
-                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, st.f);
-                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, st.f);
+                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
+                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 // rho_k = sum_i f_i as a balanced tree (short dependency chains)
                 const R* f = st.f;
                 ra = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + (f[7] + f[8])));
@@ -747,6 +753,57 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
 }
 
 // ------------------------------------------------------------------------------------------------
+// Sliding walls (Sec. 3.1, Couette flow), applied to a freshly written post-collision buffer.  At a
+// node of row 0 (ny-1) of a walled y, the diagonals 7, 8 (5, 6) leave across the wall and come back
+// only to the node itself, by halfway bounce-back, as f_opp(i) = f*_i + 2 w rho_k (e_opp(i) . u_w) /
+// c_s^2 with rho_k = sum_j f*_j at the node.  Storing them reflected lets the pull take every
+// bounce-back as it is, so the step kernel carries no code for it.  One thread per column of the
+// two wall rows of each listed case (blockIdx.y = 2 * list index + upper); ghost copies of periodic
+// x are rewritten with the node.
+// ------------------------------------------------------------------------------------------------
+template <class S>
+__global__ void k_sliding_walls(const DevCase* __restrict__ cases, const int* __restrict__ list,
+                                const uint16_t* __restrict__ flags_all, S* __restrict__ buf_all) {
+    using R = typename ComputeOf<S>::type;
+    constexpr int G = Layout<S>::G;
+    const int ci = list[blockIdx.y >> 1];
+    const bool upper = blockIdx.y & 1;
+    const DevCase& C = cases[ci];
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= C.nx) return;
+    const int Y = upper ? C.ny - 1 : 0;
+    if (flags_all[C.d_off + (long long)Y * C.nx + X] & kSolidBit) return;
+    const double uw = upper ? C.u_wall[1] : C.u_wall[0];
+    if (uw == 0.0) return;
+    const long long plane = (long long)C.ny * C.pitch;
+    S* p = buf_all + C.f_off + (long long)Y * C.pitch + X + G;
+    const int ip = upper ? 6 : 7, im = upper ? 5 : 8;  // returning as e_x = +1 / -1
+    for (int k = 0; k < 2; ++k) {
+        R v[9];
+        R rho = (R)0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            v[j] = sload<S, R>(p + (long long)(9 * k + j) * plane);
+            if constexpr (Store<S>::kShift) v[j] += (R)(wq(j) * C.rho0[k]);
+            rho += v[j];
+        }
+        const R a = (R)(6.0 * wq(5)) * rho * (R)uw;
+        const R nv[2] = {v[ip] + a, v[im] - a};
+        const int q[2] = {ip, im};
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            R o = nv[m];
+            if constexpr (Store<S>::kShift) o -= (R)(wq(q[m]) * C.rho0[k]);
+            const S sv = to_store<S, R>(o);
+            S* pq = p + (long long)(9 * k + q[m]) * plane;
+            *pq = sv;
+            if (C.bc_x == kPeriodic && X < G) pq[C.nx] = sv;
+            if (C.bc_x == kPeriodic && X >= C.nx - G) pq[-C.nx] = sv;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // State transfer kernels (dense doubles [2][9][ny][nx] <-> the post-collision buffer)
 // ------------------------------------------------------------------------------------------------
 __global__ void k_feq_rest(const DevCase* __restrict__ cases, int c, const uint8_t* __restrict__ solid_all,
@@ -781,6 +838,7 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
         const uint16_t fl = flags_all[C.d_off + s];
         const long long o = (long long)Y * C.pitch + X + G;
         for (int k = 0; k < 2; ++k) {
+            double vs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 double v = 0.0;
@@ -798,6 +856,13 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
                         ty -= (ty >= C.ny) ? C.ny : 0;
                         v = f[(long long)(9 * k + i) * N + (long long)ty * C.nx + tx];
                     }
+                }
+                vs[i] = v;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                double v = vs[i];
+                if (!(fl & kSolidBit)) {
                     if constexpr (Store<S>::kShift) v -= wq(i) * C.rho0[k];
                 }
                 const S sv = to_store<S, R>((R)v);
@@ -834,7 +899,7 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
             const int yp = Y + 1 >= C.ny ? (C.bc_y == kPeriodic ? 0 : C.ny - 1) : Y + 1;
             const bool inlet = C.bc_x == kOpen && X == 0, outlet = C.bc_x == kOpen && X == C.nx - 1;
             pull<true, S, R>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch, fin + (long long)yp * C.pitch,
-                             P.plane, X + G, fl, inlet, outlet, P, P, v);
+                             P.plane, X + G, fl, inlet, outlet, P, P, Y, v);
         }
 #pragma unroll
         for (int q = 0; q < 18; ++q) f[(long long)q * N + s] = (double)v[q];
@@ -970,7 +1035,16 @@ cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s) {
     StepArgs a = make_args(c, 0, c.nitems, o4, nullptr);
     a.in_buf = in_buf;
     a.fout = c.f[1 - in_buf];
-    return dispatch(c, a, s, false, c.grid_blocks);
+    cudaError_t e = dispatch(c, a, s, false, c.grid_blocks);
+    if (e != cudaSuccess || c.slide_n == 0) return e;
+    const dim3 grid((unsigned)((c.slide_max_nx + 127) / 128), (unsigned)(2 * c.slide_n));
+    switch (c.storage) {
+        case LBM_STORE_F64: k_sliding_walls<double><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (double*)a.fout); break;
+        case LBM_STORE_F32: k_sliding_walls<float><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (float*)a.fout); break;
+        case LBM_STORE_F16_SHIFTED: k_sliding_walls<__half><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (__half*)a.fout); break;
+        default: k_sliding_walls<__nv_bfloat16><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (__nv_bfloat16*)a.fout); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fields(Ctx& c, int ci, double* rhoA, double* rhoB, double* ux, double* uy, bool diag) {

@@ -42,7 +42,8 @@ class lbm_grid(ctypes.Structure):
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("lambda_", c_double),
                 ("G_w2", c_double), ("delta", c_double), ("g", c_double * 2), ("u_in", c_double),
-                ("rho_in", c_double * 2), ("rho0_store", c_double * 2)]
+                ("rho_in", c_double * 2), ("rho0_store", c_double * 2), ("u_wall", c_double * 2),
+                ("inlet_profile", c_int32), ("pad_", c_int32)]
 
 
 class lbm_diag(ctypes.Structure):
@@ -154,8 +155,12 @@ def _host(a, dtype) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+INLET = {"uniform": 0, "poiseuille": 1}
+
+
 def make_params(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8, g=(0.0, 0.0),
-                u_in=0.0, rho_in=(1.0, 0.03), rho0_store=(0.0, 0.0), **_ignored) -> lbm_params:
+                u_in=0.0, rho_in=(1.0, 0.03), rho0_store=(0.0, 0.0), u_wall=(0.0, 0.0), inlet_profile="uniform",
+                **_ignored) -> lbm_params:
     p = lbm_params()
     p.tau[0], p.tau[1] = tau
     p.G_AB = G
@@ -167,6 +172,8 @@ def make_params(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, d
     p.u_in = u_in
     p.rho_in[0], p.rho_in[1] = rho_in
     p.rho0_store[0], p.rho0_store[1] = rho0_store
+    p.u_wall[0], p.u_wall[1] = u_wall
+    p.inlet_profile = INLET[inlet_profile]
     return p
 
 

@@ -89,6 +89,8 @@ class Scenario:
     g: tuple = (0.0, 0.0)
     u_in: float = 0.0
     rho_in: tuple = (RHO_M, RHO_D)
+    u_wall: tuple = (0.0, 0.0)         # x-velocity of the lower / upper wall (bc_y = wall)
+    inlet_profile: str = "uniform"     # uniform | poiseuille (open x)
     surface: dict | None = None  # for the contact angle: {"kind": "flat"|"circle", ...}
     # 16-bit storage keeps f_i - w_i rho0 per component; the dissolved-phase density serves both
     # phases best (ignored by FP32 / FP64 storage)
@@ -106,7 +108,8 @@ class Scenario:
     def params(self) -> dict:
         return dict(bc_x=self.bc_x, bc_y=self.bc_y, scheme=self.scheme, tau=tuple(self.tau),
                     G=self.G, lam=self.lam, Gw2=self.Gw2, delta=self.delta, g=tuple(self.g),
-                    u_in=self.u_in, rho_in=tuple(self.rho_in))
+                    u_in=self.u_in, rho_in=tuple(self.rho_in), u_wall=tuple(self.u_wall),
+                    inlet_profile=self.inlet_profile)
 
 
 def _grid(ny, nx):
@@ -261,6 +264,45 @@ def cocurrent_channel(nx: int = 4096, ny: int = 256, frac_A: float = 0.4, g: flo
     lam = lambda_for_angle(120.0) if lam is None else lam
     return Scenario(f"cocurrent_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
                     g=(g, 0.0), lam=lam, G=G)
+
+
+NU_SEC3 = 0.17                   # kinematic viscosity of both fluids in Secs. 3.1 and 3.3
+TAU_SEC3 = 3.0 * NU_SEC3 + 0.5    # nu = c_s^2 (tau - 1/2)
+
+
+def couette_channel(nx: int = 50, ny: int = 100, U: float = 0.005, lam: float | None = None,
+                    seed: int = 7, G: float = G_DEFAULT, scheme: str = "improved",
+                    amp: float = NOISE_AMP) -> Scenario:
+    """Two-layer Couette flow (Sec. 3.1, Fig. 3b): x periodic, walls half a cell below row 0 and
+    above row ny-1 sliding at -U (lower) and +U (upper); A in the central half of the channel
+    (|y - H/2| <= H/4), B next to both walls; nu = 0.17 for both fluids."""
+    y, x = _grid(ny, nx)
+    solid = np.zeros((ny, nx), np.uint8)
+    s = y + 0.5
+    inside = np.abs(s - ny / 2.0) <= ny / 4.0
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    lam = lambda_for_angle(90.0) if lam is None else lam
+    return Scenario(f"couette_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall", scheme=scheme,
+                    tau=(TAU_SEC3, TAU_SEC3), G=G, lam=lam, u_wall=(-U, U))
+
+
+def square_obstacle_channel(nx: int = 350, ny: int = 150, side: int = 25, center=(122, 75), r: float = 25.0,
+                            drop=(55, 75), Re: float = 7.5, theta: float = 30.2, seed: int = 8,
+                            G: float = G_DEFAULT, scheme: str = "improved", amp: float = NOISE_AMP) -> Scenario:
+    """Droplet driven past a square obstacle in a microchannel (Sec. 3.3, Fig. 12): walls half a
+    cell below row 0 and above row ny-1; a square of the given side centred at ``center``; a
+    droplet of A (radius r) at ``drop``, B elsewhere; a velocity inlet at x = 0 with the Poiseuille
+    profile of peak U_m (fluid B enters), outflow at x = nx-1; nu = 0.17; lambda for the static
+    angle ``theta`` on the square.  U_m from Re = U_m (2 r) / nu."""
+    y, x = _grid(ny, nx)
+    h = side / 2.0
+    solid = ((np.abs(x - center[0]) < h) & (np.abs(y - center[1]) < h)).astype(np.uint8)
+    inside = (x - drop[0]) ** 2 + (y - drop[1]) ** 2 <= r * r
+    rA, rB = _phase_fields(inside, solid, seed, amp)
+    Um = Re * NU_SEC3 / (2.0 * r)
+    return Scenario(f"square_obstacle_{nx}x{ny}", solid, rA, rB, bc_x="open", bc_y="wall", scheme=scheme,
+                    tau=(TAU_SEC3, TAU_SEC3), G=G, lam=lambda_for_angle(theta), u_in=Um,
+                    rho_in=(RHO_D, RHO_M), inlet_profile="poiseuille")
 
 
 def ensemble_cases(ncases: int = 256, nmin: int = 64, nmax: int = 512, seed: int = 5,

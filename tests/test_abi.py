@@ -4,6 +4,7 @@ absence of a GB300 as LBM_ECUDA (there is no CPU fallback)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -40,13 +41,29 @@ def test_library_exports_every_declared_symbol(lbm):
     assert sorted(lbm.SYMBOLS) == _declared_functions()
 
 
-def test_struct_layouts_match_header(lbm):
-    assert ctypes.sizeof(lbm.lbm_grid) == 16
-    assert ctypes.sizeof(lbm.lbm_params) == 8 * 13 + 8   # int32 mode padded to 8
-    assert lbm.lbm_params.lambda_.offset == 32
-    assert ctypes.sizeof(lbm.lbm_diag) == 9 * 8 + 8 + 8
-    assert ctypes.sizeof(lbm.lbm_surface) == 8 + 4 * 8
-    assert ctypes.sizeof(lbm.lbm_info_t) == 8 + 6 * 8 + 24
+def test_struct_layouts_match_header(lbm, tmp_path):
+    """Every field of the binding's ctypes structures sits at the offset the C compiler gives the
+    header's struct (gcc, offsetof / sizeof), so layout changes cannot drift apart."""
+    structs = {"lbm_grid": lbm.lbm_grid, "lbm_params": lbm.lbm_params, "lbm_diag": lbm.lbm_diag,
+               "lbm_surface": lbm.lbm_surface, "lbm_info_t": lbm.lbm_info_t, "lbm_case": lbm.lbm_case}
+    c_names = {"lambda_": "lambda"}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            cf = c_names.get(fname, fname)
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {cf}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
 
 
 def _case(n=16):
@@ -67,6 +84,26 @@ def test_invalid_parameters_are_rejected(lbm, field, value):
         setattr(p, field, value)
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(lbm.make_grid(16, 16), solid, p, a, b)
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("bc_x,bc_y,field,value", [
+    ("periodic", "wall", "inlet_profile", 2),           # no such profile
+    ("periodic", "wall", "inlet_profile", 1),           # the Poiseuille inlet needs an open x
+    ("open", "periodic", "inlet_profile", 1),           # ... and walls in y
+    ("periodic", "periodic", "u_wall", (0.01, 0.0)),    # sliding walls need walls in y
+    ("open", "wall", "u_wall", (0.0, 0.01)),            # ... and a closed x
+    ("periodic", "wall", "u_wall", (float("inf"), 0.0)),
+])
+def test_inlet_profile_and_sliding_wall_parameters_are_checked(lbm, bc_x, bc_y, field, value):
+    solid, a, b = _case()
+    p = lbm.make_params()
+    if field == "u_wall":
+        p.u_wall[0], p.u_wall[1] = value
+    else:
+        p.inlet_profile = value
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_grid(16, 16, bc_x, bc_y), solid, p, a, b)
     assert e.value.status == lbm.LBM_EINVAL
 
 

@@ -58,6 +58,9 @@ SCENARIOS = {
     "porous_open": small_porous,
     "original_cyl": lambda: S.cylinder_droplet(96, lam=0.5, scheme="original"),
     "pillar8": pillar_case,
+    "couette_sliding": lambda: S.couette_channel(nx=40, ny=48, U=0.01),
+    "square_obstacle_small": lambda: S.square_obstacle_channel(nx=140, ny=60, side=10, center=(49, 30), r=10.0,
+                                                               drop=(22, 30)),
     "gw2_equals_G": lambda: S.Scenario(**{**S.cylinder_droplet(64, lam=0.7).__dict__, "Gw2": None}),
 }
 
@@ -86,7 +89,7 @@ def test_wall_list_bit_exact(name):
 # ---------------------------------------------------------------------------------------------
 # state transfer
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "pillar8"])
+@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "pillar8", "couette_sliding", "square_obstacle_small"])
 def test_initial_state_and_roundtrip(name):
     sc = SCENARIOS[name]()
     cfg = ocfg(sc)
@@ -150,6 +153,38 @@ def test_f32_one_step_from_developed_state(name):
     scale = np.abs(o).max(axis=(2, 3), keepdims=True)
     assert np.max(np.abs(g - o) / scale) <= 2e-6
     lat.close()
+
+
+@pytest.mark.parametrize("storage,atol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_single_phase_couette_reaches_the_linear_profile(storage, atol):
+    """Sec. 3.1's sliding walls on the GPU: single phase (G = 0) between walls at -U and +U, the
+    steady state is the exact linear Couette profile (as the oracle's pin)."""
+    nx, ny, U = 8, 16, 0.01
+    solid = np.zeros((ny, nx), np.uint8)
+    sc = S.Scenario("couette_single", solid, np.ones((ny, nx)), np.full((ny, nx), 1e-3), bc_x="periodic",
+                    bc_y="wall", G=0.0, Gw2=0.0, u_wall=(-U, U))
+    lat = lbm.Lattice(sc, storage)
+    lat.step(3000)
+    _, _, ux, uy = lat.fields()
+    lat.close()
+    s = np.arange(ny) + 0.5
+    exact = -U + 2 * U * s / ny
+    np.testing.assert_allclose(ux, np.repeat(exact[:, None], nx, axis=1), rtol=0, atol=atol)
+    assert np.max(np.abs(uy)) < atol
+
+
+def test_square_obstacle_350x150_matches_oracle():
+    """Sec. 3.3's case at its own size (Poiseuille inlet, outflow, square obstacle, droplet):
+    FP32 after 100 steps within the stated bar."""
+    sc = S.square_obstacle_channel()
+    cfg, f = orun(sc, 100)
+    o = oracle.fields(cfg, sc.solid, f)
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(100)
+    g = lat.fields()
+    lat.close()
+    assert rel_rho(g, o, sc.solid) <= 1e-5
+    assert max(np.max(np.abs(g[2] - o[2])), np.max(np.abs(g[3] - o[3]))) <= 1e-6
 
 
 def test_fields_and_diagnostics_match_oracle():
