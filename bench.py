@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -294,6 +295,9 @@ def run_ours(args):
     surfaces = [c.surface for c in cases]
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(cases, storage=args.storage, cuda_stream=stream.cuda_stream)
+    # launch shape (row-chunk height, wall-list path) picked by the library's autotuner on the live
+    # state, before the timed region
+    tuned_ms = None if args.no_autotune else lbm.lbm_autotune(lat.ctx, 4)
     info = lat.info()
     nodes = info["nodes"]
     fluid = info["fluid_nodes"]
@@ -395,6 +399,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_step",
                      "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
+        "launch": {"block_threads": info["block_threads"], "block_rows": info["block_rows"],
+                   "grid_blocks": info["grid_blocks"], "work_items": info["work_items"],
+                   "wall_inline": info["wall_inline"], "autotuned": tuned_ms is not None,
+                   "autotune_best_ms": tuned_ms},
         "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
         **({"scheme_comparison": [{"case": c.name, "lambda": c.lam, "scheme": c.scheme, "theta_deg": t,
