@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_geometry.cu", "lbm_contact.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_geometry.cu", "lbm_contact.cu", "lbm_noalloc.cu", "lbm3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
 

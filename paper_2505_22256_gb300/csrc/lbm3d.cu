@@ -1,0 +1,855 @@
+// Three-dimensional form of the time step (arXiv 2505.22256, Sec. 3.5) and its C ABI
+// (include/lbm3d.h).
+//
+// State: the post-collision populations f*_i^k of one lattice, SoA [2][19][N] in the storage /
+// compute type R (float or double), N = nx ny nz, x fastest; two buffers.  One time step is two
+// launches:
+//   k3_rho    pull f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link (halfway
+//             bounce-back, Sec. 3.5); rho_k = sum_i f_i (Eq. 3) into two density arrays
+//   k3_step   the same pull for the node's own populations and momentum (Eq. 4); cohesion (Eq. 8)
+//             and adhesion (Eq. 9, local parameter of Eqs. 10-12) on the 92-offset eighth-order
+//             stencil read from the density arrays -- nodes with a solid node inside the stencil
+//             apply the second-layer copy x + sign(e) (Sec. 2.4) and the solid switch; body force;
+//             velocity with Guo's half-force shift (Eq. 5); SRT collision with Guo forcing (Eqs. 1,
+//             2, 6, 7) written to the other buffer.  Its fields form writes rho and u in FP64 and
+//             per-block diagnostic sums instead of colliding.
+// The density arrays (2 R per node) are small enough to stay largely in L2 while k3_step reads
+// its stencil from them.  Periodic in x, y and z.
+#include <math.h>
+#include <stdarg.h>
+
+#include <mutex>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "../../include/lbm3d.h"
+
+namespace lbm {
+lbm_status report_error(lbm_status s, const char* fmt, ...);
+}
+
+using namespace lbm;
+
+namespace {
+
+// D3Q19: 0 rest; 1..6 = +x, -x, +y, -y, +z, -z; 7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0),
+// (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1)
+__host__ __device__ __forceinline__ constexpr int e3x(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int e3y(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1 : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int e3z(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1 : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp3(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
+__host__ __device__ __forceinline__ constexpr double w19(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+// eighth-order stencil weights by |e|^2 (0: not in the stencil)
+__host__ __device__ __forceinline__ constexpr double w92(int q) {
+    return q == 1 ? 4.0 / 45.0 : q == 2 ? 1.0 / 21.0 : q == 3 ? 2.0 / 105.0 : q == 4 ? 5.0 / 504.0
+         : q == 5 ? 1.0 / 315.0 : q == 6 ? 1.0 / 630.0 : q == 8 ? 1.0 / 5040.0 : 0.0;
+}
+
+// node flags: bits 0..17 link i = bit+1 blocked (x - e_i solid); 18 solid; 19 a solid node lies in
+// the 92-offset stencil; 20 a solid node within three cells (Chebyshev; contact-angle exclusion)
+constexpr uint32_t k3Solid = 1u << 18;
+constexpr uint32_t k3Wall = 1u << 19;
+constexpr uint32_t k3Near = 1u << 20;
+
+struct Geo3 {
+    int nx, ny, nz;
+    long long N;
+};
+
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ long long site(const Geo3& g, int x, int y, int z) {
+    return ((long long)wrapc(z, g.nz) * g.ny + wrapc(y, g.ny)) * g.nx + wrapc(x, g.nx);
+}
+
+template <class R>
+struct P3 {
+    R omega[2], cF[2], G, Gw2, lam, delta, s1, s2, s3, t2, t3, g[3];
+    int mode;
+};
+
+__global__ void k3_flags(Geo3 g, const uint8_t* __restrict__ solid, uint32_t* __restrict__ flags) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    uint32_t f = 0;
+    if (solid[s]) f |= k3Solid;
+    for (int i = 1; i < 19; ++i)
+        if (solid[site(g, x - e3x(i), y - e3y(i), z - e3z(i))]) f |= 1u << (i - 1);
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                if (!solid[site(g, x + dx, y + dy, z + dz)]) continue;
+                f |= k3Near;
+                const int q = dx * dx + dy * dy + dz * dz;
+                if (dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2 && w92(q) != 0.0) f |= k3Wall;
+            }
+    flags[s] = f;
+}
+
+// the node's 38 post-streaming populations
+template <class R>
+__device__ __forceinline__ void pull3(const Geo3& g, const R* __restrict__ fs, uint32_t fl, int x, int y, int z,
+                                      long long s, R (&f)[38]) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        long long src;
+        int q;
+        if (i > 0 && ((fl >> (i - 1)) & 1u)) {
+            src = s;
+            q = opp3(i);
+        } else {
+            src = i == 0 ? s : site(g, x - e3x(i), y - e3y(i), z - e3z(i));
+            q = i;
+        }
+        f[i] = fs[(long long)q * g.N + src];
+        f[19 + i] = fs[(long long)(19 + q) * g.N + src];
+    }
+}
+
+// sum of the 19 populations of one component as a balanced tree (rounding grows with the depth,
+// not the count)
+template <class R>
+__device__ __forceinline__ R sum19(const R* f) {
+    const R a = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]));
+    const R b = ((f[8] + f[9]) + (f[10] + f[11])) + ((f[12] + f[13]) + (f[14] + f[15]));
+    return (a + b) + (f[16] + (f[17] + f[18]));
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
+                                              R* __restrict__ rhoA, R* __restrict__ rhoB) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const uint32_t fl = flags[s];
+    R a = (R)0, b = (R)0;
+    if (!(fl & k3Solid)) {
+        R f[38];
+        pull3<R>(g, fs, fl, x, y, z, s, f);
+        a = sum19<R>(f);
+        b = sum19<R>(f + 19);
+    }
+    rhoA[s] = a;
+    rhoB[s] = b;
+}
+
+constexpr int k3DiagN = 12;  // mass A, mass B, mom x, y, z, umax, rhoA min/max, rhoB min/max, n, unstable
+
+__device__ __forceinline__ double d3_combine(int q, double a, double b) {
+    if (q == 5 || q == 7 || q == 9) return fmax(a, b);
+    if (q == 6 || q == 8) return fmin(a, b);
+    if (q == 11) return fmax(a, b);
+    return a + b;
+}
+__device__ __forceinline__ double d3_neutral(int q) {
+    return (q == 6 || q == 8) ? INFINITY : (q == 7 || q == 9) ? -INFINITY : 0.0;
+}
+
+// One node per thread.  kFields: write rho_A, rho_B, u (FP64) and per-block diagnostic records
+// (block index blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
+template <class R, bool kFields>
+__global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
+                                               const uint8_t* __restrict__ solid, const R* __restrict__ fs,
+                                               const R* __restrict__ rhoA, const R* __restrict__ rhoB,
+                                               R* __restrict__ fout, double* __restrict__ o5, double* __restrict__ part) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const bool in = x < g.nx;
+    const long long s = ((long long)z * g.ny + y) * g.nx + (in ? x : 0);
+    const uint32_t fl = in ? flags[s] : k3Solid;
+    double rec[k3DiagN];
+    if constexpr (kFields)
+        for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
+    if (!(fl & k3Solid)) {
+        R f[38];
+        pull3<R>(g, fs, fl, x, y, z, s, f);
+        // momentum from the differences of opposite populations (i odd, opp(i) = i + 1)
+        R m[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const R t = (f[i] - f[i + 1]) + (f[19 + i] - f[20 + i]);
+            m[0] += e3x(i) * t;
+            m[1] += e3y(i) * t;
+            m[2] += e3z(i) * t;
+        }
+        const R rA = rhoA[s], rB = rhoB[s];
+        R gA[3] = {(R)0, (R)0, (R)0}, gB[3] = {(R)0, (R)0, (R)0}, ad[3] = {(R)0, (R)0, (R)0};
+        // sums over symmetric pairs (e, -e): w e (psi(x+e) - psi(x-e)), the differences first
+        if (!(fl & k3Wall)) {  // no solid node in the stencil: plain sums (solid density is 0 anyway)
+#pragma unroll
+            for (int dz = 0; dz <= 2; ++dz)
+#pragma unroll
+                for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;  // one of each pair
+                        const int q = dx * dx + dy * dy + dz * dz;
+                        if (w92(q) == 0.0) continue;
+                        const long long np = site(g, x + dx, y + dy, z + dz), nm = site(g, x - dx, y - dy, z - dz);
+                        const R w = (R)w92(q);
+                        const R a = __ldg(rhoA + np) - __ldg(rhoA + nm), b = __ldg(rhoB + np) - __ldg(rhoB + nm);
+                        gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
+                        gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
+                    }
+        } else {  // second-layer copy of x + sign(e) for non-fluid second-layer sites; solid switch
+            for (int dz = 0; dz <= 2; ++dz)
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+                        const int q = dx * dx + dy * dy + dz * dz;
+                        const double wq = w92(q);
+                        if (wq == 0.0) continue;
+                        const bool second = dx == 2 || dx == -2 || dy == 2 || dy == -2 || dz == 2 || dz == -2;
+                        R va[2], vb[2], vs[2];
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            const int sg = side == 0 ? 1 : -1;
+                            const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
+                            long long n = site(g, x + ex, y + ey, z + ez);
+                            if (second && solid[n]) n = site(g, x + (ex > 0) - (ex < 0), y + (ey > 0) - (ey < 0), z + (ez > 0) - (ez < 0));
+                            const bool sol = solid[n] != 0;
+                            va[side] = sol ? (R)0 : rhoA[n];
+                            vb[side] = sol ? (R)0 : rhoB[n];
+                            vs[side] = sol ? (R)1 : (R)0;
+                        }
+                        const R w = (R)wq, a = va[0] - va[1], b = vb[0] - vb[1], sw = vs[0] - vs[1];
+                        gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
+                        gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
+                        ad[0] += w * dx * sw; ad[1] += w * dy * sw; ad[2] += w * dz * sw;
+                    }
+        }
+        R GA = (R)0;
+        if (fl & k3Wall) {
+            if (P.mode == 1) {
+                const R re = (rA - rB) / (rA + rB);
+                R h;
+                if (re > P.delta) h = P.lam;
+                else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
+                else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
+                else h = (R)1;
+                GA = P.Gw2 * h;
+            } else {
+                GA = P.lam * P.Gw2;
+            }
+        }
+        R FA[3], FB[3], u[3];
+        const R rho = rA + rB;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            FA[d] = -P.G * rA * gB[d] - GA * rA * ad[d] + rA * P.g[d];
+            FB[d] = -P.G * rB * gA[d] - P.Gw2 * rB * ad[d] + rB * P.g[d];
+            u[d] = (m[d] + (R)0.5 * (FA[d] + FB[d])) / rho;
+        }
+        if constexpr (kFields) {
+            if (o5) {
+                o5[s] = (double)rA;
+                o5[g.N + s] = (double)rB;
+                o5[2 * g.N + s] = (double)u[0];
+                o5[3 * g.N + s] = (double)u[1];
+                o5[4 * g.N + s] = (double)u[2];
+            }
+            const double dr = (double)rho;
+            rec[0] = (double)rA;
+            rec[1] = (double)rB;
+            rec[2] = dr * (double)u[0];
+            rec[3] = dr * (double)u[1];
+            rec[4] = dr * (double)u[2];
+            const double um = sqrt((double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
+            rec[5] = um;
+            rec[6] = rec[7] = (double)rA;
+            rec[8] = rec[9] = (double)rB;
+            rec[10] = 1.0;
+            rec[11] = (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB)) ? 1.0 : 0.0;
+        } else {
+            const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const R rk = k == 0 ? rA : rB;
+                const R* F = k == 0 ? FA : FB;
+                const R om = P.omega[k], cf = P.cF[k];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    const R eu = e3x(i) * u[0] + e3y(i) * u[1] + e3z(i) * u[2];
+                    const R eF = e3x(i) * F[0] + e3y(i) * F[1] + e3z(i) * F[2];
+                    const R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+                    const R feq = (R)w19(i) * rk * ((R)1 + (R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * usq);
+                    const R Fi = (R)w19(i) * ((R)3 * (eF - uF) + (R)9 * eu * eF);
+                    const R v = f[19 * k + i];
+                    fout[(long long)(19 * k + i) * g.N + s] = v + om * (feq - v) + cf * Fi;
+                }
+            }
+        }
+    } else if (kFields && in && o5) {
+        for (int q = 0; q < 5; ++q) o5[q * g.N + s] = 0.0;
+    }
+    if constexpr (kFields) {
+        __shared__ double red[4][k3DiagN];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int q = 0; q < k3DiagN; ++q) {
+            double v = rec[q];
+            for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (lane == 0) red[warp][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+            for (int q = 0; q < k3DiagN; ++q) {
+                double v = red[0][q];
+                for (int w2 = 1; w2 < 4; ++w2) v = d3_combine(q, v, red[w2][q]);
+                part[b * k3DiagN + q] = v;
+            }
+        }
+    }
+}
+
+// Combine the per-block records in block order (one warp; deterministic).
+__global__ void k3_diag_final(long long nblocks, const double* __restrict__ part, double* __restrict__ out) {
+    const int lane = threadIdx.x;
+    for (int q = 0; q < k3DiagN; ++q) {
+        double v = d3_neutral(q);
+        for (long long b = lane; b < nblocks; b += 32) v = d3_combine(q, v, part[b * k3DiagN + q]);
+        for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (lane == 0) out[q] = v;
+    }
+}
+
+// post-streaming populations (FP64 [2][19][N]) <-> post-collision buffer
+template <class R>
+__global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs, double* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const uint32_t fl = flags[s];
+    R v[38];
+    if (fl & k3Solid) {
+        for (int q = 0; q < 38; ++q) v[q] = (R)0;
+    } else {
+        pull3<R>(g, fs, fl, x, y, z, s, v);
+    }
+    for (int q = 0; q < 38; ++q) f[(long long)q * g.N + s] = (double)v[q];
+}
+
+template <class R>
+__global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ f, R* __restrict__ fs) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const uint32_t fl = flags[s];
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 19; ++i) {
+            double v = 0.0;
+            if (!(fl & k3Solid)) {
+                // f*_i(x) streams to x + e_i; if that node is solid it comes back as f_opp(i)(x)
+                if (i > 0 && ((fl >> (opp3(i) - 1)) & 1u)) v = f[(long long)(19 * k + opp3(i)) * g.N + s];
+                else v = f[(long long)(19 * k + i) * g.N + (i == 0 ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i)))];
+            }
+            fs[(long long)(19 * k + i) * g.N + s] = (R)v;
+        }
+}
+
+template <class R>
+__global__ void k3_feq(Geo3 g, const uint8_t* __restrict__ solid, const double* __restrict__ rA, const double* __restrict__ rB,
+                       double* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const bool sol = solid[s] != 0;
+    for (int i = 0; i < 19; ++i) {
+        f[(long long)i * g.N + s] = sol ? 0.0 : w19(i) * rA[s];
+        f[(long long)(19 + i) * g.N + s] = sol ? 0.0 : w19(i) * rB[s];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Contact angle on a sphere (FP64): interface points, algebraic sphere fit, one Gauss-Newton step
+// ------------------------------------------------------------------------------------------------
+constexpr int kC3Threads = 256;
+constexpr int kC3Blocks = 512;
+constexpr int kC3Vals = 14;
+
+template <class R>
+struct Ca3 {
+    Geo3 g;
+    const uint32_t* flags;
+    const R* rA;
+    const R* rB;
+};
+
+template <class R>
+__device__ __forceinline__ bool ca3_usable(const Ca3<R>& c, long long s) { return (c.flags[s] & (k3Solid | k3Near)) == 0; }
+
+__device__ __forceinline__ double phi3(double a, double b) { return (a - b) / (a + b); }
+__device__ __forceinline__ bool phi3_pos(double a, double b) {
+    const double sum = a + b;
+    return (sum > 0.0 && sum < INFINITY) ? a > b : phi3(a, b) > 0.0;
+}
+
+// st: 0 N, 1-3 centroid, 4-6 centre, 7 r, 8 rms, 9 theta, 10 status (1: too few points)
+template <class R>
+__global__ void k3_ca_pass(Ca3<R> c, int pass, const double* __restrict__ st, double* __restrict__ part) {
+    double acc[kC3Vals];
+    for (int q = 0; q < kC3Vals; ++q) acc[q] = 0.0;
+    const double m0 = st[1], m1 = st[2], m2 = st[3], c0 = st[4], c1 = st[5], c2 = st[6], r = st[7];
+    const Geo3& g = c.g;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.N; s += (long long)gridDim.x * blockDim.x) {
+        if (!ca3_usable(c, s)) continue;
+        const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+        const double ra = (double)c.rA[s], rb = (double)c.rB[s];
+        const bool pa = phi3_pos(ra, rb);
+        for (int axis = 0; axis < 3; ++axis) {
+            const int lim = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+            const int coord = axis == 0 ? x : (axis == 1 ? y : z);
+            if (coord + 1 >= lim) continue;  // no pair across the periodic seam
+            const long long sn = s + (axis == 0 ? 1 : (axis == 1 ? (long long)g.nx : (long long)g.nx * g.ny));
+            if (!ca3_usable(c, sn)) continue;
+            const double qa = (double)c.rA[sn], qb = (double)c.rB[sn];
+            if (pa == phi3_pos(qa, qb)) continue;
+            const double a = phi3(ra, rb), b = phi3(qa, qb);
+            double p[3] = {(double)x, (double)y, (double)z};
+            p[axis] += a / (a - b);
+            if (pass == 0) {
+                acc[0] += 1.0;
+                acc[1] += p[0];
+                acc[2] += p[1];
+                acc[3] += p[2];
+            } else if (pass == 1) {
+                const double q0 = p[0] - m0, q1 = p[1] - m1, q2 = p[2] - m2, qq = q0 * q0 + q1 * q1 + q2 * q2;
+                acc[0] += q0 * q0; acc[1] += q0 * q1; acc[2] += q0 * q2;
+                acc[3] += q1 * q1; acc[4] += q1 * q2; acc[5] += q2 * q2;
+                acc[6] += q0; acc[7] += q1; acc[8] += q2;
+                acc[9] += q0 * qq; acc[10] += q1 * qq; acc[11] += q2 * qq; acc[12] += qq;
+            } else if (pass == 2) {
+                const double d0 = p[0] - c0, d1 = p[1] - c1, d2 = p[2] - c2;
+                const double d = sqrt(d0 * d0 + d1 * d1 + d2 * d2), res = d - r;
+                const double j[4] = {-d0 / d, -d1 / d, -d2 / d, -1.0};
+                int k = 0;
+                for (int a2 = 0; a2 < 4; ++a2)
+                    for (int b2 = a2; b2 < 4; ++b2) acc[k++] += j[a2] * j[b2];
+                for (int a2 = 0; a2 < 4; ++a2) acc[10 + a2] += j[a2] * res;
+            } else {
+                const double d0 = p[0] - c0, d1 = p[1] - c1, d2 = p[2] - c2;
+                const double res = sqrt(d0 * d0 + d1 * d1 + d2 * d2) - r;
+                acc[0] += res * res;
+            }
+        }
+    }
+    __shared__ double red[kC3Threads / 32][kC3Vals];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < kC3Vals; ++q) {
+        double v = acc[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kC3Vals; ++q) {
+            double v = 0.0;
+            for (int w = 0; w < kC3Threads / 32; ++w) v += red[w][q];
+            part[blockIdx.x * kC3Vals + q] = v;
+        }
+}
+
+__device__ void solve4(double A[4][4], double b[4], double x[4]) {
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+        for (int k = 0; k < 4; ++k) {
+            const double t = A[c][k];
+            A[c][k] = A[p][k];
+            A[p][k] = t;
+        }
+        const double t = b[c];
+        b[c] = b[p];
+        b[p] = t;
+        for (int r = c + 1; r < 4; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < 4; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+}
+
+__global__ void k3_ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st, double sc0,
+                            double sc1, double sc2, double R) {
+    double S[kC3Vals];
+    const int lane = threadIdx.x & 31;
+    for (int q = 0; q < kC3Vals; ++q) {
+        double v = 0.0;
+        for (int b = lane; b < nblocks; b += 32) v += part[b * kC3Vals + q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        S[q] = v;
+    }
+    if (lane != 0) return;
+    if (pass == 0) {
+        st[0] = S[0];
+        st[10] = S[0] < 8.0 ? 1.0 : 0.0;
+        for (int d = 0; d < 3; ++d) st[1 + d] = S[0] > 0.0 ? S[1 + d] / S[0] : 0.0;
+    } else if (pass == 1) {
+        if (st[10] != 0.0) return;
+        // [2q, 1] [c; d] = |q|^2 in the least-squares sense
+        double A[4][4] = {{4 * S[0], 4 * S[1], 4 * S[2], 2 * S[6]},
+                          {4 * S[1], 4 * S[3], 4 * S[4], 2 * S[7]},
+                          {4 * S[2], 4 * S[4], 4 * S[5], 2 * S[8]},
+                          {2 * S[6], 2 * S[7], 2 * S[8], st[0]}};
+        double b[4] = {2 * S[9], 2 * S[10], 2 * S[11], S[12]};
+        double x[4];
+        solve4(A, b, x);
+        st[7] = sqrt(x[3] + x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int d = 0; d < 3; ++d) st[4 + d] = st[1 + d] + x[d];
+    } else if (pass == 2) {
+        if (st[10] != 0.0) return;
+        double A[4][4];
+        int k = 0;
+        for (int a = 0; a < 4; ++a)
+            for (int b2 = a; b2 < 4; ++b2) {
+                A[a][b2] = S[k];
+                A[b2][a] = S[k];
+                ++k;
+            }
+        double b[4] = {-S[10], -S[11], -S[12], -S[13]};
+        double x[4];
+        solve4(A, b, x);
+        for (int d = 0; d < 3; ++d) st[4 + d] += x[d];
+        st[7] += x[3];
+    } else {
+        if (st[10] != 0.0) return;
+        st[8] = sqrt(S[0] / st[0]);
+        const double d0 = st[4] - sc0, d1 = st[5] - sc1, d2 = st[6] - sc2, r = st[7];
+        double cth = (R * R + r * r - (d0 * d0 + d1 * d1 + d2 * d2)) / (2.0 * r * R);
+        cth = cth > 1.0 ? 1.0 : (cth < -1.0 ? -1.0 : cth);
+        st[9] = acos(cth) * (180.0 / 3.14159265358979323846);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+struct lbm3d_ctx {
+    int storage = LBM_STORE_F32;
+    size_t elem = 4;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Geo3 g{};
+    P3<float> pf{};
+    P3<double> pd{};
+    long long nfluid = 0;
+    uint8_t* solid = nullptr;
+    uint32_t* flags = nullptr;
+    unsigned char* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    unsigned char* rho = nullptr;  // [2][N] in the compute type
+    double* part = nullptr;        // per-block diagnostic records
+    long long nparts = 0;
+    double* dout = nullptr;        // [k3DiagN]
+    double* ca = nullptr;          // contact angle: status record + block partials
+    double* scratch = nullptr;     // [38][N] doubles for population transfers and fields (on demand)
+};
+
+namespace {
+
+bool fin(double v) { return isfinite(v) != 0; }
+
+template <class R>
+P3<R> make_p3(const lbm3d_params& p) {
+    P3<R> P;
+    for (int k = 0; k < 2; ++k) {
+        P.omega[k] = (R)(1.0 / p.tau[k]);
+        P.cF[k] = (R)(1.0 - 0.5 / p.tau[k]);
+    }
+    P.G = (R)p.G_AB;
+    P.Gw2 = (R)p.G_w2;
+    P.lam = (R)p.lambda;
+    P.delta = (R)p.delta;
+    const double l = p.lambda, dl = p.delta;
+    P.s1 = (R)(2.0 * l / (1.0 + l));                          // Eq. 12 coefficients
+    P.s2 = (R)(2.0 * (l * l - l) / (dl * (1.0 + l)));
+    P.s3 = (R)((l - l * l) / (dl * dl * (1.0 + l)));
+    P.t2 = (R)(2.0 * (l - 1.0) / (dl * (1.0 + l)));
+    P.t3 = (R)((l - 1.0) / (dl * dl * (1.0 + l)));
+    for (int d = 0; d < 3; ++d) P.g[d] = (R)p.g[d];
+    P.mode = p.mode;
+    return P;
+}
+
+dim3 grid3(const Geo3& g) { return dim3((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz); }
+
+cudaError_t scratch_for(lbm3d_ctx* c) {
+    if (c->scratch) return cudaSuccess;
+    return cudaMalloc(&c->scratch, (size_t)38 * c->g.N * sizeof(double));
+}
+
+template <class R>
+cudaError_t step_once(lbm3d_ctx* c) {
+    const dim3 gr = grid3(c->g);
+    const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
+    R* rA = reinterpret_cast<R*>(c->rho);
+    R* rB = rA + c->g.N;
+    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rA, rB);
+    const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
+    k3_step<R, false><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rA, rB,
+                                                 reinterpret_cast<R*>(c->f[1 - c->cur]), nullptr, nullptr);
+    c->cur ^= 1;
+    return cudaGetLastError();
+}
+
+// densities of the current state into c->rho, then the fields form (o5 may be NULL)
+template <class R>
+cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
+    const dim3 gr = grid3(c->g);
+    const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
+    R* rA = reinterpret_cast<R*>(c->rho);
+    R* rB = rA + c->g.N;
+    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rA, rB);
+    const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
+    k3_step<R, true><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rA, rB, nullptr, o5, c->part);
+    if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
+    return cudaGetLastError();
+}
+
+cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
+    return c->storage == LBM_STORE_F64 ? fields_pass<double>(c, o5, diag) : fields_pass<float>(c, o5, diag);
+}
+
+template <class R>
+cudaError_t density_pass(lbm3d_ctx* c) {
+    R* rA = reinterpret_cast<R*>(c->rho);
+    k3_rho<R><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]), rA, rA + c->g.N);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t ca_passes(lbm3d_ctx* c, const double* sc, double R_) {
+    Ca3<R> ca{c->g, c->flags, reinterpret_cast<const R*>(c->rho), reinterpret_cast<const R*>(c->rho) + c->g.N};
+    double* st = c->ca;
+    double* part = c->ca + 16;
+    cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c->stream);
+    if (e != cudaSuccess) return e;
+    for (int pass = 0; pass < 4; ++pass) {
+        k3_ca_pass<R><<<kC3Blocks, kC3Threads, 0, c->stream>>>(ca, pass, st, part);
+        k3_ca_solve<<<1, 32, 0, c->stream>>>(pass, kC3Blocks, part, st, sc[0], sc[1], sc[2], R_);
+    }
+    return cudaGetLastError();
+}
+
+void free3(lbm3d_ctx* c) {
+    void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+#define TRY3(call, what)                                                                                 \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            lbm_status s_ = e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;                    \
+            if (e_ == cudaErrorMemoryAllocation) cudaGetLastError();                                     \
+            return report_error(s_, "%s: %s", what, cudaGetErrorString(e_));                              \
+        }                                                                                                \
+    } while (0)
+
+extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid, const lbm3d_params* p,
+                                   const double* rA0, const double* rB0, int32_t storage, void* cuda_stream,
+                                   lbm3d_ctx** out) {
+    if (!out) return report_error(LBM_EINVAL, "NULL output pointer");
+    *out = nullptr;
+    if (!grid || !solid || !p || !rA0 || !rB0) return report_error(LBM_EINVAL, "NULL argument");
+    if (grid->nx < 5 || grid->ny < 5 || grid->nz < 5) return report_error(LBM_EINVAL, "nx, ny, nz must be >= 5");
+    if (grid->ny > 65535 || grid->nz > 65535) return report_error(LBM_EINVAL, "ny, nz must be <= 65535");
+    if (storage != LBM_STORE_F32 && storage != LBM_STORE_F64) return report_error(LBM_EINVAL, "3-D storage must be FP32 or FP64");
+    for (int k = 0; k < 2; ++k)
+        if (!fin(p->tau[k]) || p->tau[k] <= 0.5) return report_error(LBM_EINVAL, "tau[%d] must be > 0.5", k);
+    if (!fin(p->G_AB) || !fin(p->G_w2) || !fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2]))
+        return report_error(LBM_EINVAL, "non-finite parameter");
+    if (!fin(p->lambda) || p->lambda <= 0.0) return report_error(LBM_EINVAL, "lambda must be > 0");
+    if (!fin(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return report_error(LBM_EINVAL, "delta must lie in (0, 1]");
+    if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return report_error(LBM_EINVAL, "bad mode");
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    long long nf = 0;
+    for (long long s = 0; s < N; ++s) {
+        if (solid[s]) continue;
+        ++nf;
+        if (!fin(rA0[s]) || !fin(rB0[s]) || rA0[s] <= 0.0 || rB0[s] <= 0.0)
+            return report_error(LBM_EINVAL, "initial densities must be finite and > 0 at fluid node %lld", s);
+    }
+    if (nf == 0) return report_error(LBM_EINVAL, "the mask has no fluid node");
+    int dev = 0;
+    cudaDeviceProp prop;
+    TRY3(cudaGetDevice(&dev), "cudaGetDevice");
+    TRY3(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return report_error(LBM_ECUDA, "this library is built for sm_103a (GB300); device %d is sm_%d%d", dev, prop.major, prop.minor);
+
+    lbm3d_ctx* c = new (std::nothrow) lbm3d_ctx();
+    if (!c) return report_error(LBM_ENOMEM, "host allocation");
+    auto bail = [&](lbm_status s) {
+        free3(c);
+        delete c;
+        return s;
+    };
+#define STEP3(call, what)                                                                            \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) {                                                                     \
+            lbm_status s_ = e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;                \
+            if (e_ == cudaErrorMemoryAllocation) cudaGetLastError();                                 \
+            report_error(s_, "%s: %s", what, cudaGetErrorString(e_));                                 \
+            return bail(s_);                                                                         \
+        }                                                                                            \
+    } while (0)
+    c->storage = storage;
+    c->elem = storage == LBM_STORE_F64 ? 8 : 4;
+    c->g = Geo3{grid->nx, grid->ny, grid->nz, N};
+    c->pf = make_p3<float>(*p);
+    c->pd = make_p3<double>(*p);
+    c->nfluid = nf;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        STEP3(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+        c->own_stream = true;
+    }
+    const dim3 gr = grid3(c->g);
+    c->nparts = (long long)gr.x * gr.y * gr.z;
+    STEP3(cudaMalloc(&c->solid, N), "mask");
+    STEP3(cudaMalloc(&c->flags, N * sizeof(uint32_t)), "flags");
+    STEP3(cudaMalloc(&c->f[0], 38 * N * c->elem), "population buffer");
+    STEP3(cudaMalloc(&c->f[1], 38 * N * c->elem), "population buffer");
+    STEP3(cudaMalloc(&c->rho, 2 * N * c->elem), "densities");
+    STEP3(cudaMalloc(&c->part, c->nparts * k3DiagN * sizeof(double)), "diagnostics");
+    STEP3(cudaMalloc(&c->dout, k3DiagN * sizeof(double)), "diagnostics");
+    STEP3(cudaMalloc(&c->ca, (16 + kC3Blocks * kC3Vals) * sizeof(double)), "contact-angle scratch");
+    STEP3(cudaMemsetAsync(c->f[0], 0, 38 * N * c->elem, c->stream), "memset");
+    STEP3(cudaMemsetAsync(c->f[1], 0, 38 * N * c->elem, c->stream), "memset");
+    STEP3(cudaMemcpy(c->solid, solid, N, cudaMemcpyHostToDevice), "mask upload");
+    k3_flags<<<gr, 128, 0, c->stream>>>(c->g, c->solid, c->flags);
+    STEP3(cudaGetLastError(), "flags kernel");
+    STEP3(scratch_for(c), "transfer scratch");
+    STEP3(cudaMemcpyAsync(c->scratch + 36 * N, rA0, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "density upload");
+    STEP3(cudaMemcpyAsync(c->scratch + 37 * N, rB0, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "density upload");
+    STEP3(cudaStreamSynchronize(c->stream), "upload");
+    // f = f^eq(rho, 0) into scratch [0, 38 N) -- the densities sit in its last two planes and are
+    // read before planes 36, 37 are overwritten by the same thread
+    k3_feq<double><<<gr, 128, 0, c->stream>>>(c->g, c->solid, c->scratch + 36 * N, c->scratch + 37 * N, c->scratch);
+    STEP3(cudaGetLastError(), "init kernel");
+    if (storage == LBM_STORE_F64) k3_set<double><<<gr, 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[0]);
+    else k3_set<float><<<gr, 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[0]);
+    STEP3(cudaGetLastError(), "init kernel");
+    STEP3(cudaStreamSynchronize(c->stream), "initialisation");
+    cudaFree(c->scratch);  // transfers allocate it again on demand
+    c->scratch = nullptr;
+#undef STEP3
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" void lbm3d_destroy(lbm3d_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free3(c);
+    delete c;
+}
+
+extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
+    if (!c) return report_error(LBM_EINVAL, "NULL context");
+    if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
+    for (int64_t t = 0; t < n; ++t) {
+        const cudaError_t e = c->storage == LBM_STORE_F64 ? step_once<double>(c) : step_once<float>(c);
+        TRY3(e, "step kernels");
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_fields(lbm3d_ctx* c, double* rA, double* rB, double* ux, double* uy, double* uz,
+                                   int32_t on_device) {
+    if (!c) return report_error(LBM_EINVAL, "NULL context");
+    TRY3(scratch_for(c), "fields scratch");
+    TRY3(run_fields(c, c->scratch, false), "fields kernels");
+    double* outs[5] = {rA, rB, ux, uy, uz};
+    const long long N = c->g.N;
+    for (int q = 0; q < 5; ++q)
+        if (outs[q])
+            TRY3(cudaMemcpyAsync(outs[q], c->scratch + q * N, N * sizeof(double),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+                 "fields copy");
+    if (!on_device) TRY3(cudaStreamSynchronize(c->stream), "fields");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_get_populations(lbm3d_ctx* c, double* f) {
+    if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
+    TRY3(scratch_for(c), "transfer scratch");
+    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, (const double*)c->f[c->cur], c->scratch);
+    else k3_get<float><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, (const float*)c->f[c->cur], c->scratch);
+    TRY3(cudaGetLastError(), "read-back kernel");
+    TRY3(cudaMemcpyAsync(f, c->scratch, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read-back");
+    TRY3(cudaStreamSynchronize(c->stream), "read-back");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_set_populations(lbm3d_ctx* c, const double* f) {
+    if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
+    TRY3(scratch_for(c), "transfer scratch");
+    TRY3(cudaMemcpyAsync(c->scratch, f, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[c->cur]);
+    else k3_set<float><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[c->cur]);
+    TRY3(cudaGetLastError(), "state kernel");
+    TRY3(cudaStreamSynchronize(c->stream), "upload");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_diagnostics(lbm3d_ctx* c, lbm3d_diag* out) {
+    if (!c || !out) return report_error(LBM_EINVAL, "NULL argument");
+    TRY3(run_fields(c, nullptr, true), "diagnostics kernels");
+    double v[k3DiagN];
+    TRY3(cudaMemcpyAsync(v, c->dout, sizeof v, cudaMemcpyDeviceToHost, c->stream), "diagnostics read-back");
+    TRY3(cudaStreamSynchronize(c->stream), "diagnostics");
+    out->mass_A = v[0];
+    out->mass_B = v[1];
+    out->mom_x = v[2];
+    out->mom_y = v[3];
+    out->mom_z = v[4];
+    out->umax = v[5];
+    out->rhoA_min = v[6];
+    out->rhoA_max = v[7];
+    out->rhoB_min = v[8];
+    out->rhoB_max = v[9];
+    out->n_fluid = (int64_t)llround(v[10]);
+    out->unstable = v[11] != 0.0;
+    out->pad_ = 0;
+    if (out->unstable) return report_error(LBM_EUNSTABLE, "non-finite or non-positive density");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_contact_angle(lbm3d_ctx* c, const double* sc, double R, double* theta_deg, double* fit_rms,
+                                          int64_t* npoints) {
+    if (!c || !sc) return report_error(LBM_EINVAL, "NULL argument");
+    if (!(R > 0.0) || !fin(sc[0]) || !fin(sc[1]) || !fin(sc[2])) return report_error(LBM_EINVAL, "bad sphere");
+    cudaError_t e = c->storage == LBM_STORE_F64 ? density_pass<double>(c) : density_pass<float>(c);
+    TRY3(e, "density kernel");
+    e = c->storage == LBM_STORE_F64 ? ca_passes<double>(c, sc, R) : ca_passes<float>(c, sc, R);
+    TRY3(e, "contact-angle kernels");
+    double h[16];
+    TRY3(cudaMemcpyAsync(h, c->ca, sizeof h, cudaMemcpyDeviceToHost, c->stream), "contact-angle read-back");
+    TRY3(cudaStreamSynchronize(c->stream), "contact angle");
+    if (npoints) *npoints = (int64_t)llround(h[0]);
+    if (h[10] != 0.0) return report_error(LBM_ESTATE, "only %.0f interface points", h[0]);
+    if (theta_deg) *theta_deg = h[9];
+    if (fit_rms) *fit_rms = h[8];
+    return LBM_OK;
+}

@@ -1,0 +1,137 @@
+"""ctypes binding of the 3-D C ABI (include/lbm3d.h): argument marshalling only.  The calls run in
+the same in-tree CUDA library as the 2-D ones (``lbm.load_library``)."""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_double, c_int32, c_int64, c_uint8, c_void_p
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbm
+
+SYMBOLS3 = ("lbm3d_create", "lbm3d_destroy", "lbm3d_step", "lbm3d_fields", "lbm3d_get_populations",
+            "lbm3d_set_populations", "lbm3d_diagnostics", "lbm3d_contact_angle")
+
+
+class lbm3d_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32)]
+
+
+class lbm3d_params(ctypes.Structure):
+    _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("lambda_", c_double),
+                ("G_w2", c_double), ("delta", c_double), ("g", c_double * 3)]
+
+
+class lbm3d_diag(ctypes.Structure):
+    _fields_ = [("mass_A", c_double), ("mass_B", c_double), ("mom_x", c_double), ("mom_y", c_double),
+                ("mom_z", c_double), ("umax", c_double), ("rhoA_min", c_double), ("rhoA_max", c_double),
+                ("rhoB_min", c_double), ("rhoB_max", c_double), ("n_fluid", c_int64), ("unstable", c_int32),
+                ("pad_", c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+_ready = False
+
+
+def _lib():
+    global _ready
+    lib = lbm.load_library()
+    if not _ready:
+        d = POINTER(c_double)
+        lib.lbm3d_create.argtypes = [POINTER(lbm3d_grid), POINTER(c_uint8), POINTER(lbm3d_params), d, d, c_int32,
+                                     c_void_p, POINTER(c_void_p)]
+        lib.lbm3d_destroy.argtypes = [c_void_p]
+        lib.lbm3d_destroy.restype = None
+        lib.lbm3d_step.argtypes = [c_void_p, c_int64]
+        lib.lbm3d_fields.argtypes = [c_void_p] + [c_void_p] * 5 + [c_int32]
+        lib.lbm3d_get_populations.argtypes = [c_void_p, c_void_p]
+        lib.lbm3d_set_populations.argtypes = [c_void_p, c_void_p]
+        lib.lbm3d_diagnostics.argtypes = [c_void_p, POINTER(lbm3d_diag)]
+        lib.lbm3d_contact_angle.argtypes = [c_void_p, POINTER(c_double), c_double, d, d, POINTER(c_int64)]
+        for name in SYMBOLS3:
+            if name != "lbm3d_destroy":
+                getattr(lib, name).restype = c_int32
+        _ready = True
+    return lib
+
+
+def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8,
+                 g=(0.0, 0.0, 0.0)) -> lbm3d_params:
+    p = lbm3d_params()
+    p.tau[0], p.tau[1] = tau
+    p.G_AB = G
+    p.mode = lbm.LBM_ADS_IMPROVED if scheme == "improved" else lbm.LBM_ADS_ORIGINAL
+    p.lambda_ = lam
+    p.G_w2 = G if Gw2 is None else Gw2
+    p.delta = delta
+    for i in range(3):
+        p.g[i] = g[i]
+    return p
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Lattice3:
+    """One 3-D lattice on the GPU (periodic in x, y, z; solid mask; FP32 or FP64)."""
+
+    def __init__(self, solid, rhoA0, rhoB0, params: dict, storage: str = "f32", cuda_stream: int | None = None):
+        solid = _c(solid, np.uint8)
+        self.nz, self.ny, self.nx = solid.shape
+        g = lbm3d_grid(self.nx, self.ny, self.nz)
+        p = make_params3(**params)
+        a, b = _c(rhoA0, np.float64), _c(rhoB0, np.float64)
+        ctx = c_void_p()
+        st = lbm.STORAGE[storage]
+        lbm._check(_lib().lbm3d_create(ctypes.byref(g), solid.ctypes.data_as(POINTER(c_uint8)), ctypes.byref(p),
+                                       a.ctypes.data_as(POINTER(c_double)), b.ctypes.data_as(POINTER(c_double)),
+                                       st, c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    def close(self):
+        if self.ctx:
+            _lib().lbm3d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int):
+        lbm._check(_lib().lbm3d_step(self.ctx, int(n)))
+
+    def fields(self):
+        out = [np.zeros((self.nz, self.ny, self.nx)) for _ in range(5)]
+        lbm._check(_lib().lbm3d_fields(self.ctx, *[o.ctypes.data for o in out], 0))
+        return tuple(out)
+
+    def populations(self) -> np.ndarray:
+        f = np.zeros((2, 19, self.nz, self.ny, self.nx))
+        lbm._check(_lib().lbm3d_get_populations(self.ctx, f.ctypes.data))
+        return f
+
+    def set_populations(self, f):
+        f = _c(f, np.float64)
+        assert f.shape == (2, 19, self.nz, self.ny, self.nx)
+        lbm._check(_lib().lbm3d_set_populations(self.ctx, f.ctypes.data))
+
+    def diagnostics(self, allow_unstable: bool = False) -> dict:
+        d = lbm3d_diag()
+        st = _lib().lbm3d_diagnostics(self.ctx, ctypes.byref(d))
+        if not (allow_unstable and st == lbm.LBM_EUNSTABLE):
+            lbm._check(st)
+        return d.as_dict()
+
+    def contact_angle(self, sphere: dict):
+        """(theta_deg, fit_rms, npoints) against the solid sphere {"c": (x, y, z), "R": R_eff}."""
+        c = (c_double * 3)(*sphere["c"])
+        th, rms, n = c_double(), c_double(), c_int64()
+        lbm._check(_lib().lbm3d_contact_angle(self.ctx, c, float(sphere["R"]), ctypes.byref(th), ctypes.byref(rms),
+                                              ctypes.byref(n)))
+        return th.value, rms.value, n.value

@@ -348,3 +348,58 @@ def scheme_comparison(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110,
             sc.name = f"{scheme}_{sc.name}"
             out.append(sc)
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# 3-D (Sec. 3.5): a droplet on a solid sphere, periodic in x, y and z
+# ------------------------------------------------------------------------------------------------
+@dataclass
+class Scenario3:
+    """One 3-D lattice case: mask and initial densities [nz][ny][nx], parameters, the sphere."""
+    name: str
+    solid: np.ndarray
+    rhoA0: np.ndarray
+    rhoB0: np.ndarray
+    tau: tuple = (TAU_SEC3, TAU_SEC3)
+    G: float = G_DEFAULT
+    lam: float = 1.0
+    Gw2: float | None = GW2_DEFAULT
+    delta: float = 0.8
+    g: tuple = (0.0, 0.0, 0.0)
+    scheme: str = "improved"
+    sphere: dict | None = None   # {"c": (x, y, z), "R": effective radius} for the contact angle
+
+    @property
+    def shape(self):
+        return self.solid.shape
+
+    def params(self) -> dict:
+        return dict(tau=tuple(self.tau), G=self.G, scheme=self.scheme, lam=self.lam, Gw2=self.Gw2,
+                    delta=self.delta, g=tuple(self.g))
+
+
+def sphere_droplet_3d(nx: int = 200, ny: int = 200, nz: int = 280, R: float = 50.0, sphere=(100.0, 100.0, 100.0),
+                      r: float = 45.0, drop=(100.0, 100.0, 180.0), lam: float = 1.0, seed: int = 9,
+                      G: float = G_DEFAULT, scheme: str = "improved", amp: float = NOISE_AMP) -> Scenario3:
+    """Sec. 3.5: a droplet of A (radius r, centre ``drop``) on a solid sphere (radius R, centre
+    ``sphere``), B elsewhere, periodic in every direction; the paper's 200x200x280 grid by default
+    (lambda = 0.38, 1, 2.1 for theta ~ 45, 90, 146 degrees).  Noise as in 2-D, counter over the
+    node index z (ny nx) + y nx + x."""
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    solid = ((x - sphere[0]) ** 2 + (y - sphere[1]) ** 2 + (z - sphere[2]) ** 2 <= R * R).astype(np.uint8)
+    inside = (x - drop[0]) ** 2 + (y - drop[1]) ** 2 + (z - drop[2]) ** 2 <= r * r
+    rA = np.where(inside, RHO_M, RHO_D) + node_noise(seed, nz * ny, nx, 0, amp).reshape(nz, ny, nx)
+    rB = np.where(inside, RHO_D, RHO_M) + node_noise(seed, nz * ny, nx, 1, amp).reshape(nz, ny, nx)
+    rA[solid == 1] = 0.0
+    rB[solid == 1] = 0.0
+    return Scenario3(f"sphere_droplet_{nx}x{ny}x{nz}", solid, rA, rB, G=G, lam=lam, scheme=scheme,
+                     sphere={"c": tuple(sphere), "R": R + 0.5})
+
+
+def sphere_droplet_3d_small(n: int = 40, lam: float = 1.0, seed: int = 9, scheme: str = "improved",
+                            amp: float = NOISE_AMP) -> Scenario3:
+    """The Sec. 3.5 geometry scaled to an n x n x 1.4n box (R = n/4, r = 0.225 n, centres as in the
+    paper scaled by n/200)."""
+    k = n / 200.0
+    return sphere_droplet_3d(nx=n, ny=n, nz=int(round(1.4 * n)), R=50 * k, sphere=(100 * k, 100 * k, 100 * k),
+                             r=45 * k, drop=(100 * k, 100 * k, 180 * k), lam=lam, seed=seed, scheme=scheme, amp=amp)

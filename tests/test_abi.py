@@ -150,3 +150,82 @@ def test_status_strings(lbm):
     assert lbm.status_name(0) == "LBM_OK"
     assert lbm.status_name(4) == "LBM_EUNSTABLE"
     assert lbm.status_name(99) == "LBM_UNKNOWN"
+
+
+# ---------------------------------------------------------------------------------------------
+# the 3-D ABI (include/lbm3d.h)
+# ---------------------------------------------------------------------------------------------
+def _declared3():
+    text = open(os.path.join(ROOT, "include", "lbm3d.h")).read()
+    return sorted(set(re.findall(r"\b(lbm3d_\w+)\s*\(", text)))
+
+
+def test_3d_header_declarations_match_binding_and_exports(lbm):
+    from paper_2505_22256_gb300 import lbm3d
+
+    assert sorted(lbm3d.SYMBOLS3) == _declared3()
+    lib = lbm.load_library()
+    for name in lbm3d.SYMBOLS3:
+        assert hasattr(lib, name), name
+
+
+def test_3d_struct_layouts_match_header(lbm, tmp_path):
+    from paper_2505_22256_gb300 import lbm3d
+
+    structs = {"lbm3d_grid": lbm3d.lbm3d_grid, "lbm3d_params": lbm3d.lbm3d_params, "lbm3d_diag": lbm3d.lbm3d_diag}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm3d.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            cf = "lambda" if fname == "lambda_" else fname
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {cf}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout3.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout3"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+@pytest.mark.parametrize("what", ["tau", "lambda", "delta", "mode", "size", "storage", "density", "allsolid"])
+def test_3d_invalid_input_is_rejected_before_any_device_work(lbm, what):
+    from paper_2505_22256_gb300 import lbm3d
+
+    n = 8
+    solid = np.zeros((n, n, n), np.uint8)
+    a = np.full((n, n, n), 0.5)
+    params = dict(tau=(1.0, 1.0), lam=1.0, delta=0.8, scheme="improved")
+    storage = "f32"
+    if what == "tau":
+        params["tau"] = (0.5, 1.0)
+    elif what == "lambda":
+        params["lam"] = 0.0
+    elif what == "delta":
+        params["delta"] = 1.5
+    elif what == "size":
+        solid, a = solid[:, :, :4], a[:, :, :4]
+    elif what == "storage":
+        storage = "f16"
+    elif what == "density":
+        a = a.copy()
+        a[2, 3, 4] = -1.0
+    elif what == "allsolid":
+        solid = np.ones_like(solid)
+    if what == "mode":
+        p = lbm3d.make_params3()
+        p.mode = 5
+        g = lbm3d.lbm3d_grid(n, n, n)
+        ctx = ctypes.c_void_p()
+        st = lbm3d._lib().lbm3d_create(ctypes.byref(g), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                       ctypes.byref(p), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, None, ctypes.byref(ctx))
+        assert st == lbm.LBM_EINVAL
+        return
+    with pytest.raises(lbm.LbmError) as e:
+        lbm3d.Lattice3(solid, a, a, params, storage)
+    assert e.value.status == lbm.LBM_EINVAL

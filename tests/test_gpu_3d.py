@@ -1,0 +1,177 @@
+"""GPU parity of the 3-D form (Sec. 3.5) against the 3-D FP64 oracle, through the C ABI
+(include/lbm3d.h): FP64 to ~1e-10; FP32 after 100 steps to 1e-5 of the main-phase density (see the
+test); the contact-angle routine on the same state, the steady angle within 0.5 degrees,
+conservation and the lambda = 1 identity."""
+import numpy as np
+import pytest
+
+from oracle import d3
+from paper_2505_22256_gb300 import lbm, lbm3d, scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2505_22256_gb300 import build
+
+    build.build()
+    d3.build()
+    lbm.load_library()
+
+
+def ocfg(sc):
+    nz, ny, nx = sc.shape
+    p = sc.params()
+    return d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
+                      delta=p["delta"], g=p["g"])
+
+
+def orun(sc, n):
+    cfg = ocfg(sc)
+    return cfg, d3.run3(cfg, sc.solid, d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0), n)
+
+
+def lattice(sc, storage):
+    return lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), storage)
+
+
+def rel_rho(g, o, solid, floor=0.0):
+    """max |d rho_k| / max(rho_k, floor) over fluid nodes."""
+    fl = solid == 0
+    return max(float(np.max(np.abs(g[k] - o[k])[fl] / np.maximum(o[k][fl], floor))) for k in (0, 1))
+
+
+CASES = {
+    "sphere24": lambda: S.sphere_droplet_3d_small(24, lam=0.6),
+    "sphere24_hydrophobic": lambda: S.sphere_droplet_3d_small(24, lam=2.1, seed=4),
+    "sphere24_original": lambda: S.sphere_droplet_3d_small(24, lam=0.5, scheme="original"),
+    "odd_box": lambda: S.sphere_droplet_3d(nx=21, ny=17, nz=26, R=5.0, sphere=(10.0, 8.0, 9.0), r=5.5,
+                                           drop=(10.0, 8.0, 17.0), lam=1.3),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_initial_state_and_population_roundtrip(name):
+    sc = CASES[name]()
+    cfg = ocfg(sc)
+    f0 = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    lat = lattice(sc, "f64")
+    np.testing.assert_allclose(lat.populations(), f0, rtol=1e-15, atol=1e-17)
+    f5 = d3.run3(cfg, sc.solid, f0, 5)
+    lat.set_populations(f5)
+    np.testing.assert_allclose(lat.populations(), f5, rtol=1e-15, atol=1e-17)
+    lat.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_f64_matches_oracle_after_30_steps(name):
+    sc = CASES[name]()
+    cfg, f = orun(sc, 30)
+    o = d3.fields3(cfg, sc.solid, f)
+    lat = lattice(sc, "f64")
+    lat.step(30)
+    g = lat.fields()
+    assert rel_rho(g, o, sc.solid) <= 1e-10
+    assert max(float(np.max(np.abs(g[k] - o[k]))) for k in (2, 3, 4)) <= 1e-11
+    np.testing.assert_allclose(lat.populations(), f, rtol=1e-9, atol=1e-13)
+    lat.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_f32_matches_oracle_after_100_steps(name):
+    """FP32 bar of the 3-D form after 100 steps: |d rho_k| <= 1e-5 rho_m (absolute, at the
+    main-phase density rho_m = 1) and |d u| <= 1e-6.  The FP32 state drifts from the FP64 one by a
+    few 1e-6 in absolute terms here (the 3-D stencil has 92 terms and 19 populations per
+    component); at the dissolved-phase level that is about 1e-5 relative, reported below and held
+    under 5e-5."""
+    sc = CASES[name]()
+    cfg, f = orun(sc, 100)
+    o = d3.fields3(cfg, sc.solid, f)
+    lat = lattice(sc, "f32")
+    lat.step(100)
+    g = lat.fields()
+    lat.close()
+    fl = sc.solid == 0
+    dabs = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (0, 1))
+    drel = rel_rho(g, o, sc.solid)
+    print(f"{name}: max |d rho| {dabs:.2e}, max relative {drel:.2e}")
+    assert dabs <= 1e-5 * S.RHO_M
+    assert drel <= 5e-5
+    assert max(float(np.max(np.abs(g[k] - o[k]))) for k in (2, 3, 4)) <= 1e-6
+
+
+def test_diagnostics_match_oracle():
+    sc = CASES["sphere24"]()
+    cfg, f = orun(sc, 40)
+    od = d3.diagnostics3(cfg, sc.solid, f)
+    lat = lattice(sc, "f64")
+    lat.step(40)
+    d = lat.diagnostics()
+    lat.close()
+    for k in ("mass_A", "mass_B", "rhoA_min", "rhoA_max", "rhoB_min", "rhoB_max", "umax"):
+        assert d[k] == pytest.approx(od[k], rel=1e-10), k
+    for k in ("mom_x", "mom_y", "mom_z"):
+        assert d[k] == pytest.approx(od[k], rel=1e-8, abs=1e-12), k
+    assert d["n_fluid"] == int((sc.solid == 0).sum()) and d["unstable"] == 0
+
+
+def test_mass_conservation_f32():
+    sc = CASES["sphere24"]()
+    lat = lattice(sc, "f32")
+    m0 = lat.diagnostics()
+    lat.step(500)
+    m1 = lat.diagnostics()
+    lat.close()
+    for k in ("mass_A", "mass_B"):
+        assert abs(m1[k] / m0[k] - 1) < 2e-5, (k, m0[k], m1[k])
+
+
+def test_lambda_one_makes_both_schemes_identical():
+    out = []
+    for scheme in ("improved", "original"):
+        lat = lattice(S.sphere_droplet_3d_small(24, lam=1.0, scheme=scheme), "f32")
+        lat.step(60)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_contact_angle_routine_matches_oracle_on_the_same_state():
+    sc = S.sphere_droplet_3d_small(32, lam=0.6)
+    cfg, f = orun(sc, 300)
+    oth, orms, on = d3.contact_angle_sphere(cfg, sc.solid, f, sc.sphere)
+    lat = lattice(sc, "f64")
+    lat.set_populations(f)
+    th, rms, n = lat.contact_angle(sc.sphere)
+    lat.close()
+    assert n == on
+    assert th == pytest.approx(oth, abs=1e-8)
+    assert rms == pytest.approx(orms, rel=1e-6, abs=1e-10)
+
+
+@pytest.mark.parametrize("lam", [0.38, 2.1])
+def test_contact_angle_after_1500_steps_within_half_a_degree(lam):
+    """Sec. 3.5's case at 32 x 32 x 45: the GPU's angle after 1,500 FP32 steps is the oracle's
+    to 0.5 degrees."""
+    sc = S.sphere_droplet_3d_small(32, lam=lam)
+    cfg, f = orun(sc, 1500)
+    oth, _, _ = d3.contact_angle_sphere(cfg, sc.solid, f, sc.sphere)
+    lat = lattice(sc, "f32")
+    lat.step(1500)
+    th, _, _ = lat.contact_angle(sc.sphere)
+    lat.close()
+    assert abs(th - oth) <= 0.5, (th, oth)
+
+
+def test_paper_size_lattice_steps_stably_and_conserves_mass():
+    """The paper's 200 x 200 x 280 grid (11.2 M nodes): 20 FP32 steps, finite, masses kept."""
+    sc = S.sphere_droplet_3d(lam=1.0)
+    lat = lattice(sc, "f32")
+    m0 = lat.diagnostics()
+    lat.step(20)
+    m1 = lat.diagnostics()
+    lat.close()
+    assert m1["unstable"] == 0
+    for k in ("mass_A", "mass_B"):
+        assert abs(m1[k] / m0[k] - 1) < 1e-5
