@@ -57,9 +57,11 @@ def parse():
                          "ensemble: 256 uneven cases + the 4096x256 co-current channel; compare: the "
                          "sweep under the improved and the original scheme (14 cases); obstacle: 64 "
                          "replicas of the 350x150 square-obstacle channel (Poiseuille inlet); couette: "
-                         "512 replicas of the 50x100 two-layer Couette channel (sliding walls)")
+                         "512 replicas of the 50x100 two-layer Couette channel (sliding walls); sphere3d: "
+                         "the 3-D droplet on a sphere, 200x200x280 (Sec. 3.5)")
     ap.add_argument("--n", type=int, default=1024, help="sweep: lattice side of each case")
-    ap.add_argument("--size", default=None, help="throat / porous: lattice WxH (default 2048x512 / 4096x2048)")
+    ap.add_argument("--size", default=None, help="throat / porous: lattice WxH (default 2048x512 / 4096x2048); "
+                                                 "sphere3d: n for the geometry scaled to n x n x 1.4n")
     ap.add_argument("--cases", type=int, default=7, help="sweep: number of lambda values (1..7)")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
@@ -69,7 +71,8 @@ def parse():
     return ap.parse_args()
 
 
-WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare", "obstacle", "couette")
+WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare", "obstacle", "couette", "sphere3d")
+BYTES_PER_NODE_3D = {"f32": 304, "f64": 608}  # 2 components x 19 populations, read + written
 
 
 def workload(args, rank=0):
@@ -243,10 +246,30 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    if args.workload == "sphere3d":
+        vals, base = [], None
+        for k in range(args.warmup + args.steps):
+            b = cpu_baseline_3d(per_step)
+            if k >= args.warmup:
+                vals.append(b["value"])
+                base = b
+        value = statistics.mean(vals)
+        nodes = 200 * 200 * 280
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": nodes * args.inner / (value * 1e6) * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "3-D droplet on a sphere, 200x200x280 per GPU (R=50, r=45, lambda=1, periodic)",
+                           "storage": args.storage, "inner_steps": args.inner},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                                 "sample": base["sample"]},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     cases, desc = workload(args)
     # each step: a bounded sample of the workload (time steps of one case), sized so that the whole
     # --steps/--warmup run stays within a few minutes
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     base = None
     vals = []
     for k in range(args.warmup + args.steps):
@@ -428,10 +451,161 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------
+# the 3-D workload (Sec. 3.5): one 200x200x280 lattice per GPU
+# ------------------------------------------------------------------------------------------------
+def sphere3d_case(args, rank=0):
+    from paper_2505_22256_gb300 import scenarios as S
+
+    if args.size:  # the geometry scaled to n x n x 1.4 n
+        return S.sphere_droplet_3d_small(int(args.size), lam=1.0, seed=9 + 1000 * rank)
+    return S.sphere_droplet_3d(lam=1.0, seed=9 + 1000 * rank)
+
+
+def cpu_baseline_3d(seconds: float) -> dict:
+    from oracle import d3
+    from paper_2505_22256_gb300 import scenarios as S
+
+    sc = S.sphere_droplet_3d_small(64)  # the same geometry scaled to 64 x 64 x 90
+    nz, ny, nx = sc.shape
+    p = sc.params()
+    cfg = d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
+                     delta=p["delta"], g=p["g"])
+    f = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f = d3.run3(cfg, sc.solid, f, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 10000:
+            break
+    return {"value": nx * ny * nz * n / el / 1e6, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+            "sample": f"the Sec. 3.5 geometry scaled to {nx}x{ny}x{nz}, {n} FP64 time steps in {el:.1f} s on "
+                      f"{cfg.nthreads} host threads"}
+
+
+def run_ours_3d(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_22256_gb300 import lbm3d
+
+    if args.storage not in BYTES_PER_NODE_3D:
+        raise SystemExit("the 3-D workload runs in f32 or f64")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    sc = sphere3d_case(args, rank)
+    stream = torch.cuda.Stream()
+    lat = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), args.storage, cuda_stream=stream.cuda_stream)
+    nodes = int(sc.solid.size)
+    fluid = int((sc.solid == 0).sum())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def bench_step(pairs=None):
+        if pairs is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        lat.step(args.inner)
+        if pairs is not None:
+            b.record(stream)
+            pairs.append((a, b))
+        lat.diagnostics(allow_unstable=True)
+        try:
+            return lat.contact_angle(sc.sphere)[0]
+        except Exception:
+            return None
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    pairs = []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0.record(stream)
+    theta = None
+    for _ in range(args.steps):
+        theta = bench_step(pairs)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = sum(a.elapsed_time(b) for a, b in pairs)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launch_ms = step_ms / (args.inner * args.steps)  # one time step: density pass + fused pass
+    algo = BYTES_PER_NODE_3D[args.storage] * fluid
+    peak, peak_kind = hbm_peak()
+    d = lat.diagnostics(allow_unstable=True)
+    lat.close()
+
+    e2e = None
+    if not args.no_e2e:
+        k = max(1, args.steps // 4)
+        out = [np.zeros(sc.solid.shape) for _ in range(5)]
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        for _ in range(k):
+            l2 = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), args.storage, cuda_stream=stream.cuda_stream)
+            l2.step(args.inner)
+            rA, rB, ux, uy, uz = l2.fields()
+            l2.close()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - s0
+        e2e = {"value": world * nodes * args.inner * k / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": nodes * (1 + 16),
+               "d2h_bytes_per_step": nodes * 5 * 8,
+               "step": "lbm3d_create from host mask and densities, lbm3d_step(%d), lbm3d_fields to host" % args.inner}
+
+    line = {
+        "metric": METRIC, "value": world * nodes * args.inner * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": f"3-D droplet on a sphere, {'x'.join(map(str, sc.shape[::-1]))} per GPU "
+                               f"(the Sec. 3.5 geometry, lambda=1, periodic), "
+                               f"{args.inner} time steps + diagnostics + contact angle per step",
+                   "storage": args.storage, "nodes_per_gpu": nodes, "fluid_nodes_per_gpu": fluid,
+                   "inner_steps": args.inner, "parallelism": f"one lattice per GPU x{world} (no collective)",
+                   "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE_3D[args.storage] / 2 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": algo / (launch_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": algo / (launch_ms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k3_rho + k3_step (one time step)", "algorithmic_bytes_per_launch": algo,
+                     "launch_ms": launch_ms},
+        "e2e": e2e, "gpu_launches": (2 * args.inner + 3 + 9) * args.steps, "clocks": clk,
+        "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
+        "sample_diagnostics": {"theta_deg": theta, "umax": d["umax"], "unstable": d["unstable"]},
+    }
+    if rank == 0:
+        if not args.no_cpu and world == 1:
+            line["cpu_baseline"] = cpu_baseline_3d(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sphere3d":
+        return run_ours_3d(args)
     return run_ours(args)
 
 

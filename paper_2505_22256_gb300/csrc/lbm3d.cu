@@ -13,8 +13,9 @@
 //             velocity with Guo's half-force shift (Eq. 5); SRT collision with Guo forcing (Eqs. 1,
 //             2, 6, 7) written to the other buffer.  Its fields form writes rho and u in FP64 and
 //             per-block diagnostic sums instead of colliding.
-// The density arrays (2 R per node) are small enough to stay largely in L2 while k3_step reads
-// its stencil from them.  Periodic in x, y and z.
+// The densities, interleaved (rho_A, rho_B) per node, are small enough to stay largely in L2
+// while k3_step reads its stencil from them; each thread precomputes its wrapped neighbourhood
+// (32-bit indices), so a stencil site costs one add and one 64-bit load.  Periodic in x, y and z.
 #include <math.h>
 #include <stdarg.h>
 
@@ -92,19 +93,46 @@ __global__ void k3_flags(Geo3 g, const uint8_t* __restrict__ solid, uint32_t* __
     flags[s] = f;
 }
 
+// Wrapped neighbourhood of one node: the x index and the y, z offsets (y nx, z nx ny) for the
+// displacements -2..2, as 32-bit values, so every stencil site is one three-operand add.
+struct Nb3 {
+    int xw[5], yo[5], zo[5];
+    __device__ __forceinline__ Nb3(const Geo3& g, int x, int y, int z) {
+        const int nxy = g.nx * g.ny;
+#pragma unroll
+        for (int d = -2; d <= 2; ++d) {
+            xw[d + 2] = wrapc(x + d, g.nx);
+            yo[d + 2] = wrapc(y + d, g.ny) * g.nx;
+            zo[d + 2] = wrapc(z + d, g.nz) * nxy;
+        }
+    }
+    __device__ __forceinline__ int at(int dx, int dy, int dz) const { return zo[dz + 2] + yo[dy + 2] + xw[dx + 2]; }
+};
+
+// density pair (rho_A, rho_B) of a node, stored interleaved
+template <class R>
+struct Rho2;
+template <>
+struct Rho2<float> {
+    using T = float2;
+};
+template <>
+struct Rho2<double> {
+    using T = double2;
+};
+
 // the node's 38 post-streaming populations
 template <class R>
-__device__ __forceinline__ void pull3(const Geo3& g, const R* __restrict__ fs, uint32_t fl, int x, int y, int z,
-                                      long long s, R (&f)[38]) {
+__device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const R* __restrict__ fs, uint32_t fl, int s,
+                                      R (&f)[38]) {
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        long long src;
-        int q;
+        int src, q;
         if (i > 0 && ((fl >> (i - 1)) & 1u)) {
             src = s;
             q = opp3(i);
         } else {
-            src = i == 0 ? s : site(g, x - e3x(i), y - e3y(i), z - e3z(i));
+            src = i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i));
             q = i;
         }
         f[i] = fs[(long long)q * g.N + src];
@@ -123,20 +151,22 @@ __device__ __forceinline__ R sum19(const R* f) {
 
 template <class R>
 __global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
-                                              R* __restrict__ rhoA, R* __restrict__ rhoB) {
+                                              typename Rho2<R>::T* __restrict__ rho) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const int s = (z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
-    R a = (R)0, b = (R)0;
+    typename Rho2<R>::T r;
+    r.x = (R)0;
+    r.y = (R)0;
     if (!(fl & k3Solid)) {
+        const Nb3 nb(g, x, y, z);
         R f[38];
-        pull3<R>(g, fs, fl, x, y, z, s, f);
-        a = sum19<R>(f);
-        b = sum19<R>(f + 19);
+        pull3<R>(g, nb, fs, fl, s, f);
+        r.x = sum19<R>(f);
+        r.y = sum19<R>(f + 19);
     }
-    rhoA[s] = a;
-    rhoB[s] = b;
+    rho[s] = r;
 }
 
 constexpr int k3DiagN = 12;  // mass A, mass B, mom x, y, z, umax, rhoA min/max, rhoB min/max, n, unstable
@@ -156,18 +186,19 @@ __device__ __forceinline__ double d3_neutral(int q) {
 template <class R, bool kFields>
 __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
                                                const uint8_t* __restrict__ solid, const R* __restrict__ fs,
-                                               const R* __restrict__ rhoA, const R* __restrict__ rhoB,
-                                               R* __restrict__ fout, double* __restrict__ o5, double* __restrict__ part) {
+                                               const typename Rho2<R>::T* __restrict__ rho, R* __restrict__ fout,
+                                               double* __restrict__ o5, double* __restrict__ part) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const bool in = x < g.nx;
-    const long long s = ((long long)z * g.ny + y) * g.nx + (in ? x : 0);
+    const int s = (z * g.ny + y) * g.nx + (in ? x : 0);
     const uint32_t fl = in ? flags[s] : k3Solid;
     double rec[k3DiagN];
     if constexpr (kFields)
         for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
     if (!(fl & k3Solid)) {
+        const Nb3 nb(g, x, y, z);
         R f[38];
-        pull3<R>(g, fs, fl, x, y, z, s, f);
+        pull3<R>(g, nb, fs, fl, s, f);
         // momentum from the differences of opposite populations (i odd, opp(i) = i + 1)
         R m[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
@@ -177,10 +208,11 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
             m[1] += e3y(i) * t;
             m[2] += e3z(i) * t;
         }
-        const R rA = rhoA[s], rB = rhoB[s];
+        const typename Rho2<R>::T r0 = rho[s];
+        const R rA = r0.x, rB = r0.y;
         R gA[3] = {(R)0, (R)0, (R)0}, gB[3] = {(R)0, (R)0, (R)0}, ad[3] = {(R)0, (R)0, (R)0};
         // sums over symmetric pairs (e, -e): w e (psi(x+e) - psi(x-e)), the differences first
-        if (!(fl & k3Wall)) {  // no solid node in the stencil: plain sums (solid density is 0 anyway)
+        if (!(fl & k3Wall)) {  // no solid node in the stencil (solid density is 0 anyway)
 #pragma unroll
             for (int dz = 0; dz <= 2; ++dz)
 #pragma unroll
@@ -190,15 +222,15 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
                         if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;  // one of each pair
                         const int q = dx * dx + dy * dy + dz * dz;
                         if (w92(q) == 0.0) continue;
-                        const long long np = site(g, x + dx, y + dy, z + dz), nm = site(g, x - dx, y - dy, z - dz);
-                        const R w = (R)w92(q);
-                        const R a = __ldg(rhoA + np) - __ldg(rhoA + nm), b = __ldg(rhoB + np) - __ldg(rhoB + nm);
+                        const typename Rho2<R>::T p = __ldg(rho + nb.at(dx, dy, dz)), n = __ldg(rho + nb.at(-dx, -dy, -dz));
+                        const R w = (R)w92(q), a = p.x - n.x, b = p.y - n.y;
                         gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
                         gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
                     }
         } else {  // second-layer copy of x + sign(e) for non-fluid second-layer sites; solid switch
             for (int dz = 0; dz <= 2; ++dz)
                 for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
                     for (int dx = -2; dx <= 2; ++dx) {
                         if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
                         const int q = dx * dx + dy * dy + dz * dz;
@@ -210,11 +242,12 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
                         for (int side = 0; side < 2; ++side) {
                             const int sg = side == 0 ? 1 : -1;
                             const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
-                            long long n = site(g, x + ex, y + ey, z + ez);
-                            if (second && solid[n]) n = site(g, x + (ex > 0) - (ex < 0), y + (ey > 0) - (ey < 0), z + (ez > 0) - (ez < 0));
+                            int n = nb.at(ex, ey, ez);
+                            if (second && solid[n]) n = nb.at((ex > 0) - (ex < 0), (ey > 0) - (ey < 0), (ez > 0) - (ez < 0));
                             const bool sol = solid[n] != 0;
-                            va[side] = sol ? (R)0 : rhoA[n];
-                            vb[side] = sol ? (R)0 : rhoB[n];
+                            const typename Rho2<R>::T v = rho[n];
+                            va[side] = sol ? (R)0 : v.x;
+                            vb[side] = sol ? (R)0 : v.y;
                             vs[side] = sol ? (R)1 : (R)0;
                         }
                         const R w = (R)wq, a = va[0] - va[1], b = vb[0] - vb[1], sw = vs[0] - vs[1];
@@ -329,7 +362,8 @@ __global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __re
     if (fl & k3Solid) {
         for (int q = 0; q < 38; ++q) v[q] = (R)0;
     } else {
-        pull3<R>(g, fs, fl, x, y, z, s, v);
+        const Nb3 nb(g, x, y, z);
+        pull3<R>(g, nb, fs, fl, (int)s, v);
     }
     for (int q = 0; q < 38; ++q) f[(long long)q * g.N + s] = (double)v[q];
 }
@@ -376,8 +410,7 @@ template <class R>
 struct Ca3 {
     Geo3 g;
     const uint32_t* flags;
-    const R* rA;
-    const R* rB;
+    const typename Rho2<R>::T* rho;  // interleaved (rho_A, rho_B)
 };
 
 template <class R>
@@ -399,7 +432,8 @@ __global__ void k3_ca_pass(Ca3<R> c, int pass, const double* __restrict__ st, do
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.N; s += (long long)gridDim.x * blockDim.x) {
         if (!ca3_usable(c, s)) continue;
         const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
-        const double ra = (double)c.rA[s], rb = (double)c.rB[s];
+        const typename Rho2<R>::T r0 = c.rho[s];
+        const double ra = (double)r0.x, rb = (double)r0.y;
         const bool pa = phi3_pos(ra, rb);
         for (int axis = 0; axis < 3; ++axis) {
             const int lim = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
@@ -407,7 +441,8 @@ __global__ void k3_ca_pass(Ca3<R> c, int pass, const double* __restrict__ st, do
             if (coord + 1 >= lim) continue;  // no pair across the periodic seam
             const long long sn = s + (axis == 0 ? 1 : (axis == 1 ? (long long)g.nx : (long long)g.nx * g.ny));
             if (!ca3_usable(c, sn)) continue;
-            const double qa = (double)c.rA[sn], qb = (double)c.rB[sn];
+            const typename Rho2<R>::T r1 = c.rho[sn];
+            const double qa = (double)r1.x, qb = (double)r1.y;
             if (pa == phi3_pos(qa, qb)) continue;
             const double a = phi3(ra, rb), b = phi3(qa, qb);
             double p[3] = {(double)x, (double)y, (double)z};
@@ -595,11 +630,10 @@ template <class R>
 cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gr = grid3(c->g);
     const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
-    R* rA = reinterpret_cast<R*>(c->rho);
-    R* rB = rA + c->g.N;
-    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rA, rB);
+    auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
+    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, false><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rA, rB,
+    k3_step<R, false><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho,
                                                  reinterpret_cast<R*>(c->f[1 - c->cur]), nullptr, nullptr);
     c->cur ^= 1;
     return cudaGetLastError();
@@ -610,11 +644,10 @@ template <class R>
 cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
     const dim3 gr = grid3(c->g);
     const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
-    R* rA = reinterpret_cast<R*>(c->rho);
-    R* rB = rA + c->g.N;
-    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rA, rB);
+    auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
+    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, true><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rA, rB, nullptr, o5, c->part);
+    k3_step<R, true><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, nullptr, o5, c->part);
     if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
     return cudaGetLastError();
 }
@@ -625,14 +658,14 @@ cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
 
 template <class R>
 cudaError_t density_pass(lbm3d_ctx* c) {
-    R* rA = reinterpret_cast<R*>(c->rho);
-    k3_rho<R><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]), rA, rA + c->g.N);
+    k3_rho<R><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]),
+                                                   reinterpret_cast<typename Rho2<R>::T*>(c->rho));
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t ca_passes(lbm3d_ctx* c, const double* sc, double R_) {
-    Ca3<R> ca{c->g, c->flags, reinterpret_cast<const R*>(c->rho), reinterpret_cast<const R*>(c->rho) + c->g.N};
+    Ca3<R> ca{c->g, c->flags, reinterpret_cast<const typename Rho2<R>::T*>(c->rho)};
     double* st = c->ca;
     double* part = c->ca + 16;
     cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c->stream);
@@ -671,6 +704,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     if (!grid || !solid || !p || !rA0 || !rB0) return report_error(LBM_EINVAL, "NULL argument");
     if (grid->nx < 5 || grid->ny < 5 || grid->nz < 5) return report_error(LBM_EINVAL, "nx, ny, nz must be >= 5");
     if (grid->ny > 65535 || grid->nz > 65535) return report_error(LBM_EINVAL, "ny, nz must be <= 65535");
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) - 1) return report_error(LBM_EINVAL, "lattice too large (2^31 nodes)");
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F64) return report_error(LBM_EINVAL, "3-D storage must be FP32 or FP64");
     for (int k = 0; k < 2; ++k)
         if (!fin(p->tau[k]) || p->tau[k] <= 0.5) return report_error(LBM_EINVAL, "tau[%d] must be > 0.5", k);
