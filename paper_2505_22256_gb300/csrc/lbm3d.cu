@@ -75,8 +75,8 @@ struct P3 {
 };
 
 __global__ void k3_flags(Geo3 g, const uint8_t* __restrict__ solid, uint32_t* __restrict__ flags) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
     uint32_t f = 0;
     if (solid[s]) f |= k3Solid;
@@ -152,8 +152,8 @@ __device__ __forceinline__ R sum19(const R* f) {
 template <class R>
 __global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
                                               typename Rho2<R>::T* __restrict__ rho) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
     const int s = (z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
     typename Rho2<R>::T r;
@@ -188,9 +188,9 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
                                                const uint8_t* __restrict__ solid, const R* __restrict__ fs,
                                                const typename Rho2<R>::T* __restrict__ rho, R* __restrict__ fout,
                                                double* __restrict__ o5, double* __restrict__ part) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    const bool in = x < g.nx;
-    const int s = (z * g.ny + y) * g.nx + (in ? x : 0);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    const bool in = x < g.nx && y < g.ny;
+    const int s = (z * g.ny + (in ? y : 0)) * g.nx + (in ? x : 0);
     const uint32_t fl = in ? flags[s] : k3Solid;
     double rec[k3DiagN];
     if constexpr (kFields)
@@ -322,14 +322,14 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
     }
     if constexpr (kFields) {
         __shared__ double red[4][k3DiagN];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int lane = threadIdx.x, warp = threadIdx.y;  // blocks of 32 x 4
         for (int q = 0; q < k3DiagN; ++q) {
             double v = rec[q];
             for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
             if (lane == 0) red[warp][q] = v;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
             const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
             for (int q = 0; q < k3DiagN; ++q) {
                 double v = red[0][q];
@@ -354,8 +354,8 @@ __global__ void k3_diag_final(long long nblocks, const double* __restrict__ part
 // post-streaming populations (FP64 [2][19][N]) <-> post-collision buffer
 template <class R>
 __global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs, double* __restrict__ f) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
     R v[38];
@@ -370,8 +370,8 @@ __global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __re
 
 template <class R>
 __global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ f, R* __restrict__ fs) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
     for (int k = 0; k < 2; ++k)
@@ -389,8 +389,8 @@ __global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double*
 template <class R>
 __global__ void k3_feq(Geo3 g, const uint8_t* __restrict__ solid, const double* __restrict__ rA, const double* __restrict__ rB,
                        double* __restrict__ f) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
     const bool sol = solid[s] != 0;
     for (int i = 0; i < 19; ++i) {
@@ -619,7 +619,9 @@ P3<R> make_p3(const lbm3d_params& p) {
     return P;
 }
 
-dim3 grid3(const Geo3& g) { return dim3((unsigned)((g.nx + 127) / 128), (unsigned)g.ny, (unsigned)g.nz); }
+// node kernels run blocks of 32 x 4 nodes (x, y), so that a block's stencil rows share L1
+dim3 grid3(const Geo3& g) { return dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz); }
+const dim3 kBlock3(32, 4, 1);
 
 cudaError_t scratch_for(lbm3d_ctx* c) {
     if (c->scratch) return cudaSuccess;
@@ -631,9 +633,9 @@ cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gr = grid3(c->g);
     const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
-    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rho);
+    k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, false><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho,
+    k3_step<R, false><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho,
                                                  reinterpret_cast<R*>(c->f[1 - c->cur]), nullptr, nullptr);
     c->cur ^= 1;
     return cudaGetLastError();
@@ -645,9 +647,9 @@ cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
     const dim3 gr = grid3(c->g);
     const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
-    k3_rho<R><<<gr, 128, 0, c->stream>>>(c->g, c->flags, fs, rho);
+    k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, true><<<gr, 128, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, nullptr, o5, c->part);
+    k3_step<R, true><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, nullptr, o5, c->part);
     if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
     return cudaGetLastError();
 }
@@ -658,7 +660,7 @@ cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
 
 template <class R>
 cudaError_t density_pass(lbm3d_ctx* c) {
-    k3_rho<R><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]),
+    k3_rho<R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]),
                                                    reinterpret_cast<typename Rho2<R>::T*>(c->rho));
     return cudaGetLastError();
 }
@@ -771,7 +773,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     STEP3(cudaMemsetAsync(c->f[0], 0, 38 * N * c->elem, c->stream), "memset");
     STEP3(cudaMemsetAsync(c->f[1], 0, 38 * N * c->elem, c->stream), "memset");
     STEP3(cudaMemcpy(c->solid, solid, N, cudaMemcpyHostToDevice), "mask upload");
-    k3_flags<<<gr, 128, 0, c->stream>>>(c->g, c->solid, c->flags);
+    k3_flags<<<gr, kBlock3, 0, c->stream>>>(c->g, c->solid, c->flags);
     STEP3(cudaGetLastError(), "flags kernel");
     STEP3(scratch_for(c), "transfer scratch");
     STEP3(cudaMemcpyAsync(c->scratch + 36 * N, rA0, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "density upload");
@@ -779,10 +781,10 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     STEP3(cudaStreamSynchronize(c->stream), "upload");
     // f = f^eq(rho, 0) into scratch [0, 38 N) -- the densities sit in its last two planes and are
     // read before planes 36, 37 are overwritten by the same thread
-    k3_feq<double><<<gr, 128, 0, c->stream>>>(c->g, c->solid, c->scratch + 36 * N, c->scratch + 37 * N, c->scratch);
+    k3_feq<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->solid, c->scratch + 36 * N, c->scratch + 37 * N, c->scratch);
     STEP3(cudaGetLastError(), "init kernel");
-    if (storage == LBM_STORE_F64) k3_set<double><<<gr, 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[0]);
-    else k3_set<float><<<gr, 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[0]);
+    if (storage == LBM_STORE_F64) k3_set<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[0]);
+    else k3_set<float><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[0]);
     STEP3(cudaGetLastError(), "init kernel");
     STEP3(cudaStreamSynchronize(c->stream), "initialisation");
     cudaFree(c->scratch);  // transfers allocate it again on demand
@@ -828,8 +830,8 @@ extern "C" lbm_status lbm3d_fields(lbm3d_ctx* c, double* rA, double* rB, double*
 extern "C" lbm_status lbm3d_get_populations(lbm3d_ctx* c, double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
-    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, (const double*)c->f[c->cur], c->scratch);
-    else k3_get<float><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, (const float*)c->f[c->cur], c->scratch);
+    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const double*)c->f[c->cur], c->scratch);
+    else k3_get<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const float*)c->f[c->cur], c->scratch);
     TRY3(cudaGetLastError(), "read-back kernel");
     TRY3(cudaMemcpyAsync(f, c->scratch, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read-back");
     TRY3(cudaStreamSynchronize(c->stream), "read-back");
@@ -840,8 +842,8 @@ extern "C" lbm_status lbm3d_set_populations(lbm3d_ctx* c, const double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
     TRY3(cudaMemcpyAsync(c->scratch, f, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
-    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[c->cur]);
-    else k3_set<float><<<grid3(c->g), 128, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[c->cur]);
+    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[c->cur]);
+    else k3_set<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[c->cur]);
     TRY3(cudaGetLastError(), "state kernel");
     TRY3(cudaStreamSynchronize(c->stream), "upload");
     return LBM_OK;
