@@ -154,30 +154,40 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Three tensor maps per case: one row of all 18 planes of each population buffer, T [+8] columns
-// from column x - G (the ghost columns included), and one row of the ghost-padded flags, as the
-// step kernel loads them.
+// Three tensor maps per case: one row of all 9 planes of (A, B) pairs of each population buffer, T
+// columns from column x - G (the ghost columns included), and one row of the ghost-padded flags, as
+// the step kernel loads them.  A pair is one tensor element (8-byte words for FP32, 4-byte for the
+// 16-bit types); an FP64 pair is two 8-byte words along an extra innermost dimension.
 lbm_status build_tmaps(Ctx& c) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int T = c.block_threads, G = ghost_cols(c.storage), XB = box_extra_cols(c.storage);
     if (T + XB > 256) return fail(LBM_EINVAL, "block of %d threads needs a tensor box wider than 256 columns", T);
-    CUtensorMapDataType dt = c.storage == LBM_STORE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                           : c.storage == LBM_STORE_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                           : c.storage == LBM_STORE_F16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const bool f64 = c.storage == LBM_STORE_F64;
+    const CUtensorMapDataType dt = c.elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint64_t pb = 2 * c.elem;  // bytes of one pair
     std::vector<CUtensorMap> maps(3 * c.hcases.size());
     for (size_t ci = 0; ci < c.hcases.size(); ++ci) {
         const DevCase& d = c.hcases[ci];
         for (int buf = 0; buf < 2; ++buf) {
-            void* base = (char*)c.f[buf] + (size_t)d.f_off * c.elem;
-            cuuint64_t dims[3] = {(cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 18};
-            cuuint64_t strides[2] = {(cuuint64_t)d.pitch * c.elem, (cuuint64_t)d.pitch * d.ny * c.elem};
-            cuuint32_t box[3] = {(cuuint32_t)(T + XB), 1, 18};
-            cuuint32_t estr[3] = {1, 1, 1};
-            CUresult r = enc(&maps[3 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            void* base = (char*)c.f[buf] + (size_t)d.f_off * pb;
+            const cuuint64_t row = (cuuint64_t)d.pitch * pb;
+            CUresult r;
+            if (f64) {
+                cuuint64_t dims[4] = {2, (cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 9};
+                cuuint64_t strides[3] = {pb, row, row * d.ny};
+                cuuint32_t box[4] = {2, (cuuint32_t)(T + XB), 1, 9};
+                cuuint32_t estr[4] = {1, 1, 1, 1};
+                r = enc(&maps[3 * ci + buf], dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                cuuint64_t dims[3] = {(cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 9};
+                cuuint64_t strides[2] = {row, row * d.ny};
+                cuuint32_t box[3] = {(cuuint32_t)(T + XB), 1, 9};
+                cuuint32_t estr[3] = {1, 1, 1};
+                r = enc(&maps[3 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
             if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "tensor map of case %zu rejected (CUresult %d)", ci, (int)r);
         }
         // flag rows: T + 8 columns from column x - 8 (8 ghost columns per side)
@@ -380,9 +390,9 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         hc.nfluid = nfluid[i];
         c.cases.push_back(hc);
         DevCase d = make_desc(cs[i].grid, cs[i].params);
-        const int per_line = (int)(128 / c.elem);  // rows start on 128-byte boundaries
+        const int per_line = (int)(128 / (2 * c.elem));  // rows of pairs start on 128-byte boundaries
         d.pitch = (d.nx + 2 * ghost_cols(storage) + per_line - 1) / per_line * per_line;
-        d.f_off = c.pop_elems;
+        d.f_off = c.pop_elems / 2;
         d.d_off = c.dense_elems;
         fill_case_params(d);
         c.pop_elems += 18LL * d.ny * d.pitch;
@@ -950,7 +960,7 @@ lbm_status lbm_save(lbm_ctx* ctx, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, "LBMGB300", 8);
-    h.version = 1;
+    h.version = 2;  // 2: (A, B) pairs per direction
     h.storage = c.storage;
     h.ncases = (int32_t)c.cases.size();
     h.steps = c.steps;
@@ -971,7 +981,7 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path) {
     CkptHeader h;
     std::vector<unsigned char> buf(c.pop_elems * c.elem);
     bool ok = fread(&h, sizeof h, 1, fp) == 1;
-    if (ok && (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1 || h.storage != c.storage ||
+    if (ok && (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2 || h.storage != c.storage ||
                h.ncases != (int32_t)c.cases.size() || h.bytes != (int64_t)buf.size() || h.hash != params_hash(c))) {
         fclose(fp);
         return fail(LBM_EIO, "%s does not match this context", path);

@@ -71,7 +71,7 @@ __host__ __device__ __forceinline__ constexpr double w8(int e2) {
 template <class R>
 struct CaseParams {
     int nx, ny, pitch, bc_x, bc_y, mode;
-    long long plane;  // ny * pitch
+    long long plane;  // ny * pitch (pairs)
     R omega[2], cF[2];
     R G, Gw2, lam, delta, s1, s2, s3, t2, t3;
     R gx, gy;
@@ -87,10 +87,10 @@ struct CaseParams {
 // Per-case descriptor (device copy; built on the host).
 // ------------------------------------------------------------------------------------------------
 struct DevCase {
-    int nx, ny, pitch;      // pitch: elements per stored population row (ghost columns included)
+    int nx, ny, pitch;      // pitch: (A, B) pairs per stored population row (ghost columns included)
     int bc_x, bc_y;
     int mode;               // 0 original, 1 improved
-    long long f_off;        // element offset of the case's [18][ny][pitch] block in a population buffer
+    long long f_off;        // pair offset of the case's [9][ny][pitch] block of (A, B) pairs in a buffer
     long long d_off;        // element offset of the case's [ny][nx] block in per-node arrays
     long long w_off;        // first wall-list entry of the case
     long long nwall;        // wall-list entries of the case
@@ -176,6 +176,71 @@ struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     __device__ __forceinline__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
+
+// ------------------------------------------------------------------------------------------------
+// The population buffers hold f*_i^A and f*_i^B of one node side by side: plane i (0..8) of a case
+// is [ny][pitch] pairs (A, B).  One vector access moves both components of a direction.
+// ------------------------------------------------------------------------------------------------
+template <class S>
+struct alignas(2 * sizeof(S)) Pair {
+    S a, b;
+};
+
+// Load the pair at p as compute-type values; 16-bit types add the storage shifts (shA, shB) back
+// with the mixed-precision add (the widening is exact, so each value is rounded once).
+template <class S, class R>
+__device__ __forceinline__ void load_pair(const Pair<S>* p, R shA, R shB, R& va, R& vb);
+template <>
+__device__ __forceinline__ void load_pair<double, double>(const Pair<double>* p, double, double, double& va,
+                                                          double& vb) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    va = v.x;
+    vb = v.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<float, float>(const Pair<float>* p, float, float, float& va, float& vb) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    va = v.x;
+    vb = v.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<__half, float>(const Pair<__half>* p, float shA, float shB, float& va,
+                                                         float& vb) {
+    const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "add.rn.f32.f16 %0, lo, %3;\n\tadd.rn.f32.f16 %1, hi, %4;\n\t}"
+        : "=f"(va), "=f"(vb)
+        : "r"(u), "f"(shA), "f"(shB));
+}
+template <>
+__device__ __forceinline__ void load_pair<__nv_bfloat16, float>(const Pair<__nv_bfloat16>* p, float shA, float shB,
+                                                                float& va, float& vb) {
+    const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "add.rn.f32.bf16 %0, lo, %3;\n\tadd.rn.f32.bf16 %1, hi, %4;\n\t}"
+        : "=f"(va), "=f"(vb)
+        : "r"(u), "f"(shA), "f"(shB));
+}
+
+// Store a pair (values already shifted for 16-bit types; round to nearest even).
+template <class S, class R>
+__device__ __forceinline__ void store_pair(Pair<S>* p, R va, R vb);
+template <>
+__device__ __forceinline__ void store_pair<double, double>(Pair<double>* p, double va, double vb) {
+    *reinterpret_cast<double2*>(p) = make_double2(va, vb);
+}
+template <>
+__device__ __forceinline__ void store_pair<float, float>(Pair<float>* p, float va, float vb) {
+    *reinterpret_cast<float2*>(p) = make_float2(va, vb);
+}
+template <>
+__device__ __forceinline__ void store_pair<__half, float>(Pair<__half>* p, float va, float vb) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(va, vb);
+}
+template <>
+__device__ __forceinline__ void store_pair<__nv_bfloat16, float>(Pair<__nv_bfloat16>* p, float va, float vb) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(va, vb);
+}
 
 // Compute type for a storage type: FP64 storage computes in FP64, everything else in FP32.
 template <class S>

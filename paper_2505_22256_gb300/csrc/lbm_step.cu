@@ -2,9 +2,9 @@
 // kernels that read and write its state.
 //
 // State: one buffer per time level holds the post-collision populations f*_i^k of every case as
-// [18][ny][pitch] planes of the storage type S (plane q = 9k + i).  Column x of a row lives at
-// element x + G; the G ghost columns on each side repeat the opposite edge when x is periodic, so
-// a tensor box never has to wrap.
+// [9][ny][pitch] planes of pairs (f*_i^A, f*_i^B) of the storage type S (plane i): one vector access
+// moves both components of a direction.  Column x of a row lives at pair x + G; the G ghost columns
+// on each side repeat the opposite edge when x is periodic, so a tensor box never has to wrap.
 //
 // One launch of k_step performs, for every fluid node x:
 //   pull    f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link (halfway bounce-back,
@@ -18,14 +18,14 @@
 //
 // Work decomposition.  A work item is a column window of one case (T - 8 interior columns) by a
 // chunk of rows.  One thread per window column marches down the rows.  Data path per row:
-//   * the tensor engine loads the whole row of f* (all 18 planes, T [+8] columns) into a ring of
+//   * the tensor engine loads the whole row of f* (all 9 planes of pairs, T columns) into a ring of
 //     kSlots shared-memory slots, about four rows ahead, each slot completing on its mbarrier;
 //   * every thread pulls its 18 populations from the three slots around the row, sums rho_A,
 //     rho_B into a six-row density ring and keeps the populations in registers;
 //   * after one barrier, each interior thread forms the row sums of the density gradient
 //     (D1 = rho(x+1) - rho(x-1), D2, and the |dy| = 1, 2 weighted sums) and adds them into a
 //     five-row window of partial gradients; the row two rows up is then complete, is collided and
-//     written straight to global memory (one coalesced store per plane and warp).
+//     written straight to global memory (one coalesced pair store per plane and warp).
 // Densities of halo rows and columns are recomputed by neighbouring items; one launch needs no
 // grid-wide synchronisation.
 #include <math.h>
@@ -63,75 +63,38 @@ __device__ __forceinline__ R shift_of(const Params<R>& P, int k, int i) {
     return i == 0 ? P.sh0[k] : (i <= 4 ? P.sh1[k] : P.sh5[k]);
 }
 
-// storage <-> compute conversions
-template <class S, class R>
-__device__ __forceinline__ R sload(const S* p) { return (R)*p; }
-template <>
-__device__ __forceinline__ float sload<__half, float>(const __half* p) { return __half2float(*p); }
-template <>
-__device__ __forceinline__ float sload<__nv_bfloat16, float>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
-// 16-bit storage holds f - w rho0: load and add the shift back in one mixed-precision add (the
-// widening is exact, so this rounds once, like a conversion followed by an FP32 add)
-template <class S, class R>
-__device__ __forceinline__ R sload_shifted(const S* p, R shift);
-template <>
-__device__ __forceinline__ float sload_shifted<__half, float>(const __half* p, float shift) {
-    float r;
-    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(__half_as_ushort(*p)), "f"(shift));
-    return r;
-}
-template <>
-__device__ __forceinline__ float sload_shifted<__nv_bfloat16, float>(const __nv_bfloat16* p, float shift) {
-    float r;
-    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(__bfloat16_as_ushort(*p)), "f"(shift));
-    return r;
-}
-
-template <class S, class R>
-__device__ __forceinline__ S to_store(R v) { return (S)v; }
-template <>
-__device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
-
 // ------------------------------------------------------------------------------------------------
-// Pull of one node's 18 populations.  rm / r0 / rp point at the rows y-1, y, y+1 (plane stride ps,
-// column c of the node, lattice row y); used with the shared-memory row slots (step kernel) and
-// with global memory (state read-back).  The plain form assumes no blocked link and no open column.
-// Pin: the rarely used constants (inlet, sliding walls).
+// Pull of one node's 18 populations.  rm / r0 / rp point at the rows y-1, y, y+1 (plane stride ps
+// pairs, column c of the node, lattice row y); used with the shared-memory row slots (step kernel)
+// and with global memory (state read-back).  The plain form assumes no blocked link and no open
+// column.  Pin: the rarely used constants (inlet).
 // ------------------------------------------------------------------------------------------------
-template <bool kGeneral, class S, class R>
-__device__ __forceinline__ void pull(const S* __restrict__ rm, const S* __restrict__ r0, const S* __restrict__ rp,
-                                     long long ps, int c, uint16_t fl, bool inlet, bool outlet, const Params<R>& P,
-                                     const Params<R>& Pin, int y, R (&f)[18]) {
+template <bool kGeneral, class S, class R, class I>
+__device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<S>* __restrict__ r0,
+                                     const Pair<S>* __restrict__ rp, I ps, int c, uint16_t fl, bool inlet, bool outlet,
+                                     const Params<R>& P, const Params<R>& Pin, int y, R (&f)[18]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const S* src;
-        long long off;
+        const Pair<S>* src;
+        I off;
         if (i == 0) {
             src = r0;
             off = c;
         } else if (!kGeneral) {
             src = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
-            off = (long long)i * ps + c - cx(i);
+            off = (I)i * ps + c - cx(i);
         } else {
             if (cx(i) > 0 && inlet) continue;  // entering through the inlet: set below
             const bool blocked = (fl >> (i - 1)) & 1u;
             int b = c;
             if (cx(i) < 0 && outlet) b = (fl & kOutletOwnBit) ? c : c - 1;  // copied from upstream
-            const S* nsrc = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+            const Pair<S>* nsrc = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
             src = blocked ? r0 : nsrc;
-            off = blocked ? (long long)opp(i) * ps + b : (long long)i * ps + b - cx(i);
+            off = blocked ? (I)opp(i) * ps + b : (I)i * ps + b - cx(i);
         }
         R va, vb;
-        if constexpr (Store<S>::kShift) {
-            va = sload_shifted<S, R>(src + off, shift_of(P, 0, i));
-            vb = sload_shifted<S, R>(src + off + 9 * ps, shift_of(P, 1, i));
-        } else {
-            va = sload<S, R>(src + off);
-            vb = sload<S, R>(src + off + 9 * ps);
-        }
+        if constexpr (Store<S>::kShift) load_pair<S, R>(src + off, shift_of(P, 0, i), shift_of(P, 1, i), va, vb);
+        else load_pair<S, R>(src + off, (R)0, (R)0, va, vb);
         f[i] = va;
         f[9 + i] = vb;
     }
@@ -366,17 +329,19 @@ __device__ __forceinline__ void collide_comp(const R* f, int k, R rho, R ux, R u
     }
 }
 
+// Ghost columns per side of a stored row (>= 3, and a 16-byte multiple for every pair size).  The
+// tensor box of a window starts G columns left of the window (column xs - G, pair xs) and is T
+// pairs wide, which covers the columns xs - 3 .. xs + T - 6 that the density columns pull from.
 template <class S>
 struct Layout {
-    static constexpr int G = sizeof(S) == 2 ? 8 : 4;   // ghost columns per side (16 B multiple, >= 3)
-    static constexpr int XB = sizeof(S) == 2 ? 8 : 0;  // box columns beyond the block width
+    static constexpr int G = 4;
 };
 
 template <class S, class R>
 struct SmemPlan {
     size_t pop_bytes, slot_bytes, ring_off, bar_off, total;
     __host__ __device__ explicit SmemPlan(int T) {
-        pop_bytes = ((size_t)(T + Layout<S>::XB) * 18 * sizeof(S) + 127) / 128 * 128;
+        pop_bytes = ((size_t)T * 9 * sizeof(Pair<S>) + 127) / 128 * 128;
         slot_bytes = pop_bytes + ((size_t)(T + 8) * sizeof(uint16_t) + 127) / 128 * 128;  // + the flags row
         ring_off = kSlots * slot_bytes;
         bar_off = (ring_off + 4 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
@@ -408,13 +373,13 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
     constexpr int T = kT, Wi = T - 8;
     const int t = threadIdx.x;
     constexpr int G = Layout<S>::G;
-    constexpr int BX = T + Layout<S>::XB;
+    constexpr int BX = T;  // pairs per plane of a row slot
     const SmemPlan<S, R> plan(T);
     R* ringA = reinterpret_cast<R*>(smem + plan.ring_off);
     R* ringB = ringA + 2 * kRing * T;
     const uint32_t bar0 = smem_u32(smem + plan.bar_off);
     const uint32_t slot0 = smem_u32(smem);
-    const uint32_t box_bytes = (uint32_t)((size_t)BX * 18 * sizeof(S) + (size_t)(T + 8) * sizeof(uint16_t));
+    const uint32_t box_bytes = (uint32_t)((size_t)BX * 9 * sizeof(Pair<S>) + (size_t)(T + 8) * sizeof(uint16_t));
     const R* wax = reinterpret_cast<const R*>(a.wa);
     const R* way = wax + a.dense_total;
 
@@ -463,7 +428,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
         const bool outlet = P.bc_x == kOpen && X == P.nx - 1;
         const int nload = (y1 + 2) - (y0 - 3) + 1;  // f* rows y0-3 .. y1+2
         const int r_first = dir > 0 ? y0 - 3 : y1 + 2, r_last = dir > 0 ? y1 + 2 : y0 - 3;
-        S* fo = reinterpret_cast<S*>(a.fout) + C.f_off;
+        Pair<S>* fo = reinterpret_cast<Pair<S>*>(a.fout) + C.f_off;
 
         auto wrap_row = [&](int r) -> int {
             if (P.bc_y == kPeriodic) r += r < 0 ? P.ny : (r >= P.ny ? -P.ny : 0);
@@ -474,7 +439,8 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
         auto issue = [&]() {
             const uint32_t dst = slot0 + issue_slot * (uint32_t)plan.slot_bytes;
             mbar_expect_tx(bar0 + 8 * issue_slot, box_bytes);
-            tma_load_3d(dst, lmap, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
+            if constexpr (sizeof(S) == 8) tma_load_4d(dst, lmap, 0, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
+            else tma_load_3d(dst, lmap, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
             tma_load_2d(dst + (uint32_t)plan.pop_bytes, fmap, xs, wrap_row(next_row), bar0 + 8 * issue_slot);
             next_row += dir;
             if (++issue_slot == kSlots) {
@@ -509,11 +475,11 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             R ra = 0, rb = 0;
             const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
             if (!(st.fl & kSolidBit)) {
-                const S* rm = reinterpret_cast<const S*>(slot_back(dir > 0 ? 2 : 0));
-                const S* r0 = reinterpret_cast<const S*>(s0);
-                const S* rp = reinterpret_cast<const S*>(slot_back(dir > 0 ? 0 : 2));
-                if (general) pull<true, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
-                else pull<false, S, R>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
+                const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(slot_back(dir > 0 ? 2 : 0));
+                const Pair<S>* r0 = reinterpret_cast<const Pair<S>*>(s0);
+                const Pair<S>* rp = reinterpret_cast<const Pair<S>*>(slot_back(dir > 0 ? 0 : 2));
+                if (general) pull<true, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
+                else pull<false, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 // rho_k = sum_i f_i as a balanced tree (short dependency chains)
                 const R* f = st.f;
                 ra = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + (f[7] + f[8])));
@@ -628,20 +594,24 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 R o[18];
                 collide_comp<R>(f, 0, rA, ux, uy, FAx, FAy, P.omega[0], P.cF[0], o);
                 collide_comp<R>(f, 1, rB, ux, uy, FBx, FBy, P.omega[1], P.cF[1], o);
-                S* out = fo + (long long)y * P.pitch + x + G;
+                Pair<S>* out = fo + (long long)y * P.pitch + x + G;
 #pragma unroll
-                for (int q = 0; q < 18; ++q) {
-                    R v = o[q];
-                    if constexpr (Store<S>::kShift) v -= shift_of(P, q / 9, q % 9);
-                    o[q] = v;
-                    *out = to_store<S, R>(v);
+                for (int i = 0; i < 9; ++i) {
+                    R va = o[i], vb = o[9 + i];
+                    if constexpr (Store<S>::kShift) {
+                        va -= shift_of(P, 0, i);
+                        vb -= shift_of(P, 1, i);
+                    }
+                    o[i] = va;
+                    o[9 + i] = vb;
+                    store_pair<S, R>(out, va, vb);
                     out += P.plane;
                 }
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
-                    S* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
+                    Pair<S>* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
 #pragma unroll
-                    for (int q = 0; q < 18; ++q) {
-                        *gout = to_store<S, R>(o[q]);
+                    for (int i = 0; i < 9; ++i) {
+                        store_pair<S, R>(gout, o[i], o[9 + i]);
                         gout += P.plane;
                     }
                 }
@@ -763,7 +733,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
 // ------------------------------------------------------------------------------------------------
 template <class S>
 __global__ void k_sliding_walls(const DevCase* __restrict__ cases, const int* __restrict__ list,
-                                const uint16_t* __restrict__ flags_all, S* __restrict__ buf_all) {
+                                const uint16_t* __restrict__ flags_all, Pair<S>* __restrict__ buf_all) {
     using R = typename ComputeOf<S>::type;
     constexpr int G = Layout<S>::G;
     const int ci = list[blockIdx.y >> 1];
@@ -776,30 +746,30 @@ __global__ void k_sliding_walls(const DevCase* __restrict__ cases, const int* __
     const double uw = upper ? C.u_wall[1] : C.u_wall[0];
     if (uw == 0.0) return;
     const long long plane = (long long)C.ny * C.pitch;
-    S* p = buf_all + C.f_off + (long long)Y * C.pitch + X + G;
+    Pair<S>* p = buf_all + C.f_off + (long long)Y * C.pitch + X + G;
     const int ip = upper ? 6 : 7, im = upper ? 5 : 8;  // returning as e_x = +1 / -1
-    for (int k = 0; k < 2; ++k) {
-        R v[9];
-        R rho = (R)0;
+    auto shift = [&](int k, int j) -> R { return Store<S>::kShift ? (R)(wq(j) * C.rho0[k]) : (R)0; };
+    R v[2][9];
+    R rho[2] = {(R)0, (R)0};
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            v[j] = sload<S, R>(p + (long long)(9 * k + j) * plane);
-            if constexpr (Store<S>::kShift) v[j] += (R)(wq(j) * C.rho0[k]);
-            rho += v[j];
-        }
-        const R a = (R)(6.0 * wq(5)) * rho * (R)uw;
-        const R nv[2] = {v[ip] + a, v[im] - a};
-        const int q[2] = {ip, im};
+    for (int j = 0; j < 9; ++j) {
+        load_pair<S, R>(p + j * plane, shift(0, j), shift(1, j), v[0][j], v[1][j]);
+        rho[0] += v[0][j];
+        rho[1] += v[1][j];
+    }
+    const int q[2] = {ip, im};
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            R o = nv[m];
-            if constexpr (Store<S>::kShift) o -= (R)(wq(q[m]) * C.rho0[k]);
-            const S sv = to_store<S, R>(o);
-            S* pq = p + (long long)(9 * k + q[m]) * plane;
-            *pq = sv;
-            if (C.bc_x == kPeriodic && X < G) pq[C.nx] = sv;
-            if (C.bc_x == kPeriodic && X >= C.nx - G) pq[-C.nx] = sv;
+    for (int m = 0; m < 2; ++m) {
+        R o[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const R a = (R)(6.0 * wq(5)) * rho[k] * (R)uw;
+            o[k] = (m == 0 ? v[k][ip] + a : v[k][im] - a) - shift(k, q[m]);
         }
+        Pair<S>* pq = p + q[m] * plane;
+        store_pair<S, R>(pq, o[0], o[1]);
+        if (C.bc_x == kPeriodic && X < G) store_pair<S, R>(pq + C.nx, o[0], o[1]);
+        if (C.bc_x == kPeriodic && X >= C.nx - G) store_pair<S, R>(pq - C.nx, o[0], o[1]);
     }
 }
 
@@ -826,17 +796,18 @@ __global__ void k_feq_rest(const DevCase* __restrict__ cases, int c, const uint8
 // pull reproduces f exactly (up to the storage rounding).  Ghost columns are filled as well.
 template <class S>
 __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint16_t* __restrict__ flags_all,
-                            const double* __restrict__ f, S* __restrict__ out_all) {
+                            const double* __restrict__ f, Pair<S>* __restrict__ out_all) {
     using R = typename ComputeOf<S>::type;
     constexpr int G = Layout<S>::G;
     const DevCase C = cases[c];
     const long long N = (long long)C.nx * C.ny;
     const long long plane = (long long)C.ny * C.pitch;
-    S* out = out_all + C.f_off;
+    Pair<S>* out = out_all + C.f_off;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
         const uint16_t fl = flags_all[C.d_off + s];
         const long long o = (long long)Y * C.pitch + X + G;
+        R ov[2][9];
         for (int k = 0; k < 2; ++k) {
             double vs[9];
 #pragma unroll
@@ -865,12 +836,15 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
                 if (!(fl & kSolidBit)) {
                     if constexpr (Store<S>::kShift) v -= wq(i) * C.rho0[k];
                 }
-                const S sv = to_store<S, R>((R)v);
-                S* p = out + (long long)(9 * k + i) * plane;
-                p[o] = sv;
-                if (C.bc_x == kPeriodic && X < G) p[o + C.nx] = sv;
-                if (C.bc_x == kPeriodic && X >= C.nx - G) p[o - C.nx] = sv;
+                ov[k][i] = (R)v;
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            Pair<S>* p = out + i * plane;
+            store_pair<S, R>(p + o, ov[0][i], ov[1][i]);
+            if (C.bc_x == kPeriodic && X < G) store_pair<S, R>(p + o + C.nx, ov[0][i], ov[1][i]);
+            if (C.bc_x == kPeriodic && X >= C.nx - G) store_pair<S, R>(p + o - C.nx, ov[0][i], ov[1][i]);
         }
     }
 }
@@ -878,13 +852,13 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
 // Post-collision buffer -> post-streaming populations (dense doubles), 0 at solid nodes.
 template <class S>
 __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint16_t* __restrict__ flags_all,
-                            const S* __restrict__ fin_all, double* __restrict__ f) {
+                            const Pair<S>* __restrict__ fin_all, double* __restrict__ f) {
     using R = typename ComputeOf<S>::type;
     constexpr int G = Layout<S>::G;
     const DevCase C = cases[c];
     const Params<R> P = load_params<R>(C);
     const long long N = (long long)C.nx * C.ny;
-    const S* fin = fin_all + C.f_off;
+    const Pair<S>* fin = fin_all + C.f_off;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
         const uint16_t fl = flags_all[C.d_off + s];
@@ -898,8 +872,8 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
             const int ym = Y - 1 < 0 ? (C.bc_y == kPeriodic ? C.ny - 1 : 0) : Y - 1;
             const int yp = Y + 1 >= C.ny ? (C.bc_y == kPeriodic ? 0 : C.ny - 1) : Y + 1;
             const bool inlet = C.bc_x == kOpen && X == 0, outlet = C.bc_x == kOpen && X == C.nx - 1;
-            pull<true, S, R>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch, fin + (long long)yp * C.pitch,
-                             P.plane, X + G, fl, inlet, outlet, P, P, Y, v);
+            pull<true, S, R, long long>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch,
+                                        fin + (long long)yp * C.pitch, P.plane, X + G, fl, inlet, outlet, P, P, Y, v);
         }
 #pragma unroll
         for (int q = 0; q < 18; ++q) f[(long long)q * N + s] = (double)v[q];
@@ -1000,8 +974,8 @@ int blocks_for(long long n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 
 
 }  // namespace
 
-int ghost_cols(int storage) { return (storage == LBM_STORE_F16_SHIFTED || storage == LBM_STORE_BF16_SHIFTED) ? 8 : 4; }
-int box_extra_cols(int storage) { return (storage == LBM_STORE_F16_SHIFTED || storage == LBM_STORE_BF16_SHIFTED) ? 8 : 0; }
+int ghost_cols(int) { return Layout<float>::G; }
+int box_extra_cols(int) { return 0; }
 
 int step_smem_bytes(int storage, int threads) {
     switch (storage) {
@@ -1039,10 +1013,10 @@ cudaError_t launch_step(Ctx& c, int in_buf, cudaStream_t s) {
     if (e != cudaSuccess || c.slide_n == 0) return e;
     const dim3 grid((unsigned)((c.slide_max_nx + 127) / 128), (unsigned)(2 * c.slide_n));
     switch (c.storage) {
-        case LBM_STORE_F64: k_sliding_walls<double><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (double*)a.fout); break;
-        case LBM_STORE_F32: k_sliding_walls<float><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (float*)a.fout); break;
-        case LBM_STORE_F16_SHIFTED: k_sliding_walls<__half><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (__half*)a.fout); break;
-        default: k_sliding_walls<__nv_bfloat16><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (__nv_bfloat16*)a.fout); break;
+        case LBM_STORE_F64: k_sliding_walls<double><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (Pair<double>*)a.fout); break;
+        case LBM_STORE_F32: k_sliding_walls<float><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (Pair<float>*)a.fout); break;
+        case LBM_STORE_F16_SHIFTED: k_sliding_walls<__half><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (Pair<__half>*)a.fout); break;
+        default: k_sliding_walls<__nv_bfloat16><<<grid, 128, 0, s>>>(c.dcases, c.slide_list, c.flags, (Pair<__nv_bfloat16>*)a.fout); break;
     }
     return cudaGetLastError();
 }
@@ -1094,10 +1068,10 @@ cudaError_t launch_set_state(Ctx& c, int ci, const double* dense_f) {
     const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
     const int g = blocks_for(N);
     switch (c.storage) {
-        case LBM_STORE_F64: k_set_state<double><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (double*)c.f[c.cur]); break;
-        case LBM_STORE_F32: k_set_state<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (float*)c.f[c.cur]); break;
-        case LBM_STORE_F16_SHIFTED: k_set_state<__half><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (__half*)c.f[c.cur]); break;
-        default: k_set_state<__nv_bfloat16><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (__nv_bfloat16*)c.f[c.cur]); break;
+        case LBM_STORE_F64: k_set_state<double><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (Pair<double>*)c.f[c.cur]); break;
+        case LBM_STORE_F32: k_set_state<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (Pair<float>*)c.f[c.cur]); break;
+        case LBM_STORE_F16_SHIFTED: k_set_state<__half><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (Pair<__half>*)c.f[c.cur]); break;
+        default: k_set_state<__nv_bfloat16><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, dense_f, (Pair<__nv_bfloat16>*)c.f[c.cur]); break;
     }
     return cudaGetLastError();
 }
@@ -1106,10 +1080,10 @@ cudaError_t launch_get_state(Ctx& c, int ci, double* dense_f) {
     const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
     const int g = blocks_for(N);
     switch (c.storage) {
-        case LBM_STORE_F64: k_get_state<double><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const double*)c.f[c.cur], dense_f); break;
-        case LBM_STORE_F32: k_get_state<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const float*)c.f[c.cur], dense_f); break;
-        case LBM_STORE_F16_SHIFTED: k_get_state<__half><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const __half*)c.f[c.cur], dense_f); break;
-        default: k_get_state<__nv_bfloat16><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const __nv_bfloat16*)c.f[c.cur], dense_f); break;
+        case LBM_STORE_F64: k_get_state<double><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const Pair<double>*)c.f[c.cur], dense_f); break;
+        case LBM_STORE_F32: k_get_state<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const Pair<float>*)c.f[c.cur], dense_f); break;
+        case LBM_STORE_F16_SHIFTED: k_get_state<__half><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const Pair<__half>*)c.f[c.cur], dense_f); break;
+        default: k_get_state<__nv_bfloat16><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.flags, (const Pair<__nv_bfloat16>*)c.f[c.cur], dense_f); break;
     }
     return cudaGetLastError();
 }
