@@ -64,6 +64,56 @@ __device__ __forceinline__ R shift_of(const Params<R>& P, int k, int i) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// Component pairs.  Every per-component quantity of the step (the populations f_i^A, f_i^B, the
+// densities, their gradients, forces and relaxation rates) is held as a pair (A, B), so that in
+// FP32 one packed FP32x2 instruction (sm_100 and later) does the work of both components.  Each
+// lane rounds exactly like the scalar operation.  FP64 pairs are two scalar operations.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using T = float2;
+};
+template <>
+struct PairOf<double> {
+    using T = double2;
+};
+template <class R>
+using V2 = typename PairOf<R>::T;
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <class R, class T>
+__device__ __forceinline__ V2<R> vbc(T v) {  // the same value in both lanes, in the compute type
+    return V2<R>{(R)v, (R)v};
+}
+
+// Load the pair of direction i at p (16-bit types add the storage shift of each component back).
+template <class S, class R>
+__device__ __forceinline__ V2<R> load_v2(const Pair<S>* p, const Params<R>& P, int i) {
+    V2<R> v;
+    if constexpr (Store<S>::kShift) load_pair<S, R>(p, shift_of(P, 0, i), shift_of(P, 1, i), v.x, v.y);
+    else load_pair<S, R>(p, (R)0, (R)0, v.x, v.y);
+    return v;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Pull of one node's 18 populations.  rm / r0 / rp point at the rows y-1, y, y+1 (plane stride ps
 // pairs, column c of the node, lattice row y); used with the shared-memory row slots (step kernel)
 // and with global memory (state read-back).  The plain form assumes no blocked link and no open
@@ -72,7 +122,7 @@ __device__ __forceinline__ R shift_of(const Params<R>& P, int k, int i) {
 template <bool kGeneral, class S, class R, class I>
 __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<S>* __restrict__ r0,
                                      const Pair<S>* __restrict__ rp, I ps, int c, uint16_t fl, bool inlet, bool outlet,
-                                     const Params<R>& P, const Params<R>& Pin, int y, R (&f)[18]) {
+                                     const Params<R>& P, const Params<R>& Pin, int y, V2<R> (&f)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const Pair<S>* src;
@@ -92,11 +142,7 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
             src = blocked ? r0 : nsrc;
             off = blocked ? (I)opp(i) * ps + b : (I)i * ps + b - cx(i);
         }
-        R va, vb;
-        if constexpr (Store<S>::kShift) load_pair<S, R>(src + off, shift_of(P, 0, i), shift_of(P, 1, i), va, vb);
-        else load_pair<S, R>(src + off, (R)0, (R)0, va, vb);
-        f[i] = va;
-        f[9 + i] = vb;
+        f[i] = load_v2<S, R>(src + off, P, i);
     }
     if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in(y), 0))
         R sc = (R)1;
@@ -104,12 +150,10 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
             const R s = (R)y + (R)0.5;
             sc = Pin.prof_c * s * ((R)Pin.ny - s);
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            f[9 * k + 1] = f[9 * k + 3] + Pin.d1[k] * sc;
-            f[9 * k + 5] = f[9 * k + 7] + Pin.d5[k] * sc;
-            f[9 * k + 8] = f[9 * k + 6] + Pin.d5[k] * sc;
-        }
+        const V2<R> s2 = vbc<R>(sc), d1 = V2<R>{Pin.d1[0], Pin.d1[1]}, d5 = V2<R>{Pin.d5[0], Pin.d5[1]};
+        f[1] = vfma(d1, s2, f[3]);
+        f[5] = vfma(d5, s2, f[7]);
+        f[8] = vfma(d5, s2, f[6]);
     }
 }
 
@@ -160,33 +204,29 @@ struct Diag {
 
 template <class R>
 struct RowState {
-    R f[18];
+    V2<R> f[9];  // (f_i^A, f_i^B)
     uint16_t fl;
     uint32_t sub;
     R ax, ay;
 };
 
-// five-row window of partial gradients per component (index 0 = the row being collided)
+// five-row window of partial gradients, both components per entry (index 0 = the row being
+// collided)
 template <class R>
 struct Grad {
-    R x[2][5], y[2][5];
+    V2<R> x[5], y[5];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int j = 0; j < 5; ++j) x[k][j] = y[k][j] = (R)0;
+        for (int j = 0; j < 5; ++j) x[j] = y[j] = vbc<R>(0);
     }
     __device__ __forceinline__ void shift() {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                x[k][j] = x[k][j + 1];
-                y[k][j] = y[k][j + 1];
-            }
-            x[k][4] = (R)0;
-            y[k][4] = (R)0;
+        for (int j = 0; j < 4; ++j) {
+            x[j] = x[j + 1];
+            y[j] = y[j + 1];
         }
+        x[4] = vbc<R>(0);
+        y[4] = vbc<R>(0);
     }
 };
 
@@ -197,25 +237,26 @@ struct Grad {
 // D1 = rho(x+1) - rho(x-1), D2 = rho(x+2) - rho(x-2), R_k = w(k^2) rho + w(1+k^2) S1 + w(4+k^2) S2
 // with S1, S2 the sums of the same pairs.
 template <class R>
-__device__ __forceinline__ void add_row(const R* __restrict__ ring, int base, Grad<R>& g, int k, R dir) {
-    const R m2 = ring[base - 2], m1 = ring[base - 1], c0 = ring[base], p1 = ring[base + 1], p2 = ring[base + 2];
-    const R D1 = p1 - m1, D2 = p2 - m2, S1 = p1 + m1, S2 = p2 + m2;
-    const R w1 = (R)w8(1), w2 = (R)w8(2), w4 = (R)w8(4), w5 = (R)w8(5), w8v = (R)w8(8);
-    const R X0 = w1 * D1 + (R)2 * w4 * D2;
-    const R X1 = w2 * D1 + (R)2 * w5 * D2;
-    const R X2 = w5 * D1 + (R)2 * w8v * D2;
+__device__ __forceinline__ void add_row(const V2<R>* __restrict__ ring, int base, Grad<R>& g, R dir) {
+    using V = V2<R>;
+    const V m2 = ring[base - 2], m1 = ring[base - 1], c0 = ring[base], p1 = ring[base + 1], p2 = ring[base + 2];
+    const V D1 = vsub(p1, m1), D2 = vsub(p2, m2), S1 = vadd(p1, m1), S2 = vadd(p2, m2);
+    const V X0 = vfma(vbc<R>(w8(1)), D1, vmul(vbc<R>(2 * w8(4)), D2));
+    const V X1 = vfma(vbc<R>(w8(2)), D1, vmul(vbc<R>(2 * w8(5)), D2));
+    const V X2 = vfma(vbc<R>(w8(5)), D1, vmul(vbc<R>(2 * w8(8)), D2));
     // window slot j holds target row r - 2 dir + j dir, i.e. dy = r - target = dir (2 - j)
-    const R R1 = dir * (w1 * c0 + w2 * S1 + w5 * S2);
-    const R R2 = dir * (R)2 * (w4 * c0 + w5 * S1 + w8v * S2);
-    g.x[k][0] += X2;
-    g.y[k][0] += R2;
-    g.x[k][1] += X1;
-    g.y[k][1] += R1;
-    g.x[k][2] += X0;
-    g.x[k][3] += X1;
-    g.y[k][3] -= R1;
-    g.x[k][4] += X2;
-    g.y[k][4] -= R2;
+    const V R1 = vmul(vbc<R>(dir), vfma(vbc<R>(w8(1)), c0, vfma(vbc<R>(w8(2)), S1, vmul(vbc<R>(w8(5)), S2))));
+    const V R2 =
+        vmul(vbc<R>((R)2 * dir), vfma(vbc<R>(w8(4)), c0, vfma(vbc<R>(w8(5)), S1, vmul(vbc<R>(w8(8)), S2))));
+    g.x[0] = vadd(g.x[0], X2);
+    g.y[0] = vadd(g.y[0], R2);
+    g.x[1] = vadd(g.x[1], X1);
+    g.y[1] = vadd(g.y[1], R1);
+    g.x[2] = vadd(g.x[2], X0);
+    g.x[3] = vadd(g.x[3], X1);
+    g.y[3] = vsub(g.y[3], R1);
+    g.x[4] = vadd(g.x[4], X2);
+    g.y[4] = vsub(g.y[4], R2);
 }
 
 // Second-layer substitution of Table 1 on top of the bulk gradient.  The row sums give
@@ -252,8 +293,8 @@ __device__ __forceinline__ void substitution_coefficients(uint32_t sub, SubCoef<
 }
 
 template <class R>
-struct Grad4 {
-    R ax, ay, bx, by;
+struct Grad2 {
+    V2<R> x, y;  // (A, B) gradient corrections
 };
 
 // Gradient correction of a wall-list node (ring slots from sb0 = row y-2 at this column).
@@ -261,19 +302,16 @@ struct Grad4 {
 // densities beyond the edge.  The step kernel inlines it where wall-list nodes are common and calls
 // the out-of-line copy otherwise, so that warps without wall-list nodes keep a small loop.
 template <class R>
-__device__ __forceinline__ Grad4<R> substitution_correction(const R* __restrict__ ringA, const R* __restrict__ ringB,
-                                                            int sb0, uint32_t sub, bool open_edge) {
+__device__ __forceinline__ Grad2<R> substitution_correction(const V2<R>* __restrict__ ring, int sb0, uint32_t sub,
+                                                            bool open_edge) {
     SubCoef<R> sc;
     substitution_coefficients<R>(sub, sc);
-    Grad4<R> g{(R)0, (R)0, (R)0, (R)0};
+    Grad2<R> g{vbc<R>(0), vbc<R>(0)};
 #pragma unroll
     for (int p = 1; p <= 8; ++p) {
-        const int o = sb0 + (cy(p) + 2) * kTc + cx(p);
-        const R nA = ringA[o], nB = ringB[o];
-        g.ax += sc.x[p - 1] * nA;
-        g.ay += sc.y[p - 1] * nA;
-        g.bx += sc.x[p - 1] * nB;
-        g.by += sc.y[p - 1] * nB;
+        const V2<R> n = ring[sb0 + (cy(p) + 2) * kTc + cx(p)];
+        g.x = vfma(vbc<R>(sc.x[p - 1]), n, g.x);
+        g.y = vfma(vbc<R>(sc.y[p - 1]), n, g.y);
     }
     if (open_edge) {
         // beyond an open column a second-layer site is not fluid, but the ring holds the clamped
@@ -281,12 +319,10 @@ __device__ __forceinline__ Grad4<R> substitution_correction(const R* __restrict_
 #pragma unroll
         for (int n = 8; n < 24; ++n) {
             if ((sub >> n) & 1u) {
-                const int o = sb0 + (s24y(n) + 2) * kTc + s24x(n);
-                const R w = (R)w8(s24x(n) * s24x(n) + s24y(n) * s24y(n));
-                g.ax -= w * (R)s24x(n) * ringA[o];
-                g.ay -= w * (R)s24y(n) * ringA[o];
-                g.bx -= w * (R)s24x(n) * ringB[o];
-                g.by -= w * (R)s24y(n) * ringB[o];
+                const V2<R> v = ring[sb0 + (s24y(n) + 2) * kTc + s24x(n)];
+                const double w = w8(s24x(n) * s24x(n) + s24y(n) * s24y(n));
+                g.x = vsub(g.x, vmul(vbc<R>(w * s24x(n)), v));
+                g.y = vsub(g.y, vmul(vbc<R>(w * s24y(n)), v));
             }
         }
     }
@@ -294,44 +330,46 @@ __device__ __forceinline__ Grad4<R> substitution_correction(const R* __restrict_
 }
 
 template <class R>
-__device__ __noinline__ Grad4<R> substitution_correction_call(const R* __restrict__ ringA, const R* __restrict__ ringB,
-                                                              int sb0, uint32_t sub, bool open_edge) {
-    return substitution_correction<R>(ringA, ringB, sb0, sub, open_edge);
+__device__ __noinline__ Grad2<R> substitution_correction_call(const V2<R>* __restrict__ ring, int sb0, uint32_t sub,
+                                                              bool open_edge) {
+    return substitution_correction<R>(ring, sb0, sub, open_edge);
 }
 
-// SRT collision with Guo forcing for one component (Eqs. 1, 2, 6, 7), written per pair (e, -e).
-// With a = e.u, b = e.F, c_s^2 = 1/3:
+// SRT collision with Guo forcing (Eqs. 1, 2, 6, 7), both components at once and written per pair
+// of directions (e, -e).  With a = e.u, b = e.F_k, c_s^2 = 1/3:
 //   f^eq_i = w rho (1 + 3a + 4.5a^2 - 1.5u^2),   F_i = w (3b - 3 u.F + 9ab)   (Guo's term, Eq. 7)
 // and f*_i = (1 - om) f_i + om f^eq_i + cF F_i splits into the part even in e,
 //   w [C0 + 4.5 a (om rho a + 2 cF b)],   C0 = om rho (1 - 1.5u^2) - 3 cF u.F,
 // and the odd part 3 w (om rho a + cF b).  With P = om rho a + cF b:
 //   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,   f*_0 = (1 - om) f_0 + w_0 C0.
+// Lanes are the components: rho, F, om and cF are (A, B) pairs; u is shared.
 template <class R>
-__device__ __forceinline__ void collide_comp(const R* f, int k, R rho, R ux, R uy, R Fx, R Fy, R om, R cf,
-                                             R (&out)[18]) {
-    const R om1 = (R)1 - om;
-    const R wr = om * rho;
-    const R C0 = wr * ((R)1 - (R)1.5 * (ux * ux + uy * uy)) - (R)3 * cf * (ux * Fx + uy * Fy);
-    out[9 * k] = om1 * f[9 * k] + (R)(4.0 / 9.0) * C0;
-    const R s1 = (R)(1.0 / 9.0) * C0, s5 = (R)(1.0 / 36.0) * C0;
+__device__ __forceinline__ void collide(const V2<R>* f, V2<R> rho, R ux, R uy, V2<R> Fx, V2<R> Fy, V2<R> om,
+                                        V2<R> cf, V2<R> (&out)[9]) {
+    using V = V2<R>;
+    const V om1 = vsub(vbc<R>(1), om);
+    const V wr = vmul(om, rho);
+    const V ux2 = vbc<R>(ux), uy2 = vbc<R>(uy);
+    const V t = vfma(vbc<R>(-1.5), vfma(ux2, ux2, vmul(uy2, uy2)), vbc<R>(1));
+    const V uF = vfma(uy2, Fy, vmul(ux2, Fx));
+    const V C0 = vfma(wr, t, vmul(vmul(vbc<R>(-3), cf), uF));
+    out[0] = vfma(om1, f[0], vmul(vbc<R>(4.0 / 9.0), C0));
+    const V s1 = vmul(vbc<R>(1.0 / 9.0), C0), s5 = vmul(vbc<R>(1.0 / 36.0), C0);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {  // pairs (1,3): e = (1,0); (2,4): (0,1); (5,7): (1,1); (6,8): (-1,1)
-        const R a = p == 0 ? ux : p == 1 ? uy : p == 2 ? ux + uy : uy - ux;
-        const R b = p == 0 ? Fx : p == 1 ? Fy : p == 2 ? Fx + Fy : Fy - Fx;
+        const V a = p == 0 ? ux2 : p == 1 ? uy2 : p == 2 ? vadd(ux2, uy2) : vsub(uy2, ux2);
+        const V b = p == 0 ? Fx : p == 1 ? Fy : p == 2 ? vadd(Fx, Fy) : vsub(Fy, Fx);
         const double w = p < 2 ? 1.0 / 9.0 : 1.0 / 36.0;
-        const R cb = cf * b;
-        const R P = wr * a + cb;
-        const R sym = (p < 2 ? s1 : s5) + (R)(4.5 * w) * (a * (P + cb));
-        const R anti = (R)(3.0 * w) * P;
+        const V cb = vmul(cf, b);
+        const V P = vfma(wr, a, cb);
+        const V sym = vfma(vbc<R>(4.5 * w), vmul(a, vadd(P, cb)), p < 2 ? s1 : s5);
+        const V anti = vmul(vbc<R>(3.0 * w), P);
         const int ip = p < 2 ? 1 + p : 3 + p, im = p < 2 ? 3 + p : 5 + p;
-        out[9 * k + ip] = om1 * f[9 * k + ip] + (sym + anti);
-        out[9 * k + im] = om1 * f[9 * k + im] + (sym - anti);
+        out[ip] = vfma(om1, f[ip], vadd(sym, anti));
+        out[im] = vfma(om1, f[im], vsub(sym, anti));
     }
 }
 
-// Ghost columns per side of a stored row (>= 3, and a 16-byte multiple for every pair size).  The
-// tensor box of a window starts G columns left of the window (column xs - G, pair xs) and is T
-// pairs wide, which covers the columns xs - 3 .. xs + T - 6 that the density columns pull from.
 template <class S>
 struct Layout {
     static constexpr int G = 4;
@@ -375,8 +413,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
     constexpr int G = Layout<S>::G;
     constexpr int BX = T;  // pairs per plane of a row slot
     const SmemPlan<S, R> plan(T);
-    R* ringA = reinterpret_cast<R*>(smem + plan.ring_off);
-    R* ringB = ringA + 2 * kRing * T;
+    V2<R>* ring = reinterpret_cast<V2<R>*>(smem + plan.ring_off);  // (rho_A, rho_B) per column
     const uint32_t bar0 = smem_u32(smem + plan.bar_off);
     const uint32_t slot0 = smem_u32(smem);
     const uint32_t box_bytes = (uint32_t)((size_t)BX * 9 * sizeof(Pair<S>) + (size_t)(T + 8) * sizeof(uint16_t));
@@ -472,7 +509,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             st.fl = (rcol && (P.bc_y == kPeriodic || (r >= 0 && r < P.ny)))
                         ? reinterpret_cast<const uint16_t*>(s0 + plan.pop_bytes)[t + 6]
                         : kSolidBit;
-            R ra = 0, rb = 0;
+            V2<R> rho2 = vbc<R>(0);
             const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
             if (!(st.fl & kSolidBit)) {
                 const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(slot_back(dir > 0 ? 2 : 0));
@@ -481,9 +518,9 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 if (general) pull<true, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 else pull<false, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 // rho_k = sum_i f_i as a balanced tree (short dependency chains)
-                const R* f = st.f;
-                ra = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + (f[7] + f[8])));
-                rb = ((f[9] + f[10]) + (f[11] + f[12])) + ((f[13] + f[14]) + (f[15] + (f[16] + f[17])));
+                const V2<R>* f = st.f;
+                rho2 = vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])),
+                            vadd(vadd(f[4], f[5]), vadd(f[6], vadd(f[7], f[8]))));
                 if (st.fl & kWallBit) {
                     const long long o = C.d_off + (long long)wrap_row(r) * P.nx + X;
                     st.sub = __ldg(a.wsub + o);
@@ -492,10 +529,8 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 }
             }
             const int s = m * T + t;
-            ringA[s] = ra;
-            ringB[s] = rb;
-            ringA[s + kRing * T] = ra;
-            ringB[s + kRing * T] = rb;
+            ring[s] = rho2;
+            ring[s + kRing * T] = rho2;
             return ok;
         };
 
@@ -517,22 +552,22 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                 return;
             }
             const int sb0 = lo * T + t;
-            const R rA = ringA[sb0 + 2 * T], rB = ringB[sb0 + 2 * T];
-            R gAx = g.x[0][0], gAy = g.y[0][0], gBx = g.x[1][0], gBy = g.y[1][0];
+            const V2<R> r2 = ring[sb0 + 2 * T];
+            const R rA = r2.x, rB = r2.y;
+            V2<R> gx = g.x[0], gy = g.y[0];
             const bool wall = (st.fl & kWallBit) != 0;
             if (wall) {
                 const bool open_edge = P.bc_x == kOpen && (X < 2 || X >= P.nx - 2);
-                Grad4<R> c4;
-                if constexpr (kWallInline) c4 = substitution_correction<R>(ringA, ringB, sb0, st.sub, open_edge);
-                else c4 = substitution_correction_call<R>(ringA, ringB, sb0, st.sub, open_edge);
-                gAx += c4.ax;
-                gAy += c4.ay;
-                gBx += c4.bx;
-                gBy += c4.by;
+                Grad2<R> c2;
+                if constexpr (kWallInline) c2 = substitution_correction<R>(ring, sb0, st.sub, open_edge);
+                else c2 = substitution_correction_call<R>(ring, sb0, st.sub, open_edge);
+                gx = vadd(gx, c2.x);
+                gy = vadd(gy, c2.y);
             }
             // cohesion: each component is pushed by the other's pseudopotential gradient (Eq. 8)
-            R FAx = -P.G * rA * gBx, FAy = -P.G * rA * gBy;
-            R FBx = -P.G * rB * gAx, FBy = -P.G * rB * gAy;
+            const R nGA = -P.G * rA, nGB = -P.G * rB;
+            R FAx = nGA * gx.y, FAy = nGA * gy.y;
+            R FBx = nGB * gx.x, FBy = nGB * gy.x;
             if (wall) {  // adhesion (Eq. 9), G_w1 local in the improved scheme (Eqs. 10, 12)
                 R GA;
                 const Params<R>& Q = s_par;
@@ -556,11 +591,11 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             FAy += rA * P.gy;
             FBx += rB * P.gx;
             FBy += rB * P.gy;
-            const R* f = st.f;
-            const R s1 = f[1] + f[10], s2 = f[2] + f[11], s3 = f[3] + f[12], s4 = f[4] + f[13];
-            const R s5 = f[5] + f[14], s6 = f[6] + f[15], s7 = f[7] + f[16], s8 = f[8] + f[17];
-            const R mx = (s1 - s3) + ((s5 - s7) + (s8 - s6));
-            const R my = (s2 - s4) + ((s5 - s7) + (s6 - s8));
+            const V2<R>* f = st.f;
+            // momentum per component, then summed over the components (Eq. 4)
+            const V2<R> d13 = vsub(f[1], f[3]), d24 = vsub(f[2], f[4]), d57 = vsub(f[5], f[7]), d68 = vsub(f[6], f[8]);
+            const V2<R> mx2 = vadd(d13, vsub(d57, d68)), my2 = vadd(d24, vadd(d57, d68));
+            const R mx = mx2.x + mx2.y, my = my2.x + my2.y;
             const R rho = rA + rB;
             const R inv = (R)1 / rho;
             const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
@@ -591,27 +626,21 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
                     if (!(rA > (R)0) || !(rB > (R)0) || !isfinite(u2) || !isfinite(rA) || !isfinite(rB)) dg.bad = true;
                 }
             } else {
-                R o[18];
-                collide_comp<R>(f, 0, rA, ux, uy, FAx, FAy, P.omega[0], P.cF[0], o);
-                collide_comp<R>(f, 1, rB, ux, uy, FBx, FBy, P.omega[1], P.cF[1], o);
+                V2<R> o[9];
+                collide<R>(f, r2, ux, uy, V2<R>{FAx, FBx}, V2<R>{FAy, FBy}, V2<R>{P.omega[0], P.omega[1]},
+                           V2<R>{P.cF[0], P.cF[1]}, o);
                 Pair<S>* out = fo + (long long)y * P.pitch + x + G;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    R va = o[i], vb = o[9 + i];
-                    if constexpr (Store<S>::kShift) {
-                        va -= shift_of(P, 0, i);
-                        vb -= shift_of(P, 1, i);
-                    }
-                    o[i] = va;
-                    o[9 + i] = vb;
-                    store_pair<S, R>(out, va, vb);
+                    if constexpr (Store<S>::kShift) o[i] = vsub(o[i], V2<R>{shift_of(P, 0, i), shift_of(P, 1, i)});
+                    store_pair<S, R>(out, o[i].x, o[i].y);
                     out += P.plane;
                 }
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
                     Pair<S>* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        store_pair<S, R>(gout, o[i], o[9 + i]);
+                        store_pair<S, R>(gout, o[i].x, o[i].y);
                         gout += P.plane;
                     }
                 }
@@ -642,9 +671,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             if (__syncthreads_or(!mine)) return false;
             if (t == 0 && (dir > 0 ? next_row <= r_last : next_row >= r_last)) issue();  // slot of q-dir is free
             if (interior) {
-                const int base = mq * T + t;
-                add_row<R>(ringA, base, g, 0, rdir);
-                add_row<R>(ringB, base, g, 1, rdir);
+                add_row<R>(ring, mq * T + t, g, rdir);
             }
             const int y = q - 2 * dir;
             // slot of row y - 2: q - 4 when marching up (= mq + 2 mod kRing), q itself marching down
@@ -862,10 +889,10 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
         const uint16_t fl = flags_all[C.d_off + s];
-        R v[18];
+        V2<R> v[9];
         if (fl & kSolidBit) {
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = 0;
+            for (int i = 0; i < 9; ++i) v[i] = vbc<R>(0);
         } else {
             // rows beyond a wall are reached only through blocked links; clamping keeps the unused
             // row pointer inside the buffer
@@ -876,7 +903,10 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
                                         fin + (long long)yp * C.pitch, P.plane, X + G, fl, inlet, outlet, P, P, Y, v);
         }
 #pragma unroll
-        for (int q = 0; q < 18; ++q) f[(long long)q * N + s] = (double)v[q];
+        for (int i = 0; i < 9; ++i) {
+            f[(long long)i * N + s] = (double)v[i].x;
+            f[(long long)(9 + i) * N + s] = (double)v[i].y;
+        }
     }
 }
 
