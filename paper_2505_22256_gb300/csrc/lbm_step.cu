@@ -99,6 +99,11 @@ __device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
     return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
+// 1 / x: FP32 takes the hardware reciprocal approximation (within 2 ulp; it only scales the
+// velocity), FP64 the correctly rounded division.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <class R, class T>
 __device__ __forceinline__ V2<R> vbc(T v) {  // the same value in both lanes, in the compute type
     return V2<R>{(R)v, (R)v};
@@ -429,9 +434,12 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
 
     // Row loads are numbered per block: load n goes to slot n % kSlots and completes phase
     // n / kSlots of that slot's barrier.  (slot, parity) of the next load to issue and of the next
-    // load to wait for advance incrementally.
-    int issue_slot = 0, wait_slot = 0;
+    // load to wait for advance incrementally; so_m / so_0 / so_p are the byte offsets of the slots
+    // of the last three rows waited for.
+    int issue_slot = 0;
     uint32_t issue_par = 0, wait_par = 0;
+    uint32_t wait_off = 0, wait_bar = bar0;
+    uint32_t so_m = 0, so_0 = 0, so_p = 0;
     bool failed = false;
 
     // Work items are claimed from a counter, so blocks that share a busy SM take fewer of them.  The
@@ -486,25 +494,24 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             }
         };
         auto wait_next = [&]() -> bool {  // wait for the oldest load not yet waited for
-            const bool okw = mbar_wait_bounded(bar0 + 8 * wait_slot, wait_par);
-            if (++wait_slot == kSlots) {
-                wait_slot = 0;
+            const bool okw = mbar_wait_bounded(wait_bar, wait_par);
+            so_m = so_0;
+            so_0 = so_p;
+            so_p = wait_off;
+            wait_off += (uint32_t)plan.slot_bytes;
+            wait_bar += 8;
+            if (wait_bar == bar0 + 8 * kSlots) {
+                wait_bar = bar0;
+                wait_off = 0;
                 wait_par ^= 1u;
             }
             return okw;
         };
-        // the slot just waited for holds row r+dir; rows r and r-dir sit in the two before it
-        auto slot_back = [&](int back) -> const unsigned char* {
-            int sidx = wait_slot - 1 - back;
-            sidx += sidx < 0 ? kSlots : 0;
-            sidx += sidx < 0 ? kSlots : 0;
-            return smem + sidx * plan.slot_bytes;
-        };
 
         // densities of row r into the ring, populations of row r into st
         auto rho_row = [&](int r, int m, RowState<R>& st) -> bool {
-            const bool ok = wait_next();  // f* row r+dir
-            const unsigned char* s0 = slot_back(1);
+            const bool ok = wait_next();  // f* row r+dir; rows r and r-dir sit in the two slots before
+            const unsigned char* s0 = smem + so_0;
             // node flags of row r; rows beyond a wall boundary are solid
             st.fl = (rcol && (P.bc_y == kPeriodic || (r >= 0 && r < P.ny)))
                         ? reinterpret_cast<const uint16_t*>(s0 + plan.pop_bytes)[t + 6]
@@ -512,9 +519,9 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             V2<R> rho2 = vbc<R>(0);
             const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
             if (!(st.fl & kSolidBit)) {
-                const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(slot_back(dir > 0 ? 2 : 0));
+                const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_m : so_p));
                 const Pair<S>* r0 = reinterpret_cast<const Pair<S>*>(s0);
-                const Pair<S>* rp = reinterpret_cast<const Pair<S>*>(slot_back(dir > 0 ? 0 : 2));
+                const Pair<S>* rp = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_p : so_m));
                 if (general) pull<true, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 else pull<false, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
                 // rho_k = sum_i f_i as a balanced tree (short dependency chains)
@@ -597,7 +604,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             const V2<R> mx2 = vadd(d13, vsub(d57, d68)), my2 = vadd(d24, vadd(d57, d68));
             const R mx = mx2.x + mx2.y, my = my2.x + my2.y;
             const R rho = rA + rB;
-            const R inv = (R)1 / rho;
+            const R inv = recip(rho);
             const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
             const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
             if constexpr (kFields) {
@@ -633,8 +640,7 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     if constexpr (Store<S>::kShift) o[i] = vsub(o[i], V2<R>{shift_of(P, 0, i), shift_of(P, 1, i)});
-                    store_pair<S, R>(out, o[i].x, o[i].y);
-                    out += P.plane;
+                    store_pair<S, R>(out + i * P.plane, o[i].x, o[i].y);
                 }
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
                     Pair<S>* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
