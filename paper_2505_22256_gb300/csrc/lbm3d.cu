@@ -5,17 +5,17 @@
 // compute type R (float or double), N = nx ny nz, x fastest; two buffers.  One time step is two
 // launches:
 //   k3_rho    pull f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link (halfway
-//             bounce-back, Sec. 3.5); rho_k = sum_i f_i (Eq. 3) into two density arrays
-//   k3_step   the same pull for the node's own populations and momentum (Eq. 4); cohesion (Eq. 8)
+//             bounce-back, Sec. 3.5); (rho_A, rho_B) = sum_i f_i (Eq. 3) into one interleaved
+//             density array
+//   k3_march  the same pull for the node's own populations and momentum (Eq. 4); cohesion (Eq. 8)
 //             and adhesion (Eq. 9, local parameter of Eqs. 10-12) on the 92-offset eighth-order
-//             stencil read from the density arrays -- nodes with a solid node inside the stencil
-//             apply the second-layer copy x + sign(e) (Sec. 2.4) and the solid switch; body force;
-//             velocity with Guo's half-force shift (Eq. 5); SRT collision with Guo forcing (Eqs. 1,
-//             2, 6, 7) written to the other buffer.  Its fields form writes rho and u in FP64 and
-//             per-block diagnostic sums instead of colliding.
-// The densities, interleaved (rho_A, rho_B) per node, are small enough to stay largely in L2
-// while k3_step reads its stencil from them; each thread precomputes its wrapped neighbourhood
-// (32-bit indices), so a stencil site costs one add and one 64-bit load.  Periodic in x, y and z.
+//             stencil -- nodes with a solid node inside the stencil apply the second-layer copy
+//             x + sign(e) (Sec. 2.4) and the solid switch; body force; velocity with Guo's
+//             half-force shift (Eq. 5); SRT collision with Guo forcing (Eqs. 1, 2, 6, 7) written to
+//             the other buffer.  Blocks march along z with the stencil's density planes in shared
+//             memory.  k3_fields is its fields form: rho and u in FP64 and per-block diagnostic sums
+//             instead of colliding.
+// Periodic in x, y and z.
 #include <math.h>
 #include <stdarg.h>
 
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict
     const int s = (z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
     typename Rho2<R>::T r;
-    r.x = (R)0;
-    r.y = (R)0;
+    r.x = (R)-1;  // solid sites carry -1: the step kernel's wall path tells them apart by the sign
+    r.y = (R)-1;
     if (!(fl & k3Solid)) {
         const Nb3 nb(g, x, y, z);
         R f[38];
@@ -181,20 +181,20 @@ __device__ __forceinline__ double d3_neutral(int q) {
     return (q == 6 || q == 8) ? INFINITY : (q == 7 || q == 9) ? -INFINITY : 0.0;
 }
 
-// One node per thread.  kFields: write rho_A, rho_B, u (FP64) and per-block diagnostic records
-// (block index blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
-template <class R, bool kFields>
-__global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
-                                               const uint8_t* __restrict__ solid, const R* __restrict__ fs,
-                                               const typename Rho2<R>::T* __restrict__ rho, R* __restrict__ fout,
-                                               double* __restrict__ o5, double* __restrict__ part) {
+// Fields form of the step, one node per thread: the same pull, moments and forces as the step
+// kernel below, writing rho_A, rho_B, u (FP64) and per-block diagnostic records (block index
+// blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
+template <class R>
+__global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
+                                                 const uint8_t* __restrict__ solid, const R* __restrict__ fs,
+                                                 const typename Rho2<R>::T* __restrict__ rho,
+                                                 double* __restrict__ o5, double* __restrict__ part) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     const bool in = x < g.nx && y < g.ny;
     const int s = (z * g.ny + (in ? y : 0)) * g.nx + (in ? x : 0);
     const uint32_t fl = in ? flags[s] : k3Solid;
     double rec[k3DiagN];
-    if constexpr (kFields)
-        for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
+    for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
     if (!(fl & k3Solid)) {
         const Nb3 nb(g, x, y, z);
         R f[38];
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
             FB[d] = -P.G * rB * gA[d] - P.Gw2 * rB * ad[d] + rB * P.g[d];
             u[d] = (m[d] + (R)0.5 * (FA[d] + FB[d])) / rho;
         }
-        if constexpr (kFields) {
+        {
             if (o5) {
                 o5[s] = (double)rA;
                 o5[g.N + s] = (double)rB;
@@ -298,29 +298,11 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
             rec[8] = rec[9] = (double)rB;
             rec[10] = 1.0;
             rec[11] = (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB)) ? 1.0 : 0.0;
-        } else {
-            const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const R rk = k == 0 ? rA : rB;
-                const R* F = k == 0 ? FA : FB;
-                const R om = P.omega[k], cf = P.cF[k];
-#pragma unroll
-                for (int i = 0; i < 19; ++i) {
-                    const R eu = e3x(i) * u[0] + e3y(i) * u[1] + e3z(i) * u[2];
-                    const R eF = e3x(i) * F[0] + e3y(i) * F[1] + e3z(i) * F[2];
-                    const R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-                    const R feq = (R)w19(i) * rk * ((R)1 + (R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * usq);
-                    const R Fi = (R)w19(i) * ((R)3 * (eF - uF) + (R)9 * eu * eF);
-                    const R v = f[19 * k + i];
-                    fout[(long long)(19 * k + i) * g.N + s] = v + om * (feq - v) + cf * Fi;
-                }
-            }
         }
-    } else if (kFields && in && o5) {
+    } else if (in && o5) {
         for (int q = 0; q < 5; ++q) o5[q * g.N + s] = 0.0;
     }
-    if constexpr (kFields) {
+    {
         __shared__ double red[4][k3DiagN];
         const int lane = threadIdx.x, warp = threadIdx.y;  // blocks of 32 x 4
         for (int q = 0; q < k3DiagN; ++q) {
@@ -337,6 +319,265 @@ __global__ void __launch_bounds__(128) k3_step(Geo3 g, P3<R> P, const uint32_t* 
                 part[b * k3DiagN + q] = v;
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Step kernel of the 3-D form.  A block of 32 x 4 columns (x, y) marches over a chunk of z planes.
+// The density pairs (rho_A, rho_B) of the planes z-2 .. z+2 over the block's columns and a halo of
+// two on each side (36 x 8 sites per plane) sit in a six-plane shared-memory ring; solid sites
+// hold -1, so nodes near the wall take the second-layer copy and the solid switch out of the ring
+// as well.  Each thread loads its share of the halo of plane z+4 into registers one plane before
+// it enters the ring, and the flags of the next plane.  Per plane: pull of the node's 38
+// populations, stencil sums out of the ring, moments, forces, collision, store; one barrier.  Both
+// components share each instruction: densities, gradients, forces and populations are (A, B) pairs.
+// ------------------------------------------------------------------------------------------------
+constexpr int k3TX = 32, k3TY = 4, k3T = k3TX * k3TY;   // block = 32 x 4 columns
+constexpr int k3HX = k3TX + 4, k3HY = k3TY + 4;           // halo region of one plane: 36 x 8
+constexpr int k3HP = k3HX * k3HY;
+constexpr int k3HN = (k3HP + k3T - 1) / k3T;              // halo sites loaded per thread
+constexpr int k3Ring = 6;                                 // density planes resident
+
+template <class R>
+constexpr size_t k3_ring_bytes() {
+    return (size_t)k3Ring * k3HP * sizeof(V2<R>);
+}
+template <class R>
+constexpr size_t k3_march_smem() {
+    return k3_ring_bytes<R>();
+}
+
+#ifndef LBM3_MIN_BLOCKS
+#define LBM3_MIN_BLOCKS 3
+#endif
+template <class R>
+__global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
+    k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
+             const V2<R>* __restrict__ rho, R* __restrict__ fout) {
+    using V = V2<R>;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    V* ring = reinterpret_cast<V*>(smem3);
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * k3TX + tx;
+    const int x0 = blockIdx.x * k3TX, y0 = blockIdx.y * k3TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+    const bool active = x < g.nx && y < g.ny;
+    const int nxy = g.nx * g.ny;
+
+    // this thread's halo sites: in-plane offsets of the wrapped columns
+    int hoff[k3HN];
+#pragma unroll
+    for (int k = 0; k < k3HN; ++k) {
+        const int j = t + k * k3T;
+        const int hx = j % k3HX, hy = j / k3HX;
+        const int gx = ((x0 - 2 + hx) % g.nx + g.nx) % g.nx, gy = ((y0 - 2 + hy) % g.ny + g.ny) % g.ny;
+        hoff[k] = j < k3HP ? gy * g.nx + gx : -1;
+    }
+    auto load_plane = [&](int p, V (&v)[k3HN]) {
+        const int zo = wrapc(p, g.nz) * nxy;
+#pragma unroll
+        for (int k = 0; k < k3HN; ++k)
+            if (hoff[k] >= 0) v[k] = __ldg(rho + zo + hoff[k]);
+    };
+    auto slot = [&](int p) -> int { return wrapc(p % k3Ring, k3Ring); };  // ring slot of plane p >= -2
+    auto store_plane = [&](int p, const V (&v)[k3HN]) {
+        V* dst = ring + slot(p) * k3HP;
+#pragma unroll
+        for (int k = 0; k < k3HN; ++k)
+            if (hoff[k] >= 0) dst[t + k * k3T] = v[k];
+    };
+    const int yx = active ? y * g.nx + x : 0;
+    const Nb3 nb(g, active ? x : 0, active ? y : 0, 0);
+    // the node's 38 populations at plane z: f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link
+    auto pull_plane = [&](int z, uint32_t fl, V (&f)[19]) {
+        const int s = z * nxy + yx;
+        const int zoff[3] = {wrapc(z - 1, g.nz) * nxy, z * nxy, wrapc(z + 1, g.nz) * nxy};
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            int src, q;
+            if (i > 0 && ((fl >> (i - 1)) & 1u)) {
+                src = s;
+                q = opp3(i);
+            } else {
+                src = i == 0 ? s : zoff[1 - e3z(i)] + nb.yo[2 - e3y(i)] + nb.xw[2 - e3x(i)];
+                q = i;
+            }
+            f[i] = V{fs[(long long)q * g.N + src], fs[(long long)(19 + q) * g.N + src]};
+        }
+    };
+
+    // prologue: planes z0-2 .. z0+2 into the ring, plane z0+3 into registers, populations of z0
+    uint32_t fl_nx = active ? flags[z0 * nxy + yx] : k3Solid;
+    {
+        V v[5][k3HN];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) load_plane(z0 - 2 + d, v[d]);
+#pragma unroll
+        for (int d = 0; d < 5; ++d) store_plane(z0 - 2 + d, v[d]);
+    }
+    V nxt[k3HN];
+    load_plane(z0 + 3, nxt);
+    __syncthreads();
+
+    for (int z = z0; z < z1; ++z) {
+        V nn[k3HN];
+        if (z + 4 <= z1 + 1) load_plane(z + 4, nn);  // planes up to z1 + 1 are needed
+        const uint32_t fl = fl_nx;  // the flags are loaded one plane ahead
+        if (z + 1 < z1 && active) fl_nx = flags[(z + 1) * nxy + yx];
+        const int s = z * nxy + yx;
+        if (!(fl & k3Solid)) {
+            V f[19];
+            pull_plane(z, fl, f);
+            // the node's stencil out of the ring: bs[d] = plane z - 2 + d at the node's column
+            const V* bs[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) bs[d] = ring + slot(z - 2 + d) * k3HP + (ty + 2) * k3HX + (tx + 2);
+            const V r2 = bs[2][0];
+            V gx = vbc<R>(0), gy = vbc<R>(0), gz = vbc<R>(0);  // (A, B) density gradients
+            R ad[3] = {(R)0, (R)0, (R)0};
+            if (!(fl & k3Wall)) {
+                // symmetric pairs (e, -e): w e (rho(x+e) - rho(x-e)), the differences first; two sets
+                // of partial sums (odd / even dx) shorten the dependency chains
+                V hx[2] = {gx, gx}, hy[2] = {gy, gy}, hz[2] = {gz, gz};
+#pragma unroll
+                for (int dz = 0; dz <= 2; ++dz)
+#pragma unroll
+                    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                        for (int dx = -2; dx <= 2; ++dx) {
+                            if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;  // one of each pair
+                            const int q = dx * dx + dy * dy + dz * dz;
+                            if (w92(q) == 0.0) continue;
+                            const int h = dx & 1;
+                            const V a = vsub(bs[2 + dz][dy * k3HX + dx], bs[2 - dz][-dy * k3HX - dx]);
+                            if (dx != 0) hx[h] = vfma(vbc<R>(w92(q) * dx), a, hx[h]);
+                            if (dy != 0) hy[h] = vfma(vbc<R>(w92(q) * dy), a, hy[h]);
+                            if (dz != 0) hz[h] = vfma(vbc<R>(w92(q) * dz), a, hz[h]);
+                        }
+                gx = vadd(hx[0], hx[1]);
+                gy = vadd(hy[0], hy[1]);
+                gz = vadd(hz[0], hz[1]);
+            } else {  // second-layer copy of x + sign(e) for non-fluid second-layer sites; solid switch
+                // (solid sites hold -1 in the ring)
+#pragma unroll
+                for (int dz = 0; dz <= 2; ++dz)
+#pragma unroll
+                    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                        for (int dx = -2; dx <= 2; ++dx) {
+                            if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+                            const int q = dx * dx + dy * dy + dz * dz;
+                            const double wq = w92(q);
+                            if (wq == 0.0) continue;
+                            const bool second = dx == 2 || dx == -2 || dy == 2 || dy == -2 || dz == 2 || dz == -2;
+                            V v[2];
+                            R vs[2];
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const int sg = side == 0 ? 1 : -1;
+                                const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
+                                V w = bs[2 + ez][ey * k3HX + ex];
+                                if (second && w.x < (R)0) {
+                                    const int fx = (ex > 0) - (ex < 0), fy = (ey > 0) - (ey < 0), fz = (ez > 0) - (ez < 0);
+                                    w = bs[2 + fz][fy * k3HX + fx];
+                                }
+                                const bool sol = w.x < (R)0;
+                                v[side] = sol ? vbc<R>(0) : w;
+                                vs[side] = sol ? (R)1 : (R)0;
+                            }
+                            const V a = vsub(v[0], v[1]);
+                            const R w = (R)wq, sw = vs[0] - vs[1];
+                            gx = vfma(vbc<R>(wq * dx), a, gx);
+                            gy = vfma(vbc<R>(wq * dy), a, gy);
+                            gz = vfma(vbc<R>(wq * dz), a, gz);
+                            ad[0] += w * dx * sw;
+                            ad[1] += w * dy * sw;
+                            ad[2] += w * dz * sw;
+                        }
+            }
+            const R rA = r2.x, rB = r2.y;
+            R GA = (R)0;
+            if (fl & k3Wall) {
+                if (P.mode == 1) {
+                    const R re = (rA - rB) / (rA + rB);
+                    R h;
+                    if (re > P.delta) h = P.lam;
+                    else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
+                    else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
+                    else h = (R)1;
+                    GA = P.Gw2 * h;
+                } else {
+                    GA = P.lam * P.Gw2;
+                }
+            }
+            // momentum per component from the differences of opposite populations (i odd, opp = i + 1)
+            V mv[3] = {vbc<R>(0), vbc<R>(0), vbc<R>(0)};
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                const V d = vsub(f[i], f[i + 1]);
+                if (e3x(i) != 0) mv[0] = e3x(i) > 0 ? vadd(mv[0], d) : vsub(mv[0], d);
+                if (e3y(i) != 0) mv[1] = e3y(i) > 0 ? vadd(mv[1], d) : vsub(mv[1], d);
+                if (e3z(i) != 0) mv[2] = e3z(i) > 0 ? vadd(mv[2], d) : vsub(mv[2], d);
+            }
+            const V gv[3] = {gx, gy, gz};
+            const R inv = recip(rA + rB);
+            V F[3];
+            R u[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                // each component is pushed by the other's gradient (Eq. 8); adhesion (Eq. 9); body force
+                const R FA = -P.G * rA * gv[d].y - GA * rA * ad[d] + rA * P.g[d];
+                const R FB = -P.G * rB * gv[d].x - P.Gw2 * rB * ad[d] + rB * P.g[d];
+                F[d] = V{FA, FB};
+                u[d] = ((mv[d].x + mv[d].y) + (R)0.5 * (FA + FB)) * inv;
+            }
+            // SRT collision with Guo forcing, per pair of directions (e, -e), both components at
+            // once.  With a = e.u, b = e.F_k, P = om rho a + cF b, C0 = om rho (1 - 1.5u^2) - 3 cF u.F:
+            //   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,  f*_0 = (1 - om) f_0 + w_0 C0
+            const V om = V{P.omega[0], P.omega[1]}, cf = V{P.cF[0], P.cF[1]};
+            const V om1 = vsub(vbc<R>(1), om);
+            const V wr = vmul(om, r2);
+            const V u2v[3] = {vbc<R>(u[0]), vbc<R>(u[1]), vbc<R>(u[2])};
+            const R tq = (R)1 - (R)1.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const V uF = vfma(u2v[2], F[2], vfma(u2v[1], F[1], vmul(u2v[0], F[0])));
+            const V C0 = vfma(wr, vbc<R>(tq), vmul(vmul(vbc<R>(-3), cf), uF));
+            V o[19];
+            o[0] = vfma(om1, f[0], vmul(vbc<R>(w19(0)), C0));
+            const V sAx = vmul(vbc<R>(w19(1)), C0), sDg = vmul(vbc<R>(w19(7)), C0);
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                auto dot = [&](const V* vv) -> V {  // e_i . vv for a pair-valued vector
+                    V r = vbc<R>(0);
+                    bool first = true;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int e = d == 0 ? e3x(i) : d == 1 ? e3y(i) : e3z(i);
+                        if (e == 0) continue;
+                        if (first) r = e > 0 ? vv[d] : vsub(vbc<R>(0), vv[d]);
+                        else r = e > 0 ? vadd(r, vv[d]) : vsub(r, vv[d]);
+                        first = false;
+                    }
+                    return r;
+                };
+                const double w = w19(i);
+                const V a = dot(u2v), b = dot(F);
+                const V cb = vmul(cf, b);
+                const V Pp = vfma(wr, a, cb);
+                const V sym = vfma(vbc<R>(4.5 * w), vmul(a, vadd(Pp, cb)), i <= 6 ? sAx : sDg);
+                const V anti = vmul(vbc<R>(3.0 * w), Pp);
+                o[i] = vfma(om1, f[i], vadd(sym, anti));
+                o[i + 1] = vfma(om1, f[i + 1], vsub(sym, anti));
+            }
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                fout[(long long)i * g.N + s] = o[i].x;
+                fout[(long long)(19 + i) * g.N + s] = o[i].y;
+            }
+        }
+        if (z + 3 <= z1 + 1) store_plane(z + 3, nxt);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < k3HN; ++k) nxt[k] = nn[k];
     }
 }
 
@@ -623,6 +864,15 @@ P3<R> make_p3(const lbm3d_params& p) {
 dim3 grid3(const Geo3& g) { return dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz); }
 const dim3 kBlock3(32, 4, 1);
 
+// z planes per block of the step kernel: about 16, spread evenly over nz
+#ifndef LBM3_ZCHUNK
+#define LBM3_ZCHUNK 16
+#endif
+int zchunk3(const Geo3& g) {
+    const int chunks = (g.nz + LBM3_ZCHUNK - 1) / LBM3_ZCHUNK;
+    return (g.nz + chunks - 1) / chunks;
+}
+
 cudaError_t scratch_for(lbm3d_ctx* c) {
     if (c->scratch) return cudaSuccess;
     return cudaMalloc(&c->scratch, (size_t)38 * c->g.N * sizeof(double));
@@ -635,8 +885,11 @@ cudaError_t step_once(lbm3d_ctx* c) {
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
     k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, false><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho,
-                                                 reinterpret_cast<R*>(c->f[1 - c->cur]), nullptr, nullptr);
+    const int zc = zchunk3(c->g);
+    const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
+                  (unsigned)((c->g.nz + zc - 1) / zc));
+    k3_march<R><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho,
+                                                               reinterpret_cast<R*>(c->f[1 - c->cur]));
     c->cur ^= 1;
     return cudaGetLastError();
 }
@@ -649,7 +902,7 @@ cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
     k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_step<R, true><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, nullptr, o5, c->part);
+    k3_fields<R><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, o5, c->part);
     if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
     return cudaGetLastError();
 }
@@ -804,6 +1057,13 @@ extern "C" void lbm3d_destroy(lbm3d_ctx* c) {
 extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
     if (!c) return report_error(LBM_EINVAL, "NULL context");
     if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
+    // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
+    TRY3(c->storage == LBM_STORE_F64
+             ? cudaFuncSetAttribute(k3_march<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k3_march_smem<double>())
+             : cudaFuncSetAttribute(k3_march<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k3_march_smem<float>()),
+         "step kernel attributes");
     for (int64_t t = 0; t < n; ++t) {
         const cudaError_t e = c->storage == LBM_STORE_F64 ? step_once<double>(c) : step_once<float>(c);
         TRY3(e, "step kernels");

@@ -242,6 +242,52 @@ __device__ __forceinline__ void store_pair<__nv_bfloat16, float>(Pair<__nv_bfloa
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(va, vb);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Component pairs.  Every per-component quantity of a step (the populations f_i^A, f_i^B, the
+// densities, their gradients, forces and relaxation rates) is held as a pair (A, B), so that in
+// FP32 one packed FP32x2 instruction (sm_100 and later) does the work of both components.  Each
+// lane rounds exactly like the scalar operation.  FP64 pairs are two scalar operations.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using T = float2;
+};
+template <>
+struct PairOf<double> {
+    using T = double2;
+};
+template <class R>
+using V2 = typename PairOf<R>::T;
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <class R, class T>
+__device__ __forceinline__ V2<R> vbc(T v) {  // the same value in both lanes, in the compute type
+    return V2<R>{(R)v, (R)v};
+}
+
+// 1 / x: FP32 takes the hardware reciprocal approximation (within 2 ulp; it only scales
+// velocities), FP64 the correctly rounded division.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Compute type for a storage type: FP64 storage computes in FP64, everything else in FP32.
 template <class S>
 struct ComputeOf {
