@@ -585,7 +585,7 @@ def run_ours_3d(args):
                    "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE_3D[args.storage] / 2 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": algo / (launch_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": algo / (launch_ms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k3_rho + k3_step (one time step)", "algorithmic_bytes_per_launch": algo,
+                     "kernel": "k3_rho + k3_march (one time step)", "algorithmic_bytes_per_launch": algo,
                      "launch_ms": launch_ms},
         "e2e": e2e, "gpu_launches": (2 * args.inner + 3 + 9) * args.steps, "clocks": clk,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
