@@ -1,8 +1,9 @@
 // Three-dimensional form of the time step (arXiv 2505.22256, Sec. 3.5) and its C ABI
 // (include/lbm3d.h).
 //
-// State: the post-collision populations f*_i^k of one lattice, SoA [2][19][N] in the storage /
-// compute type R (float or double), N = nx ny nz, x fastest; two buffers.  One time step is two
+// State: the post-collision populations f*_i^k of one lattice, [19][N] pairs (f*_i^A, f*_i^B) in the
+// storage / compute type R (float or double), N = nx ny nz, x fastest; two buffers.  One vector
+// access moves both components of a direction.  One time step is two
 // launches:
 //   k3_rho    pull f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) across a blocked link (halfway
 //             bounce-back, Sec. 3.5); (rho_A, rho_B) = sum_i f_i (Eq. 3) into one interleaved
@@ -121,9 +122,9 @@ struct Rho2<double> {
     using T = double2;
 };
 
-// the node's 38 post-streaming populations
+// the node's 38 post-streaming populations (f[i]: component A, f[19 + i]: component B)
 template <class R>
-__device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const R* __restrict__ fs, uint32_t fl, int s,
+__device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const V2<R>* __restrict__ fs, uint32_t fl, int s,
                                       R (&f)[38]) {
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -135,22 +136,14 @@ __device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const R* __r
             src = i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i));
             q = i;
         }
-        f[i] = fs[(long long)q * g.N + src];
-        f[19 + i] = fs[(long long)(19 + q) * g.N + src];
+        const V2<R> v = fs[(long long)q * g.N + src];
+        f[i] = v.x;
+        f[19 + i] = v.y;
     }
 }
 
-// sum of the 19 populations of one component as a balanced tree (rounding grows with the depth,
-// not the count)
 template <class R>
-__device__ __forceinline__ R sum19(const R* f) {
-    const R a = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]));
-    const R b = ((f[8] + f[9]) + (f[10] + f[11])) + ((f[12] + f[13]) + (f[14] + f[15]));
-    return (a + b) + (f[16] + (f[17] + f[18]));
-}
-
-template <class R>
-__global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
+__global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
                                               typename Rho2<R>::T* __restrict__ rho) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
@@ -161,10 +154,17 @@ __global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict
     r.y = (R)-1;
     if (!(fl & k3Solid)) {
         const Nb3 nb(g, x, y, z);
-        R f[38];
-        pull3<R>(g, nb, fs, fl, s, f);
-        r.x = sum19<R>(f);
-        r.y = sum19<R>(f + 19);
+        V2<R> f[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const bool bl = i > 0 && ((fl >> (i - 1)) & 1u);
+            f[i] = fs[(long long)(bl ? opp3(i) : i) * g.N + (bl || i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i)))];
+        }
+        // rho_k = sum_i f_i as a balanced tree (rounding grows with the depth, not the count), both
+        // components at once
+        const V2<R> a = vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])), vadd(vadd(f[4], f[5]), vadd(f[6], f[7])));
+        const V2<R> b = vadd(vadd(vadd(f[8], f[9]), vadd(f[10], f[11])), vadd(vadd(f[12], f[13]), vadd(f[14], f[15])));
+        r = vadd(vadd(a, b), vadd(f[16], vadd(f[17], f[18])));
     }
     rho[s] = r;
 }
@@ -186,7 +186,7 @@ __device__ __forceinline__ double d3_neutral(int q) {
 // blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
 template <class R>
 __global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
-                                                 const uint8_t* __restrict__ solid, const R* __restrict__ fs,
+                                                 const uint8_t* __restrict__ solid, const V2<R>* __restrict__ fs,
                                                  const typename Rho2<R>::T* __restrict__ rho,
                                                  double* __restrict__ o5, double* __restrict__ part) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
@@ -347,13 +347,59 @@ constexpr size_t k3_march_smem() {
     return k3_ring_bytes<R>();
 }
 
+// Stencil sums of a node whose stencil reaches a solid site (out of line: few nodes take it, and
+// keeping it out of the step kernel's body leaves that body its registers).  Second-layer copy of
+// x + sign(e) for a solid second-layer site (Sec. 2.4), density 0 and solid switch 1 at a solid
+// site; solid sites hold -1 in the ring.  b0..b4: ring rows of the planes z-2..z+2 at the node.
+template <class R>
+__device__ __noinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, const V2<R>* b2, const V2<R>* b3,
+                                           const V2<R>* b4, V2<R>& gx, V2<R>& gy, V2<R>& gz, R (&ad)[3]) {
+    using V = V2<R>;
+    const V* bs[5] = {b0, b1, b2, b3, b4};
+#pragma unroll
+    for (int dz = 0; dz <= 2; ++dz)
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx) {
+                if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
+                const int q = dx * dx + dy * dy + dz * dz;
+                const double wq = w92(q);
+                if (wq == 0.0) continue;
+                const bool second = dx == 2 || dx == -2 || dy == 2 || dy == -2 || dz == 2 || dz == -2;
+                V v[2];
+                R vs[2];
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int sg = side == 0 ? 1 : -1;
+                    const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
+                    V w = bs[2 + ez][ey * k3HX + ex];
+                    if (second && w.x < (R)0) {
+                        const int fx = (ex > 0) - (ex < 0), fy = (ey > 0) - (ey < 0), fz = (ez > 0) - (ez < 0);
+                        w = bs[2 + fz][fy * k3HX + fx];
+                    }
+                    const bool sol = w.x < (R)0;
+                    v[side] = sol ? vbc<R>(0) : w;
+                    vs[side] = sol ? (R)1 : (R)0;
+                }
+                const V a = vsub(v[0], v[1]);
+                const R w = (R)wq, sw = vs[0] - vs[1];
+                gx = vfma(vbc<R>(wq * dx), a, gx);
+                gy = vfma(vbc<R>(wq * dy), a, gy);
+                gz = vfma(vbc<R>(wq * dz), a, gz);
+                ad[0] += w * dx * sw;
+                ad[1] += w * dy * sw;
+                ad[2] += w * dz * sw;
+            }
+}
+
 #ifndef LBM3_MIN_BLOCKS
 #define LBM3_MIN_BLOCKS 3
 #endif
 template <class R>
 __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
-    k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const R* __restrict__ fs,
-             const V2<R>* __restrict__ rho, R* __restrict__ fout) {
+    k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
+             const V2<R>* __restrict__ rho, V2<R>* __restrict__ fout) {
     using V = V2<R>;
     extern __shared__ __align__(16) unsigned char smem3[];
     V* ring = reinterpret_cast<V*>(smem3);
@@ -402,7 +448,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 src = i == 0 ? s : zoff[1 - e3z(i)] + nb.yo[2 - e3y(i)] + nb.xw[2 - e3x(i)];
                 q = i;
             }
-            f[i] = V{fs[(long long)q * g.N + src], fs[(long long)(19 + q) * g.N + src]};
+            f[i] = fs[(long long)q * g.N + src];
         }
     };
 
@@ -457,43 +503,8 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 gx = vadd(hx[0], hx[1]);
                 gy = vadd(hy[0], hy[1]);
                 gz = vadd(hz[0], hz[1]);
-            } else {  // second-layer copy of x + sign(e) for non-fluid second-layer sites; solid switch
-                // (solid sites hold -1 in the ring)
-#pragma unroll
-                for (int dz = 0; dz <= 2; ++dz)
-#pragma unroll
-                    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-                        for (int dx = -2; dx <= 2; ++dx) {
-                            if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
-                            const int q = dx * dx + dy * dy + dz * dz;
-                            const double wq = w92(q);
-                            if (wq == 0.0) continue;
-                            const bool second = dx == 2 || dx == -2 || dy == 2 || dy == -2 || dz == 2 || dz == -2;
-                            V v[2];
-                            R vs[2];
-#pragma unroll
-                            for (int side = 0; side < 2; ++side) {
-                                const int sg = side == 0 ? 1 : -1;
-                                const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
-                                V w = bs[2 + ez][ey * k3HX + ex];
-                                if (second && w.x < (R)0) {
-                                    const int fx = (ex > 0) - (ex < 0), fy = (ey > 0) - (ey < 0), fz = (ez > 0) - (ez < 0);
-                                    w = bs[2 + fz][fy * k3HX + fx];
-                                }
-                                const bool sol = w.x < (R)0;
-                                v[side] = sol ? vbc<R>(0) : w;
-                                vs[side] = sol ? (R)1 : (R)0;
-                            }
-                            const V a = vsub(v[0], v[1]);
-                            const R w = (R)wq, sw = vs[0] - vs[1];
-                            gx = vfma(vbc<R>(wq * dx), a, gx);
-                            gy = vfma(vbc<R>(wq * dy), a, gy);
-                            gz = vfma(vbc<R>(wq * dz), a, gz);
-                            ad[0] += w * dx * sw;
-                            ad[1] += w * dy * sw;
-                            ad[2] += w * dz * sw;
-                        }
+            } else {
+                wall_stencil3<R>(bs[0], bs[1], bs[2], bs[3], bs[4], gx, gy, gz, ad);
             }
             const R rA = r2.x, rB = r2.y;
             R GA = (R)0;
@@ -569,10 +580,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 o[i + 1] = vfma(om1, f[i + 1], vsub(sym, anti));
             }
 #pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                fout[(long long)i * g.N + s] = o[i].x;
-                fout[(long long)(19 + i) * g.N + s] = o[i].y;
-            }
+            for (int i = 0; i < 19; ++i) fout[(long long)i * g.N + s] = o[i];
         }
         if (z + 3 <= z1 + 1) store_plane(z + 3, nxt);
         __syncthreads();
@@ -594,7 +602,7 @@ __global__ void k3_diag_final(long long nblocks, const double* __restrict__ part
 
 // post-streaming populations (FP64 [2][19][N]) <-> post-collision buffer
 template <class R>
-__global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __restrict__ fs, double* __restrict__ f) {
+__global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs, double* __restrict__ f) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
@@ -610,21 +618,21 @@ __global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const R* __re
 }
 
 template <class R>
-__global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ f, R* __restrict__ fs) {
+__global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ f, V2<R>* __restrict__ fs) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
     const uint32_t fl = flags[s];
-    for (int k = 0; k < 2; ++k)
-        for (int i = 0; i < 19; ++i) {
-            double v = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        R v[2] = {(R)0, (R)0};
+        for (int k = 0; k < 2; ++k)
             if (!(fl & k3Solid)) {
                 // f*_i(x) streams to x + e_i; if that node is solid it comes back as f_opp(i)(x)
-                if (i > 0 && ((fl >> (opp3(i) - 1)) & 1u)) v = f[(long long)(19 * k + opp3(i)) * g.N + s];
-                else v = f[(long long)(19 * k + i) * g.N + (i == 0 ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i)))];
+                if (i > 0 && ((fl >> (opp3(i) - 1)) & 1u)) v[k] = (R)f[(long long)(19 * k + opp3(i)) * g.N + s];
+                else v[k] = (R)f[(long long)(19 * k + i) * g.N + (i == 0 ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i)))];
             }
-            fs[(long long)(19 * k + i) * g.N + s] = (R)v;
-        }
+        fs[(long long)i * g.N + s] = V2<R>{v[0], v[1]};
+    }
 }
 
 template <class R>
@@ -881,7 +889,7 @@ cudaError_t scratch_for(lbm3d_ctx* c) {
 template <class R>
 cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gr = grid3(c->g);
-    const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
+    const V2<R>* fs = reinterpret_cast<const V2<R>*>(c->f[c->cur]);
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
     k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
@@ -889,7 +897,7 @@ cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
                   (unsigned)((c->g.nz + zc - 1) / zc));
     k3_march<R><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho,
-                                                               reinterpret_cast<R*>(c->f[1 - c->cur]));
+                                                               reinterpret_cast<V2<R>*>(c->f[1 - c->cur]));
     c->cur ^= 1;
     return cudaGetLastError();
 }
@@ -898,7 +906,7 @@ cudaError_t step_once(lbm3d_ctx* c) {
 template <class R>
 cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
     const dim3 gr = grid3(c->g);
-    const R* fs = reinterpret_cast<const R*>(c->f[c->cur]);
+    const V2<R>* fs = reinterpret_cast<const V2<R>*>(c->f[c->cur]);
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
     k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
     const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
@@ -913,7 +921,7 @@ cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
 
 template <class R>
 cudaError_t density_pass(lbm3d_ctx* c) {
-    k3_rho<R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const R*>(c->f[c->cur]),
+    k3_rho<R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const V2<R>*>(c->f[c->cur]),
                                                    reinterpret_cast<typename Rho2<R>::T*>(c->rho));
     return cudaGetLastError();
 }
@@ -1036,8 +1044,8 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     // read before planes 36, 37 are overwritten by the same thread
     k3_feq<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->solid, c->scratch + 36 * N, c->scratch + 37 * N, c->scratch);
     STEP3(cudaGetLastError(), "init kernel");
-    if (storage == LBM_STORE_F64) k3_set<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[0]);
-    else k3_set<float><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[0]);
+    if (storage == LBM_STORE_F64) k3_set<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double2*)c->f[0]);
+    else k3_set<float><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float2*)c->f[0]);
     STEP3(cudaGetLastError(), "init kernel");
     STEP3(cudaStreamSynchronize(c->stream), "initialisation");
     cudaFree(c->scratch);  // transfers allocate it again on demand
@@ -1090,8 +1098,8 @@ extern "C" lbm_status lbm3d_fields(lbm3d_ctx* c, double* rA, double* rB, double*
 extern "C" lbm_status lbm3d_get_populations(lbm3d_ctx* c, double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
-    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const double*)c->f[c->cur], c->scratch);
-    else k3_get<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const float*)c->f[c->cur], c->scratch);
+    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const double2*)c->f[c->cur], c->scratch);
+    else k3_get<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const float2*)c->f[c->cur], c->scratch);
     TRY3(cudaGetLastError(), "read-back kernel");
     TRY3(cudaMemcpyAsync(f, c->scratch, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read-back");
     TRY3(cudaStreamSynchronize(c->stream), "read-back");
@@ -1102,8 +1110,8 @@ extern "C" lbm_status lbm3d_set_populations(lbm3d_ctx* c, const double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
     TRY3(cudaMemcpyAsync(c->scratch, f, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
-    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double*)c->f[c->cur]);
-    else k3_set<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float*)c->f[c->cur]);
+    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double2*)c->f[c->cur]);
+    else k3_set<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float2*)c->f[c->cur]);
     TRY3(cudaGetLastError(), "state kernel");
     TRY3(cudaStreamSynchronize(c->stream), "upload");
     return LBM_OK;
