@@ -221,25 +221,61 @@ def committed_traffic(storage: str, nodes_per_launch: int):
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
 # ------------------------------------------------------------------------------------------------
-def cpu_baseline(args, seconds: float) -> dict:
+# max relative |d rho| after PARITY_STEPS steps that the GPU tests hold each storage mode to
+PARITY_STEPS = 100
+PARITY_BAR = {"f32": 1e-5, "f16": 5e-3, "bf16": 5e-2, "f64": 1e-10}
+
+
+def parity_record(storage, case, err_rho, err_u, bar_note=None) -> dict:
+    rec = {"storage": storage, "steps": PARITY_STEPS, "case": case, "max_rel_drho": err_rho, "max_abs_du": err_u,
+           "bar_max_rel_drho": PARITY_BAR.get(storage), "within_bar": err_rho <= PARITY_BAR.get(storage, 0.0)}
+    if bar_note:
+        rec["bar_note"] = bar_note
+    return rec
+
+
+def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
+    """The FP64 oracle timed on one case of the workload.  parity: also run that case on the GPU in
+    the bench's storage mode from the same initial state and report its error against the oracle's
+    fields after PARITY_STEPS steps (the oracle's first PARITY_STEPS steps are part of the timed
+    sample)."""
+    import numpy as np
+
     import oracle
 
     cases, _ = workload(args)
     sc = max(cases, key=lambda c: c.nx * c.ny) if args.workload != "sweep" else cases[len(cases) // 2]
     cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
     f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    need = PARITY_STEPS if parity else 1
+    snap = None
     n = 0
     t0 = time.perf_counter()
     while True:
         f = oracle.run(cfg, sc.solid, f, 1)
         n += 1
+        if parity and n == PARITY_STEPS:
+            snap = f.copy()
         el = time.perf_counter() - t0
-        if el >= seconds or n >= 10000:
+        if (el >= seconds and n >= need) or n >= 10000:
             break
     mlups = sc.nx * sc.ny * n / el / 1e6
-    return {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
-            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, {sc.name}), {n} FP64 time steps "
-                      f"in {el:.1f} s on {cfg.nthreads} host threads"}
+    out = {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+           "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, {sc.name}), {n} FP64 time steps "
+                     f"in {el:.1f} s on {cfg.nthreads} host threads"}
+    if parity and snap is not None:
+        from paper_2505_22256_gb300 import lbm
+
+        o = oracle.fields(cfg, sc.solid, snap)
+        lat = lbm.Lattice(sc, args.storage)
+        lat.step(PARITY_STEPS)
+        g = lat.fields()
+        lat.close()
+        fl = sc.solid == 0
+        err_rho = max(float(np.max(np.abs(g[k] - o[k])[fl] / o[k][fl])) for k in (0, 1))
+        err_u = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (2, 3))
+        out["parity"] = parity_record(args.storage, f"{sc.name} ({sc.nx}x{sc.ny})", err_rho, err_u)
+    return out
 
 
 def run_reference(args):
@@ -442,7 +478,7 @@ def run_ours(args):
     lat.close()
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds, parity=True)
         elif not args.no_cpu:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
@@ -462,7 +498,11 @@ def sphere3d_case(args, rank=0):
     return S.sphere_droplet_3d(lam=1.0, seed=9 + 1000 * rank)
 
 
-def cpu_baseline_3d(seconds: float) -> dict:
+def cpu_baseline_3d(seconds: float, storage: str | None = None) -> dict:
+    """The 3-D FP64 oracle timed on the Sec. 3.5 geometry scaled to 64 x 64 x 90.  storage: also run
+    that lattice on the GPU and report its error against the oracle after PARITY_STEPS steps."""
+    import numpy as np
+
     from oracle import d3
     from paper_2505_22256_gb300 import scenarios as S
 
@@ -472,16 +512,38 @@ def cpu_baseline_3d(seconds: float) -> dict:
     cfg = d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
                      delta=p["delta"], g=p["g"])
     f = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    need = PARITY_STEPS if storage else 1
+    snap = None
     n, t0 = 0, time.perf_counter()
     while True:
         f = d3.run3(cfg, sc.solid, f, 1)
         n += 1
+        if storage and n == PARITY_STEPS:
+            snap = f.copy()
         el = time.perf_counter() - t0
-        if el >= seconds or n >= 10000:
+        if (el >= seconds and n >= need) or n >= 10000:
             break
-    return {"value": nx * ny * nz * n / el / 1e6, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
-            "sample": f"the Sec. 3.5 geometry scaled to {nx}x{ny}x{nz}, {n} FP64 time steps in {el:.1f} s on "
-                      f"{cfg.nthreads} host threads"}
+    out = {"value": nx * ny * nz * n / el / 1e6, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+           "sample": f"the Sec. 3.5 geometry scaled to {nx}x{ny}x{nz}, {n} FP64 time steps in {el:.1f} s on "
+                     f"{cfg.nthreads} host threads"}
+    if storage and snap is not None:
+        from paper_2505_22256_gb300 import lbm3d
+
+        o = d3.fields3(cfg, sc.solid, snap)
+        lat = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, p, storage)
+        lat.step(PARITY_STEPS)
+        g = lat.fields()
+        lat.close()
+        fl = sc.solid == 0
+        err_rho = max(float(np.max(np.abs(g[k] - o[k])[fl] / o[k][fl])) for k in (0, 1))
+        err_u = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (2, 3, 4))
+        note = ("the 3-D FP32 bar is |d rho_k| <= 1e-5 rho_m absolute with the relative error held under 5e-5"
+                if storage == "f32" else None)
+        out["parity"] = parity_record(storage, f"sphere droplet {nx}x{ny}x{nz}", err_rho, err_u, note)
+        if storage == "f32":
+            out["parity"]["bar_max_rel_drho"] = 5e-5
+            out["parity"]["within_bar"] = err_rho <= 5e-5
+    return out
 
 
 def run_ours_3d(args):
@@ -593,7 +655,7 @@ def run_ours_3d(args):
     }
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline_3d(args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline_3d(args.cpu_seconds, args.storage)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
