@@ -48,6 +48,10 @@ CASES = {
     "sphere24_original": lambda: S.sphere_droplet_3d_small(24, lam=0.5, scheme="original"),
     "odd_box": lambda: S.sphere_droplet_3d(nx=21, ny=17, nz=26, R=5.0, sphere=(10.0, 8.0, 9.0), r=5.5,
                                            drop=(10.0, 8.0, 17.0), lam=1.3),
+    # the step kernel's edges: a partial 32-column tile (nx = 40), a last tile three rows high
+    # (ny = 11 in tiles of 4) and z planes split into uneven chunks (37 = 13 + 13 + 11)
+    "uneven_chunks": lambda: S.sphere_droplet_3d(nx=40, ny=11, nz=37, R=4.0, sphere=(20.0, 5.0, 9.0), r=4.5,
+                                                 drop=(20.0, 5.0, 19.0), lam=0.9),
 }
 
 
