@@ -497,9 +497,18 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         }
     }
 
-    // work list and launch shape; the wall-list correction is inlined where wall-list nodes are
-    // common (more than 4 % of the fluid nodes), called out of line otherwise
-    c.block_threads = 128;
+    // work list and launch shape.  Block width: the one that launches fewer thread columns over all
+    // cases (windows of width - 8 interior columns; 64 wins on lattices narrower than about 56
+    // columns).  The wall-list correction is inlined where wall-list nodes are common (more than 4 %
+    // of the fluid nodes), called out of line otherwise.
+    {
+        long long cols[2] = {0, 0};
+        const int widths[2] = {128, 64};
+        for (int w = 0; w < 2; ++w)
+            for (const DevCase& d : c.hcases)
+                cols[w] += (long long)((d.nx + widths[w] - 9) / (widths[w] - 8)) * widths[w] * d.ny;
+        c.block_threads = cols[1] < cols[0] ? 64 : 128;
+    }
     c.block_rows = 0;
     {
         long long fl = 0;
@@ -863,7 +872,7 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
 
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
-    if (threads != 128) return fail(LBM_EINVAL, "the step kernel is built for 128 threads per block");
+    if (threads != 128 && threads != 64) return fail(LBM_EINVAL, "the step kernel is built for 64 or 128 threads per block");
     if (rows < 0) return fail(LBM_EINVAL, "rows must be >= 0 (0 = automatic)");
     Ctx& c = ctx->c;
     CUDA_TRY(cudaStreamSynchronize(c.stream));
@@ -884,7 +893,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
     Ctx& c = ctx->c;
-    const int cand_t[] = {128};
+    const int cand_t[] = {128, 64};
     const int cand_r[] = {0, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));

@@ -40,7 +40,8 @@ namespace {
 // Rows of densities kept in shared memory.  Each row is written twice, at ring slot m and m + kRing,
 // so the five consecutive rows a collision reads sit at consecutive slots from one base.
 constexpr int kRing = 6;
-constexpr int kTc = 128;  // threads per block of the step kernel = window columns (ring row length)
+// Threads per block of the step kernel = window columns = density ring row length: 128, or 64 for
+// lattices too narrow to fill a 120-column window (both are built; the context picks one).
 #ifndef LBM_SLOTS
 #define LBM_SLOTS 5
 #endif
@@ -260,7 +261,7 @@ struct Grad2 {
 // open_edge: the node lies within two columns of an open boundary, where the ring holds clamped
 // densities beyond the edge.  The step kernel inlines it where wall-list nodes are common and calls
 // the out-of-line copy otherwise, so that warps without wall-list nodes keep a small loop.
-template <class R>
+template <class R, int TC>
 __device__ __forceinline__ Grad2<R> substitution_correction(const V2<R>* __restrict__ ring, int sb0, uint32_t sub,
                                                             bool open_edge) {
     SubCoef<R> sc;
@@ -268,7 +269,7 @@ __device__ __forceinline__ Grad2<R> substitution_correction(const V2<R>* __restr
     Grad2<R> g{vbc<R>(0), vbc<R>(0)};
 #pragma unroll
     for (int p = 1; p <= 8; ++p) {
-        const V2<R> n = ring[sb0 + (cy(p) + 2) * kTc + cx(p)];
+        const V2<R> n = ring[sb0 + (cy(p) + 2) * TC + cx(p)];
         g.x = vfma(vbc<R>(sc.x[p - 1]), n, g.x);
         g.y = vfma(vbc<R>(sc.y[p - 1]), n, g.y);
     }
@@ -278,7 +279,7 @@ __device__ __forceinline__ Grad2<R> substitution_correction(const V2<R>* __restr
 #pragma unroll
         for (int n = 8; n < 24; ++n) {
             if ((sub >> n) & 1u) {
-                const V2<R> v = ring[sb0 + (s24y(n) + 2) * kTc + s24x(n)];
+                const V2<R> v = ring[sb0 + (s24y(n) + 2) * TC + s24x(n)];
                 const double w = w8(s24x(n) * s24x(n) + s24y(n) * s24y(n));
                 g.x = vsub(g.x, vmul(vbc<R>(w * s24x(n)), v));
                 g.y = vsub(g.y, vmul(vbc<R>(w * s24y(n)), v));
@@ -288,10 +289,10 @@ __device__ __forceinline__ Grad2<R> substitution_correction(const V2<R>* __restr
     return g;
 }
 
-template <class R>
+template <class R, int TC>
 __device__ __noinline__ Grad2<R> substitution_correction_call(const V2<R>* __restrict__ ring, int sb0, uint32_t sub,
                                                               bool open_edge) {
-    return substitution_correction<R>(ring, sb0, sub, open_edge);
+    return substitution_correction<R, TC>(ring, sb0, sub, open_edge);
 }
 
 // SRT collision with Guo forcing (Eqs. 1, 2, 6, 7), both components at once and written per pair
@@ -362,12 +363,16 @@ struct StepArgs {
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
-constexpr int kT = kTc;  // threads per block = columns per window (interior kT - 8)
+// blocks per SM the launch bounds ask for: the same registers per thread at either width
+template <class S, int T>
+constexpr int step_min_blocks() {
+    return (sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) * (128 / T);
+}
 
-template <class S, class R, bool kFields, bool kWallInline>
-__global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_step(StepArgs a) {
+template <class S, class R, bool kFields, bool kWallInline, int T>
+__global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int T = kT, Wi = T - 8;
+    constexpr int Wi = T - 8;  // interior columns of a window
     const int t = threadIdx.x;
     constexpr int G = Layout<S>::G;
     constexpr int BX = T;  // pairs per plane of a row slot
@@ -520,8 +525,8 @@ __global__ void __launch_bounds__(kT, sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) k_ste
             if (wall) {
                 const bool open_edge = P.bc_x == kOpen && (X < 2 || X >= P.nx - 2);
                 Grad2<R> c2;
-                if constexpr (kWallInline) c2 = substitution_correction<R>(ring, sb0, st.sub, open_edge);
-                else c2 = substitution_correction_call<R>(ring, sb0, st.sub, open_edge);
+                if constexpr (kWallInline) c2 = substitution_correction<R, T>(ring, sb0, st.sub, open_edge);
+                else c2 = substitution_correction_call<R, T>(ring, sb0, st.sub, open_edge);
                 gx = vadd(gx, c2.x);
                 gy = vadd(gy, c2.y);
             }
@@ -894,20 +899,25 @@ __global__ void k_diag_reduce(const DevCase* __restrict__ cases, int c, const do
     }
 }
 
-template <class S>
+template <class S, int T>
 void* kernel_ptr(int variant) {
     using R = typename ComputeOf<S>::type;
-    return variant == 2 ? (void*)k_step<S, R, true, false>
-                        : (variant == 1 ? (void*)k_step<S, R, false, true> : (void*)k_step<S, R, false, false>);
+    return variant == 2 ? (void*)k_step<S, R, true, false, T>
+                        : (variant == 1 ? (void*)k_step<S, R, false, true, T> : (void*)k_step<S, R, false, false, T>);
+}
+
+template <class S>
+void* kernel_ptr_w(int variant, int threads) {
+    return threads == 64 ? kernel_ptr<S, 64>(variant) : kernel_ptr<S, 128>(variant);
 }
 
 // variant 0: step, wall path out of line; 1: step, wall path inline; 2: fields pass
-void* step_kernel(int storage, int variant) {
+void* step_kernel(int storage, int variant, int threads) {
     switch (storage) {
-        case LBM_STORE_F64: return kernel_ptr<double>(variant);
-        case LBM_STORE_F32: return kernel_ptr<float>(variant);
-        case LBM_STORE_F16_SHIFTED: return kernel_ptr<__half>(variant);
-        default: return kernel_ptr<__nv_bfloat16>(variant);
+        case LBM_STORE_F64: return kernel_ptr_w<double>(variant, threads);
+        case LBM_STORE_F32: return kernel_ptr_w<float>(variant, threads);
+        case LBM_STORE_F16_SHIFTED: return kernel_ptr_w<__half>(variant, threads);
+        default: return kernel_ptr_w<__nv_bfloat16>(variant, threads);
     }
 }
 
@@ -940,15 +950,21 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
     return a;
 }
 
+template <class S, int T>
+cudaError_t launch_step_w(const Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
+    using R = typename ComputeOf<S>::type;
+    const size_t smem = smem_for<S>(T);
+    if (fields) k_step<S, R, true, false, T><<<grid, T, smem, s>>>(a);
+    else if (c.wall_inline) k_step<S, R, false, true, T><<<grid, T, smem, s>>>(a);
+    else k_step<S, R, false, false, T><<<grid, T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <class S>
 cudaError_t launch_step_t(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
-    using R = typename ComputeOf<S>::type;
-    if (c.block_threads != kT) return cudaErrorInvalidConfiguration;
-    const size_t smem = smem_for<S>(kT);
-    if (fields) k_step<S, R, true, false><<<grid, kT, smem, s>>>(a);
-    else if (c.wall_inline) k_step<S, R, false, true><<<grid, kT, smem, s>>>(a);
-    else k_step<S, R, false, false><<<grid, kT, smem, s>>>(a);
-    return cudaGetLastError();
+    if (c.block_threads == 128) return launch_step_w<S, 128>(c, a, s, fields, grid);
+    if (c.block_threads == 64) return launch_step_w<S, 64>(c, a, s, fields, grid);
+    return cudaErrorInvalidConfiguration;
 }
 
 cudaError_t dispatch(Ctx& c, const StepArgs& a, cudaStream_t s, bool fields, int grid) {
@@ -979,14 +995,15 @@ int step_smem_bytes(int storage, int threads) {
 cudaError_t step_occupancy(int storage, int threads, int* blocks_per_sm) {
     const int bytes = step_smem_bytes(storage, threads);
     for (int v = 0; v < 3; ++v) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel(storage, v), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e =
+            cudaFuncSetAttribute(step_kernel(storage, v, threads), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
     }
     // the most restrictive of the three variants sets the resident blocks
     int m = 1 << 30;
     for (int v = 0; v < 3; ++v) {
         int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel(storage, v), threads, bytes);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel(storage, v, threads), threads, bytes);
         if (e != cudaSuccess) return e;
         m = b < m ? b : m;
     }

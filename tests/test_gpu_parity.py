@@ -237,7 +237,36 @@ def test_launch_shapes_agree():
                 np.testing.assert_array_equal(f, f16)
             f16 = f
     with pytest.raises(lbm.LbmError):
-        lbm.lbm_set_launch(lbm.Lattice(sc, "f32").ctx, 64, 16)
+        lbm.lbm_set_launch(lbm.Lattice(sc, "f32").ctx, 96, 16)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("name", ["ragged131x77", "couette_sliding", "porous_open"])
+def test_block_widths_give_identical_states(name, storage):
+    """The step kernel's 64- and 128-column forms do the same arithmetic per node, so with the same
+    row chunks they reach bit-identical states: a ragged periodic lattice (several windows of
+    either width), a narrow channel with sliding walls, and a porous medium with open columns."""
+    sc = SCENARIOS[name]()
+    out = []
+    for width in (128, 64):
+        lat = lbm.Lattice(sc, storage)
+        lbm.lbm_set_launch(lat.ctx, width, 16)
+        assert lat.info()["block_threads"] == width
+        lat.step(37)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_default_block_width_follows_the_lattice_width():
+    """lbm_create picks the width that launches fewer thread columns: 64 for a 50-column channel,
+    128 for a 1024-column lattice."""
+    narrow = lbm.Lattice(S.couette_channel(nx=50, ny=40), "f32")
+    wide = lbm.Lattice(S.cylinder_droplet(64, nx=1024, R=12, r=15), "f32")
+    assert narrow.info()["block_threads"] == 64
+    assert wide.info()["block_threads"] == 128
+    narrow.close()
+    wide.close()
 
 
 def test_wall_paths_agree_and_default_choice():
