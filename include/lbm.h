@@ -212,6 +212,17 @@ lbm_status lbm_set_densities(lbm_ctx* ctx, int32_t case_index, const double* rho
 lbm_status lbm_fields(lbm_ctx* ctx, int32_t case_index, double* rho_A, double* rho_B, double* ux,
                       double* uy, int32_t on_device);
 
+/* Every case of the context at once (the same results as the per-case calls, bit for bit): arrays
+ * of sum_i nx_i ny_i doubles holding the cases back to back in case order, each [ny][nx].  Host
+ * arrays (on_device = 0) move in one copy per array and the call synchronises once; device arrays
+ * (on_device = 1) are read or written on the context's stream.  The first host-array call (or a
+ * device call with a NULL field output) allocates 32 bytes per node of all cases, held until
+ * lbm_destroy (LBM_ENOMEM when that fails).
+ * lbm_set_densities_all: f = f^eq(rho_k, 0) in every case, as lbm_set_densities.
+ * lbm_fields_all: rho_A, rho_B, ux, uy of every case, as lbm_fields; any output may be NULL. */
+lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0, int32_t on_device);
+lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device);
+
 /* Global FP64 diagnostics of one case (host output; synchronises).  Returns LBM_EUNSTABLE, with
  * *out filled, when the state holds a non-finite or non-positive density. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t case_index, lbm_diag* out);

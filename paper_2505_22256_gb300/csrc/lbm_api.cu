@@ -337,7 +337,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.fields_all, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -667,6 +667,62 @@ lbm_status lbm_fields(lbm_ctx* ctx, int32_t ci, double* rho_A, double* rho_B, do
     double* outs[4] = {rho_A, rho_B, ux, uy};
     for (int q = 0; q < 4; ++q)
         if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], c.fields + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return check_device_error(c);
+}
+
+// Scratch of four doubles per node of all cases for the batched host transfers.
+static lbm_status fields_all_scratch(Ctx& c) {
+    if (c.fields_all) return LBM_OK;
+    const cudaError_t e = cudaMalloc(&c.fields_all, (size_t)4 * c.dense_elems * sizeof(double));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        c.fields_all = nullptr;
+        return fail(LBM_ENOMEM, "batched transfer scratch: out of device memory");
+    }
+    CUDA_TRY(e);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0, int32_t on_device) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!rho_A0 || !rho_B0) return fail(LBM_EINVAL, "NULL density");
+    Ctx& c = ctx->c;
+    const long long total = c.dense_elems;
+    const double *a = rho_A0, *b = rho_B0;
+    if (!on_device) {
+        lbm_status s = fields_all_scratch(c);
+        if (s != LBM_OK) return s;
+        CUDA_TRY(cudaMemcpyAsync(c.fields_all, rho_A0, total * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        CUDA_TRY(cudaMemcpyAsync(c.fields_all + total, rho_B0, total * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        a = c.fields_all;
+        b = c.fields_all + total;
+    }
+    for (int ci = 0; ci < (int)c.hcases.size(); ++ci) {
+        const long long off = c.hcases[ci].d_off;
+        CUDA_TRY(launch_feq_rest(c, ci, a + off, b + off, c.dense));
+        CUDA_TRY(launch_set_state(c, ci, c.dense));
+    }
+    ++c.version;
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    Ctx& c = ctx->c;
+    const long long total = c.dense_elems;
+    double* outs[4] = {rho_A, rho_B, ux, uy};
+    if (!on_device || !rho_A || !rho_B || !ux || !uy) {
+        lbm_status s = fields_all_scratch(c);
+        if (s != LBM_OK) return s;
+    }
+    double* dst[4];
+    for (int q = 0; q < 4; ++q) dst[q] = (on_device && outs[q]) ? outs[q] : c.fields_all + q * total;
+    CUDA_TRY(launch_fields_all(c, dst[0], dst[1], dst[2], dst[3]));
+    if (on_device) return LBM_OK;
+    for (int q = 0; q < 4; ++q)
+        if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], dst[q], total * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     return check_device_error(c);
 }

@@ -72,6 +72,7 @@ struct Ctx {
     double* dense = nullptr;         // [18 * max case nodes] doubles for population transfers
     long long dense_cap = 0;
     double* fields = nullptr;        // [4][max case nodes]
+    double* fields_all = nullptr;    // [4][all nodes] for the batched host transfers (on first use)
     double* diag_part = nullptr;     // [nitems][kDiagN]
     double* diag_out = nullptr;      // [ncases][kDiagN]
     double* ca_work = nullptr;       // contact-angle reductions
@@ -99,6 +100,9 @@ cudaError_t launch_diag_reduce(Ctx& c, int case_index);
 // partial sums of every case in one launch over the per-case lists, then one reduction per case
 cudaError_t launch_diag_all(Ctx& c);
 // densities of every case into [dense_elems] arrays indexed d_off + y nx + x (zero at solid nodes)
+// every case's fields at once (fields_global indexing: case d_off + y nx + x); ux_all / uy_all may be
+// NULL for densities only
+cudaError_t launch_fields_all(Ctx& c, double* rhoA_all, double* rhoB_all, double* ux_all, double* uy_all);
 cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all);
 cudaError_t launch_set_state(Ctx& c, int case_index, const double* dense_f);
 cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);

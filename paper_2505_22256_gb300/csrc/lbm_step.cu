@@ -1045,13 +1045,17 @@ cudaError_t launch_diag_reduce(Ctx& c, int ci) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
-    double* o4[4] = {rhoA_all, rhoB_all, nullptr, nullptr};
+cudaError_t launch_fields_all(Ctx& c, double* rhoA_all, double* rhoB_all, double* ux_all, double* uy_all) {
+    double* o4[4] = {rhoA_all, rhoB_all, ux_all, uy_all};
     const int n = c.nitems_all - c.nitems;
     const int grid = n < c.grid_blocks ? n : c.grid_blocks;
     StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, nullptr);
     a.fields_global = 1;
     return dispatch(c, a, c.stream, true, grid);
+}
+
+cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
+    return launch_fields_all(c, rhoA_all, rhoB_all, nullptr, nullptr);
 }
 
 cudaError_t launch_diag_all(Ctx& c) {

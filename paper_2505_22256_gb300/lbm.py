@@ -32,7 +32,8 @@ SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_
            "lbm_set_densities", "lbm_fields", "lbm_diagnostics", "lbm_contact_angle", "lbm_wall_list",
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
            "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc",
-           "lbm_diagnostics_all", "lbm_contact_angle_all", "lbm_set_wall_path")
+           "lbm_diagnostics_all", "lbm_contact_angle_all", "lbm_set_wall_path", "lbm_set_densities_all",
+           "lbm_fields_all")
 
 
 class lbm_grid(ctypes.Structure):
@@ -119,6 +120,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_load.argtypes = [ctx_p, ctypes.c_char_p]
     lib.lbm_diagnostics_noalloc.argtypes = [c_void_p] * 5 + [c_int32, c_int32, c_void_p, POINTER(lbm_diag)]
     lib.lbm_diagnostics_all.argtypes = [ctx_p, POINTER(lbm_diag)]
+    lib.lbm_set_densities_all.argtypes = [ctx_p, c_void_p, c_void_p, c_int32]
+    lib.lbm_fields_all.argtypes = [ctx_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]
     lib.lbm_contact_angle_all.argtypes = [ctx_p, POINTER(lbm_surface), c_void_p, c_void_p, c_void_p]
     lib.lbm_status_str.argtypes = [c_int32]
     lib.lbm_status_str.restype = ctypes.c_char_p
@@ -244,6 +247,24 @@ def lbm_fields(ctx, case_index: int, rho_A=None, rho_B=None, ux=None, uy=None, o
             assert a.dtype == np.float64 and a.flags.c_contiguous
     _check(load_library().lbm_fields(ctx, case_index, _ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy),
                                      1 if on_device else 0))
+
+
+def lbm_set_densities_all(ctx, rho_A0, rho_B0, on_device: bool = False) -> None:
+    """All cases at once: cases back to back in case order, each [ny][nx] (flat float64 arrays of
+    sum nx ny elements, or device buffers if on_device)."""
+    if on_device:
+        _check(load_library().lbm_set_densities_all(ctx, _ptr(rho_A0), _ptr(rho_B0), 1))
+    else:
+        a, b = _host(rho_A0, np.float64), _host(rho_B0, np.float64)
+        _check(load_library().lbm_set_densities_all(ctx, a.ctypes.data, b.ctypes.data, 0))
+
+
+def lbm_fields_all(ctx, rho_A=None, rho_B=None, ux=None, uy=None, on_device: bool = False) -> None:
+    """Fields of all cases into the given arrays (cases back to back in case order)."""
+    for a in (rho_A, rho_B, ux, uy):
+        if a is not None and not on_device:
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(load_library().lbm_fields_all(ctx, _ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy), 1 if on_device else 0))
 
 
 def lbm_diagnostics(ctx, case_index: int = 0, allow_unstable: bool = False) -> dict:
@@ -405,6 +426,18 @@ class Lattice:
         out = [np.zeros((sc.ny, sc.nx)) for _ in range(4)]
         lbm_fields(self.ctx, case, *out)
         return tuple(out)
+
+    def fields_all(self):
+        """Fields of every case from one batched call: a list of (rho_A, rho_B, ux, uy) per case."""
+        total = sum(sc.nx * sc.ny for sc in self.scenarios)
+        out = [np.zeros(total) for _ in range(4)]
+        lbm_fields_all(self.ctx, *out)
+        res, o = [], 0
+        for sc in self.scenarios:
+            n = sc.nx * sc.ny
+            res.append(tuple(a[o:o + n].reshape(sc.ny, sc.nx) for a in out))
+            o += n
+        return res
 
     def populations(self, case: int = 0) -> np.ndarray:
         sc = self.scenarios[case]

@@ -330,6 +330,40 @@ def test_ensemble_equals_single_cases():
     ens.close()
 
 
+def test_batched_transfers_equal_per_case_calls():
+    """lbm_fields_all and lbm_set_densities_all over an uneven ensemble give the per-case calls'
+    results bit for bit: fields to host arrays and to device arrays, densities from host arrays."""
+    import torch
+
+    cases = [SCENARIOS["cylinder96"](), SCENARIOS["porous_open"](), SCENARIOS["ragged131x77"](), SCENARIOS["pillar8"]()]
+    ens = lbm.Lattice(cases, "f32")
+    ens.step(23)
+    batch = ens.fields_all()
+    flat = [np.concatenate([ens.fields(i)[q].ravel() for i in range(len(cases))]) for q in range(4)]
+    for i in range(len(cases)):
+        for q in range(4):
+            np.testing.assert_array_equal(batch[i][q], ens.fields(i)[q])
+    total = sum(sc.nx * sc.ny for sc in cases)
+    dev = [torch.full((total,), -7.0, dtype=torch.float64, device="cuda") for _ in range(4)]
+    lbm.lbm_fields_all(ens.ctx, *dev, on_device=True)
+    lbm.lbm_synchronize(ens.ctx)
+    for q in range(4):
+        np.testing.assert_array_equal(dev[q].cpu().numpy(), flat[q])
+    # new densities for every case, per case and batched, from the same host values
+    rng = np.random.default_rng(5)
+    newA = [np.where(sc.solid == 1, 0.0, sc.rhoA0 * (1 + 1e-3 * rng.standard_normal(sc.solid.shape))) for sc in cases]
+    newB = [np.where(sc.solid == 1, 0.0, sc.rhoB0 * (1 + 1e-3 * rng.standard_normal(sc.solid.shape))) for sc in cases]
+    for i in range(len(cases)):
+        lbm.lbm_set_densities(ens.ctx, i, newA[i], newB[i])
+    per_case = [ens.populations(i) for i in range(len(cases))]
+    ens.step(3)
+    lbm.lbm_set_densities_all(ens.ctx, np.concatenate([a.ravel() for a in newA]),
+                              np.concatenate([b.ravel() for b in newB]))
+    for i in range(len(cases)):
+        np.testing.assert_array_equal(ens.populations(i), per_case[i])
+    ens.close()
+
+
 def test_batched_diagnostics_and_contact_angles_equal_per_case_calls():
     """lbm_diagnostics_all / lbm_contact_angle_all over an uneven ensemble give each case's
     lbm_diagnostics / lbm_contact_angle result bit for bit; a case without a surface is skipped."""
