@@ -44,7 +44,7 @@ BYTES_PER_NODE = {"f32": 144, "f16": 72, "bf16": 72, "f64": 288}
 KERNEL_SOURCES = ("paper_2505_22256_gb300/csrc/lbm_step.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -68,11 +68,33 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare", "obstacle", "couette", "sphere3d")
 BYTES_PER_NODE_3D = {"f32": 304, "f64": 608}  # 2 components x 19 populations, read + written
+
+
+# ------------------------------------------------------------------------------------------------
+# Multi-rank plumbing (one process per GPU, no collective on the data path)
+# ------------------------------------------------------------------------------------------------
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (a job takes its slowest rank's time); the value itself
+    when the job runs alone."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, nodes_per_rank: int, steps_per_rank: int, total_ms: float) -> float:
+    """Whole-job lattice updates per second (millions): every rank updates nodes_per_rank nodes
+    steps_per_rank times (weak scaling) within the job's time total_ms."""
+    return world * nodes_per_rank * steps_per_rank / (total_ms / 1e3) / 1e6
 
 
 def workload(args, rank=0):
@@ -393,14 +415,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
     step_ms = sum(a.elapsed_time(b) for a, b in pairs)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * nodes * args.inner * args.steps / (total_ms / 1e3) / 1e6
+    value = job_mlups(world, nodes, args.inner * args.steps, total_ms)
     launch_ms = step_ms / (args.inner * args.steps)
     algo_bytes = BYTES_PER_NODE[args.storage] * fluid
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
@@ -436,14 +454,10 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        el = time.perf_counter() - s0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - s0, world, "cuda")
         h2d = sum(2 * c.nx * c.ny * 8 for c in cases)
         d2h = sum(4 * c.nx * c.ny * 8 for c in cases)
-        e2e = {"value": world * nodes * args.inner * ksteps / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_mlups(world, nodes, args.inner * ksteps, el * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "step": "lbm_set_densities_all (pinned host, all cases), lbm_step(%d), lbm_fields_all (pinned host, "
                        "all cases)" % args.inner}
@@ -607,13 +621,9 @@ def run_ours_3d(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
     step_ms = sum(a.elapsed_time(b) for a, b in pairs)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    launch_ms = step_ms / (args.inner * args.steps)  # one time step: density pass + fused pass
+    launch_ms = step_ms / (args.inner * args.steps)  # one time step: density pass + march pass
     algo = BYTES_PER_NODE_3D[args.storage] * fluid
     peak, peak_kind = hbm_peak()
     d = lat.diagnostics(allow_unstable=True)
@@ -624,6 +634,7 @@ def run_ours_3d(args):
         k = max(1, args.steps // 4)
         out = [np.zeros(sc.solid.shape) for _ in range(5)]
         torch.cuda.synchronize()
+        barrier()
         s0 = time.perf_counter()
         for _ in range(k):
             l2 = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), args.storage, cuda_stream=stream.cuda_stream)
@@ -631,13 +642,14 @@ def run_ours_3d(args):
             rA, rB, ux, uy, uz = l2.fields()
             l2.close()
         torch.cuda.synchronize()
-        el = time.perf_counter() - s0
-        e2e = {"value": world * nodes * args.inner * k / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": nodes * (1 + 16),
+        barrier()
+        el = max_over_ranks(time.perf_counter() - s0, world, "cuda")
+        e2e = {"value": job_mlups(world, nodes, args.inner * k, el * 1e3), "unit": UNIT, "h2d_bytes_per_step": nodes * (1 + 16),
                "d2h_bytes_per_step": nodes * 5 * 8,
                "step": "lbm3d_create from host mask and densities, lbm3d_step(%d), lbm3d_fields to host" % args.inner}
 
     line = {
-        "metric": METRIC, "value": world * nodes * args.inner * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+        "metric": METRIC, "value": job_mlups(world, nodes, args.inner * args.steps, total_ms), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": f"3-D droplet on a sphere, {'x'.join(map(str, sc.shape[::-1]))} per GPU "
