@@ -41,7 +41,8 @@ METRIC = "MLUPS (2-comp D2Q9) & % of GB300 HBM peak; FP32/FP16-store vs FP64 at 
 UNIT = "MLUPS"
 INNER = 100            # time steps per bench step
 BYTES_PER_NODE = {"f32": 144, "f16": 72, "bf16": 72, "f64": 288}
-KERNEL_SOURCES = ("paper_2505_22256_gb300/csrc/lbm_step.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh")
+KERNEL_SOURCES = ("paper_2505_22256_gb300/csrc/lbm_step.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh",
+                  "paper_2505_22256_gb300/csrc/lbm_tma.cuh")
 
 
 def parse(argv=None):

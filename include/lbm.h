@@ -289,6 +289,16 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
  * captured graph. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
 
+/* Failure-detection self-test (no counterpart in the paper).  Runs a one-thread kernel whose
+ * pipeline wait can never complete (an mbarrier that nothing arrives on), bounded by limit_ms
+ * milliseconds (0 < limit_ms <= 1000) exactly like the step kernel's tensor-load waits.  On giving up
+ * it sets the context's device error word, and the call synchronises and reports it the way a
+ * stalled step would be reported: LBM_ECUDA with a message naming the wait.  No copy is issued and
+ * nothing stays in flight, so the GPU and the CUDA context stay usable, but the error word stays
+ * set: every later synchronising call on this context reports it, so destroy the context
+ * afterwards.  LBM_EINVAL for a limit outside the range. */
+lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, double limit_ms);
+
 /* Choose the step kernel's form for wall-list nodes (the second-layer correction of Table 1): 1
  * inlines it (faster where wall-list nodes are common, e.g. porous media), 0 calls an out-of-line
  * copy (keeps the loop of warps without wall-list nodes small).  lbm_create picks 1 when wall-list

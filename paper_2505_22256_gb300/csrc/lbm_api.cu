@@ -15,6 +15,7 @@
 #include <cudaTypedefs.h>
 
 #include "lbm_internal.h"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 int contact_work_doubles();
@@ -324,7 +325,9 @@ lbm_status check_device_error(Ctx& c) {
     int e = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, c.err, sizeof e, cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
-    if (e) return fail(LBM_ECUDA, "a tensor-load wait inside the step kernel gave up (device error word %d)", e);
+    if (e)
+        return fail(LBM_ECUDA, "a bounded wait inside a kernel gave up (device error word %d: bit 1 a step kernel's "
+                               "tensor-load wait, bit 2 the wait self-test)", e);
     return LBM_OK;
 }
 
@@ -935,6 +938,40 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     c.block_threads = threads;
     c.block_rows = rows;
     return build_items(c);
+}
+
+namespace {
+// ------------------------------------------------------------------------------------------------
+// Self-test of the bounded pipeline wait: one thread initialises an mbarrier that nothing will ever
+// arrive on, waits for it through the step kernel's bounded wait with a short limit, and on giving up
+// records error bit 2 in the context's error word, as a step kernel records bit 1.  No copy is
+// issued, so nothing is left in flight when the kernel returns.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_wait_selftest(int* __restrict__ err, unsigned long long limit_cycles) {
+    __shared__ __align__(8) unsigned long long bar_word;
+    if (threadIdx.x != 0) return;
+    const uint32_t bar = smem_u32(&bar_word);
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(bar, 0, limit_cycles)) atomicOr(err, 2);
+}
+
+}  // namespace
+
+lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, double limit_ms) {
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!(limit_ms > 0.0) || limit_ms > 1000.0) return fail(LBM_EINVAL, "limit_ms must lie in (0, 1000]");
+    Ctx& c = ctx->c;
+    int rate_khz = 0;  // SM clock in kHz = cycles per millisecond
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (cudaDeviceGetAttribute(&rate_khz, cudaDevAttrClockRate, dev) != cudaSuccess || rate_khz <= 0) {
+        cudaGetLastError();
+        rate_khz = 2000000;
+    }
+    k_wait_selftest<<<1, 32, 0, c.stream>>>(c.err, (unsigned long long)(limit_ms * rate_khz));
+    CUDA_TRY(cudaGetLastError());
+    return check_device_error(c);
 }
 
 lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction) {

@@ -40,14 +40,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; gives up after about a second of
-// polling (try_wait itself suspends for a bounded time) and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; gives up after limit_cycles SM clock cycles
+// of polling (default about 2 s at 2 GHz; try_wait itself suspends for a bounded time) and returns
+// false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_cycles = 4000000000ULL) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > 4000000000ULL) return false;  // ~2 s at 2 GHz
+        if (clock64() - t0 > limit_cycles) return false;
     }
 }
 

@@ -33,7 +33,7 @@ SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
            "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc",
            "lbm_diagnostics_all", "lbm_contact_angle_all", "lbm_set_wall_path", "lbm_set_densities_all",
-           "lbm_fields_all")
+           "lbm_fields_all", "lbm_selftest_wait_timeout")
 
 
 class lbm_grid(ctypes.Structure):
@@ -121,6 +121,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_diagnostics_noalloc.argtypes = [c_void_p] * 5 + [c_int32, c_int32, c_void_p, POINTER(lbm_diag)]
     lib.lbm_diagnostics_all.argtypes = [ctx_p, POINTER(lbm_diag)]
     lib.lbm_set_densities_all.argtypes = [ctx_p, c_void_p, c_void_p, c_int32]
+    lib.lbm_selftest_wait_timeout.argtypes = [ctx_p, c_double]
     lib.lbm_fields_all.argtypes = [ctx_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]
     lib.lbm_contact_angle_all.argtypes = [ctx_p, POINTER(lbm_surface), c_void_p, c_void_p, c_void_p]
     lib.lbm_status_str.argtypes = [c_int32]
@@ -265,6 +266,11 @@ def lbm_fields_all(ctx, rho_A=None, rho_B=None, ux=None, uy=None, on_device: boo
         if a is not None and not on_device:
             assert a.dtype == np.float64 and a.flags.c_contiguous
     _check(load_library().lbm_fields_all(ctx, _ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy), 1 if on_device else 0))
+
+
+def lbm_selftest_wait_timeout(ctx, limit_ms: float) -> None:
+    """Drive a kernel's bounded pipeline wait to its limit; raises the error a stalled step raises."""
+    _check(load_library().lbm_selftest_wait_timeout(ctx, float(limit_ms)))
 
 
 def lbm_diagnostics(ctx, case_index: int = 0, allow_unstable: bool = False) -> dict:

@@ -505,3 +505,26 @@ def test_synchronize_gives_up_after_its_time_limit():
     assert e.value.status == lbm.LBM_ETIMEOUT
     lat.sync(0)
     lat.close()
+
+
+def test_a_pipeline_wait_that_never_completes_gives_up_and_is_reported():
+    """The step kernel's bounded wait, driven to its limit on an mbarrier that nothing arrives on
+    (no fault, no hang): the kernel records the error word, the host reports it as a stalled step,
+    and the GPU stays usable for the next context."""
+    sc = SCENARIOS["cylinder96"]()
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(5)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_selftest_wait_timeout(lat.ctx, 20.0)
+    assert e.value.status == lbm.LBM_ECUDA
+    assert "gave up" in str(e.value) and "self-test" in str(e.value)
+    with pytest.raises(lbm.LbmError):  # the error word stays set for this context
+        lat.diagnostics()
+    lat.close()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_selftest_wait_timeout(lbm.Lattice(sc, "f32").ctx, 0.0)
+    assert e.value.status == lbm.LBM_EINVAL
+    fresh = lbm.Lattice(sc, "f32")
+    fresh.step(50)
+    assert fresh.diagnostics()["unstable"] == 0
+    fresh.close()
