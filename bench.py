@@ -43,6 +43,7 @@ INNER = 100            # time steps per bench step
 BYTES_PER_NODE = {"f32": 144, "f16": 72, "bf16": 72, "f64": 288}
 KERNEL_SOURCES = ("paper_2505_22256_gb300/csrc/lbm_step.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh",
                   "paper_2505_22256_gb300/csrc/lbm_tma.cuh")
+KERNEL_SOURCES_3D = ("paper_2505_22256_gb300/csrc/lbm3d.cu", "paper_2505_22256_gb300/csrc/lbm_device.cuh")
 
 
 def parse(argv=None):
@@ -214,18 +215,18 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic(storage: str, nodes_per_launch: int):
+def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step", sources=KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, scaled to this launch's nodes; None when
     the summary is missing or was taken on a different version of the kernel source."""
-    p = os.path.join(ROOT, "profiles", f"k_step_{storage}_counters.txt")
+    p = os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters.txt")
     try:
         kv = {}
         with open(p) as fh:
@@ -233,7 +234,7 @@ def committed_traffic(storage: str, nodes_per_launch: int):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
             return None
         per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
         return per_node * nodes_per_launch
@@ -660,7 +661,9 @@ def run_ours_3d(args):
                    "inner_steps": args.inner, "parallelism": f"one lattice per GPU x{world} (no collective)",
                    "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE_3D[args.storage] / 2 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": algo / (launch_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": algo / (launch_ms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": algo / (launch_ms / 1e3) / 1e9 / peak,
+                     "traffic": committed_traffic(args.storage, nodes, "k3_step", KERNEL_SOURCES_3D),
+                     "peak_kind": peak_kind,
                      "kernel": "k3_rho + k3_march (one time step)", "algorithmic_bytes_per_launch": algo,
                      "launch_ms": launch_ms},
         "e2e": e2e, "gpu_launches": (2 * args.inner + 3 + 9) * args.steps, "clocks": clk,
