@@ -48,6 +48,30 @@ def test_sweep_1024_seven_cases_one_step_parity_and_mass():
     lat.close()
 
 
+@pytest.mark.parametrize("workload", ["sweep", "couette"])
+def test_autotuned_launch_shape_one_step_parity(workload):
+    """The launch shape bench.py times is the one lbm_autotune(ctx, 4) picks on the live state (block
+    width, wall-list form, row chunks); one more step in that shape matches the oracle's step from
+    the same state, and mass is kept over the tuning steps."""
+    cases = S.lambda_sweep_cylinder(1024) if workload == "sweep" else \
+        [S.couette_channel(seed=7 + 100 * j) for j in range(512)]
+    lat = lbm.Lattice(cases, "f32")
+    m0 = lat.diagnostics(0)
+    lbm.lbm_autotune(lat.ctx, 4)
+    info = lat.info()
+    assert info["block_threads"] in (64, 128) and info["wall_inline"] in (0, 1)
+    lat.step(7)
+    sample = (0, len(cases) // 2, len(cases) - 1)
+    before = {i: lat.populations(i) for i in sample}
+    lat.step(1)
+    for i in sample:
+        _compare_step(cases[i], before[i], lat.populations(i), 2e-6)
+    m1 = lat.diagnostics(0)
+    for k in ("mass_A", "mass_B"):
+        assert abs(m1[k] / m0[k] - 1) < 1e-5, k
+    lat.close()
+
+
 def test_porous_4096x2048_open_boundaries_one_step_parity():
     sc = S.porous_disks()
     fl = sc.solid == 0
