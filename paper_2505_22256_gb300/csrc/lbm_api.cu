@@ -172,19 +172,19 @@ lbm_status build_tmaps(Ctx& c) {
         const DevCase& d = c.hcases[ci];
         for (int buf = 0; buf < 2; ++buf) {
             void* base = (char*)c.f[buf] + (size_t)d.f_off * pb;
-            const cuuint64_t row = (cuuint64_t)d.pitch * pb;
+            const cuuint64_t plane = (cuuint64_t)d.pitch * pb, row = 9 * plane;  // [ny][9][pitch] pairs
             CUresult r;
             if (f64) {
-                cuuint64_t dims[4] = {2, (cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 9};
-                cuuint64_t strides[3] = {pb, row, row * d.ny};
-                cuuint32_t box[4] = {2, (cuuint32_t)(T + XB), 1, 9};
+                cuuint64_t dims[4] = {2, (cuuint64_t)(d.nx + 2 * G), 9, (cuuint64_t)d.ny};
+                cuuint64_t strides[3] = {pb, plane, row};
+                cuuint32_t box[4] = {2, (cuuint32_t)(T + XB), 9, 1};
                 cuuint32_t estr[4] = {1, 1, 1, 1};
                 r = enc(&maps[3 * ci + buf], dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             } else {
-                cuuint64_t dims[3] = {(cuuint64_t)(d.nx + 2 * G), (cuuint64_t)d.ny, 9};
-                cuuint64_t strides[2] = {row, row * d.ny};
-                cuuint32_t box[3] = {(cuuint32_t)(T + XB), 1, 9};
+                cuuint64_t dims[3] = {(cuuint64_t)(d.nx + 2 * G), 9, (cuuint64_t)d.ny};
+                cuuint64_t strides[2] = {plane, row};
+                cuuint32_t box[3] = {(cuuint32_t)(T + XB), 9, 1};
                 cuuint32_t estr[3] = {1, 1, 1};
                 r = enc(&maps[3 * ci + buf], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1062,7 +1062,7 @@ lbm_status lbm_save(lbm_ctx* ctx, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, "LBMGB300", 8);
-    h.version = 2;  // 2: (A, B) pairs per direction
+    h.version = 3;  // 3: (A, B) pairs, the nine planes of a row side by side
     h.storage = c.storage;
     h.ncases = (int32_t)c.cases.size();
     h.steps = c.steps;
@@ -1083,7 +1083,7 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path) {
     CkptHeader h;
     std::vector<unsigned char> buf(c.pop_elems * c.elem);
     bool ok = fread(&h, sizeof h, 1, fp) == 1;
-    if (ok && (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2 || h.storage != c.storage ||
+    if (ok && (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3 || h.storage != c.storage ||
                h.ncases != (int32_t)c.cases.size() || h.bytes != (int64_t)buf.size() || h.hash != params_hash(c))) {
         fclose(fp);
         return fail(LBM_EIO, "%s does not match this context", path);

@@ -70,8 +70,8 @@ __host__ __device__ __forceinline__ constexpr double w8(int e2) {
 // ------------------------------------------------------------------------------------------------
 template <class R>
 struct CaseParams {
-    int nx, ny, pitch, bc_x, bc_y, mode;
-    long long plane;  // ny * pitch (pairs)
+    int nx, ny, row, bc_x, bc_y, mode;  // row: stride of lattice rows (9 planes x pitch pairs)
+    long long plane;                    // stride of the planes of one row (pitch pairs)
     R omega[2], cF[2];
     R G, Gw2, lam, delta, s1, s2, s3, t2, t3;
     R gx, gy;
@@ -87,10 +87,10 @@ struct CaseParams {
 // Per-case descriptor (device copy; built on the host).
 // ------------------------------------------------------------------------------------------------
 struct DevCase {
-    int nx, ny, pitch;      // pitch: (A, B) pairs per stored population row (ghost columns included)
+    int nx, ny, pitch;      // pitch: (A, B) pairs per row of one plane (ghost columns included)
     int bc_x, bc_y;
     int mode;               // 0 original, 1 improved
-    long long f_off;        // pair offset of the case's [9][ny][pitch] block of (A, B) pairs in a buffer
+    long long f_off;        // pair offset of the case's [ny][9][pitch] block of (A, B) pairs in a buffer
     long long d_off;        // element offset of the case's [ny][nx] block in per-node arrays
     long long w_off;        // first wall-list entry of the case
     long long nwall;        // wall-list entries of the case
@@ -112,8 +112,8 @@ struct DevCase {
 // Derive pf / pd from the double fields above (host side, after pitch is known).
 template <class R>
 inline void fill_case_params_as(const DevCase& d, CaseParams<R>& P) {
-    P.nx = d.nx; P.ny = d.ny; P.pitch = d.pitch; P.bc_x = d.bc_x; P.bc_y = d.bc_y; P.mode = d.mode;
-    P.plane = (long long)d.ny * d.pitch;
+    P.nx = d.nx; P.ny = d.ny; P.row = 9 * d.pitch; P.bc_x = d.bc_x; P.bc_y = d.bc_y; P.mode = d.mode;
+    P.plane = d.pitch;
     for (int k = 0; k < 2; ++k) {
         P.omega[k] = (R)d.omega[k];
         P.cF[k] = (R)d.cF[k];

@@ -2,8 +2,8 @@
 // kernels that read and write its state.
 //
 // State: one buffer per time level holds the post-collision populations f*_i^k of every case as
-// [9][ny][pitch] planes of pairs (f*_i^A, f*_i^B) of the storage type S (plane i): one vector access
-// moves both components of a direction.  Column x of a row lives at pair x + G; the G ghost columns
+// [ny][9][pitch] pairs (f*_i^A, f*_i^B) of the storage type S: the nine direction planes of a lattice
+// row lie next to each other, and one vector access moves both components of a direction.  Column x of a row lives at pair x + G; the G ghost columns
 // on each side repeat the opposite edge when x is periodic, so a tensor box never has to wrap.
 //
 // One launch of k_step performs, for every fluid node x:
@@ -443,8 +443,8 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
         auto issue = [&]() {
             const uint32_t dst = slot0 + issue_slot * (uint32_t)plan.slot_bytes;
             mbar_expect_tx(bar0 + 8 * issue_slot, box_bytes);
-            if constexpr (sizeof(S) == 8) tma_load_4d(dst, lmap, 0, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
-            else tma_load_3d(dst, lmap, xs, wrap_row(next_row), 0, bar0 + 8 * issue_slot);
+            if constexpr (sizeof(S) == 8) tma_load_4d(dst, lmap, 0, xs, 0, wrap_row(next_row), bar0 + 8 * issue_slot);
+            else tma_load_3d(dst, lmap, xs, 0, wrap_row(next_row), bar0 + 8 * issue_slot);
             tma_load_2d(dst + (uint32_t)plan.pop_bytes, fmap, xs, wrap_row(next_row), bar0 + 8 * issue_slot);
             next_row += dir;
             if (++issue_slot == kSlots) {
@@ -595,14 +595,14 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                 V2<R> o[9];
                 collide<R>(f, r2, ux, uy, V2<R>{FAx, FBx}, V2<R>{FAy, FBy}, V2<R>{P.omega[0], P.omega[1]},
                            V2<R>{P.cF[0], P.cF[1]}, o);
-                Pair<S>* out = fo + (long long)y * P.pitch + x + G;
+                Pair<S>* out = fo + (long long)y * P.row + x + G;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     if constexpr (Store<S>::kShift) o[i] = vsub(o[i], V2<R>{shift_of(P, 0, i), shift_of(P, 1, i)});
                     store_pair<S, R>(out + i * P.plane, o[i].x, o[i].y);
                 }
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
-                    Pair<S>* gout = fo + (long long)y * P.pitch + (x < G ? x + P.nx + G : x - P.nx + G);
+                    Pair<S>* gout = fo + (long long)y * P.row + (x < G ? x + P.nx + G : x - P.nx + G);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         store_pair<S, R>(gout, o[i].x, o[i].y);
@@ -737,8 +737,8 @@ __global__ void k_sliding_walls(const DevCase* __restrict__ cases, const int* __
     if (flags_all[C.d_off + (long long)Y * C.nx + X] & kSolidBit) return;
     const double uw = upper ? C.u_wall[1] : C.u_wall[0];
     if (uw == 0.0) return;
-    const long long plane = (long long)C.ny * C.pitch;
-    Pair<S>* p = buf_all + C.f_off + (long long)Y * C.pitch + X + G;
+    const long long plane = C.pitch;
+    Pair<S>* p = buf_all + C.f_off + (long long)Y * 9 * C.pitch + X + G;
     const int ip = upper ? 6 : 7, im = upper ? 5 : 8;  // returning as e_x = +1 / -1
     auto shift = [&](int k, int j) -> R { return Store<S>::kShift ? (R)(wq(j) * C.rho0[k]) : (R)0; };
     R v[2][9];
@@ -793,12 +793,12 @@ __global__ void k_set_state(const DevCase* __restrict__ cases, int c, const uint
     constexpr int G = Layout<S>::G;
     const DevCase C = cases[c];
     const long long N = (long long)C.nx * C.ny;
-    const long long plane = (long long)C.ny * C.pitch;
+    const long long plane = C.pitch;
     Pair<S>* out = out_all + C.f_off;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
         const uint16_t fl = flags_all[C.d_off + s];
-        const long long o = (long long)Y * C.pitch + X + G;
+        const long long o = (long long)Y * 9 * C.pitch + X + G;
         R ov[2][9];
         for (int k = 0; k < 2; ++k) {
             double vs[9];
@@ -864,8 +864,9 @@ __global__ void k_get_state(const DevCase* __restrict__ cases, int c, const uint
             const int ym = Y - 1 < 0 ? (C.bc_y == kPeriodic ? C.ny - 1 : 0) : Y - 1;
             const int yp = Y + 1 >= C.ny ? (C.bc_y == kPeriodic ? 0 : C.ny - 1) : Y + 1;
             const bool inlet = C.bc_x == kOpen && X == 0, outlet = C.bc_x == kOpen && X == C.nx - 1;
-            pull<true, S, R, long long>(fin + (long long)ym * C.pitch, fin + (long long)Y * C.pitch,
-                                        fin + (long long)yp * C.pitch, P.plane, X + G, fl, inlet, outlet, P, P, Y, v);
+            const long long rs = 9LL * C.pitch;
+            pull<true, S, R, long long>(fin + ym * rs, fin + Y * rs, fin + yp * rs, P.plane, X + G, fl, inlet, outlet, P,
+                                        P, Y, v);
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
