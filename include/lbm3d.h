@@ -82,6 +82,12 @@ lbm_status lbm3d_fields(lbm3d_ctx* ctx, double* rho_A, double* rho_B, double* ux
 lbm_status lbm3d_get_populations(lbm3d_ctx* ctx, double* f);
 lbm_status lbm3d_set_populations(lbm3d_ctx* ctx, const double* f);
 
+/* Re-initialise the lattice from new densities, f = f^eq(rho_k, 0), as lbm3d_create does (the same
+ * state bit for bit) but without rebuilding the geometry.  rho_A, rho_B: [nz][ny][nx] doubles on
+ * the host (on_device = 0: copied before return; the first such call allocates 16 bytes per node,
+ * held until lbm3d_destroy) or on the device (on_device = 1: read on the context's stream). */
+lbm_status lbm3d_set_densities(lbm3d_ctx* ctx, const double* rho_A, const double* rho_B, int32_t on_device);
+
 /* FP64 diagnostics over the fluid nodes (host output; synchronises).  LBM_EUNSTABLE when a
  * density is non-finite or <= 0, or a velocity non-finite (the record is still written). */
 lbm_status lbm3d_diagnostics(lbm3d_ctx* ctx, lbm3d_diag* out);

@@ -635,6 +635,28 @@ __global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double*
     }
 }
 
+// f = f^eq(rho_k, 0) written straight into the post-collision buffer as the pull expects it (the
+// state k3_feq + k3_set give, bit for bit, without the [38][N] transfer scratch): the stored f*_i
+// at x is w_i rho(x + e_i), or w_i rho(x) when x + e_i is solid (the link comes back by
+// bounce-back), and 0 at solid nodes.
+template <class R>
+__global__ void k3_set_rest(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ rA,
+                            const double* __restrict__ rB, V2<R>* __restrict__ fs) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long s = ((long long)z * g.ny + y) * g.nx + x;
+    const uint32_t fl = flags[s];
+    for (int i = 0; i < 19; ++i) {
+        V2<R> v{(R)0, (R)0};
+        if (!(fl & k3Solid)) {
+            const bool bl = i > 0 && ((fl >> (opp3(i) - 1)) & 1u);
+            const long long t = (bl || i == 0) ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i));
+            v = V2<R>{(R)(w19(i) * rA[t]), (R)(w19(i) * rB[t])};
+        }
+        fs[(long long)i * g.N + s] = v;
+    }
+}
+
 template <class R>
 __global__ void k3_feq(Geo3 g, const uint8_t* __restrict__ solid, const double* __restrict__ rA, const double* __restrict__ rB,
                        double* __restrict__ f) {
@@ -840,6 +862,7 @@ struct lbm3d_ctx {
     double* dout = nullptr;        // [k3DiagN]
     double* ca = nullptr;          // contact angle: status record + block partials
     double* scratch = nullptr;     // [38][N] doubles for population transfers and fields (on demand)
+    double* dens = nullptr;        // [2][N] doubles for lbm3d_set_densities from host arrays (on demand)
 };
 
 namespace {
@@ -941,7 +964,7 @@ cudaError_t ca_passes(lbm3d_ctx* c, const double* sc, double R_) {
 }
 
 void free3(lbm3d_ctx* c) {
-    void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->scratch};
+    void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->scratch, c->dens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1103,6 +1126,25 @@ extern "C" lbm_status lbm3d_get_populations(lbm3d_ctx* c, double* f) {
     TRY3(cudaGetLastError(), "read-back kernel");
     TRY3(cudaMemcpyAsync(f, c->scratch, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read-back");
     TRY3(cudaStreamSynchronize(c->stream), "read-back");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_set_densities(lbm3d_ctx* c, const double* rho_A, const double* rho_B, int32_t on_device) {
+    if (!c || !rho_A || !rho_B) return report_error(LBM_EINVAL, "NULL argument");
+    const long long N = c->g.N;
+    const double *a = rho_A, *b = rho_B;
+    if (!on_device) {
+        if (!c->dens) TRY3(cudaMalloc(&c->dens, (size_t)2 * N * sizeof(double)), "density buffer");
+        TRY3(cudaMemcpyAsync(c->dens, rho_A, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
+        TRY3(cudaMemcpyAsync(c->dens + N, rho_B, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
+        a = c->dens;
+        b = c->dens + N;
+    }
+    if (c->storage == LBM_STORE_F64)
+        k3_set_rest<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (double2*)c->f[c->cur]);
+    else k3_set_rest<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (float2*)c->f[c->cur]);
+    TRY3(cudaGetLastError(), "state kernel");
+    if (!on_device) TRY3(cudaStreamSynchronize(c->stream), "upload");
     return LBM_OK;
 }
 

@@ -11,7 +11,7 @@ import numpy as np
 from . import lbm
 
 SYMBOLS3 = ("lbm3d_create", "lbm3d_destroy", "lbm3d_step", "lbm3d_fields", "lbm3d_get_populations",
-            "lbm3d_set_populations", "lbm3d_diagnostics", "lbm3d_contact_angle")
+            "lbm3d_set_populations", "lbm3d_diagnostics", "lbm3d_contact_angle", "lbm3d_set_densities")
 
 
 class lbm3d_grid(ctypes.Structure):
@@ -49,6 +49,7 @@ def _lib():
         lib.lbm3d_fields.argtypes = [c_void_p] + [c_void_p] * 5 + [c_int32]
         lib.lbm3d_get_populations.argtypes = [c_void_p, c_void_p]
         lib.lbm3d_set_populations.argtypes = [c_void_p, c_void_p]
+        lib.lbm3d_set_densities.argtypes = [c_void_p, c_void_p, c_void_p, c_int32]
         lib.lbm3d_diagnostics.argtypes = [c_void_p, POINTER(lbm3d_diag)]
         lib.lbm3d_contact_angle.argtypes = [c_void_p, POINTER(c_double), c_double, d, d, POINTER(c_int64)]
         for name in SYMBOLS3:
@@ -108,8 +109,14 @@ class Lattice3:
 
     def fields(self):
         out = [np.zeros((self.nz, self.ny, self.nx)) for _ in range(5)]
-        lbm._check(_lib().lbm3d_fields(self.ctx, *[o.ctypes.data for o in out], 0))
+        self.fields_into(*out)
         return tuple(out)
+
+    def fields_into(self, rho_A, rho_B, ux, uy, uz):
+        """Fields into the given host float64 arrays of shape [nz][ny][nx] (any may be None)."""
+        for a in (rho_A, rho_B, ux, uy, uz):
+            assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nx * self.ny * self.nz)
+        lbm._check(_lib().lbm3d_fields(self.ctx, *[lbm._ptr(o) for o in (rho_A, rho_B, ux, uy, uz)], 0))
 
     def populations(self) -> np.ndarray:
         f = np.zeros((2, 19, self.nz, self.ny, self.nx))
@@ -120,6 +127,15 @@ class Lattice3:
         f = _c(f, np.float64)
         assert f.shape == (2, 19, self.nz, self.ny, self.nx)
         lbm._check(_lib().lbm3d_set_populations(self.ctx, f.ctypes.data))
+
+    def set_densities(self, rho_A, rho_B, on_device: bool = False):
+        """f = f^eq(rho_k, 0) from new densities ([nz][ny][nx]; host arrays, or device buffers)."""
+        if on_device:
+            lbm._check(_lib().lbm3d_set_densities(self.ctx, lbm._ptr(rho_A), lbm._ptr(rho_B), 1))
+        else:
+            a, b = _c(rho_A, np.float64), _c(rho_B, np.float64)
+            assert a.shape == b.shape == (self.nz, self.ny, self.nx)
+            lbm._check(_lib().lbm3d_set_densities(self.ctx, a.ctypes.data, b.ctypes.data, 0))
 
     def diagnostics(self, allow_unstable: bool = False) -> dict:
         d = lbm3d_diag()
