@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -245,6 +246,20 @@ def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
 # ------------------------------------------------------------------------------------------------
+def host_info() -> dict:
+    """The host cores the oracle runs on: their count and, where the system reports it, the model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or platform.machine()}
+
+
 # max relative |d rho| after PARITY_STEPS steps that the GPU tests hold each storage mode to
 PARITY_STEPS = 100
 PARITY_BAR = {"f32": 1e-5, "f16": 5e-3, "bf16": 5e-2, "f64": 1e-10}
@@ -286,7 +301,19 @@ def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
     mlups = sc.nx * sc.ny * n / el / 1e6
     out = {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, {sc.name}), {n} FP64 time steps "
-                     f"in {el:.1f} s on {cfg.nthreads} host threads"}
+                     f"in {el:.1f} s on {cfg.nthreads} host threads", "host": host_info()}
+    if parity:
+        # the same oracle on one host thread, continuing from the state reached (about 4 s)
+        cfg1 = oracle.Config(nx=sc.nx, ny=sc.ny, nthreads=1, **sc.params())
+        n1, t1 = 0, time.perf_counter()
+        while True:
+            f = oracle.run(cfg1, sc.solid, f, 1)
+            n1 += 1
+            el1 = time.perf_counter() - t1
+            if el1 >= min(4.0, seconds) or n1 >= 10000:
+                break
+        out["single_thread_value"] = sc.nx * sc.ny * n1 / el1 / 1e6
+        out["single_thread_sample"] = f"{n1} FP64 time steps of the same case in {el1:.1f} s on 1 host thread"
     if parity and snap is not None:
         from paper_2505_22256_gb300 import lbm
 
@@ -542,7 +569,7 @@ def cpu_baseline_3d(seconds: float, storage: str | None = None) -> dict:
             break
     out = {"value": nx * ny * nz * n / el / 1e6, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
            "sample": f"the Sec. 3.5 geometry scaled to {nx}x{ny}x{nz}, {n} FP64 time steps in {el:.1f} s on "
-                     f"{cfg.nthreads} host threads"}
+                     f"{cfg.nthreads} host threads", "host": host_info()}
     if storage and snap is not None:
         from paper_2505_22256_gb300 import lbm3d
 
