@@ -1086,6 +1086,7 @@ extern "C" void lbm3d_destroy(lbm3d_ctx* c) {
 }
 
 extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
+    NvtxRange nvtx_("lbm3d_step");
     if (!c) return report_error(LBM_EINVAL, "NULL context");
     if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
     // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
@@ -1104,6 +1105,7 @@ extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
 
 extern "C" lbm_status lbm3d_fields(lbm3d_ctx* c, double* rA, double* rB, double* ux, double* uy, double* uz,
                                    int32_t on_device) {
+    NvtxRange nvtx_("lbm3d_fields");
     if (!c) return report_error(LBM_EINVAL, "NULL context");
     TRY3(scratch_for(c), "fields scratch");
     TRY3(run_fields(c, c->scratch, false), "fields kernels");

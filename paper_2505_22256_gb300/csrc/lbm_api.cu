@@ -577,6 +577,7 @@ void lbm_destroy(lbm_ctx* ctx) {
 }
 
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
+    NvtxRange nvtx_("lbm_step");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (n < 0) return fail(LBM_EINVAL, "negative step count");
     Ctx& c = ctx->c;
@@ -655,6 +656,7 @@ lbm_status lbm_set_densities(lbm_ctx* ctx, int32_t ci, const double* rho_A0, con
 }
 
 lbm_status lbm_fields(lbm_ctx* ctx, int32_t ci, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device) {
+    NvtxRange nvtx_("lbm_fields");
     lbm_status s = check_case(ctx, ci);
     if (s != LBM_OK) return s;
     Ctx& c = ctx->c;
@@ -688,6 +690,7 @@ static lbm_status fields_all_scratch(Ctx& c) {
 }
 
 lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0, int32_t on_device) {
+    NvtxRange nvtx_("lbm_set_densities_all");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (!rho_A0 || !rho_B0) return fail(LBM_EINVAL, "NULL density");
     Ctx& c = ctx->c;
@@ -712,6 +715,7 @@ lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const doubl
 }
 
 lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device) {
+    NvtxRange nvtx_("lbm_fields_all");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     Ctx& c = ctx->c;
     const long long total = c.dense_elems;
@@ -731,6 +735,7 @@ lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
+    NvtxRange nvtx_("lbm_diagnostics");
     lbm_status s = check_case(ctx, ci);
     if (s != LBM_OK) return s;
     if (!out) return fail(LBM_EINVAL, "NULL output");
@@ -764,6 +769,7 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {
 
 lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surface, double* theta_deg, double* fit_rms,
                              int64_t* npoints) {
+    NvtxRange nvtx_("lbm_contact_angle");
     lbm_status s = check_case(ctx, ci);
     if (s != LBM_OK) return s;
     if (!surface) return fail(LBM_EINVAL, "NULL surface");
@@ -785,6 +791,7 @@ lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surfac
 }
 
 lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out) {
+    NvtxRange nvtx_("lbm_diagnostics_all");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (!out) return fail(LBM_EINVAL, "NULL output");
     Ctx& c = ctx->c;
@@ -821,6 +828,7 @@ lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out) {
 
 lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, double* theta_deg, double* fit_rms,
                                  int64_t* npoints) {
+    NvtxRange nvtx_("lbm_contact_angle_all");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (!surfaces) return fail(LBM_EINVAL, "NULL surfaces");
     Ctx& c = ctx->c;
@@ -983,6 +991,7 @@ lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction) {
 }
 
 lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
+    NvtxRange nvtx_("lbm_autotune");
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
     Ctx& c = ctx->c;

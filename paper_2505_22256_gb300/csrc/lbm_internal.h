@@ -2,6 +2,7 @@
 // C-ABI layer (lbm_api.cu) calls.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,6 +21,15 @@ struct HostCase {
     lbm_grid grid;
     lbm_params params;
     int64_t nfluid = 0;
+};
+
+// NVTX range over the host side of one entry point (visible in Nsight Systems timelines; NVTX v3
+// is header-only and costs a few nanoseconds when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 struct Ctx {

@@ -54,6 +54,19 @@ static_assert(kSlots >= 4, "the pull of a row needs three resident rows plus one
 template <class R>
 using Params = CaseParams<R>;
 
+#ifdef LBM_BOUNDS_CHECK
+// Checked build (a sanitizer of this kernel's own indexing): every shared- and global-memory index
+// of the step kernel is tested before use; an index outside its buffer sets bit 4 of the context's
+// error word and the access is skipped.  The normal build compiles the tests away.
+__device__ __forceinline__ bool idx_ok(bool ok, int* err) {
+    if (!ok) atomicOr(err, 4);
+    return ok;
+}
+#define LBM_IDX_OK(cond) idx_ok((cond), a.err)
+#else
+#define LBM_IDX_OK(cond) true
+#endif
+
 template <class R>
 __device__ __forceinline__ Params<R> load_params(const DevCase& C) {
     return case_params<R>(C);
@@ -357,6 +370,7 @@ struct StepArgs {
     const uint32_t* wsub;      // dense: substitution mask of wall-list nodes
     const void* wa;            // dense: adhesion vectors [2][nodes] in the compute type
     long long dense_total;
+    long long pop_pairs;       // pairs in one population buffer (index checks of the checked build)
     int* err;
     int* sched;                // [0] next work item, [1] blocks finished; both back to 0 at exit
     int fields_global;         // fields mode: outputs indexed over all cases (d_off + y nx + x)
@@ -477,7 +491,7 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                         : kSolidBit;
             V2<R> rho2 = vbc<R>(0);
             const bool general = __any_sync(0xffffffffu, (st.fl & 0xFFu) != 0 || inlet || outlet);
-            if (!(st.fl & kSolidBit)) {
+            if (!(st.fl & kSolidBit) && LBM_IDX_OK(sc >= 1 && sc + 1 < BX)) {  // reads columns sc - 1 .. sc + 1
                 const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_m : so_p));
                 const Pair<S>* r0 = reinterpret_cast<const Pair<S>*>(s0);
                 const Pair<S>* rp = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_p : so_m));
@@ -489,14 +503,18 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                             vadd(vadd(f[4], f[5]), vadd(f[6], vadd(f[7], f[8]))));
                 if (st.fl & kWallBit) {
                     const long long o = C.d_off + (long long)wrap_row(r) * P.nx + X;
-                    st.sub = __ldg(a.wsub + o);
-                    st.ax = __ldg(wax + o);
-                    st.ay = __ldg(way + o);
+                    if (LBM_IDX_OK(o >= 0 && o < a.dense_total)) {
+                        st.sub = __ldg(a.wsub + o);
+                        st.ax = __ldg(wax + o);
+                        st.ay = __ldg(way + o);
+                    }
                 }
             }
             const int s = m * T + t;
-            ring[s] = rho2;
-            ring[s + kRing * T] = rho2;
+            if (LBM_IDX_OK(m >= 0 && m < kRing)) {
+                ring[s] = rho2;
+                ring[s + kRing * T] = rho2;
+            }
             return ok;
         };
 
@@ -505,8 +523,9 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
         auto update_row = [&](int y, int lo, const RowState<R>& st, const Grad<R>& g, Diag<R>& dg) {
             if (!interior || (st.fl & kSolidBit)) {
                 if constexpr (kFields) {
-                    if (interior && a.o_rA) {
-                        const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
+                    const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
+                    const long long on = a.fields_global ? a.dense_total : (long long)P.nx * P.ny;
+                    if (interior && a.o_rA && LBM_IDX_OK(o >= 0 && o < on)) {
                         a.o_rA[o] = 0.0;
                         a.o_rB[o] = 0.0;
                         if (a.o_ux) {
@@ -517,6 +536,7 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                 }
                 return;
             }
+            if (!LBM_IDX_OK(lo >= 0 && lo < kRing)) return;  // rows lo .. lo + 4, columns t - 2 .. t + 2
             const int sb0 = lo * T + t;
             const V2<R> r2 = ring[sb0 + 2 * T];
             const R rA = r2.x, rB = r2.y;
@@ -567,8 +587,9 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
             const R ux = (mx + (R)0.5 * (FAx + FBx)) * inv;
             const R uy = (my + (R)0.5 * (FAy + FBy)) * inv;
             if constexpr (kFields) {
-                if (a.o_rA) {  // null outputs: partial sums only
-                    const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
+                const long long o = (a.fields_global ? C.d_off : 0) + (long long)y * P.nx + x;
+                const long long on = a.fields_global ? a.dense_total : (long long)P.nx * P.ny;
+                if (a.o_rA && LBM_IDX_OK(o >= 0 && o < on)) {  // null outputs: partial sums only
                     a.o_rA[o] = (double)rA;
                     a.o_rB[o] = (double)rB;
                     if (a.o_ux) {  // null velocity outputs: densities only
@@ -596,13 +617,20 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                 collide<R>(f, r2, ux, uy, V2<R>{FAx, FBx}, V2<R>{FAy, FBy}, V2<R>{P.omega[0], P.omega[1]},
                            V2<R>{P.cF[0], P.cF[1]}, o);
                 Pair<S>* out = fo + (long long)y * P.row + x + G;
+                // the row's nine pairs at columns x + G of planes 0..8 lie inside the case's block
+                const long long e0 = C.f_off + (long long)y * P.row + x + G;
+                if (!LBM_IDX_OK(y >= 0 && y < P.ny && x + G >= 0 && x + G < P.plane && e0 >= 0 &&
+                                e0 + 8 * P.plane < a.pop_pairs))
+                    return;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     if constexpr (Store<S>::kShift) o[i] = vsub(o[i], V2<R>{shift_of(P, 0, i), shift_of(P, 1, i)});
                     store_pair<S, R>(out + i * P.plane, o[i].x, o[i].y);
                 }
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
-                    Pair<S>* gout = fo + (long long)y * P.row + (x < G ? x + P.nx + G : x - P.nx + G);
+                    const int gx = x < G ? x + P.nx + G : x - P.nx + G;
+                    if (!LBM_IDX_OK(gx >= 0 && gx < P.plane)) return;
+                    Pair<S>* gout = fo + (long long)y * P.row + gx;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         store_pair<S, R>(gout, o[i].x, o[i].y);
@@ -635,7 +663,7 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
             const bool mine = rho_row(q, mq, cur);
             if (__syncthreads_or(!mine)) return false;
             if (t == 0 && (dir > 0 ? next_row <= r_last : next_row >= r_last)) issue();  // slot of q-dir is free
-            if (interior) {
+            if (interior && LBM_IDX_OK(mq >= 0 && mq < kRing && t >= 2 && t + 2 < T)) {
                 add_row<R>(ring, mq * T + t, g, rdir);
             }
             const int y = q - 2 * dir;
@@ -940,6 +968,7 @@ StepArgs make_args(Ctx& c, int ib, int ie, double* o4[4], double* part) {
     a.wsub = c.wsub;
     a.wa = c.wa;
     a.dense_total = c.dense_elems;
+    a.pop_pairs = c.pop_elems / 2;
     a.err = c.err;
     a.sched = c.sched;
     a.fields_global = 0;
