@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -52,6 +53,11 @@ template <class T>
 cudaError_t dalloc(Ctx& c, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    // Failure-injection hook for tests: with LBM_TEST_FAIL_ALLOC=k in the environment, the k-th
+    // allocation of a context made here fails as if the device were out of memory.
+    if (const char* k = getenv("LBM_TEST_FAIL_ALLOC")) {
+        if (++c.alloc_count == atol(k)) return cudaErrorMemoryAllocation;
+    }
     cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
     if (e == cudaSuccess) c.device_bytes += count * sizeof(T);
     return e;

@@ -39,6 +39,7 @@ struct Ctx {
     bool own_stream = false;
     int device = 0;
     int num_sms = 0;
+    long alloc_count = 0;            // allocations made through dalloc (failure-injection hook)
 
     std::vector<HostCase> cases;
     std::vector<DevCase> hcases;     // host copy of the descriptors

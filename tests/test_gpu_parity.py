@@ -507,6 +507,41 @@ def test_synchronize_gives_up_after_its_time_limit():
     lat.close()
 
 
+def test_out_of_memory_during_create_is_reported_and_frees_everything():
+    """Failure injection on the host: LBM_TEST_FAIL_ALLOC=k makes the k-th device allocation of a
+    context fail.  For every k up to past the last allocation, lbm_create reports LBM_ENOMEM (or
+    succeeds once k is past it), device memory returns to where it was, and the next create works."""
+    import torch
+
+    sc = S.cylinder_droplet(512, lam=0.7)  # buffers of megabytes, so that a leak would show
+    warm = lbm.Lattice(sc, "f32")  # loads every kernel that creation and stepping use
+    warm.step(1)
+    warm.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    try:
+        for k in range(1, 40):
+            os.environ["LBM_TEST_FAIL_ALLOC"] = str(k)
+            try:
+                lat = lbm.Lattice(sc, "f32")
+            except lbm.LbmError as e:
+                assert e.status == lbm.LBM_ENOMEM, (k, str(e))
+                failures += 1
+                assert torch.cuda.mem_get_info()[0] == free0, k
+                continue
+            lat.close()
+            break
+    finally:
+        del os.environ["LBM_TEST_FAIL_ALLOC"]
+    assert failures >= 5  # creation makes several allocations, each of which can fail
+    lat = lbm.Lattice(sc, "f32")
+    lat.step(10)
+    assert lat.diagnostics()["unstable"] == 0
+    lat.close()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_a_pipeline_wait_that_never_completes_gives_up_and_is_reported():
     """The step kernel's bounded wait, driven to its limit on an mbarrier that nothing arrives on
     (no fault, no hang): the kernel records the error word, the host reports it as a stalled step,
