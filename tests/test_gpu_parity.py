@@ -417,6 +417,15 @@ def test_checkpoint_roundtrip_is_bit_exact():
             lbm.lbm_load(other.ctx, p)
         assert e.value.status == lbm.LBM_EIO
         other.close()
+        # a truncated file and a file with a damaged header are refused, and the state is untouched
+        raw = open(p, "rb").read()
+        for name, data in (("cut", raw[: len(raw) // 2]), ("magic", b"X" + raw[1:]), ("header", raw[:12] + b"\x7f" + raw[13:])):
+            q = os.path.join(d, name + ".lbm")
+            open(q, "wb").write(data)
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_load(lat.ctx, q)
+            assert e.value.status == lbm.LBM_EIO, name
+        np.testing.assert_array_equal(lat.populations(), a)
     lat.close()
 
 
