@@ -283,10 +283,11 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out);
 
 /* Set the step kernel's launch shape: threads per block (128 or 64, the widths the kernel is built
  * for; a work item spans that many columns minus 8 halo columns; lbm_create picks the width that
- * launches fewer thread columns over all cases) and rows per work item: >= 1 for uniform items of that height, or 0 (the default) for a guided
- * list -- long items first, then 16-row items that even out the end of the launch, the long height
- * chosen to balance the list over the resident blocks.  Rebuilds the work list and drops the
- * captured graph. */
+ * launches fewer thread columns over all cases) and rows per work item: >= 1 for uniform items of
+ * that height, or 0 (the default) for a guided list -- long items first, then 16-row items that
+ * even out the end of the launch, the long height chosen to balance the list over the resident
+ * blocks; -64 .. -1 for a guided list whose short items have -block_rows rows.  Rebuilds the work
+ * list and drops the captured graph.  LBM_EINVAL for other widths or block_rows < -64. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t block_threads, int32_t block_rows);
 
 /* Failure-detection self-test (no counterpart in the paper).  Runs a one-thread kernel whose
@@ -307,7 +308,7 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, double limit_ms);
 lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction);
 
 /* Time candidate launch shapes on the live state (both widths x both wall-list forms x the row
- * heights 0, 16, 32, 64, 128; each for `steps` steps, after one warm-up launch) and keep the
+ * settings 0, -8, 16, 32, 64, 128; each for `steps` steps, after one warm-up launch) and keep the
  * fastest.  The state advances by the steps taken; best_ms (may be NULL)
  * receives the best time per step.  Synchronises. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms);

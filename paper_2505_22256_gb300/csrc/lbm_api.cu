@@ -233,7 +233,8 @@ void push_chunks(std::vector<int4>& out, int ci, int nstrip, int Wi, int y_begin
 // Work lists.  A work item is a column window of block_threads - 8 interior columns by a chunk of
 // rows of one case; blocks of the step kernel claim items in list order from a counter.
 //  * Step list.  With block_rows > 0, uniform chunks of that height.  With block_rows = 0 (the
-//    default), a guided list: long chunks of height Hb first, then short chunks of LBM_TAIL_ROWS
+//    default; block_rows < 0 for a tail of -block_rows rows), a guided list: long chunks of height
+//    Hb first, then short chunks of LBM_TAIL_ROWS
 //    rows, enough of them to absorb the ragged end of the long ones, so that a launch lasts about
 //    (rows marched, 5 halo rows per item included) / (resident blocks) + one short item.  Hb
 //    minimises that estimate.
@@ -260,7 +261,7 @@ lbm_status build_items(Ctx& c) {
         for (int i = 0; i < ncases; ++i) push_chunks(items, i, nstrip[i], Wi, 0, c.hcases[i].ny, H);
         c.rows_used = H;
     } else {
-        const int Hs = LBM_TAIL_ROWS;
+        const int Hs = c.block_rows < 0 ? -c.block_rows : LBM_TAIL_ROWS;
         // rows of short chunks per strip of case i for a given long height hb
         auto tail_chunks = [&](int i, int hb) -> int {
             const long long need = (resident * (hb + 5) + strips * (Hs + 5) - 1) / (strips * (Hs + 5));
@@ -946,7 +947,7 @@ lbm_status lbm_info(lbm_ctx* ctx, lbm_info_t* out) {
 lbm_status lbm_set_launch(lbm_ctx* ctx, int32_t threads, int32_t rows) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     if (threads != 128 && threads != 64) return fail(LBM_EINVAL, "the step kernel is built for 64 or 128 threads per block");
-    if (rows < 0) return fail(LBM_EINVAL, "rows must be >= 0 (0 = automatic)");
+    if (rows < -64) return fail(LBM_EINVAL, "rows must be >= -64 (0 or < 0: guided list, < 0 with tail items of -rows rows)");
     Ctx& c = ctx->c;
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     c.block_threads = threads;
@@ -1002,7 +1003,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
     Ctx& c = ctx->c;
     const int cand_t[] = {128, 64};
-    const int cand_r[] = {0, 16, 32, 64, 128};
+    const int cand_r[] = {0, -8, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
