@@ -68,6 +68,27 @@ def test_initial_state_and_population_roundtrip(name):
     lat.close()
 
 
+def test_step_count_split_does_not_change_the_state():
+    """Seven steps at once, and one step at a time, give the same state bit for bit; zero steps
+    leaves the state untouched and a negative count is refused."""
+    sc = CASES["uneven_chunks"]()
+    out = []
+    for split in ([7], [1] * 7, [2, 0, 5]):
+        lat = lattice(sc, "f32")
+        before = lat.populations()
+        lat.step(0)
+        np.testing.assert_array_equal(lat.populations(), before)
+        for n in split:
+            lat.step(n)
+        with pytest.raises(lbm.LbmError) as e:
+            lat.step(-1)
+        assert e.value.status == lbm.LBM_EINVAL
+        out.append(lat.populations())
+        lat.close()
+    for f in out[1:]:
+        np.testing.assert_array_equal(f, out[0])
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_f64_matches_oracle_after_30_steps(name):
     sc = CASES[name]()

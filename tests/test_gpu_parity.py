@@ -241,6 +241,34 @@ def test_launch_shapes_agree():
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_step_count_split_does_not_change_the_state(storage):
+    """lbm_step replays a captured graph of 16 launches while at least 16 steps remain and the
+    current buffer is the first one, and launches single steps otherwise.  The state after 41 steps
+    is the same bit for bit however the count is split: all at once (two graph runs and 9 singles),
+    one step first (so the graph is not used until the buffers line up again), and one step at a
+    time.  Zero steps leaves the state untouched; a negative count is refused."""
+    sc = SCENARIOS["ragged131x77"]()
+    splits = [[41], [1, 16, 16, 8], [1] * 41]
+    out = []
+    for split in splits:
+        lat = lbm.Lattice(sc, storage)
+        lbm.lbm_set_launch(lat.ctx, 128, 16)
+        before = lat.populations()
+        lat.step(0)
+        np.testing.assert_array_equal(lat.populations(), before)
+        for n in split:
+            lat.step(n)
+        with pytest.raises(lbm.LbmError) as e:
+            lat.step(-1)
+        assert e.value.status == lbm.LBM_EINVAL
+        assert lat.info()["steps"] == 41
+        out.append(lat.populations())
+        lat.close()
+    for f in out[1:]:
+        np.testing.assert_array_equal(f, out[0])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("name", ["ragged131x77", "couette_sliding", "porous_open"])
 def test_block_widths_give_identical_states(name, storage):
     """The step kernel's 64- and 128-column forms do the same arithmetic per node, so with the same
