@@ -71,6 +71,9 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--split", action="store_true",
+                    help="strong scaling: every rank builds the same workload and steps only its share "
+                         "of the cases, assigned by node count (longest first, to the least-loaded rank)")
     return ap.parse_args(argv)
 
 
@@ -96,8 +99,32 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
 
 def job_mlups(world: int, nodes_per_rank: int, steps_per_rank: int, total_ms: float) -> float:
     """Whole-job lattice updates per second (millions): every rank updates nodes_per_rank nodes
-    steps_per_rank times (weak scaling) within the job's time total_ms."""
+    steps_per_rank times (weak scaling) within the job's time total_ms.  Under --split the caller
+    passes world = 1 and the nodes of the whole job."""
     return world * nodes_per_rank * steps_per_rank / (total_ms / 1e3) / 1e6
+
+
+def lpt_shares(sizes, world: int) -> list:
+    """Case indices per rank: cases in decreasing size (ties: lower index first), each to the rank
+    with the least work so far (ties: lower rank).  Deterministic, so every rank computes the same
+    partition from the same sizes without a collective.  The largest load is at most the mean load
+    plus the largest case (the longest-processing-time rule)."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * world
+    shares = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        shares[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(sh) for sh in shares]
+
+
+def shard(cases, rank: int, world: int):
+    """(this rank's cases, nodes of the whole job) under --split."""
+    sizes = [c.nx * c.ny for c in cases]
+    if world > len(cases):
+        raise SystemExit(f"--split: {world} ranks for {len(cases)} cases")
+    return [cases[i] for i in lpt_shares(sizes, world)[rank]], sum(sizes)
 
 
 def workload(args, rank=0):
@@ -137,13 +164,20 @@ def workload(args, rank=0):
          f"(R={160 * args.n // 1024}, r={200 * args.n // 1024}, lambda for theta=30..150 deg)")
 
 
-def config_dict(args, cases, desc, world):
+def config_dict(args, cases, desc, world, split_nodes=None):
     nodes = sum(c.nx * c.ny for c in cases)
     fluid = sum(int((c.solid == 0).sum()) for c in cases)
+    if split_nodes is None:
+        par = {"parallelism": f"ensemble x{world} (no collective)"}
+    else:  # the whole workload once, its cases shared out over the ranks
+        desc = desc.replace(" per GPU", "")
+        par = {"parallelism": f"cases split over {world} rank{'s' if world != 1 else ''} by node count "
+                              "(no collective)",
+               "job_nodes": split_nodes}
     return {
         "workload": f"{desc}, {args.inner} time steps + diagnostics + contact angle per step",
         "storage": args.storage, "cases_per_gpu": len(cases), "nodes_per_gpu": nodes,
-        "fluid_nodes_per_gpu": fluid, "inner_steps": args.inner, "parallelism": f"ensemble x{world} (no collective)",
+        "fluid_nodes_per_gpu": fluid, "inner_steps": args.inner, **par,
         "l2": "inputs larger than L2 (state %.2f GB per buffer)" % (nodes * BYTES_PER_NODE[args.storage] / 2 / 1e9),
         **({"storage_shift_rho0": list(cases[0].rho0_store)} if args.storage in ("f16", "bf16") else {}),
     }
@@ -355,6 +389,9 @@ def run_reference(args):
         print(json.dumps(line), flush=True)
         return 0
     cases, desc = workload(args)
+    split_nodes = None
+    if args.split:  # describe rank 0's share, as our arm's rank 0 does
+        cases, split_nodes = shard(cases, 0, args.gpus)
     # each step: a bounded sample of the workload (time steps of one case), sized so that the whole
     # --steps/--warmup run stays within a few minutes
     base = None
@@ -368,8 +405,8 @@ def run_reference(args):
     ms_per_step = sum(c.nx * c.ny for c in cases) * args.inner / (value * 1e6) * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(args, cases, desc, 1),
+            "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, cases, desc, args.gpus if args.split else 1, split_nodes),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -401,7 +438,14 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    cases, desc = workload(args, rank)
+    if args.split:  # the same cases on every rank (rank 0's seeds), each rank stepping its share
+        cases, desc = workload(args, 0)
+        cases, job_nodes = shard(cases, rank, world)
+        weight = 1
+    else:
+        cases, desc = workload(args, rank)
+        job_nodes = None
+        weight = world
     surfaces = [c.surface for c in cases]
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(cases, storage=args.storage, cuda_stream=stream.cuda_stream)
@@ -411,6 +455,8 @@ def run_ours(args):
     info = lat.info()
     nodes = info["nodes"]
     fluid = info["fluid_nodes"]
+    if job_nodes is None:
+        job_nodes = nodes  # per rank; weight = world counts every rank's copy
 
     def contact_angles():  # theta per case; NaN (reported as null) without a surface or an interface
         return lat.contact_angle_all(surfaces)[0]
@@ -447,7 +493,7 @@ def run_ours(args):
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
     step_ms = sum(a.elapsed_time(b) for a, b in pairs)
     ms_per_step = total_ms / args.steps
-    value = job_mlups(world, nodes, args.inner * args.steps, total_ms)
+    value = job_mlups(weight, job_nodes, args.inner * args.steps, total_ms)
     launch_ms = step_ms / (args.inner * args.steps)
     algo_bytes = BYTES_PER_NODE[args.storage] * fluid
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
@@ -486,7 +532,8 @@ def run_ours(args):
         el = max_over_ranks(time.perf_counter() - s0, world, "cuda")
         h2d = sum(2 * c.nx * c.ny * 8 for c in cases)
         d2h = sum(4 * c.nx * c.ny * 8 for c in cases)
-        e2e = {"value": job_mlups(world, nodes, args.inner * ksteps, el * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_mlups(weight, job_nodes, args.inner * ksteps, el * 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "step": "lbm_set_densities_all (pinned host, all cases), lbm_step(%d), lbm_fields_all (pinned host, "
                        "all cases)" % args.inner}
@@ -497,8 +544,9 @@ def run_ours(args):
     launches = args.inner * (2 if sliding else 1) + 2 + (9 if any(sf is not None for sf in surfaces) else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.storage, "data": "synthetic", "config": config_dict(args, cases, desc, world),
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong" if args.split else "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": config_dict(args, cases, desc, world, job_nodes if args.split else None),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_step",
                      "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
@@ -719,6 +767,8 @@ def run_ours_3d(args):
 
 def main():
     args = parse()
+    if args.split and args.workload == "sphere3d":
+        raise SystemExit("--split needs a workload of several cases")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "sphere3d":
