@@ -117,10 +117,11 @@ def _grid(ny, nx):
     return y.astype(np.float64), x.astype(np.float64)
 
 
-def _phase_fields(inside_A: np.ndarray, solid: np.ndarray, seed: int, amp: float = NOISE_AMP):
+def _phase_fields(inside_A: np.ndarray, solid: np.ndarray, seed: int, amp: float = NOISE_AMP,
+                  rho_m: float = RHO_M, rho_d: float = RHO_D):
     ny, nx = solid.shape
-    rA = np.where(inside_A, RHO_M, RHO_D) + node_noise(seed, ny, nx, 0, amp)
-    rB = np.where(inside_A, RHO_D, RHO_M) + node_noise(seed, ny, nx, 1, amp)
+    rA = np.where(inside_A, rho_m, rho_d) + node_noise(seed, ny, nx, 0, amp)
+    rB = np.where(inside_A, rho_d, rho_m) + node_noise(seed, ny, nx, 1, amp)
     rA[solid.astype(bool)] = 0.0
     rB[solid.astype(bool)] = 0.0
     return rA, rB
@@ -149,6 +150,29 @@ def cylinder_droplet(n: int = 96, R: float | None = None, r: float | None = None
     return Scenario(f"cylinder_droplet_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall",
                     scheme=scheme, tau=tuple(tau), G=G, lam=lam,
                     surface={"kind": "circle", "cx": float(cx), "cy": float(cy), "R": R + 0.5})
+
+
+def cylinder_in_box(nx: int = 300, ny: int = 350, R: float = 70.0, centre=(150.0, 130.0), r: float = 50.0,
+                    drop=(150.0, 230.0), lam: float = 1.0, seed: int = 31, scheme: str = "improved",
+                    G: float = G_DEFAULT, Gw2: float | None = GW2_DEFAULT, tau=(1.0, 1.0),
+                    rho_m: float = RHO_M, rho_d: float = RHO_D) -> Scenario:
+    """The paper's own Sec. 3.2 geometry (Fig. 5): a 300x350 box periodic in x and y, a solid
+    cylinder of radius 70 centred at (150, 130), and a droplet of A of radius 50 centred at
+    (150, 230), 0.6 r above the cylinder top.  Gw2 None means G_w2 = G."""
+    y, x = _grid(ny, nx)
+    solid = ((x - centre[0]) ** 2 + (y - centre[1]) ** 2 <= R * R).astype(np.uint8)
+    inside = (x - drop[0]) ** 2 + (y - drop[1]) ** 2 <= r * r
+    rA, rB = _phase_fields(inside, solid, seed, rho_m=rho_m, rho_d=rho_d)
+    return Scenario(f"cylinder_in_box_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="periodic",
+                    scheme=scheme, tau=tuple(tau), G=G, Gw2=Gw2, lam=lam, rho_in=(rho_m, rho_d),
+                    surface={"kind": "circle", "cx": float(centre[0]), "cy": float(centre[1]), "R": R + 0.5})
+
+
+# The parameters Sec. 3.2 states for its cylinder case: main / dissolved densities 1.02 / 0.05,
+# kinematic viscosity 0.17 (tau = 3 nu + 1/2 = 1.01) and G_w2 = G_12.  G_12 takes the mean-field
+# value for those densities in this build's weight normalisation (1.036).
+PAPER_SEC32 = {"rho_m": 1.02, "rho_d": 0.05, "tau": (1.01, 1.01), "G": round(mean_field_G(1.02, 0.05), 3),
+               "Gw2": None}
 
 
 def flat_droplet(nx: int = 64, ny: int = 48, r: float = 12.0, lam: float = 1.0, seed: int = 11,
@@ -346,6 +370,23 @@ def scheme_comparison(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110,
     for scheme in ("improved", "original"):
         for sc in lambda_sweep_cylinder(n, seed, angles, G, scheme=scheme):
             sc.name = f"{scheme}_{sc.name}"
+            out.append(sc)
+    return out
+
+
+def scheme_study(angles=(30, 50, 70, 90, 110, 130, 150), seed: int = 31, paper_params: bool = False) -> list:
+    """The comparison of Sec. 3.2 (Figs. 6, 10, 11) on the paper's 300x350 geometry: one case per
+    target angle (lambda from the correlation) under the improved scheme, then the same geometries
+    and initial states under the original scheme (G_w1 = lambda G_w2 everywhere).  paper_params
+    takes the densities, viscosity and G_w2 = G_12 of Sec. 3.2 (PAPER_SEC32) in place of this
+    build's defaults."""
+    extra = PAPER_SEC32 if paper_params else {}
+    out = []
+    for scheme in ("improved", "original"):
+        for k, th in enumerate(angles):
+            sc = cylinder_in_box(lam=lambda_for_angle(th), seed=seed * 100 + k, scheme=scheme, **extra)
+            sc.name = f"{scheme}_theta{th}_{sc.name}"
+            sc.extra["target_theta"] = float(th)
             out.append(sc)
     return out
 

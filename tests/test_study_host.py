@@ -1,0 +1,69 @@
+"""Host side of the scheme comparison (Sec. 3.2): the paper-geometry case list and the wall-layer
+statistics the study computes from the library's fields.  No GPU."""
+import numpy as np
+import pytest
+
+from paper_2505_22256_gb300 import scenarios as S
+from paper_2505_22256_gb300 import study_schemes as st
+
+
+def test_first_layer_of_a_single_solid_node_is_its_eight_neighbours():
+    solid = np.zeros((8, 8), np.uint8)
+    solid[3, 5] = 1
+    m = st.first_layer(solid)
+    want = {(3 + dy, 5 + dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1)} - {(3, 5)}
+    assert {tuple(p) for p in np.argwhere(m)} == want
+
+
+def test_first_layer_wraps_periodically_and_surrounds_a_block():
+    solid = np.zeros((8, 8), np.uint8)
+    solid[0, 0] = 1
+    got = {tuple(p) for p in np.argwhere(st.first_layer(solid))}
+    assert got == {(0, 1), (1, 0), (1, 1), (0, 7), (7, 0), (7, 7), (1, 7), (7, 1)}
+    solid = np.zeros((9, 9), np.uint8)
+    solid[3:6, 3:6] = 1
+    assert st.first_layer(solid).sum() == 5 * 5 - 3 * 3  # the ring around a 3x3 block
+
+
+def test_near_solid_is_a_periodic_square_neighbourhood():
+    solid = np.zeros((12, 12), np.uint8)
+    solid[0, 0] = 1
+    m = st.near_solid(solid, 3)
+    assert m.sum() == 7 * 7
+    assert m[3, 3] and m[-3, -3] and not m[4, 0] and not m[0, 4]
+
+
+def test_wall_layer_median_ignores_the_few_contact_line_nodes():
+    solid = np.zeros((10, 10), np.uint8)
+    solid[4:6, :] = 1  # a solid band: first layer = rows 3 and 6, 20 nodes
+    rA = np.full((10, 10), 0.03)
+    rB = np.full((10, 10), 1.0)
+    rA[3, :3] = 1.0  # A covers three first-layer nodes
+    rB[3, :3] = 0.03
+    rA[3, 3] = 0.4  # a contact-line node on the B side
+    med, share = st.wall_layer(solid, rA, rB)
+    assert med == pytest.approx(0.03)
+    assert share == pytest.approx(3 / 20)
+    rA[6, :] = 0.2  # a film of A along the other side of the band
+    med, _ = st.wall_layer(solid, rA, rB)
+    assert med == pytest.approx(0.2)
+
+
+def test_scheme_study_cases_follow_the_paper_geometry():
+    cases = S.scheme_study((30, 90, 150))
+    assert [c.scheme for c in cases] == ["improved"] * 3 + ["original"] * 3
+    for a, b in zip(cases[:3], cases[3:]):  # same geometry, initial state and lambda under both schemes
+        assert np.array_equal(a.solid, b.solid) and np.array_equal(a.rhoA0, b.rhoA0)
+        assert a.lam == b.lam and a.extra["target_theta"] == b.extra["target_theta"]
+    lams = [c.lam for c in cases[:3]]
+    assert lams == sorted(lams) and lams[1] == pytest.approx(S.lambda_for_angle(90))
+    c = cases[0]
+    assert (c.ny, c.nx) == (350, 300) and c.bc_x == c.bc_y == "periodic"
+    assert c.solid.sum() == pytest.approx(np.pi * 70 ** 2, rel=0.01)
+    inside = (c.rhoA0 > 0.5) & (c.solid == 0)
+    ys, xs = np.nonzero(inside)
+    # a disk of radius 50 about (150, 230), 0.6 r above the cylinder top, minus the cylinder
+    assert np.all((xs - 150.0) ** 2 + (ys - 230.0) ** 2 <= 50.0 ** 2)
+    assert xs.mean() == pytest.approx(150, abs=1e-9) and ys.max() == 280
+    assert np.all((xs - 150.0) ** 2 + (ys - 130.0) ** 2 > 70.0 ** 2)
+    assert c.solid[ys.min() - 1, 150] == 1  # the lowest row of A sits on the cylinder
