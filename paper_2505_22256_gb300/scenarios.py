@@ -296,7 +296,8 @@ TAU_SEC3 = 3.0 * NU_SEC3 + 0.5    # nu = c_s^2 (tau - 1/2)
 
 def couette_channel(nx: int = 50, ny: int = 100, U: float = 0.005, lam: float | None = None,
                     seed: int = 7, G: float = G_DEFAULT, scheme: str = "improved",
-                    amp: float = NOISE_AMP) -> Scenario:
+                    amp: float = NOISE_AMP, Gw2: float | None = GW2_DEFAULT, rho_m: float = RHO_M,
+                    rho_d: float = RHO_D) -> Scenario:
     """Two-layer Couette flow (Sec. 3.1, Fig. 3b): x periodic, walls half a cell below row 0 and
     above row ny-1 sliding at -U (lower) and +U (upper); A in the central half of the channel
     (|y - H/2| <= H/4), B next to both walls; nu = 0.17 for both fluids."""
@@ -304,10 +305,23 @@ def couette_channel(nx: int = 50, ny: int = 100, U: float = 0.005, lam: float | 
     solid = np.zeros((ny, nx), np.uint8)
     s = y + 0.5
     inside = np.abs(s - ny / 2.0) <= ny / 4.0
-    rA, rB = _phase_fields(inside, solid, seed, amp)
+    rA, rB = _phase_fields(inside, solid, seed, amp, rho_m=rho_m, rho_d=rho_d)
     lam = lambda_for_angle(90.0) if lam is None else lam
     return Scenario(f"couette_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="wall", scheme=scheme,
-                    tau=(TAU_SEC3, TAU_SEC3), G=G, lam=lam, u_wall=(-U, U))
+                    tau=(TAU_SEC3, TAU_SEC3), G=G, Gw2=Gw2, lam=lam, u_wall=(-U, U), rho_in=(rho_m, rho_d))
+
+
+def poiseuille_channel(nx: int = 50, ny: int = 100, g: float = 1e-6, lam: float | None = None,
+                       seed: int = 17, G: float = G_DEFAULT, scheme: str = "improved",
+                       amp: float = NOISE_AMP, Gw2: float | None = GW2_DEFAULT, rho_m: float = RHO_M,
+                       rho_d: float = RHO_D) -> Scenario:
+    """Two-layer Poiseuille flow (Sec. 3.1, Fig. 3a): the Couette channel's layers between walls
+    at rest, driven by the body acceleration g along x on both components."""
+    sc = couette_channel(nx, ny, 0.0, lam, seed, G, scheme, amp, Gw2, rho_m, rho_d)
+    sc.name = f"poiseuille_{nx}x{ny}"
+    sc.u_wall = (0.0, 0.0)
+    sc.g = (g, 0.0)
+    return sc
 
 
 def square_obstacle_channel(nx: int = 350, ny: int = 150, side: int = 25, center=(122, 75), r: float = 25.0,

@@ -44,3 +44,25 @@ def test_study_records_match_the_oracle():
         assert np.isfinite(r["du_last"]) and np.isfinite(r["dtheta_last"])
     table = st.table(rows)
     assert table.count("\n") == 1 + len(rows)
+
+
+def test_cocurrent_records_match_the_oracle():
+    """Two intervals of 500 steps of the Sec. 3.1 channels (Poiseuille and Couette, one angle):
+    the profile errors and extrema the study reports equal those of the oracle's state."""
+    from paper_2505_22256_gb300 import study_cocurrent as cc
+
+    cs = cc.cases((45,))
+    rows = cc.run(cs, max_steps=1000, storage="f64", interval=500)
+    for sc, r in zip(cs, rows):
+        cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+        f = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0), 1000)
+        rA, rB, ux, _ = oracle.fields(cfg, sc.solid, f)
+        u = ux.mean(axis=1)
+        rho = (rA + rB).mean(axis=1)
+        assert r["steps"] == 1000 and r["converged_at"] is None  # far from steady after 1,000 steps
+        assert r["eps_analytic"] == pytest.approx(cc.rel_l2(u, cc.analytic_profile(sc)), rel=1e-8), sc.name
+        assert r["eps_balance"] == pytest.approx(cc.rel_l2(u, cc.balance_profile(sc, rho)), rel=1e-8), sc.name
+        assert r["u_peak"] == pytest.approx(float(np.max(np.abs(u))), rel=1e-9)
+        assert r["rho_min"] == pytest.approx(float(rho.min()), rel=1e-12)
+        assert not r["unstable"]
+    assert cc.table(rows).count("\n") == 1 + len(rows)

@@ -67,3 +67,45 @@ def test_scheme_study_cases_follow_the_paper_geometry():
     assert xs.mean() == pytest.approx(150, abs=1e-9) and ys.max() == 280
     assert np.all((xs - 150.0) ** 2 + (ys - 130.0) ** 2 > 70.0 ** 2)
     assert c.solid[ys.min() - 1, 150] == 1  # the lowest row of A sits on the cylinder
+
+
+# ---------------------------------------------------------------------------------------------
+# co-current flow (Sec. 3.1)
+# ---------------------------------------------------------------------------------------------
+def test_cocurrent_cases_follow_the_paper_layout():
+    from paper_2505_22256_gb300 import study_cocurrent as cc
+
+    cs = cc.cases((45, 90, 135))
+    assert [c.extra["flow"] for c in cs] == ["poiseuille"] * 3 + ["couette"] * 3
+    for c in cs:
+        assert (c.ny, c.nx) == (100, 50) and c.bc_x == "periodic" and c.bc_y == "wall"
+        assert c.tau == (1.01, 1.01)
+        a = c.rhoA0[:, 0] > 0.5  # A in the central half: rows 25 .. 74
+        assert a.sum() == 50 and a[25] and a[74] and not a[24] and not a[75]
+    assert cs[0].g == (1e-6, 0.0) and cs[0].u_wall == (0.0, 0.0)
+    assert cs[3].g == (0.0, 0.0) and cs[3].u_wall == (-0.005, 0.005)
+
+
+def test_momentum_balance_profile_reduces_to_the_analytic_one_for_uniform_density():
+    """With a uniform density the balance is the single-fluid problem: the Couette line is reproduced
+    exactly and the Poiseuille parabola to the O(1/H^2) of the mirrored ghost row."""
+    from paper_2505_22256_gb300 import study_cocurrent as cc
+
+    p, c = cc.cases((90,))
+    rho = np.full(100, 1.03)
+    uc = cc.balance_profile(c, rho)
+    np.testing.assert_allclose(uc, cc.analytic_profile(c), rtol=0, atol=1e-15)
+    up = cc.balance_profile(p, rho)
+    ua = cc.analytic_profile(p)
+    assert cc.rel_l2(up, ua) < 3 / 100 ** 2
+    # g s (H - s) / (2 nu) at the two central nodes, s = 49.5 and 50.5 (the peak g H^2 / (8 nu) lies between)
+    assert ua.max() == pytest.approx(1e-6 * 49.5 * 50.5 / (2 * 0.17), rel=1e-12)
+    # a density dip at the two interfaces steepens the Couette profile there, and the shear stress
+    # rho nu du/dy stays the same on every face
+    rho2 = rho.copy()
+    rho2[[24, 25, 74, 75]] = 0.7
+    u2 = cc.balance_profile(c, rho2)
+    rf = 0.5 * (rho2[1:] + rho2[:-1])
+    stress = rf * np.diff(u2)
+    np.testing.assert_allclose(stress, stress[0], rtol=1e-10)
+    assert cc.rel_l2(u2, cc.analytic_profile(c)) > 1e-3
