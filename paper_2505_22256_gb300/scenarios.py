@@ -326,7 +326,8 @@ def poiseuille_channel(nx: int = 50, ny: int = 100, g: float = 1e-6, lam: float 
 
 def square_obstacle_channel(nx: int = 350, ny: int = 150, side: int = 25, center=(122, 75), r: float = 25.0,
                             drop=(55, 75), Re: float = 7.5, theta: float = 30.2, seed: int = 8,
-                            G: float = G_DEFAULT, scheme: str = "improved", amp: float = NOISE_AMP) -> Scenario:
+                            G: float = G_DEFAULT, scheme: str = "improved", amp: float = NOISE_AMP,
+                            Gw2: float | None = GW2_DEFAULT) -> Scenario:
     """Droplet driven past a square obstacle in a microchannel (Sec. 3.3, Fig. 12): walls half a
     cell below row 0 and above row ny-1; a square of the given side centred at ``center``; a
     droplet of A (radius r) at ``drop``, B elsewhere; a velocity inlet at x = 0 with the Poiseuille
@@ -339,7 +340,7 @@ def square_obstacle_channel(nx: int = 350, ny: int = 150, side: int = 25, center
     rA, rB = _phase_fields(inside, solid, seed, amp)
     Um = Re * NU_SEC3 / (2.0 * r)
     return Scenario(f"square_obstacle_{nx}x{ny}", solid, rA, rB, bc_x="open", bc_y="wall", scheme=scheme,
-                    tau=(TAU_SEC3, TAU_SEC3), G=G, lam=lambda_for_angle(theta), u_in=Um,
+                    tau=(TAU_SEC3, TAU_SEC3), G=G, Gw2=Gw2, lam=lambda_for_angle(theta), u_in=Um,
                     rho_in=(RHO_D, RHO_M), inlet_profile="poiseuille")
 
 

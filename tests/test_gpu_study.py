@@ -66,3 +66,27 @@ def test_cocurrent_records_match_the_oracle():
         assert r["rho_min"] == pytest.approx(float(rho.min()), rel=1e-12)
         assert not r["unstable"]
     assert cc.table(rows).count("\n") == 1 + len(rows)
+
+
+def test_obstacle_records_match_the_oracle():
+    """The square-obstacle case under both schemes, 150 and 300 steps: region counts, areas and
+    wall-layer medians equal those of the oracle's state."""
+    from paper_2505_22256_gb300 import study_obstacle as so
+
+    cs = so.cases()
+    rows = so.run(cs, (150, 300), storage="f64")
+    assert len(rows) == 4
+    for sc in cs:
+        cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+        f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+        for t0, t in ((0, 150), (150, 300)):
+            f = oracle.run(cfg, sc.solid, f, t - t0)
+            rA, rB, _, _ = oracle.fields(cfg, sc.solid, f)
+            want = so.snapshot(sc, rA, rB)
+            got = [r for r in rows if r["case"] == sc.name and r["step"] == t][0]
+            for k in ("regions", "wall_regions", "obstacle_regions", "largest_area", "total_area"):
+                assert got[k] == want[k], (sc.name, t, k)
+            for k in ("obstacle_layer_rhoA", "wall_layer_rhoA"):
+                assert got[k] == pytest.approx(want[k], rel=1e-9), (sc.name, t, k)
+            assert got["umax"] == pytest.approx(oracle.diagnostics(cfg, sc.solid, f)["umax"], rel=1e-8)
+    assert so.table(rows).count("\n") == 1 + len(rows)

@@ -109,3 +109,34 @@ def test_momentum_balance_profile_reduces_to_the_analytic_one_for_uniform_densit
     stress = rf * np.diff(u2)
     np.testing.assert_allclose(stress, stress[0], rtol=1e-10)
     assert cc.rel_l2(u2, cc.analytic_profile(c)) > 1e-3
+
+
+# ---------------------------------------------------------------------------------------------
+# droplet past a square obstacle (Sec. 3.3)
+# ---------------------------------------------------------------------------------------------
+def test_obstacle_snapshot_counts_regions_by_what_they_touch():
+    from paper_2505_22256_gb300 import study_obstacle as so
+
+    sc = so.cases()[0]
+    assert (sc.ny, sc.nx) == (150, 350) and sc.bc_x == "open" and sc.inlet_profile == "poiseuille"
+    assert sc.solid.sum() == 25 * 25 and sc.solid[75, 122] == 1 and sc.solid[75, 135] == 0
+    rA = np.full(sc.solid.shape, 0.03)
+    rB = np.full(sc.solid.shape, 1.0)
+    rA[sc.solid == 1] = rB[sc.solid == 1] = 0.0
+    for sl in (np.s_[70:80, 40:50],     # a free droplet
+               np.s_[0:3, 200:210],     # one on the lower channel wall
+               np.s_[149, 300],         # a single node on the upper wall
+               np.s_[61:63, 115:130]):  # a film on the obstacle's lower face (the square spans rows 63..87)
+        rA[sl], rB[sl] = 1.0, 0.03
+    # an A-enriched but B-dominated layer over the top and both side faces: 77 of the 89 B-side
+    # first-layer nodes of the square (a ring of 104, 15 of them under the film)
+    rA[63:89, 109] = rA[63:89, 135] = 0.3
+    rA[88, 109:136] = 0.3
+    d = so.snapshot(sc, rA, rB)
+    assert d["regions"] == 4 and d["wall_regions"] == 2 and d["obstacle_regions"] == 1
+    assert d["largest_area"] == 100 and d["total_area"] == 100 + 30 + 1 + 30
+    assert d["wall_layer_rhoA"] == pytest.approx(0.03)
+    ol = st.first_layer(sc.solid)
+    b_side = ol & ~((rA > rB) & (sc.solid == 0))
+    assert d["obstacle_layer_rhoA"] == pytest.approx(float(np.median(rA[b_side])))
+    assert d["obstacle_layer_rhoA"] == pytest.approx(0.3)
