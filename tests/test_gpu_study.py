@@ -90,3 +90,29 @@ def test_obstacle_records_match_the_oracle():
                 assert got[k] == pytest.approx(want[k], rel=1e-9), (sc.name, t, k)
             assert got["umax"] == pytest.approx(oracle.diagnostics(cfg, sc.solid, f)["umax"], rel=1e-8)
     assert so.table(rows).count("\n") == 1 + len(rows)
+
+
+def test_sphere3d_records_match_the_oracle():
+    """The 3-D sphere case scaled to 24 x 24 x 34, two intervals of 100 steps: the angle after each
+    interval and the diagnostics equal those of the oracle's state."""
+    from oracle import d3
+    from paper_2505_22256_gb300 import study_sphere3d as s3
+
+    d3.build()
+    rows = s3.run((0.38, 2.1), steps=200, interval=100, storage="f64", n=24)
+    for lam, r in zip((0.38, 2.1), rows):
+        sc = s3.case(lam, 24)
+        p = sc.params()
+        nz, ny, nx = sc.solid.shape
+        cfg = d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
+                         delta=p["delta"], g=p["g"])
+        f = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+        for k in range(2):
+            f = d3.run3(cfg, sc.solid, f, 100)
+            th, _, _ = d3.contact_angle_sphere(cfg, sc.solid, f, sc.sphere)
+            assert r["history"][k] == pytest.approx(th, abs=1e-6), (lam, k)
+        od = d3.diagnostics3(cfg, sc.solid, f)
+        for key in ("umax", "rhoA_min", "rhoA_max", "rhoB_min", "rhoB_max"):
+            assert r[key] == pytest.approx(od[key], rel=1e-9), (lam, key)
+        assert r["theta"] == r["history"][-1] and not r["unstable"]
+    assert s3.table(rows).count("\n") == 1 + len(rows)
