@@ -389,13 +389,16 @@ def scheme_comparison(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110,
     return out
 
 
-def scheme_study(angles=(30, 50, 70, 90, 110, 130, 150), seed: int = 31, paper_params: bool = False) -> list:
+def scheme_study(angles=(30, 50, 70, 90, 110, 130, 150), seed: int = 31, paper_params: bool = False,
+                 Gw2: float | None = -1.0) -> list:
     """The comparison of Sec. 3.2 (Figs. 6, 10, 11) on the paper's 300x350 geometry: one case per
     target angle (lambda from the correlation) under the improved scheme, then the same geometries
     and initial states under the original scheme (G_w1 = lambda G_w2 everywhere).  paper_params
     takes the densities, viscosity and G_w2 = G_12 of Sec. 3.2 (PAPER_SEC32) in place of this
-    build's defaults."""
-    extra = PAPER_SEC32 if paper_params else {}
+    build's defaults; Gw2 >= 0 (or None: G_w2 = G) overrides G_w2."""
+    extra = dict(PAPER_SEC32) if paper_params else {}
+    if Gw2 is None or Gw2 >= 0:
+        extra["Gw2"] = Gw2
     out = []
     for scheme in ("improved", "original"):
         for k, th in enumerate(angles):
