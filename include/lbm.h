@@ -77,6 +77,18 @@ typedef enum {
     LBM_ADS_IMPROVED = 1  /* Eq. 9 with G_w1(x) from the effective density, Eqs. 10-12 */
 } lbm_ads_mode;
 
+/* Second-layer reconstruction (Sec. 2.4, Table 1): a second-layer stencil node (|e|_inf = 2) that
+ * is not a fluid node takes the "information" of the first-layer node x + sign(e).  The default
+ * reads that as both the pseudopotential and the solid switch of Eq. 9.  The alternative copies the
+ * pseudopotential only; the site keeps its own solid switch in the adhesion sum (1 for a solid site
+ * or one outside a wall direction; a site beyond an open column is that column, as for the first
+ * layer).  On curved walls it gives a wider range of contact angles.  The cohesion sum is the same
+ * under both readings. */
+typedef enum {
+    LBM_SECOND_LAYER_PSI_AND_SOLID = 0, /* default */
+    LBM_SECOND_LAYER_PSI = 1
+} lbm_second_layer;
+
 typedef struct {
     double tau[2];        /* relaxation times tau_A, tau_B (Eq. 2); each > 0.5 */
     double G_AB;          /* inter-component strength G_12 (Eq. 8), stencil weights with
@@ -96,7 +108,8 @@ typedef struct {
                              rho_k the node's density (Sec. 3.1 Couette flow).  0, 0: resting walls.
                              Nonzero needs bc_y = LBM_BC_WALL and bc_x != LBM_BC_OPEN */
     int32_t inlet_profile; /* lbm_inlet_profile (LBM_BC_OPEN) */
-    int32_t pad_;
+    int32_t second_layer;  /* lbm_second_layer: what a second-layer stencil node that is not a fluid
+                              node takes from its first-layer partner x + sign(e) (Sec. 2.4, Table 1) */
 } lbm_params;
 
 /* Storage and arithmetic precision of the populations. */

@@ -147,7 +147,7 @@ class _Cfg(ctypes.Structure):
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("lam", ctypes.c_double),
                 ("Gw2", ctypes.c_double), ("delta", ctypes.c_double), ("g", ctypes.c_double * 2),
                 ("u_in", ctypes.c_double), ("rho_in", ctypes.c_double * 2),
-                ("wE8", ctypes.c_double * 5), ("inlet_profile", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("wE8", ctypes.c_double * 5), ("inlet_profile", ctypes.c_int32), ("second_layer", ctypes.c_int32),
                 ("u_wall", ctypes.c_double * 2)]
 
 
@@ -169,6 +169,9 @@ class Config:
     rho_in: tuple = (1.0, 0.03)
     inlet_profile: str = "uniform"  # uniform | poiseuille (peak u_in; Sec. 3.3)
     u_wall: tuple = (0.0, 0.0)      # x-velocity of the lower / upper wall of a walled y (Sec. 3.1)
+    # what a replaced second-layer node takes from x + sign(e) (Sec. 2.4, Table 1): "psi_and_solid"
+    # or "psi" (the non-fluid site keeps its solid switch in the adhesion sum)
+    second_layer: str = "psi_and_solid"
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
 
     def c(self) -> _Cfg:
@@ -187,6 +190,7 @@ class Config:
         s.rho_in[0], s.rho_in[1] = self.rho_in
         s.inlet_profile = {"uniform": 0, "poiseuille": 1}[self.inlet_profile]
         s.u_wall[0], s.u_wall[1] = self.u_wall
+        s.second_layer = {"psi_and_solid": 0, "psi": 1}[self.second_layer]
         for i, q in enumerate(SHELLS):
             s.wE8[i] = float(w[q])
         return s

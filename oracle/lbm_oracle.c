@@ -49,7 +49,9 @@ typedef struct {
     double rho_in[2]; /* component densities imposed at the inlet */
     double wE8[5];    /* E8 weights w(|e|^2) for |e|^2 = 1, 2, 4, 5, 8 (derived in Python) */
     int32_t inlet_profile; /* 0: uniform u_in; 1: Poiseuille profile of peak u_in (Sec. 3.3) */
-    int32_t pad_;
+    int32_t second_layer;  /* what a replaced second-layer node takes from x + sign(e) (Sec. 2.4,
+                              Table 1): 0 both psi and the solid switch, 1 psi only (the site keeps
+                              its own solid switch in the adhesion sum of Eq. 9) */
     double u_wall[2]; /* x-velocity of the lower / upper wall of a walled y direction (Sec. 3.1 Couette) */
 } oracle_cfg;
 
@@ -179,8 +181,10 @@ static void first_layer(const oracle_cfg* c, const uint8_t* solid, const double*
 
 /* E8 neighbourhood value for stencil node n (0-based) of fluid node (x, y).
  * Second-layer reconstruction (Sec. 2.4, Table 1): a second-layer node (|e|_inf = 2) that is not an
- * in-array fluid node takes the information -- both psi and the solid switch -- of the first-layer
- * node at x + sign(e).  (Table 1's n -> n-8, n-12, n-16 is exactly sign(e) in this numbering.) */
+ * in-array fluid node takes the information of the first-layer node at x + sign(e): both psi and
+ * the solid switch, or (second_layer = 1) psi alone, the site keeping its own solid switch (1 for a
+ * solid site or one outside a wall direction; a site beyond an open column is that column).  (Table 1's
+ * n -> n-8, n-12, n-16 is exactly sign(e) in this numbering.) */
 static void e8_value(const oracle_cfg* c, const uint8_t* solid, const double* rhoA,
                      const double* rhoB, int x, int y, int n, double* pA, double* pB, double* s) {
     int ex = EX[n], ey = EY[n];
@@ -197,6 +201,10 @@ static void e8_value(const oracle_cfg* c, const uint8_t* solid, const double* rh
         return;
     }
     first_layer(c, solid, rhoA, rhoB, x, y, sgn(ex), sgn(ey), pA, pB, s);
+    if (c->second_layer == 1) { /* the site's own switch (clamped along an open axis, as above) */
+        double qA, qB;
+        first_layer(c, solid, rhoA, rhoB, x, y, ex, ey, &qA, &qB, s);
+    }
 }
 
 /* Is stencil node n of (x, y) taken from somewhere other than x + e?  (second layer only) */

@@ -81,6 +81,8 @@ lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_para
     if (!finite(p->lambda) || p->lambda <= 0.0) return fail(LBM_EINVAL, "case %d: lambda must be > 0", idx);
     if (!finite(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return fail(LBM_EINVAL, "case %d: delta must lie in (0, 1]", idx);
     if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return fail(LBM_EINVAL, "case %d: bad mode", idx);
+    if (p->second_layer != LBM_SECOND_LAYER_PSI_AND_SOLID && p->second_layer != LBM_SECOND_LAYER_PSI)
+        return fail(LBM_EINVAL, "case %d: bad second_layer %d", idx, p->second_layer);
     if (p->inlet_profile != LBM_INLET_UNIFORM && p->inlet_profile != LBM_INLET_POISEUILLE)
         return fail(LBM_EINVAL, "case %d: bad inlet profile", idx);
     if (p->inlet_profile == LBM_INLET_POISEUILLE && (g->bc_x != LBM_BC_OPEN || g->bc_y != LBM_BC_WALL))

@@ -7,7 +7,8 @@
 //   subst  bit n-1 set when second-layer stencil node n (Table 1 numbering) is not a fluid node and
 //          therefore takes the information of its first-layer partner x + sign(e_n)
 //   seff   bit n-1 set when stencil node n counts as solid in the adhesion sum (Eq. 9): a solid or
-//          outside first-layer site, or a replaced second-layer node whose partner is one
+//          outside first-layer site, or a replaced second-layer node whose partner is one (when it
+//          copies the pseudopotential only: whose own site is one, clamped along an open axis)
 //   a      sum_n w(|e_n|^2) seff_n e_n  (FP64)
 // Along an open axis a first-layer site beyond the boundary column is the boundary column itself.
 #include "lbm_internal.h"
@@ -126,7 +127,7 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
                             const uint16_t* __restrict__ flags_all, uint32_t* __restrict__ wsub_all,
                             const int32_t* __restrict__ row_off, int32_t* __restrict__ wl_node,
                             uint32_t* __restrict__ wl_subst, uint32_t* __restrict__ wl_seff,
-                            double* __restrict__ wl_a, long long nwall_total) {
+                            double* __restrict__ wl_a, long long nwall_total, int psi_only) {
     const DevCase C = cases[c];
     const Geo g{C.nx, C.ny, C.bc_x, C.bc_y, solid_all + C.d_off};
     const int Y = blockIdx.x;
@@ -157,7 +158,9 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
                     s = false;
                 } else {
                     sm |= 1u << n;
-                    s = first_layer_solid(g, X, Y, (ex > 0) - (ex < 0), (ey > 0) - (ey < 0));
+                    // psi only: the site keeps its own solid switch (clamped along an open axis)
+                    s = psi_only ? first_layer_solid(g, X, Y, ex, ey)
+                                 : first_layer_solid(g, X, Y, (ex > 0) - (ex < 0), (ey > 0) - (ey < 0));
                 }
                 if (s) em |= 1u << n;
             }
@@ -236,7 +239,8 @@ cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cud
 
 cudaError_t launch_wall_fill(Ctx& c, int ci, const int32_t* row_offsets) {
     k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.wsub, row_offsets,
-                                                        c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall);
+                                                        c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall,
+                                                        c.cases[ci].params.second_layer == LBM_SECOND_LAYER_PSI);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,15 @@ def small_porous():
     return S.porous_disks(nx=192, ny=96, rmin=5, rmax=11, keep_out=(12, 12), seed=9, porosity=0.7)
 
 
+def psi_only(make):
+    """The same case with the second-layer reading that copies psi only (Sec. 2.4, Table 1)."""
+    def build():
+        sc = make()
+        sc.second_layer = "psi"
+        return sc
+    return build
+
+
 SCENARIOS = {
     "cylinder96": lambda: S.cylinder_droplet(96, lam=0.6),
     "ragged131x77": lambda: S.cylinder_droplet(77, nx=131, R=12, r=15, lam=1.4),
@@ -62,6 +71,11 @@ SCENARIOS = {
     "square_obstacle_small": lambda: S.square_obstacle_channel(nx=140, ny=60, side=10, center=(49, 30), r=10.0,
                                                                drop=(22, 30)),
     "gw2_equals_G": lambda: S.Scenario(**{**S.cylinder_droplet(64, lam=0.7).__dict__, "Gw2": None}),
+    "cylinder96_psi": psi_only(lambda: S.cylinder_droplet(96, lam=1.8)),
+    "porous_open_psi": psi_only(small_porous),
+    "pillar8_psi": psi_only(pillar_case),
+    "square_obstacle_small_psi": psi_only(lambda: S.square_obstacle_channel(nx=140, ny=60, side=10, center=(49, 30),
+                                                                            r=10.0, drop=(22, 30))),
 }
 
 

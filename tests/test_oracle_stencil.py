@@ -90,7 +90,8 @@ def _weights_float():
 def _bf_forces(cfg, solid, rhoA, rhoB):
     """Independent loop over the 5x5 box of each fluid node: cohesion (Eq. 8, other component,
     E8 weights), adhesion (Eq. 9 with the local parameter of Eq. 12 / constant G_w1), body force;
-    second-layer sites that are not in-array fluid nodes take the value of x + sign(e)."""
+    second-layer sites that are not in-array fluid nodes take the value of x + sign(e): its density
+    and its solid switch, or (second_layer "psi") its density while the site keeps its own switch."""
     W = _weights_float()
     ny, nx = solid.shape
     Gw2 = cfg.G if cfg.Gw2 is None else cfg.Gw2
@@ -135,6 +136,8 @@ def _bf_forces(cfg, solid, rhoA, rhoB):
                             vA, vB, s = rhoA[p[1], p[0]], rhoB[p[1], p[0]], 0.0
                         else:
                             vA, vB, s = first(x, y, int(np.sign(dx)), int(np.sign(dy)))
+                            if cfg.second_layer == "psi":  # the site's own switch
+                                s = first(x, y, dx, dy)[2]
                     else:
                         vA, vB, s = first(x, y, dx, dy)
                     e = np.array([dx, dy], float)
@@ -173,9 +176,10 @@ def _pillar_case(nx=8, ny=8, block=None):
     return solid
 
 
+@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
 @pytest.mark.parametrize("scheme,lam", [("improved", 0.4), ("improved", 1.7), ("original", 0.6)])
 @pytest.mark.parametrize("geom", ["pillar", "block_walls", "open_x"])
-def test_forces_match_brute_force(scheme, lam, geom):
+def test_forces_match_brute_force(scheme, lam, geom, second_layer):
     rng = np.random.default_rng(7)
     if geom == "pillar":
         solid = _pillar_case()
@@ -191,6 +195,7 @@ def test_forces_match_brute_force(scheme, lam, geom):
         solid[0, :] = 1
         cfg = oracle.Config(nx=10, ny=7, bc_x="open", bc_y="wall", scheme=scheme, lam=lam, G=1.2,
                             nthreads=1)
+    cfg.second_layer = second_layer
     ny, nx = solid.shape
     rA = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
     rB = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
@@ -241,6 +246,25 @@ def test_wall_list_single_pillar_by_hand():
     # (2,2): pillar is first-layer diagonal node 5 (1,1)
     sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 8, 2, 2)
     assert (sm, em) == (0, _bits(5)) and a_x == pytest.approx(W[2]) and a_y == pytest.approx(W[2])
+
+
+def test_wall_list_single_pillar_psi_only_by_hand():
+    """The same pillar when a replaced second-layer node copies psi only: the solid site itself
+    stays in the adhesion sum, so seff gains the replaced node and a(x) its w e term."""
+    solid = _pillar_case()
+    cfg = oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic", second_layer="psi")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    W = _weights_float()
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 4) == (0, _bits(4), 0.0, -W[1])  # first layer: unchanged
+    # (3,5): node 12 = (0,-2) replaced, counted as solid: a = w(4) (0,-2)
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 5) == (_bits(12), _bits(12), 0.0, -2 * W[4])
+    # (5,5): node 15 = (-2,-2): a = w(8) (-2,-2)
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 5) == (_bits(15), _bits(15), -2 * W[8], -2 * W[8])
+    # (5,4): knight node 19 = (-2,-1): a = w(5) (-2,-1)
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 4) == (_bits(19), _bits(19), -2 * W[5], -W[5])
+    # the substitution masks (which sites take psi from x + sign(e)) do not depend on the reading
+    _, subst0, _, _, _ = oracle.wall_list(oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic"), solid)
+    np.testing.assert_array_equal(subst, subst0)
 
 
 def test_wall_list_block_by_hand():
