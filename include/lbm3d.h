@@ -38,6 +38,9 @@ typedef struct {
     double tau[2];   /* relaxation times (Eq. 2), each > 0.5 */
     double G_AB;     /* inter-component strength (Eq. 8) */
     int32_t mode;    /* lbm_ads_mode: LBM_ADS_ORIGINAL or LBM_ADS_IMPROVED */
+    int32_t second_layer; /* lbm_second_layer (lbm.h): what a solid second-layer stencil site takes
+                             from x + sign(e) (Sec. 2.4, Table 1); the box is periodic, so every
+                             non-fluid site is solid */
     double lambda;   /* G_w1 / G_w2, > 0 */
     double G_w2;     /* adhesion parameter of component B */
     double delta;    /* half-width of Eqs. 11-12, in (0, 1] */

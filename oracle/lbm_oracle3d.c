@@ -34,7 +34,8 @@ typedef struct {
     int32_t nx, ny, nz;
     int32_t scheme;   /* original (Eq. 9, constant G_w1) or improved (Eqs. 10-12) */
     int32_t nthreads;
-    int32_t pad_;
+    int32_t second_layer; /* 0: a replaced second-layer site takes psi and the solid switch of
+                             x + sign(e); 1: psi only, the (solid) site keeping s = 1 */
     double tau[2];    /* Eq. 2 */
     double G;         /* Eq. 8 */
     double lambda;    /* G_w1 / G_w2 */
@@ -139,6 +140,7 @@ static void node_forces3(const oracle3_cfg* c, const uint8_t* solid, const doubl
                 int sx = ex, sy = ey, sz = ez;
                 int second = abs(ex) == 2 || abs(ey) == 2 || abs(ez) == 2;
                 size_t s = id3(c, x + sx, y + sy, z + sz);
+                int own_solid = solid[s] != 0;
                 if (second && solid[s]) {  /* second-layer site not fluid: first-layer partner */
                     sx = sgn(ex);
                     sy = sgn(ey);
@@ -146,7 +148,7 @@ static void node_forces3(const oracle3_cfg* c, const uint8_t* solid, const doubl
                     s = id3(c, x + sx, y + sy, z + sz);
                 }
                 double pA = solid[s] ? 0.0 : rA[s], pB = solid[s] ? 0.0 : rB[s];
-                double sw = solid[s] ? 1.0 : 0.0;
+                double sw = (solid[s] || (c->second_layer == 1 && own_solid)) ? 1.0 : 0.0;
                 gA[0] += w * pA * ex; gA[1] += w * pA * ey; gA[2] += w * pA * ez;
                 gB[0] += w * pB * ex; gB[1] += w * pB * ey; gB[2] += w * pB * ez;
                 a[0] += w * sw * ex; a[1] += w * sw * ey; a[2] += w * sw * ez;

@@ -73,6 +73,7 @@ template <class R>
 struct P3 {
     R omega[2], cF[2], G, Gw2, lam, delta, s1, s2, s3, t2, t3, g[3];
     int mode;
+    int psi;  // second-layer reading: a replaced (solid) site copies psi only and keeps s = 1
 };
 
 __global__ void k3_flags(Geo3 g, const uint8_t* __restrict__ solid, uint32_t* __restrict__ flags) {
@@ -243,12 +244,13 @@ __global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t
                             const int sg = side == 0 ? 1 : -1;
                             const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
                             int n = nb.at(ex, ey, ez);
-                            if (second && solid[n]) n = nb.at((ex > 0) - (ex < 0), (ey > 0) - (ey < 0), (ez > 0) - (ez < 0));
+                            const bool own = solid[n] != 0;
+                            if (second && own) n = nb.at((ex > 0) - (ex < 0), (ey > 0) - (ey < 0), (ez > 0) - (ez < 0));
                             const bool sol = solid[n] != 0;
                             const typename Rho2<R>::T v = rho[n];
                             va[side] = sol ? (R)0 : v.x;
                             vb[side] = sol ? (R)0 : v.y;
-                            vs[side] = sol ? (R)1 : (R)0;
+                            vs[side] = (sol || (P.psi && own)) ? (R)1 : (R)0;
                         }
                         const R w = (R)wq, a = va[0] - va[1], b = vb[0] - vb[1], sw = vs[0] - vs[1];
                         gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
@@ -351,7 +353,7 @@ constexpr size_t k3_march_smem() {
 // solid second-layer site (Sec. 2.4), density 0 and solid switch 1 at a solid site; solid sites
 // hold -1 in the ring.  b0..b4: ring rows of the planes z-2..z+2 at the node.  (Inlined: an
 // out-of-line call measured 7 % slower on the full case and twice as slow on a small one.)
-template <class R>
+template <class R, bool kPsi>
 __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, const V2<R>* b2, const V2<R>* b3,
                                            const V2<R>* b4, V2<R>& gx, V2<R>& gy, V2<R>& gz, R (&ad)[3]) {
     using V = V2<R>;
@@ -374,13 +376,14 @@ __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, 
                     const int sg = side == 0 ? 1 : -1;
                     const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
                     V w = bs[2 + ez][ey * k3HX + ex];
-                    if (second && w.x < (R)0) {
+                    const bool own = w.x < (R)0;
+                    if (second && own) {
                         const int fx = (ex > 0) - (ex < 0), fy = (ey > 0) - (ey < 0), fz = (ez > 0) - (ez < 0);
                         w = bs[2 + fz][fy * k3HX + fx];
                     }
                     const bool sol = w.x < (R)0;
                     v[side] = sol ? vbc<R>(0) : w;
-                    vs[side] = sol ? (R)1 : (R)0;
+                    vs[side] = (sol || (kPsi && own)) ? (R)1 : (R)0;
                 }
                 const V a = vsub(v[0], v[1]);
                 const R w = (R)wq, sw = vs[0] - vs[1];
@@ -396,7 +399,7 @@ __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, 
 #ifndef LBM3_MIN_BLOCKS
 #define LBM3_MIN_BLOCKS 3
 #endif
-template <class R>
+template <class R, bool kPsi>
 __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
     k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
              const V2<R>* __restrict__ rho, V2<R>* __restrict__ fout) {
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 gy = vadd(hy[0], hy[1]);
                 gz = vadd(hz[0], hz[1]);
             } else {
-                wall_stencil3<R>(bs[0], bs[1], bs[2], bs[3], bs[4], gx, gy, gz, ad);
+                wall_stencil3<R, kPsi>(bs[0], bs[1], bs[2], bs[3], bs[4], gx, gy, gz, ad);
             }
             const R rA = r2.x, rB = r2.y;
             R GA = (R)0;
@@ -888,6 +891,7 @@ P3<R> make_p3(const lbm3d_params& p) {
     P.t3 = (R)((l - 1.0) / (dl * dl * (1.0 + l)));
     for (int d = 0; d < 3; ++d) P.g[d] = (R)p.g[d];
     P.mode = p.mode;
+    P.psi = p.second_layer == LBM_SECOND_LAYER_PSI;
     return P;
 }
 
@@ -919,8 +923,11 @@ cudaError_t step_once(lbm3d_ctx* c) {
     const int zc = zchunk3(c->g);
     const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
                   (unsigned)((c->g.nz + zc - 1) / zc));
-    k3_march<R><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho,
-                                                               reinterpret_cast<V2<R>*>(c->f[1 - c->cur]));
+    V2<R>* fo = reinterpret_cast<V2<R>*>(c->f[1 - c->cur]);
+    if (P.psi)
+        k3_march<R, true><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
+    else
+        k3_march<R, false><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
     c->cur ^= 1;
     return cudaGetLastError();
 }
@@ -999,6 +1006,8 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     if (!fin(p->lambda) || p->lambda <= 0.0) return report_error(LBM_EINVAL, "lambda must be > 0");
     if (!fin(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return report_error(LBM_EINVAL, "delta must lie in (0, 1]");
     if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return report_error(LBM_EINVAL, "bad mode");
+    if (p->second_layer != LBM_SECOND_LAYER_PSI_AND_SOLID && p->second_layer != LBM_SECOND_LAYER_PSI)
+        return report_error(LBM_EINVAL, "bad second_layer");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     long long nf = 0;
     for (long long s = 0; s < N; ++s) {
@@ -1091,10 +1100,10 @@ extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
     if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
     // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
     TRY3(c->storage == LBM_STORE_F64
-             ? cudaFuncSetAttribute(k3_march<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k3_march_smem<double>())
-             : cudaFuncSetAttribute(k3_march<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k3_march_smem<float>()),
+             ? cudaFuncSetAttribute(c->pd.psi ? k3_march<double, true> : k3_march<double, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_march_smem<double>())
+             : cudaFuncSetAttribute(c->pf.psi ? k3_march<float, true> : k3_march<float, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_march_smem<float>()),
          "step kernel attributes");
     for (int64_t t = 0; t < n; ++t) {
         const cudaError_t e = c->storage == LBM_STORE_F64 ? step_once<double>(c) : step_once<float>(c);

@@ -19,7 +19,8 @@ class lbm3d_grid(ctypes.Structure):
 
 
 class lbm3d_params(ctypes.Structure):
-    _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("lambda_", c_double),
+    _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("second_layer", c_int32),
+                ("lambda_", c_double),
                 ("G_w2", c_double), ("delta", c_double), ("g", c_double * 3)]
 
 
@@ -60,7 +61,7 @@ def _lib():
 
 
 def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8,
-                 g=(0.0, 0.0, 0.0)) -> lbm3d_params:
+                 g=(0.0, 0.0, 0.0), second_layer="psi_and_solid") -> lbm3d_params:
     p = lbm3d_params()
     p.tau[0], p.tau[1] = tau
     p.G_AB = G
@@ -70,6 +71,7 @@ def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, 
     p.delta = delta
     for i in range(3):
         p.g[i] = g[i]
+    p.second_layer = lbm.SECOND_LAYER[second_layer]
     return p
 
 

@@ -432,6 +432,7 @@ class Scenario3:
     g: tuple = (0.0, 0.0, 0.0)
     scheme: str = "improved"
     sphere: dict | None = None   # {"c": (x, y, z), "R": effective radius} for the contact angle
+    second_layer: str = "psi_and_solid"  # or "psi" (Sec. 2.4, Table 1)
 
     @property
     def shape(self):
@@ -439,7 +440,7 @@ class Scenario3:
 
     def params(self) -> dict:
         return dict(tau=tuple(self.tau), G=self.G, scheme=self.scheme, lam=self.lam, Gw2=self.Gw2,
-                    delta=self.delta, g=tuple(self.g))
+                    delta=self.delta, g=tuple(self.g), second_layer=self.second_layer)
 
 
 def sphere_droplet_3d(nx: int = 200, ny: int = 200, nz: int = 280, R: float = 50.0, sphere=(100.0, 100.0, 100.0),

@@ -19,18 +19,20 @@ from . import lbm3d, scenarios as S
 PAPER_THETA = {0.38: 45.0, 1.0: 90.0, 2.1: 146.0}
 
 
-def case(lam: float, n: int = 200):
-    return S.sphere_droplet_3d(lam=lam) if n == 200 else S.sphere_droplet_3d_small(n, lam=lam)
+def case(lam: float, n: int = 200, second_layer: str = "psi_and_solid"):
+    sc = S.sphere_droplet_3d(lam=lam) if n == 200 else S.sphere_droplet_3d_small(n, lam=lam)
+    sc.second_layer = second_layer
+    return sc
 
 
 def run(lams=(0.38, 1.0, 2.1), steps: int = 30000, interval: int = 5000, storage: str = "f32",
-        n: int = 200) -> list[dict]:
+        n: int = 200, second_layer: str = "psi_and_solid") -> list[dict]:
     """One record per lambda."""
     if interval < 1 or steps < interval:
         raise ValueError("need steps >= interval >= 1")
     out = []
     for lam in lams:
-        sc = case(lam, n)
+        sc = case(lam, n, second_layer)
         lat = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), storage)
         try:
             angles = []
@@ -70,9 +72,11 @@ def main(argv=None) -> int:
     ap.add_argument("--n", type=int, default=200, help="200: the paper's box; else the geometry scaled to n")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
     ap.add_argument("--lambdas", default="0.38,1,2.1")
+    ap.add_argument("--second-layer", default="psi_and_solid", choices=["psi_and_solid", "psi"])
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
-    rows = run(tuple(float(v) for v in args.lambdas.split(",")), args.steps, args.interval, args.storage, args.n)
+    rows = run(tuple(float(v) for v in args.lambdas.split(",")), args.steps, args.interval, args.storage, args.n,
+               args.second_layer)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:

@@ -24,7 +24,7 @@ def ocfg(sc):
     nz, ny, nx = sc.shape
     p = sc.params()
     return d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
-                      delta=p["delta"], g=p["g"])
+                      delta=p["delta"], g=p["g"], second_layer=p["second_layer"])
 
 
 def orun(sc, n):
@@ -42,10 +42,17 @@ def rel_rho(g, o, solid, floor=0.0):
     return max(float(np.max(np.abs(g[k] - o[k])[fl] / np.maximum(o[k][fl], floor))) for k in (0, 1))
 
 
+def _psi(sc):
+    """The second-layer reading that copies psi only (Sec. 2.4, Table 1)."""
+    sc.second_layer = "psi"
+    return sc
+
+
 CASES = {
     "sphere24": lambda: S.sphere_droplet_3d_small(24, lam=0.6),
     "sphere24_hydrophobic": lambda: S.sphere_droplet_3d_small(24, lam=2.1, seed=4),
     "sphere24_original": lambda: S.sphere_droplet_3d_small(24, lam=0.5, scheme="original"),
+    "sphere24_psi": lambda: _psi(S.sphere_droplet_3d_small(24, lam=1.7, seed=6)),
     "odd_box": lambda: S.sphere_droplet_3d(nx=21, ny=17, nz=26, R=5.0, sphere=(10.0, 8.0, 9.0), r=5.5,
                                            drop=(10.0, 8.0, 17.0), lam=1.3),
     # the step kernel's edges: a partial 32-column tile (nx = 40), a last tile three rows high

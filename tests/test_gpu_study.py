@@ -105,7 +105,7 @@ def test_sphere3d_records_match_the_oracle():
         p = sc.params()
         nz, ny, nx = sc.solid.shape
         cfg = d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
-                         delta=p["delta"], g=p["g"])
+                         delta=p["delta"], g=p["g"], second_layer=p["second_layer"])
         f = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
         for k in range(2):
             f = d3.run3(cfg, sc.solid, f, 100)

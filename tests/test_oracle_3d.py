@@ -63,9 +63,12 @@ def _brute_forces(cfg, solid, rA, rB, x, y, z):
         if q not in w:
             continue
         s = site(x + e[0], y + e[1], z + e[2])
-        if max(abs(t) for t in e) == 2 and solid[s]:
+        replaced = max(abs(t) for t in e) == 2 and solid[s]
+        if replaced:
             s = site(x + int(np.sign(e[0])), y + int(np.sign(e[1])), z + int(np.sign(e[2])))
         pa, pb, sw = (0.0, 0.0, 1.0) if solid[s] else (rA[s], rB[s], 0.0)
+        if replaced and cfg.second_layer == "psi":  # psi copied, the solid site keeps its switch
+            sw = 1.0
         gA += w[q] * pa * np.array(e)
         gB += w[q] * pb * np.array(e)
         a += w[q] * sw * np.array(e)
@@ -85,7 +88,8 @@ def _brute_forces(cfg, solid, rA, rB, x, y, z):
     return FA, FB
 
 
-def test_forces_match_brute_force_next_to_a_solid_block():
+@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
+def test_forces_match_brute_force_next_to_a_solid_block(second_layer):
     n = 9
     solid = np.zeros((n, n, n), np.uint8)
     solid[3:6, 2:5, 4:7] = 1
@@ -93,7 +97,7 @@ def test_forces_match_brute_force_next_to_a_solid_block():
     rng = np.random.default_rng(5)
     rA = np.where(solid, 0.0, 0.2 + 0.8 * rng.random((n, n, n)))
     rB = np.where(solid, 0.0, 0.2 + 0.8 * rng.random((n, n, n)))
-    cfg = d3.Config3(n, n, n, G=1.1, lam=0.6, Gw2=0.35)
+    cfg = d3.Config3(n, n, n, G=1.1, lam=0.6, Gw2=0.35, second_layer=second_layer)
     f = d3.init3(cfg, solid, rA, rB)
     FA, FB, _ = d3.forces3(cfg, solid, f)
     for (z, y, x) in [(2, 3, 5), (6, 3, 5), (4, 1, 5), (4, 5, 3), (0, 0, 0), (7, 6, 2), (4, 8, 8)]:
