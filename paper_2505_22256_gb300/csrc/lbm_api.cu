@@ -805,7 +805,13 @@ lbm_status lbm_diagnostics_all(lbm_ctx* ctx, lbm_diag* out) {
     if (!out) return fail(LBM_EINVAL, "NULL output");
     Ctx& c = ctx->c;
     const int n = (int)c.hcases.size();
-    CUDA_TRY(launch_diag_all(c));
+    if (c.ca_batch) {  // the batched contact angle has its density buffer: fill it in the same pass
+        double* rho = reinterpret_cast<double*>(c.ca_batch);
+        CUDA_TRY(launch_diag_all(c, rho, rho + c.dense_elems));
+        c.ca_rho_version = c.version;
+    } else {
+        CUDA_TRY(launch_diag_all(c));
+    }
     std::vector<double> v((size_t)n * kDiagN);
     CUDA_TRY(cudaMemcpyAsync(v.data(), c.diag_out, v.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));

@@ -91,8 +91,19 @@ __device__ void ca_pass_block(const CaGeo& g, int lb, int nb, int pass, const do
     for (int q = 0; q < kCaVals; ++q) acc[q] = 0.0;
     const long long N = (long long)g.nx * g.ny;
     const double xm = st[1], ym = st[2], cxv = st[3], cyv = st[4], r = st[5];
-    for (long long s = lb * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)nb * blockDim.x) {
-        const int X = (int)(s % g.nx), Y = (int)(s / g.nx);
+    // node s = Y nx + X advanced by a fixed stride: one division per thread, not per node
+    const long long s0 = lb * (long long)blockDim.x + threadIdx.x, stride = (long long)nb * blockDim.x;
+    const int dX = (int)(stride % g.nx), dY = (int)(stride / g.nx);
+    int X = (int)(s0 % g.nx), Y = (int)(s0 / g.nx);
+    for (long long s = s0; s < N; s += stride) {
+        if (s != s0) {
+            X += dX;
+            Y += dY;
+            if (X >= g.nx) {
+                X -= g.nx;
+                ++Y;
+            }
+        }
         double px[2], py[2];
         const int n = node_points(g, X, Y, px, py);
         for (int k = 0; k < n; ++k) {
@@ -322,8 +333,11 @@ cudaError_t enqueue_contact_angle_all(Ctx& c, const lbm_surface* surf) {
     e = cudaMemcpyAsync(c.ca_batch + o_surf, surf, n * sizeof(lbm_surface), cudaMemcpyHostToDevice, c.stream);
     if (e != cudaSuccess) return e;
     double* rho = reinterpret_cast<double*>(c.ca_batch + o_rho);
-    e = launch_densities_all(c, rho, rho + c.dense_elems);
-    if (e != cudaSuccess) return e;
+    if (c.ca_rho_version != c.version) {  // not already written at this state by the diagnostics
+        e = launch_densities_all(c, rho, rho + c.dense_elems);
+        if (e != cudaSuccess) return e;
+        c.ca_rho_version = c.version;
+    }
     e = cudaMemsetAsync(c.ca_all, 0, (size_t)16 * n * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
     CaBatch b{reinterpret_cast<const CaGeo*>(c.ca_batch + o_geo), reinterpret_cast<const int*>(c.ca_batch + o_bc),

@@ -101,6 +101,7 @@ struct Ctx {
     uint64_t version = 1;            // bumped by every change of the state
     int fields_case = -1;            // case whose fields the scratch holds ...
     uint64_t fields_version = 0;     // ... computed at this state version
+    uint64_t ca_rho_version = 0;     // the batched contact angle's densities hold this state version
 };
 
 // lbm_step.cu
@@ -109,7 +110,9 @@ cudaError_t launch_fields(Ctx& c, int case_index, double* rhoA, double* rhoB, do
                           bool diag);
 cudaError_t launch_diag_reduce(Ctx& c, int case_index);
 // partial sums of every case in one launch over the per-case lists, then one reduction per case
-cudaError_t launch_diag_all(Ctx& c);
+// per-case diagnostics of all cases; with rhoA_all / rhoB_all also the densities of all cases
+// (case offsets as in the batched fields), in the same pass
+cudaError_t launch_diag_all(Ctx& c, double* rhoA_all = nullptr, double* rhoB_all = nullptr);
 // densities of every case into [dense_elems] arrays indexed d_off + y nx + x (zero at solid nodes)
 // every case's fields at once (fields_global indexing: case d_off + y nx + x); ux_all / uy_all may be
 // NULL for densities only

@@ -1088,11 +1088,12 @@ cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
     return launch_fields_all(c, rhoA_all, rhoB_all, nullptr, nullptr);
 }
 
-cudaError_t launch_diag_all(Ctx& c) {
-    double* o4[4] = {nullptr, nullptr, nullptr, nullptr};
+cudaError_t launch_diag_all(Ctx& c, double* rhoA_all, double* rhoB_all) {
+    double* o4[4] = {rhoA_all, rhoB_all, nullptr, nullptr};  // densities too when given (all cases)
     const int n = c.nitems_all - c.nitems;
     const int grid = n < c.grid_blocks ? n : c.grid_blocks;
     StepArgs a = make_args(c, c.nitems, c.nitems_all, o4, c.diag_part);
+    a.fields_global = 1;
     cudaError_t e = dispatch(c, a, c.stream, true, grid);
     if (e != cudaSuccess) return e;
     k_diag_reduce<<<(unsigned)c.hcases.size(), 32, 0, c.stream>>>(c.dcases, -1, c.diag_part, c.diag_out);

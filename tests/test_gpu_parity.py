@@ -427,6 +427,37 @@ def test_batched_diagnostics_and_contact_angles_equal_per_case_calls():
     ens.close()
 
 
+def test_batched_contact_angles_follow_the_state_with_and_without_diagnostics():
+    """Once the batched contact angle has its density buffer, lbm_diagnostics_all fills it in the
+    same pass and the contact angle reuses it at that state.  Each call must still measure the
+    current state: after a diagnostics call, after steps without one, and after the state is set
+    from the host.  Every batched angle equals the per-case call at that state, bit for bit."""
+    cases = [SCENARIOS["cylinder96"](), S.cylinder_droplet(77, nx=131, R=12, r=15, lam=1.4)]
+    ens = lbm.Lattice(cases, "f32")
+    surfaces = [sc.surface for sc in cases]
+
+    def check():
+        th, rms, npts = ens.contact_angle_all(surfaces)
+        for i in range(len(cases)):
+            assert (th[i], rms[i], npts[i]) == ens.contact_angle(i), i
+        return th
+
+    t0 = check()                      # first call: allocates the buffer, computes the densities
+    ens.step(200)
+    ens.diagnostics_all()             # fills the buffer at this state
+    t1 = check()
+    ens.step(200)                     # no diagnostics: the buffer is stale and must be refreshed
+    t2 = check()
+    ens.diagnostics_all()
+    fresh = lbm.Lattice(cases[0], "f32")
+    f0 = fresh.populations()
+    fresh.close()
+    ens.set_populations(f0, 0)        # case 0 back to its initial state
+    t3 = check()
+    assert t1[0] != t0[0] and t2[0] != t1[0] and t3[0] == t0[0]
+    ens.close()
+
+
 def test_batched_diagnostics_match_oracle_f64():
     cases = [SCENARIOS["cylinder96"](), SCENARIOS["free64"]()]
     ens = lbm.Lattice(cases, "f64")
