@@ -240,3 +240,28 @@ def test_couette_between_sliding_walls_is_exactly_linear(u_wall):
     exact = u_wall[0] + (u_wall[1] - u_wall[0]) * s / ny
     np.testing.assert_allclose(ux, np.repeat(exact[:, None], nx, axis=1), rtol=0, atol=1e-12)
     assert np.max(np.abs(uy)) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["improved", "original"])
+@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
+def test_exchanging_the_components_at_lambda_one_exchanges_the_state(scheme, second_layer):
+    """At lambda = 1 (and equal tau) nothing distinguishes A from B: cohesion uses the other
+    component, both adhesion parameters are G_w2 (Eq. 12 gives h = 1), and the collision is the
+    same.  A droplet of B started from the swapped densities must therefore reach the swapped
+    state, up to the order of the sums over components (1e-13).  A wrong component index, or a
+    term applied to one component only, breaks this."""
+    sc = S.flat_droplet(40, 28, r=8, lam=1.0, scheme=scheme)
+    sc.solid[10:13, 6:9] = 1  # a small block as well, for curved-wall stencil sites
+    sc.rhoA0[sc.solid == 1] = 0.0
+    sc.rhoB0[sc.solid == 1] = 0.0
+    sc.second_layer = second_layer
+    cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+    fA = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0), 150)
+    fB = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoB0, sc.rhoA0), 150)
+    a = oracle.fields(cfg, sc.solid, fA)
+    b = oracle.fields(cfg, sc.solid, fB)
+    np.testing.assert_allclose(b[0], a[1], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(b[1], a[0], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(b[2], a[2], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(b[3], a[3], rtol=0, atol=1e-13)
+    assert np.max(np.abs(a[0] - a[1])) > 0.5  # a genuine two-phase state
