@@ -30,9 +30,10 @@ INTERVAL = 10000   # steps between the profiles the convergence test compares
 TOL = 1e-5         # largest change of u_x over INTERVAL steps at convergence
 
 
-def cases(angles=(45, 90, 135), paper_params: bool = False, gw2: float | None = -1.0) -> list:
+def cases(angles=(45, 90, 135), paper_params: bool = False, gw2: float | None = -1.0,
+          second_layer: str = "psi_and_solid") -> list:
     """Poiseuille then Couette channels, one per target angle.  gw2 >= 0 (or None: G_w2 = G)
-    overrides G_w2."""
+    overrides G_w2; second_layer picks the Table 1 reading."""
     extra = {k: S.PAPER_SEC32[k] for k in ("rho_m", "rho_d", "G", "Gw2")} if paper_params else {}
     if gw2 is None or gw2 >= 0:
         extra["Gw2"] = gw2
@@ -41,6 +42,7 @@ def cases(angles=(45, 90, 135), paper_params: bool = False, gw2: float | None = 
         for k, th in enumerate(angles):
             sc = make(lam=S.lambda_for_angle(th), seed=40 + 10 * k + (flow == "couette"), **extra)
             sc.name = f"{flow}_theta{th}_{sc.name}"
+            sc.second_layer = second_layer
             sc.extra.update(flow=flow, target_theta=float(th))
             out.append(sc)
     return out
@@ -146,10 +148,11 @@ def main(argv=None) -> int:
     ap.add_argument("--paper-params", action="store_true",
                     help="densities 1.02 / 0.05 and G_w2 = G_12 as stated in Sec. 3.1")
     ap.add_argument("--gw2", type=float, default=-1.0, help="override G_w2 (>= 0)")
+    ap.add_argument("--second-layer", default="psi_and_solid", choices=["psi_and_solid", "psi"])
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     angles = tuple(int(a) for a in args.angles.split(","))
-    rows = run(cases(angles, args.paper_params, args.gw2), args.max_steps, args.storage)
+    rows = run(cases(angles, args.paper_params, args.gw2, args.second_layer), args.max_steps, args.storage)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:
