@@ -121,9 +121,9 @@ def lpt_shares(sizes, world: int) -> list:
 
 def shard(cases, rank: int, world: int):
     """(this rank's cases, nodes of the whole job) under --split."""
-    sizes = [c.nx * c.ny for c in cases]
     if world > len(cases):
         raise SystemExit(f"--split: {world} ranks for {len(cases)} cases")
+    sizes = [c.nx * c.ny for c in cases]
     return [cases[i] for i in lpt_shares(sizes, world)[rank]], sum(sizes)
 
 

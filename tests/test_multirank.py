@@ -152,3 +152,14 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_split_needs_a_workload_of_several_cases():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "sphere3d", "--split"],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "--split needs a workload of several cases" in r.stderr
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with pytest.raises(SystemExit):
+        bench.shard([object()] * 3, 0, 4)  # more ranks than cases

@@ -140,3 +140,22 @@ def test_obstacle_snapshot_counts_regions_by_what_they_touch():
     b_side = ol & ~((rA > rB) & (sc.solid == 0))
     assert d["obstacle_layer_rhoA"] == pytest.approx(float(np.median(rA[b_side])))
     assert d["obstacle_layer_rhoA"] == pytest.approx(0.3)
+
+
+def test_study_tables_render_missing_and_unsteady_values():
+    from paper_2505_22256_gb300 import study_cocurrent as cc
+    from paper_2505_22256_gb300 import study_sphere3d as s3
+
+    rows = [{"scheme": "original", "target_theta": 150.0, "lambda": 2.17, "theta": None, "dtheta_last": float("nan"),
+             "du_last": float("nan"), "umax": 0.37, "umax_off_wall": 0.2, "rho_min": 0.02, "rho_max": 1.1,
+             "wall_layer_rhoA": float("nan"), "attached": False, "unstable": True}]
+    t = st.table(rows)
+    assert t.count("\n") == 2 and "| — |" in t and "no (unstable)" in t
+    crow = [{"flow": "couette", "target_theta": 90.0, "lambda": 0.9951, "converged_at": None, "steps": 400000,
+             "eps_analytic": 0.0955, "eps_balance": 0.0959, "u_peak": 5.4e-3, "u_peak_analytic": 4.95e-3,
+             "rho_min": 0.66}]
+    ct = cc.table(crow)
+    assert "not within 400000" in ct and "9.55 %" in ct
+    srow = [{"lambda": 0.38, "paper_theta": 45.0, "theta": 75.2, "dtheta_last": float("nan"), "umax": 0.012,
+             "rhoA_min": 0.02, "rhoA_max": 1.05, "rhoB_min": 0.02, "rhoB_max": 1.02, "unstable": False}]
+    assert "| 0.38 | 45 | 75.2 | — |" in s3.table(srow)
