@@ -540,9 +540,10 @@ def run_ours(args):
                        "all cases)" % args.inner}
 
     # step kernels (+ the sliding-wall fix-up after each step where walls slide) + (fields pass +
-    # per-case reductions) + batched contact angle (density pass + 4 x 2 passes) when any case has a surface
+    # per-case reductions) + batched contact angle (4 point passes + 4 solves) when any case has a
+    # surface; the contact angle's densities come from the diagnostics pass just before it
     sliding = any(tuple(c.u_wall) != (0.0, 0.0) for c in cases)
-    launches = args.inner * (2 if sliding else 1) + 2 + (9 if any(sf is not None for sf in surfaces) else 0)
+    launches = args.inner * (2 if sliding else 1) + 2 + (8 if any(sf is not None for sf in surfaces) else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong" if args.split else "weak",
