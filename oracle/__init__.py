@@ -148,7 +148,7 @@ class _Cfg(ctypes.Structure):
                 ("Gw2", ctypes.c_double), ("delta", ctypes.c_double), ("g", ctypes.c_double * 2),
                 ("u_in", ctypes.c_double), ("rho_in", ctypes.c_double * 2),
                 ("wE8", ctypes.c_double * 5), ("inlet_profile", ctypes.c_int32), ("second_layer", ctypes.c_int32),
-                ("u_wall", ctypes.c_double * 2)]
+                ("u_wall", ctypes.c_double * 2), ("adhesion_stencil", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 @dataclass
@@ -172,6 +172,9 @@ class Config:
     # what a replaced second-layer node takes from x + sign(e) (Sec. 2.4, Table 1): "psi_and_solid"
     # or "psi" (the non-fluid site keeps its solid switch in the adhesion sum)
     second_layer: str = "psi_and_solid"
+    # stencil of the adhesion sum of Eq. 9: "e8" (the 24-node stencil of the cohesion force, Sec. 2.4)
+    # or "d2q9" (as printed: D2Q9 weights w_i over the eight first-layer neighbours)
+    adhesion_stencil: str = "e8"
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
 
     def c(self) -> _Cfg:
@@ -191,6 +194,7 @@ class Config:
         s.inlet_profile = {"uniform": 0, "poiseuille": 1}[self.inlet_profile]
         s.u_wall[0], s.u_wall[1] = self.u_wall
         s.second_layer = {"psi_and_solid": 0, "psi": 1}[self.second_layer]
+        s.adhesion_stencil = {"e8": 0, "d2q9": 1}[self.adhesion_stencil]
         for i, q in enumerate(SHELLS):
             s.wE8[i] = float(w[q])
         return s

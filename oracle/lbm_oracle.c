@@ -53,7 +53,14 @@ typedef struct {
                               Table 1): 0 both psi and the solid switch, 1 psi only (the site keeps
                               its own solid switch in the adhesion sum of Eq. 9) */
     double u_wall[2]; /* x-velocity of the lower / upper wall of a walled y direction (Sec. 3.1 Couette) */
+    int32_t adhesion_stencil; /* stencil of the adhesion sum of Eq. 9: ADHESION_E8 (the 24-node
+                                 eighth-order stencil of the cohesion force, Sec. 2.4) or
+                                 ADHESION_D2Q9 (Eq. 9 as printed: the D2Q9 weights w_i over the
+                                 eight first-layer neighbours) */
+    int32_t pad_;
 } oracle_cfg;
+
+enum { ADHESION_E8 = 0, ADHESION_D2Q9 = 1 };
 
 /* ---------------------------------------------------------------------------------------------
  * Lattice tables.
@@ -174,9 +181,27 @@ static void first_layer(const oracle_cfg* c, const uint8_t* solid, const double*
         *pA = 0.0; *pB = 0.0; *s = 1.0;
         return;
     }
-    *pA = rhoA[idx(c, X, Y)];
-    *pB = rhoB[idx(c, X, Y)];
+    *pA = rhoA ? rhoA[idx(c, X, Y)] : 0.0;
+    *pB = rhoB ? rhoB[idx(c, X, Y)] : 0.0;
     *s = 0.0;
+}
+
+/* Adhesion sum of Eq. 9 exactly as printed, a = sum_i w_i s(x + e_i) e_i over the eight moving
+ * D2Q9 velocities with the lattice weights 1/9 (axes) and 1/36 (diagonals); s is the solid switch
+ * of the first-layer site (as in first_layer(): outside a wall direction counts as solid, beyond an
+ * open column is that column).  Opposite velocities are taken together, i = 1, 2, 5, 6 with opp(i). */
+static void adhesion_d2q9(const oracle_cfg* c, const uint8_t* solid, int x, int y, double a[2]) {
+    static const int HALF[4] = {1, 2, 5, 6};
+    a[0] = 0.0;
+    a[1] = 0.0;
+    for (int h = 0; h < 4; h++) {
+        int i = HALF[h], j = OPP[i];
+        double pA, pB, si, sj;
+        first_layer(c, solid, NULL, NULL, x, y, CX[i], CY[i], &pA, &pB, &si);
+        first_layer(c, solid, NULL, NULL, x, y, CX[j], CY[j], &pA, &pB, &sj);
+        a[0] += W9[i] * (si - sj) * CX[i];
+        a[1] += W9[i] * (si - sj) * CY[i];
+    }
 }
 
 /* E8 neighbourhood value for stencil node n (0-based) of fluid node (x, y).
@@ -218,9 +243,10 @@ static int substituted(const oracle_cfg* c, const uint8_t* solid, int x, int y, 
 /* Wall list: fluid nodes whose 24-node stencil reaches a non-fluid site (solid, or outside the
  * array along a non-periodic direction), in increasing node index y*nx + x.  Per entry: the
  * substitution mask (bit n set when stencil node n+1 is a second-layer node replaced by its
- * first-layer partner), the effective solid mask (bit n = s~ of stencil node n+1) and the static
- * adhesion vector a(x) = sum_n w(|e_n|^2) s~_n e_n.  Returns the number of entries; arrays may be
- * NULL to count only. */
+ * first-layer partner), the effective solid mask (bit n = s~ of stencil node n+1 when that node
+ * enters the adhesion sum: all 24 on the E8 stencil, the first layer n < 8 for ADHESION_D2Q9) and
+ * the static adhesion vector a(x) = sum_n w(|e_n|^2) s~_n e_n (ADHESION_D2Q9: adhesion_d2q9).
+ * Returns the number of entries; arrays may be NULL to count only. */
 int64_t oracle_wall_list(const oracle_cfg* c, const uint8_t* solid, int32_t* node, uint32_t* subst,
                          uint32_t* seff, double* ax, double* ay) {
     int64_t count = 0;
@@ -242,7 +268,8 @@ int64_t oracle_wall_list(const oracle_cfg* c, const uint8_t* solid, int32_t* nod
                 double pA, pB, s;
                 e8_value(c, solid, zero, zero, x, y, n, &pA, &pB, &s);
                 if (substituted(c, solid, x, y, n)) sm |= 1u << n;
-                if (s != 0.0) em |= 1u << n;
+                /* the printed Eq. 9 sums the first layer only */
+                if (s != 0.0 && (c->adhesion_stencil != ADHESION_D2Q9 || n < 8)) em |= 1u << n;
             }
             for (int p = 0; p < 12; p++) {
                 int n = (p / 2) * 4 + (p % 2), m = n + 2; /* pairs (1,3),(2,4),(5,7),(6,8),... */
@@ -251,6 +278,7 @@ int64_t oracle_wall_list(const oracle_cfg* c, const uint8_t* solid, int32_t* nod
                 a[0] += w * (sn - sm2) * EX[n];
                 a[1] += w * (sn - sm2) * EY[n];
             }
+            if (c->adhesion_stencil == ADHESION_D2Q9) adhesion_d2q9(c, solid, x, y, a);
             if (node) {
                 node[count] = (int32_t)idx(c, x, y);
                 subst[count] = sm;
@@ -314,7 +342,9 @@ static void node_forces(const oracle_cfg* c, const uint8_t* solid, const double*
     /* (3) cohesion, Eq. 8 read as F_k = -G_12 psi_k(x) sum_n w(|e_n|^2) psi_kbar(x + e_n) e_n
      *     (the force on one component comes from the other; E8 weights).  Symmetric pairs
      *     (e, -e) are summed first.
-     * (4) adhesion, Eq. 9 on the same stencil: F_k,ads = -G_w,k rho_k(x) sum_n w s~_n e_n. */
+     * (4) adhesion, Eq. 9: F_k,ads = -G_w,k rho_k(x) a(x), with a(x) = sum_n w s~_n e_n on the same
+     *     stencil, or (adhesion_stencil = ADHESION_D2Q9) the printed first-neighbour sum with the
+     *     D2Q9 weights (adhesion_d2q9). */
     double gA[2] = {0.0, 0.0}, gB[2] = {0.0, 0.0}, a[2] = {0.0, 0.0};
     for (int p = 0; p < 12; p++) {
         int n = (p / 2) * 4 + (p % 2), m = n + 2;
@@ -324,6 +354,7 @@ static void node_forces(const oracle_cfg* c, const uint8_t* solid, const double*
         gB[0] += w * dB * EX[n]; gB[1] += w * dB * EY[n];
         a[0] += w * ds * EX[n]; a[1] += w * ds * EY[n];
     }
+    if (c->adhesion_stencil == ADHESION_D2Q9) adhesion_d2q9(c, solid, x, y, a);
     double GwA;
     if (c->scheme == SCHEME_IMPROVED) {
         double rho_e = (rA - rB) / (rA + rB);                 /* Eq. 10 */

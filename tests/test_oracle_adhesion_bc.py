@@ -67,11 +67,14 @@ def test_fig6_parameter_pairs_follow_lambda_definition():
         assert float(lam) * 0.17 == pytest.approx(float(gw1), abs=0.006)
 
 
-def test_lambda_one_makes_improved_equal_original():
-    """P3: lambda = 1 gives G_w1(x) = G_w2 everywhere, so both schemes step identically."""
+@pytest.mark.parametrize("adhesion_stencil", ["e8", "d2q9"])
+def test_lambda_one_makes_improved_equal_original(adhesion_stencil):
+    """P3: lambda = 1 gives G_w1(x) = G_w2 everywhere, so both schemes step identically (on either
+    adhesion stencil of Eq. 9)."""
     for re in np.linspace(-1, 1, 101):
         assert oracle.local_G(re, 1.0, 0.8) == 1.0
     sc = S.cylinder_droplet(40, lam=1.0)
+    sc.adhesion_stencil = adhesion_stencil
     p = sc.params()
     f0 = None
     outs = []
@@ -265,3 +268,20 @@ def test_interface_points_skip_nodes_near_solid():
     assert ns[:4].all() and not ns[4:ny - 3].any() and ns[ny - 3:].all()
     pts = oracle.interface_points(cfg, solid, rA, rB)
     assert len(pts) == nx and np.allclose(pts[:, 1], 9.5)
+
+
+def test_d2q9_adhesion_makes_the_second_layer_readings_identical():
+    """Under the printed Eq. 9 (first-layer adhesion sum) the two readings of what a replaced
+    second-layer node copies (psi and the solid switch, or psi only) differ only in switches that
+    no longer enter any sum, so they step bit for bit alike on a curved wall -- while on the E8
+    adhesion stencil they differ."""
+    outs = {}
+    for stencil in ("d2q9", "e8"):
+        for layer in ("psi_and_solid", "psi"):
+            sc = S.cylinder_droplet(40, lam=1.6)
+            sc.adhesion_stencil, sc.second_layer = stencil, layer
+            cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+            outs[stencil, layer] = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0), 40)
+    assert np.array_equal(outs["d2q9", "psi_and_solid"], outs["d2q9", "psi"])
+    assert np.max(np.abs(outs["e8", "psi_and_solid"] - outs["e8", "psi"])) > 1e-8
+    assert np.max(np.abs(outs["e8", "psi_and_solid"] - outs["d2q9", "psi"])) > 1e-6

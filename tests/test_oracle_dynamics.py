@@ -213,9 +213,11 @@ def test_laplace_law():
 # ---------------------------------------------------------------------------------------------
 # P10: mirror symmetry of a symmetric flat-wall case
 # ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("adhesion_stencil", ["e8", "d2q9"])
 @pytest.mark.parametrize("lam", [0.4, 1.8])
-def test_flat_wall_mirror_symmetry(lam):
+def test_flat_wall_mirror_symmetry(lam, adhesion_stencil):
     sc = S.flat_droplet(nx=40, ny=30, r=9, lam=lam, amp=0.0)
+    sc.adhesion_stencil = adhesion_stencil
     cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
     f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
     f = oracle.run(cfg, sc.solid, f, 400)
@@ -242,9 +244,11 @@ def test_couette_between_sliding_walls_is_exactly_linear(u_wall):
     assert np.max(np.abs(uy)) < 1e-14
 
 
-@pytest.mark.parametrize("scheme", ["improved", "original"])
-@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
-def test_exchanging_the_components_at_lambda_one_exchanges_the_state(scheme, second_layer):
+@pytest.mark.parametrize("scheme,second_layer,adhesion_stencil",
+                         [("improved", "psi_and_solid", "e8"), ("original", "psi_and_solid", "e8"),
+                          ("improved", "psi", "e8"), ("original", "psi", "e8"),
+                          ("improved", "psi_and_solid", "d2q9"), ("original", "psi_and_solid", "d2q9")])
+def test_exchanging_the_components_at_lambda_one_exchanges_the_state(scheme, second_layer, adhesion_stencil):
     """At lambda = 1 (and equal tau) nothing distinguishes A from B: cohesion uses the other
     component, both adhesion parameters are G_w2 (Eq. 12 gives h = 1), and the collision is the
     same.  A droplet of B started from the swapped densities must therefore reach the swapped
@@ -255,6 +259,7 @@ def test_exchanging_the_components_at_lambda_one_exchanges_the_state(scheme, sec
     sc.rhoA0[sc.solid == 1] = 0.0
     sc.rhoB0[sc.solid == 1] = 0.0
     sc.second_layer = second_layer
+    sc.adhesion_stencil = adhesion_stencil
     cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
     fA = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0), 150)
     fB = oracle.run(cfg, sc.solid, oracle.init(cfg, sc.solid, sc.rhoB0, sc.rhoA0), 150)

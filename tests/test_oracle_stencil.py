@@ -91,7 +91,9 @@ def _bf_forces(cfg, solid, rhoA, rhoB):
     """Independent loop over the 5x5 box of each fluid node: cohesion (Eq. 8, other component,
     E8 weights), adhesion (Eq. 9 with the local parameter of Eq. 12 / constant G_w1), body force;
     second-layer sites that are not in-array fluid nodes take the value of x + sign(e): its density
-    and its solid switch, or (second_layer "psi") its density while the site keeps its own switch."""
+    and its solid switch, or (second_layer "psi") its density while the site keeps its own switch.
+    With adhesion_stencil "d2q9" the adhesion sum is Eq. 9 as printed: the eight first neighbours
+    with the lattice weights 1/9 (axes) and 1/36 (diagonals) times their solid switch."""
     W = _weights_float()
     ny, nx = solid.shape
     Gw2 = cfg.G if cfg.Gw2 is None else cfg.Gw2
@@ -144,6 +146,13 @@ def _bf_forces(cfg, solid, rhoA, rhoB):
                     gA += w * vA * e
                     gB += w * vB * e
                     a += w * s * e
+            if cfg.adhesion_stencil == "d2q9":
+                a = np.zeros(2)
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        if dx or dy:
+                            wi = 1.0 / 9.0 if abs(dx) + abs(dy) == 1 else 1.0 / 36.0
+                            a += wi * first(x, y, dx, dy)[2] * np.array([dx, dy], float)
             rA, rB = rhoA[y, x], rhoB[y, x]
             if cfg.scheme == "improved":
                 re = (rA - rB) / (rA + rB)
@@ -176,10 +185,11 @@ def _pillar_case(nx=8, ny=8, block=None):
     return solid
 
 
+@pytest.mark.parametrize("adhesion_stencil", ["e8", "d2q9"])
 @pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
 @pytest.mark.parametrize("scheme,lam", [("improved", 0.4), ("improved", 1.7), ("original", 0.6)])
 @pytest.mark.parametrize("geom", ["pillar", "block_walls", "open_x"])
-def test_forces_match_brute_force(scheme, lam, geom, second_layer):
+def test_forces_match_brute_force(scheme, lam, geom, second_layer, adhesion_stencil):
     rng = np.random.default_rng(7)
     if geom == "pillar":
         solid = _pillar_case()
@@ -196,6 +206,7 @@ def test_forces_match_brute_force(scheme, lam, geom, second_layer):
         cfg = oracle.Config(nx=10, ny=7, bc_x="open", bc_y="wall", scheme=scheme, lam=lam, G=1.2,
                             nthreads=1)
     cfg.second_layer = second_layer
+    cfg.adhesion_stencil = adhesion_stencil
     ny, nx = solid.shape
     rA = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
     rB = rng.uniform(0.02, 1.1, (ny, nx)) * (1 - solid)
@@ -301,3 +312,65 @@ def test_wall_list_counts_outside_of_wall_direction():
     assert em == _bits(4, 7, 8, 12, 19, 20, 15, 16, 23, 24)
     assert sm == _bits(12, 15, 16, 19, 20, 23, 24)
     assert a_y == pytest.approx(-(W[1] + 2 * W[2] + 2 * W[4] + 6 * W[5] + 4 * W[8]))
+
+
+# ---------------------------------------------------------------------------------------------
+# Eq. 9 as printed: D2Q9 weights over the first layer (adhesion_stencil = "d2q9")
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
+def test_wall_list_single_pillar_d2q9_adhesion_by_hand(second_layer):
+    """The 8x8 pillar under the printed Eq. 9: a(x) = sum_i w_i s(x + e_i) e_i with w = 1/9 on the
+    axes and 1/36 on the diagonals.  Only the eight first neighbours of the pillar feel it, whatever
+    the second-layer reading; the substitution masks (cohesion) are unchanged."""
+    solid = _pillar_case()
+    cfg = oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic", second_layer=second_layer,
+                        adhesion_stencil="d2q9")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    # (3,4): the pillar is first-layer node 4 = e_4 = (0,-1): a = (1/9) (0,-1)
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 4) == (0, _bits(4), 0.0, -1.0 / 9.0)
+    # (2,3): pillar at e_1 = (1,0)
+    assert _entry(node, subst, seff, ax, ay, 8, 2, 3) == (0, _bits(1), 1.0 / 9.0, 0.0)
+    # (2,2): pillar at e_5 = (1,1): a = (1/36) (1,1)
+    assert _entry(node, subst, seff, ax, ay, 8, 2, 2) == (0, _bits(5), 1.0 / 36.0, 1.0 / 36.0)
+    # (4,2): pillar at e_6 = (-1,1)
+    assert _entry(node, subst, seff, ax, ay, 8, 4, 2) == (0, _bits(6), -1.0 / 36.0, 1.0 / 36.0)
+    # second-layer nodes of the pillar: still in the wall list (cohesion substitution), no adhesion
+    assert _entry(node, subst, seff, ax, ay, 8, 3, 5) == (_bits(12), 0, 0.0, 0.0)
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 5) == (_bits(15), 0, 0.0, 0.0)
+    assert _entry(node, subst, seff, ax, ay, 8, 5, 4) == (_bits(19), 0, 0.0, 0.0)
+    _, subst_e8, _, _, _ = oracle.wall_list(oracle.Config(nx=8, ny=8, bc_x="periodic", bc_y="periodic"), solid)
+    np.testing.assert_array_equal(subst, subst_e8)
+
+
+def test_flat_wall_d2q9_adhesion_vector():
+    """Outside a walled y: the first row sees e_4, e_7, e_8 solid, a_y = -(1/9 + 2/36) = -1/6 (the
+    D2Q9 first moment sum_(e_y < 0) w_i e_y); the second row sees no solid first neighbour."""
+    solid = np.zeros((10, 6), np.uint8)
+    cfg = oracle.Config(nx=6, ny=10, bc_x="periodic", bc_y="wall", adhesion_stencil="d2q9")
+    node, subst, seff, ax, ay = oracle.wall_list(cfg, solid)
+    assert sorted(set((node // 6).tolist())) == [0, 1, 8, 9]
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 6, 2, 0)
+    assert em == _bits(4, 7, 8) and a_x == 0.0 and a_y == pytest.approx(-1.0 / 6.0, abs=1e-16)
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 6, 2, 9)
+    assert em == _bits(2, 5, 6) and a_y == pytest.approx(1.0 / 6.0, abs=1e-16)
+    sm, em, a_x, a_y = _entry(node, subst, seff, ax, ay, 6, 2, 1)
+    assert em == 0 and a_x == 0.0 and a_y == 0.0 and sm == _bits(12, 23, 24, 15, 16)
+
+
+def test_d2q9_adhesion_force_next_to_a_wall_by_hand():
+    """Uniform densities, no cohesion (G = 0): the only force at a first-row node is the adhesion
+    of Eq. 9, F_k = -G_w,k rho_k a = G_w,k rho_k / 6 along +y (original scheme, G_w1 = lambda G_w2);
+    nodes further out feel nothing."""
+    nx, ny = 6, 9
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="periodic", bc_y="wall", scheme="original", G=0.0, lam=0.5,
+                        Gw2=0.3, adhesion_stencil="d2q9", nthreads=1)
+    f = np.zeros((2, 9, ny, nx))
+    f[0, 0] = 0.8
+    f[1, 0] = 0.1
+    FA, FB = oracle.forces(cfg, solid, f)
+    assert np.all(FA[0] == 0.0) and np.all(FB[0] == 0.0)
+    np.testing.assert_allclose(FA[1, 0], 0.5 * 0.3 * 0.8 / 6.0, rtol=1e-14)
+    np.testing.assert_allclose(FB[1, 0], 0.3 * 0.1 / 6.0, rtol=1e-14)
+    np.testing.assert_allclose(FA[1, -1], -0.5 * 0.3 * 0.8 / 6.0, rtol=1e-14)
+    assert np.all(FA[1, 1:-1] == 0.0) and np.all(FB[1, 1:-1] == 0.0)
