@@ -258,9 +258,20 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step", sources=KERNEL_SOURCES):
+STORE_TYPE = {"f32": "float, float", "f16": "__half, float", "bf16": "__nv_bfloat16, float", "f64": "double, double"}
+
+
+def step_kernel_name(storage: str, info: dict) -> str:
+    """The step kernel's template instantiation as ncu names it (storage type, compute type, fields
+    pass off, wall-list correction inlined or called, block width)."""
+    return f"k_step<{STORE_TYPE[storage]}, 0, {info['wall_inline']}, {info['block_threads']}>"
+
+
+def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step", sources=KERNEL_SOURCES,
+                      launch: dict | None = None):
     """DRAM bytes per launch from the committed ncu summary, scaled to this launch's nodes; None when
-    the summary is missing or was taken on a different version of the kernel source."""
+    the summary is missing, was taken on a different version of the kernel source, or (launch given)
+    on another instantiation or launch shape of the kernel than the one timed."""
     p = os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters.txt")
     try:
         kv = {}
@@ -271,6 +282,9 @@ def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
             return None
+        for key, want in (launch or {}).items():
+            if kv.get(key) != str(want):
+                return None
         per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
         return per_node * nodes_per_launch
     except (OSError, KeyError, ValueError):
@@ -333,7 +347,8 @@ def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
         if (el >= seconds and n >= need) or n >= 10000:
             break
     mlups = sc.nx * sc.ny * n / el / 1e6
-    out = {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+    out = {"value": mlups, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle", "sample_s": el,
+           "sample_updates": sc.nx * sc.ny * n,
            "sample": f"1 of the {len(cases)} cases ({sc.nx}x{sc.ny}, {sc.name}), {n} FP64 time steps "
                      f"in {el:.1f} s on {cfg.nthreads} host threads", "host": host_info()}
     if parity:
@@ -363,23 +378,35 @@ def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
     return out
 
 
+def extrapolation(full_updates: float, sample_updates: float, mlups: float) -> dict:
+    """How the reference arm's rate relates to a full bench step: each timed step of that arm is a
+    bounded sample (time steps of one case), so ms_per_step and steps are what ran, and the value, a
+    rate, carries over to the full workload by this factor of updates."""
+    return {"value_is_rate_of_sample": True, "sample_updates_per_step": int(sample_updates),
+            "full_step_updates": int(full_updates), "factor": full_updates / sample_updates,
+            "full_step_ms_at_this_rate": full_updates / (mlups * 1e6) * 1e3}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     if args.workload == "sphere3d":
-        vals, base = [], None
+        vals, secs, ups, base = [], [], [], None
         for k in range(args.warmup + args.steps):
             b = cpu_baseline_3d(per_step)
             if k >= args.warmup:
                 vals.append(b["value"])
+                secs.append(b["sample_s"])
+                ups.append(b["sample_updates"])
                 base = b
         value = statistics.mean(vals)
         nodes = 200 * 200 * 280
         line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": nodes * args.inner / (value * 1e6) * 1e3, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": statistics.mean(secs) * 1e3, "higher_is_better": True, "scaling": "weak",
+                "extrapolated": extrapolation(nodes * args.inner, statistics.mean(ups), value),
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "3-D droplet on a sphere, 200x200x280 per GPU (R=50, r=45, lambda=1, periodic)",
                            "storage": args.storage, "inner_steps": args.inner},
@@ -395,16 +422,19 @@ def run_reference(args):
     # each step: a bounded sample of the workload (time steps of one case), sized so that the whole
     # --steps/--warmup run stays within a few minutes
     base = None
-    vals = []
+    vals, secs, ups = [], [], []
     for k in range(args.warmup + args.steps):
         b = cpu_baseline(args, per_step)
         if k >= args.warmup:
             vals.append(b["value"])
+            secs.append(b["sample_s"])
+            ups.append(b["sample_updates"])
             base = b
     value = statistics.mean(vals)
-    ms_per_step = sum(c.nx * c.ny for c in cases) * args.inner / (value * 1e6) * 1e3
+    full_updates = sum(c.nx * c.ny for c in cases) * args.inner
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
+            "extrapolated": extrapolation(full_updates, statistics.mean(ups), value), "higher_is_better": True,
             "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, cases, desc, args.gpus if args.split else 1, split_nodes),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
@@ -498,7 +528,9 @@ def run_ours(args):
     algo_bytes = BYTES_PER_NODE[args.storage] * fluid
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = committed_traffic(args.storage, nodes)
+    traffic = committed_traffic(args.storage, nodes, launch={
+        "kernel": step_kernel_name(args.storage, info), "block_rows": info["block_rows"],
+        "grid_blocks": info["grid_blocks"]})
     dall = lat.diagnostics_all(allow_unstable=True)
     d = dall[0]
     theta = [None if th != th else float(th) for th in contact_angles()]
@@ -618,6 +650,7 @@ def cpu_baseline_3d(seconds: float, storage: str | None = None) -> dict:
         if (el >= seconds and n >= need) or n >= 10000:
             break
     out = {"value": nx * ny * nz * n / el / 1e6, "unit": UNIT, "cores": cfg.nthreads, "kind": "oracle",
+           "sample_s": el, "sample_updates": nx * ny * nz * n,
            "sample": f"the Sec. 3.5 geometry scaled to {nx}x{ny}x{nz}, {n} FP64 time steps in {el:.1f} s on "
                      f"{cfg.nthreads} host threads", "host": host_info()}
     if storage and snap is not None:

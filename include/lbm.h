@@ -89,6 +89,16 @@ typedef enum {
     LBM_SECOND_LAYER_PSI = 1
 } lbm_second_layer;
 
+/* Stencil of the adhesion sum of Eq. 9, a(x) = sum_e w(e) s(x + e) e, F_k,ads = -G_w,k rho_k a(x).
+ * Sec. 2.4 applies the eighth-order isotropy to both schemes; Eq. 9 itself is printed with the D2Q9
+ * weights w_i over the first-layer neighbours.  Under LBM_ADHESION_D2Q9 the second-layer
+ * reconstruction of Table 1 feeds the cohesion sum only, so both lbm_second_layer readings give the
+ * same state. */
+typedef enum {
+    LBM_ADHESION_E8 = 0,  /* default: the 24-node stencil and weights of the cohesion force */
+    LBM_ADHESION_D2Q9 = 1 /* as printed in Eq. 9: w_i = 1/9 (axes), 1/36 (diagonals), first layer only */
+} lbm_adhesion_stencil;
+
 typedef struct {
     double tau[2];        /* relaxation times tau_A, tau_B (Eq. 2); each > 0.5 */
     double G_AB;          /* inter-component strength G_12 (Eq. 8), stencil weights with
@@ -110,6 +120,8 @@ typedef struct {
     int32_t inlet_profile; /* lbm_inlet_profile (LBM_BC_OPEN) */
     int32_t second_layer;  /* lbm_second_layer: what a second-layer stencil node that is not a fluid
                               node takes from its first-layer partner x + sign(e) (Sec. 2.4, Table 1) */
+    int32_t adhesion_stencil; /* lbm_adhesion_stencil (Eq. 9) */
+    int32_t pad_;             /* unused; its value is ignored */
 } lbm_params;
 
 /* Storage and arithmetic precision of the populations. */
@@ -273,7 +285,8 @@ lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, doub
  * when second-layer stencil node n (numbering of Table 1: 1-8 first layer in the D2Q9 order, 9-16
  * = 2 e_(n-8), 17-20 and 21-24 the knight moves whose first-layer partner is n-12 and n-16) is
  * replaced by its first-layer partner; seff = bit n-1 set when stencil node n counts as solid in
- * the adhesion sum; a = sum_n w(|e_n|^2) seff_n e_n.  Call first with node = NULL to get *n; the
+ * the adhesion sum (first-layer bits only under LBM_ADHESION_D2Q9); a = sum_n w(e_n) seff_n e_n
+ * with the weights of the adhesion stencil.  Call first with node = NULL to get *n; the
  * arrays must then hold *n entries (any of them may be NULL). */
 lbm_status lbm_wall_list(lbm_ctx* ctx, int32_t case_index, int32_t* node, uint32_t* subst,
                          uint32_t* seff, double* ax, double* ay, int64_t* n);
@@ -356,6 +369,9 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
  *   - all calls on a device share that array, so calls that overlap on the GPU race; serialise them;
  *   - the first call on each device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture on the device.
+ *     The address is kept for the life of the process and belongs to the device's primary
+ *     context: after cudaDeviceReset (which destroys that context) it is no longer valid, so do
+ *     not call this function again in that process.
  * Returns LBM_EUNSTABLE, with *out filled, when a fluid node has a non-finite or non-positive
  * density. */
 lbm_status lbm_diagnostics_noalloc(const double* rho_A, const double* rho_B, const double* ux,

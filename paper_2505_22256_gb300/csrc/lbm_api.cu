@@ -65,6 +65,13 @@ cudaError_t dalloc(Ctx& c, T** p, size_t count) {
 
 bool finite(double v) { return isfinite(v) != 0; }
 
+// FNV-1a over a solid mask read as fluid (0) / solid (1) per node.
+uint64_t mask_hash(const uint8_t* solid, long long n) {
+    uint64_t h = 1469598103934665603ULL;
+    for (long long s = 0; s < n; ++s) h = (h ^ (uint64_t)(solid[s] != 0)) * 1099511628211ULL;
+    return h;
+}
+
 lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_params* p, const double* rA,
                          const double* rB, int idx, int64_t* nfluid) {
     if (!g || !solid || !p || !rA || !rB) return fail(LBM_EINVAL, "case %d: NULL argument", idx);
@@ -83,6 +90,8 @@ lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_para
     if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return fail(LBM_EINVAL, "case %d: bad mode", idx);
     if (p->second_layer != LBM_SECOND_LAYER_PSI_AND_SOLID && p->second_layer != LBM_SECOND_LAYER_PSI)
         return fail(LBM_EINVAL, "case %d: bad second_layer %d", idx, p->second_layer);
+    if (p->adhesion_stencil != LBM_ADHESION_E8 && p->adhesion_stencil != LBM_ADHESION_D2Q9)
+        return fail(LBM_EINVAL, "case %d: bad adhesion_stencil %d", idx, p->adhesion_stencil);
     if (p->inlet_profile != LBM_INLET_UNIFORM && p->inlet_profile != LBM_INLET_POISEUILLE)
         return fail(LBM_EINVAL, "case %d: bad inlet profile", idx);
     if (p->inlet_profile == LBM_INLET_POISEUILLE && (g->bc_x != LBM_BC_OPEN || g->bc_y != LBM_BC_WALL))
@@ -400,6 +409,7 @@ lbm_status create_impl(int ncases, const lbm_case* cs, int storage, void* stream
         hc.grid = cs[i].grid;
         hc.params = cs[i].params;
         hc.nfluid = nfluid[i];
+        hc.mask_hash = mask_hash(cs[i].solid, (long long)cs[i].grid.nx * cs[i].grid.ny);
         c.cases.push_back(hc);
         DevCase d = make_desc(cs[i].grid, cs[i].params);
         const int per_line = (int)(128 / (2 * c.elem));  // rows of pairs start on 128-byte boundaries
@@ -1063,15 +1073,26 @@ struct CkptHeader {
     uint64_t hash;
 };
 
+// FNV-1a over the grid, every parameter field by value (never the structs' padding bytes, which a C
+// caller may leave undefined) and each case's solid-mask hash, so that a checkpoint only loads into
+// a context with the same geometry and parameters.
 uint64_t params_hash(const Ctx& c) {
     uint64_t h = 1469598103934665603ULL;
     auto mix = [&](const void* p, size_t n) {
         const unsigned char* b = (const unsigned char*)p;
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
     };
+    auto mixi = [&](int64_t v) { mix(&v, sizeof v); };
+    auto mixd = [&](double v) { mix(&v, sizeof v); };
     for (const auto& hc : c.cases) {
-        mix(&hc.grid, sizeof hc.grid);
-        mix(&hc.params, sizeof hc.params);
+        const lbm_grid& g = hc.grid;
+        const lbm_params& p = hc.params;
+        mixi(g.nx); mixi(g.ny); mixi(g.bc_x); mixi(g.bc_y);
+        mixd(p.tau[0]); mixd(p.tau[1]); mixd(p.G_AB); mixi(p.mode); mixd(p.lambda); mixd(p.G_w2); mixd(p.delta);
+        mixd(p.g[0]); mixd(p.g[1]); mixd(p.u_in); mixd(p.rho_in[0]); mixd(p.rho_in[1]);
+        mixd(p.rho0_store[0]); mixd(p.rho0_store[1]); mixd(p.u_wall[0]); mixd(p.u_wall[1]);
+        mixi(p.inlet_profile); mixi(p.second_layer); mixi(p.adhesion_stencil);
+        mixi((int64_t)hc.mask_hash);
     }
     return h;
 }

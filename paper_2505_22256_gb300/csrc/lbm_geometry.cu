@@ -10,6 +10,9 @@
 //          outside first-layer site, or a replaced second-layer node whose partner is one (when it
 //          copies the pseudopotential only: whose own site is one, clamped along an open axis)
 //   a      sum_n w(|e_n|^2) seff_n e_n  (FP64)
+// With the adhesion sum of Eq. 9 as printed (LBM_ADHESION_D2Q9) only the first layer enters it:
+// seff keeps the first-layer bits and a = sum_i w_i s(x + e_i) e_i with the D2Q9 weights, opposite
+// velocities taken together (i = 1, 2, 5, 6 with opp(i)).
 // Along an open axis a first-layer site beyond the boundary column is the boundary column itself.
 #include "lbm_internal.h"
 
@@ -127,7 +130,7 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
                             const uint16_t* __restrict__ flags_all, uint32_t* __restrict__ wsub_all,
                             const int32_t* __restrict__ row_off, int32_t* __restrict__ wl_node,
                             uint32_t* __restrict__ wl_subst, uint32_t* __restrict__ wl_seff,
-                            double* __restrict__ wl_a, long long nwall_total, int psi_only) {
+                            double* __restrict__ wl_a, long long nwall_total, int psi_only, int d2q9) {
     const DevCase C = cases[c];
     const Geo g{C.nx, C.ny, C.bc_x, C.bc_y, solid_all + C.d_off};
     const int Y = blockIdx.x;
@@ -162,16 +165,25 @@ __global__ void k_wall_fill(const DevCase* __restrict__ cases, int c, const uint
                     s = psi_only ? first_layer_solid(g, X, Y, ex, ey)
                                  : first_layer_solid(g, X, Y, (ex > 0) - (ex < 0), (ey > 0) - (ey < 0));
                 }
-                if (s) em |= 1u << n;
+                if (s && (!d2q9 || n < 8)) em |= 1u << n;
             }
             double ax = 0.0, ay = 0.0;
-            for (int p = 0; p < 12; ++p) {  // pairs (n, n+2): e_(n+2) = -e_n within each group of four
-                const int n = (p / 2) * 4 + (p % 2), m = n + 2;
-                const int ex = s24x(n), ey = s24y(n);
-                const double w = w8(ex * ex + ey * ey);
-                const double ds = (double)((em >> n) & 1u) - (double)((em >> m) & 1u);
-                ax += w * ds * ex;
-                ay += w * ds * ey;
+            if (d2q9) {
+                for (int h = 0; h < 4; ++h) {  // i = 1, 2, 5, 6 and opp(i); bit i-1 is first-layer node i
+                    const int i = h < 2 ? 1 + h : 3 + h;
+                    const double ds = (double)((em >> (i - 1)) & 1u) - (double)((em >> (opp(i) - 1)) & 1u);
+                    ax += wq(i) * ds * cx(i);
+                    ay += wq(i) * ds * cy(i);
+                }
+            } else {
+                for (int p = 0; p < 12; ++p) {  // pairs (n, n+2): e_(n+2) = -e_n within each group of four
+                    const int n = (p / 2) * 4 + (p % 2), m = n + 2;
+                    const int ex = s24x(n), ey = s24y(n);
+                    const double w = w8(ex * ex + ey * ey);
+                    const double ds = (double)((em >> n) & 1u) - (double)((em >> m) & 1u);
+                    ax += w * ds * ex;
+                    ay += w * ds * ey;
+                }
             }
             wl_node[e] = Y * C.nx + X;
             wl_subst[e] = sm;
@@ -240,7 +252,8 @@ cudaError_t launch_scan_rows(const int32_t* counts, int32_t* offsets, int n, cud
 cudaError_t launch_wall_fill(Ctx& c, int ci, const int32_t* row_offsets) {
     k_wall_fill<<<c.hcases[ci].ny, 256, 0, c.stream>>>(c.dcases, ci, c.solid, c.flags, c.wsub, row_offsets,
                                                         c.wl_node, c.wl_subst, c.wl_seff, c.wl_a, c.nwall,
-                                                        c.cases[ci].params.second_layer == LBM_SECOND_LAYER_PSI);
+                                                        c.cases[ci].params.second_layer == LBM_SECOND_LAYER_PSI,
+                                                        c.cases[ci].params.adhesion_stencil == LBM_ADHESION_D2Q9);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct HostCase {
     lbm_grid grid;
     lbm_params params;
     int64_t nfluid = 0;
+    uint64_t mask_hash = 0;  // hash of the solid mask (checkpoint matching)
 };
 
 // NVTX range over the host side of one entry point (visible in Nsight Systems timelines; NVTX v3

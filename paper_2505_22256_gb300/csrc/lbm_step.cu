@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
         }
         bool ok = wait_next();   // f* row r_first
         ok = wait_next() && ok;  // f* row r_first + dir
+        ok = !__syncthreads_or(!ok);  // the whole block takes a failed wait's exit path together
         const R rdir = (R)dir;
 
         // One row of the march: densities of row q into `cur`, barrier, refill of the slot that

@@ -94,6 +94,9 @@ class Scenario:
     # what a non-fluid second-layer stencil site takes from x + sign(e) (Sec. 2.4, Table 1):
     # psi_and_solid | psi
     second_layer: str = "psi_and_solid"
+    # stencil of the adhesion sum of Eq. 9: e8 (the cohesion force's 24-node stencil) | d2q9 (as
+    # printed: D2Q9 weights over the eight first-layer neighbours)
+    adhesion_stencil: str = "e8"
     surface: dict | None = None  # for the contact angle: {"kind": "flat"|"circle", ...}
     # 16-bit storage keeps f_i - w_i rho0 per component; the dissolved-phase density serves both
     # phases best (ignored by FP32 / FP64 storage)
@@ -112,7 +115,8 @@ class Scenario:
         return dict(bc_x=self.bc_x, bc_y=self.bc_y, scheme=self.scheme, tau=tuple(self.tau),
                     G=self.G, lam=self.lam, Gw2=self.Gw2, delta=self.delta, g=tuple(self.g),
                     u_in=self.u_in, rho_in=tuple(self.rho_in), u_wall=tuple(self.u_wall),
-                    inlet_profile=self.inlet_profile, second_layer=self.second_layer)
+                    inlet_profile=self.inlet_profile, second_layer=self.second_layer,
+                    adhesion_stencil=self.adhesion_stencil)
 
 
 def _grid(ny, nx):
@@ -158,7 +162,8 @@ def cylinder_droplet(n: int = 96, R: float | None = None, r: float | None = None
 def cylinder_in_box(nx: int = 300, ny: int = 350, R: float = 70.0, centre=(150.0, 130.0), r: float = 50.0,
                     drop=(150.0, 230.0), lam: float = 1.0, seed: int = 31, scheme: str = "improved",
                     G: float = G_DEFAULT, Gw2: float | None = GW2_DEFAULT, tau=(1.0, 1.0),
-                    rho_m: float = RHO_M, rho_d: float = RHO_D, second_layer: str = "psi_and_solid") -> Scenario:
+                    rho_m: float = RHO_M, rho_d: float = RHO_D, second_layer: str = "psi_and_solid",
+                    adhesion_stencil: str = "e8") -> Scenario:
     """The paper's own Sec. 3.2 geometry (Fig. 5): a 300x350 box periodic in x and y, a solid
     cylinder of radius 70 centred at (150, 130), and a droplet of A of radius 50 centred at
     (150, 230), 0.6 r above the cylinder top.  Gw2 None means G_w2 = G."""
@@ -168,7 +173,7 @@ def cylinder_in_box(nx: int = 300, ny: int = 350, R: float = 70.0, centre=(150.0
     rA, rB = _phase_fields(inside, solid, seed, rho_m=rho_m, rho_d=rho_d)
     return Scenario(f"cylinder_in_box_{nx}x{ny}", solid, rA, rB, bc_x="periodic", bc_y="periodic",
                     scheme=scheme, tau=tuple(tau), G=G, Gw2=Gw2, lam=lam, rho_in=(rho_m, rho_d),
-                    second_layer=second_layer,
+                    second_layer=second_layer, adhesion_stencil=adhesion_stencil,
                     surface={"kind": "circle", "cx": float(centre[0]), "cy": float(centre[1]), "R": R + 0.5})
 
 
@@ -394,7 +399,7 @@ def scheme_comparison(n: int = 1024, seed: int = 2, angles=(30, 50, 70, 90, 110,
 
 
 def scheme_study(angles=(30, 50, 70, 90, 110, 130, 150), seed: int = 31, paper_params: bool = False,
-                 Gw2: float | None = -1.0, second_layer: str = "psi_and_solid") -> list:
+                 Gw2: float | None = -1.0, second_layer: str = "psi_and_solid", adhesion_stencil: str = "e8") -> list:
     """The comparison of Sec. 3.2 (Figs. 6, 10, 11) on the paper's 300x350 geometry: one case per
     target angle (lambda from the correlation) under the improved scheme, then the same geometries
     and initial states under the original scheme (G_w1 = lambda G_w2 everywhere).  paper_params
@@ -404,6 +409,7 @@ def scheme_study(angles=(30, 50, 70, 90, 110, 130, 150), seed: int = 31, paper_p
     if Gw2 is None or Gw2 >= 0:
         extra["Gw2"] = Gw2
     extra["second_layer"] = second_layer
+    extra["adhesion_stencil"] = adhesion_stencil
     out = []
     for scheme in ("improved", "original"):
         for k, th in enumerate(angles):

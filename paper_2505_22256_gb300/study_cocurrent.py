@@ -31,9 +31,9 @@ TOL = 1e-5         # largest change of u_x over INTERVAL steps at convergence
 
 
 def cases(angles=(45, 90, 135), paper_params: bool = False, gw2: float | None = -1.0,
-          second_layer: str = "psi_and_solid") -> list:
+          second_layer: str = "psi_and_solid", adhesion_stencil: str = "e8") -> list:
     """Poiseuille then Couette channels, one per target angle.  gw2 >= 0 (or None: G_w2 = G)
-    overrides G_w2; second_layer picks the Table 1 reading."""
+    overrides G_w2; second_layer picks the Table 1 reading, adhesion_stencil that of Eq. 9."""
     extra = {k: S.PAPER_SEC32[k] for k in ("rho_m", "rho_d", "G", "Gw2")} if paper_params else {}
     if gw2 is None or gw2 >= 0:
         extra["Gw2"] = gw2
@@ -43,6 +43,7 @@ def cases(angles=(45, 90, 135), paper_params: bool = False, gw2: float | None = 
             sc = make(lam=S.lambda_for_angle(th), seed=40 + 10 * k + (flow == "couette"), **extra)
             sc.name = f"{flow}_theta{th}_{sc.name}"
             sc.second_layer = second_layer
+            sc.adhesion_stencil = adhesion_stencil
             sc.extra.update(flow=flow, target_theta=float(th))
             out.append(sc)
     return out
@@ -148,11 +149,16 @@ def main(argv=None) -> int:
     ap.add_argument("--paper-params", action="store_true",
                     help="densities 1.02 / 0.05 and G_w2 = G_12 as stated in Sec. 3.1")
     ap.add_argument("--gw2", type=float, default=-1.0, help="override G_w2 (>= 0)")
+    ap.add_argument("--gw2-is-g", action="store_true", help="G_w2 = G_12 (the paper's choice)")
     ap.add_argument("--second-layer", default="psi_and_solid", choices=["psi_and_solid", "psi"])
+    ap.add_argument("--adhesion-stencil", default="e8", choices=["e8", "d2q9"],
+                    help="stencil of the adhesion sum of Eq. 9 (d2q9: as printed, first layer)")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     angles = tuple(int(a) for a in args.angles.split(","))
-    rows = run(cases(angles, args.paper_params, args.gw2, args.second_layer), args.max_steps, args.storage)
+    gw2 = None if args.gw2_is_g else args.gw2
+    rows = run(cases(angles, args.paper_params, gw2, args.second_layer, args.adhesion_stencil), args.max_steps,
+               args.storage)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:

@@ -125,13 +125,21 @@ def main(argv=None) -> int:
     ap.add_argument("--paper-params", action="store_true",
                     help="densities 1.02 / 0.05, nu = 0.17 and G_w2 = G_12 as stated in Sec. 3.2")
     ap.add_argument("--gw2", type=float, default=-1.0, help="override G_w2 (>= 0)")
+    ap.add_argument("--gw2-is-g", action="store_true", help="G_w2 = G_12 (the paper's choice)")
+    ap.add_argument("--G", type=float, default=None, help="override G_12")
     ap.add_argument("--second-layer", default="psi_and_solid", choices=["psi_and_solid", "psi"],
                     help="what a non-fluid second-layer stencil site takes from x + sign(e) (Table 1)")
+    ap.add_argument("--adhesion-stencil", default="e8", choices=["e8", "d2q9"],
+                    help="stencil of the adhesion sum of Eq. 9 (d2q9: as printed, first layer)")
     ap.add_argument("--json", default=None, help="also write the records to this file")
     args = ap.parse_args(argv)
     angles = tuple(int(a) for a in args.angles.split(","))
-    rows = run(S.scheme_study(angles, paper_params=args.paper_params, Gw2=args.gw2, second_layer=args.second_layer),
-               args.steps, args.check, args.storage)
+    cases = S.scheme_study(angles, paper_params=args.paper_params, Gw2=None if args.gw2_is_g else args.gw2,
+                           second_layer=args.second_layer, adhesion_stencil=args.adhesion_stencil)
+    if args.G is not None:
+        for sc in cases:
+            sc.G = args.G
+    rows = run(cases, args.steps, args.check, args.storage)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:

@@ -74,7 +74,8 @@ def _case(n=16):
 
 
 @pytest.mark.parametrize("field,value", [("tau", (0.5, 1.0)), ("lambda_", 0.0), ("delta", 1.5),
-                                         ("delta", 0.0), ("G_AB", float("nan")), ("mode", 7)])
+                                         ("delta", 0.0), ("G_AB", float("nan")), ("mode", 7),
+                                         ("second_layer", 2), ("adhesion_stencil", 2), ("adhesion_stencil", -1)])
 def test_invalid_parameters_are_rejected(lbm, field, value):
     solid, a, b = _case()
     p = lbm.make_params()

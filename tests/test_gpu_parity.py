@@ -49,6 +49,17 @@ def small_porous():
     return S.porous_disks(nx=192, ny=96, rmin=5, rmax=11, keep_out=(12, 12), seed=9, porosity=0.7)
 
 
+def d2q9_adhesion(make, **kw):
+    """The same case with the adhesion sum of Eq. 9 as printed (D2Q9 weights, first layer)."""
+    def build():
+        sc = make()
+        sc.adhesion_stencil = "d2q9"
+        for k, v in kw.items():
+            setattr(sc, k, v)
+        return sc
+    return build
+
+
 def psi_only(make):
     """The same case with the second-layer reading that copies psi only (Sec. 2.4, Table 1)."""
     def build():
@@ -76,6 +87,14 @@ SCENARIOS = {
     "pillar8_psi": psi_only(pillar_case),
     "square_obstacle_small_psi": psi_only(lambda: S.square_obstacle_channel(nx=140, ny=60, side=10, center=(49, 30),
                                                                             r=10.0, drop=(22, 30))),
+    "cylinder96_d2q9": d2q9_adhesion(lambda: S.cylinder_droplet(96, lam=2.17)),
+    "porous_open_d2q9": d2q9_adhesion(small_porous),
+    "pillar8_d2q9": d2q9_adhesion(pillar_case),
+    "gw2_equals_G_d2q9": d2q9_adhesion(lambda: S.cylinder_droplet(64, lam=1.7), Gw2=None),
+    "flat64x48_d2q9_original": d2q9_adhesion(lambda: S.flat_droplet(64, 48, r=12, lam=0.4, scheme="original")),
+    "square_obstacle_small_d2q9": d2q9_adhesion(lambda: S.square_obstacle_channel(nx=140, ny=60, side=10,
+                                                                                 center=(49, 30), r=10.0,
+                                                                                 drop=(22, 30))),
 }
 
 
@@ -152,7 +171,7 @@ def test_f32_matches_oracle_after_100_steps(name):
     assert du <= 1e-6, du
 
 
-@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "throat256x96", "flat64x48"])
+@pytest.mark.parametrize("name", ["cylinder96", "porous_open", "throat256x96", "flat64x48", "cylinder96_d2q9"])
 def test_f32_one_step_from_developed_state(name):
     """Every node's single update from an oracle state (rounded to FP32) matches the oracle's
     update of the same rounded state to FP32 rounding."""
@@ -490,6 +509,30 @@ def test_checkpoint_roundtrip_is_bit_exact():
             lbm.lbm_load(other.ctx, p)
         assert e.value.status == lbm.LBM_EIO
         other.close()
+        # same grid and parameters, different solid mask: refused
+        moved = SCENARIOS["cylinder96"]()
+        moved.solid = np.roll(moved.solid, 1, axis=1)
+        moved.rhoA0 = np.where(moved.solid == 1, 0.0, np.maximum(moved.rhoA0, 0.03))
+        moved.rhoB0 = np.where(moved.solid == 1, 0.0, np.maximum(moved.rhoB0, 0.03))
+        other = lbm.Lattice(moved, "f32")
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_load(other.ctx, p)
+        assert e.value.status == lbm.LBM_EIO
+        other.close()
+        # same case built from a parameter struct whose padding bytes hold garbage: accepted
+        g = lbm.make_grid(sc.nx, sc.ny, sc.bc_x, sc.bc_y)
+        par = lbm.make_params(**sc.params(), rho0_store=sc.rho0_store)  # as lbm.Lattice builds it
+        raw_par = bytearray(bytes(par))
+        mode_end = lbm.lbm_params.mode.offset + 4
+        raw_par[mode_end:lbm.lbm_params.lambda_.offset] = b"\xab" * (lbm.lbm_params.lambda_.offset - mode_end)
+        raw_par[lbm.lbm_params.pad_.offset:lbm.lbm_params.pad_.offset + 4] = b"\xcd" * 4
+        par2 = lbm.lbm_params.from_buffer_copy(bytes(raw_par))
+        ctx2 = lbm.lbm_create(g, sc.solid, par2, sc.rhoA0, sc.rhoB0, lbm.LBM_STORE_F32)
+        lbm.lbm_load(ctx2, p)
+        lbm.lbm_step(ctx2, 13)
+        twin = lbm.lbm_get_populations(ctx2, 0, sc.ny, sc.nx)
+        np.testing.assert_array_equal(twin, a)
+        lbm.lbm_destroy(ctx2)
         # a truncated file and a file with a damaged header are refused, and the state is untouched
         raw = open(p, "rb").read()
         for name, data in (("cut", raw[: len(raw) // 2]), ("magic", b"X" + raw[1:]), ("header", raw[:12] + b"\x7f" + raw[13:])):

@@ -28,14 +28,13 @@ def _compare(got, ref):
     assert got["n_fluid"] == ref["n_fluid"] and got["unstable"] == ref["unstable"] == 0
 
 
-def test_noalloc_diagnostics_match_the_context_diagnostics_on_consecutive_calls():
+def _check_consecutive_calls(cases, steps):
     torch = pytest.importorskip("torch")
     assert torch.cuda.is_available()
     # FP64 storage: both paths then form every sum in double precision and the FP64 diagnostics
     # tolerances of the parity tests apply
-    cases = [S.cylinder_droplet(96, lam=0.6), S.flat_droplet(200, 150, r=30, lam=1.3)]
     lat = lbm.Lattice(cases, "f64")
-    lat.step(40)
+    lat.step(steps)
     for case, sc in enumerate(cases):
         ref = lat.diagnostics(case)
         bufs = [torch.empty((sc.ny, sc.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
@@ -46,7 +45,28 @@ def test_noalloc_diagnostics_match_the_context_diagnostics_on_consecutive_calls(
         for _ in range(2):  # two calls in a row share the scratch array
             got = lbm.lbm_diagnostics_noalloc(*bufs, solid, sc.nx, sc.ny)
             _compare(got, ref)
+        del bufs, solid
+        torch.cuda.empty_cache()
     lat.close()
+
+
+def test_noalloc_diagnostics_match_the_context_diagnostics_on_consecutive_calls():
+    """Small lattices: 3 and 8 blocks of 4,096 nodes, fewer than one per lane of the final combine."""
+    _check_consecutive_calls([S.cylinder_droplet(96, lam=0.6), S.flat_droplet(200, 150, r=30, lam=1.3)], 40)
+
+
+def test_noalloc_diagnostics_on_a_1024_squared_lattice():
+    """256 blocks: every lane of the final combine adds eight block records in block order."""
+    _check_consecutive_calls([S.cylinder_droplet(1024, R=160.0, r=200.0, lam=0.7)], 6)
+
+
+def test_noalloc_diagnostics_at_the_node_limit():
+    """Exactly 16,777,216 nodes (4096 x 4096, periodic, one cylinder): all 4,096 block records of
+    the scratch array are written and combined (128 per lane)."""
+    sc = S.cylinder_in_box(nx=4096, ny=4096, R=600.0, centre=(2048.0, 1400.0), r=700.0, drop=(2048.0, 2600.0),
+                           lam=1.2)
+    assert sc.nx * sc.ny == 16_777_216
+    _check_consecutive_calls([sc], 2)
 
 
 def test_noalloc_diagnostics_reject_lattices_beyond_the_scratch_limit():
