@@ -69,6 +69,8 @@ def parse(argv=None):
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--wall-inline", type=int, default=None, choices=[0, 1],
+                    help="with --no-autotune: the step kernel's wall-list form (1 inlined, 0 called)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--split", action="store_true",
@@ -482,6 +484,8 @@ def run_ours(args):
     # launch shape (row-chunk height, wall-list path) picked by the library's autotuner on the live
     # state, before the timed region
     tuned_ms = None if args.no_autotune else lbm.lbm_autotune(lat.ctx, 4)
+    if args.no_autotune and args.wall_inline is not None:
+        lbm.lbm_set_wall_path(lat.ctx, args.wall_inline)
     info = lat.info()
     nodes = info["nodes"]
     fluid = info["fluid_nodes"]
@@ -493,14 +497,18 @@ def run_ours(args):
 
     def bench_step(ev_pairs=None):
         if ev_pairs is not None:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
         lat.step(args.inner)
         if ev_pairs is not None:
-            b.record(stream)
-            ev_pairs.append((a, b))
+            ev[1].record(stream)
         lat.diagnostics_all(allow_unstable=True)
+        if ev_pairs is not None:
+            ev[2].record(stream)
         contact_angles()
+        if ev_pairs is not None:
+            ev[3].record(stream)
+            ev_pairs.append(ev)
 
     for _ in range(args.warmup):
         bench_step()
@@ -521,7 +529,10 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
-    step_ms = sum(a.elapsed_time(b) for a, b in pairs)
+    step_ms = sum(e[0].elapsed_time(e[1]) for e in pairs)
+    phase_ms = {"time_steps": step_ms / args.steps,
+                "diagnostics": sum(e[1].elapsed_time(e[2]) for e in pairs) / args.steps,
+                "contact_angle": sum(e[2].elapsed_time(e[3]) for e in pairs) / args.steps}
     ms_per_step = total_ms / args.steps
     value = job_mlups(weight, job_nodes, args.inner * args.steps, total_ms)
     launch_ms = step_ms / (args.inner * args.steps)
@@ -572,10 +583,10 @@ def run_ours(args):
                        "all cases)" % args.inner}
 
     # step kernels (+ the sliding-wall fix-up after each step where walls slide) + (fields pass +
-    # per-case reductions) + batched contact angle (4 point passes + 4 solves) when any case has a
-    # surface; the contact angle's densities come from the diagnostics pass just before it
+    # per-case reductions) + batched contact angle (one point pass + one fit launch) when any case has
+    # a surface; the contact angle's densities come from the diagnostics pass just before it
     sliding = any(tuple(c.u_wall) != (0.0, 0.0) for c in cases)
-    launches = args.inner * (2 if sliding else 1) + 2 + (8 if any(sf is not None for sf in surfaces) else 0)
+    launches = args.inner * (2 if sliding else 1) + 2 + (2 if any(sf is not None for sf in surfaces) else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong" if args.split else "weak",
@@ -588,7 +599,7 @@ def run_ours(args):
                    "grid_blocks": info["grid_blocks"], "work_items": info["work_items"],
                    "wall_inline": info["wall_inline"], "autotuned": tuned_ms is not None,
                    "autotune_best_ms": tuned_ms},
-        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
+        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk, "phase_ms_per_step": phase_ms,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
         **({"scheme_comparison": [{"case": c.name, "lambda": c.lam, "scheme": c.scheme, "theta_deg": t,
                                    "umax": x["umax"], "rhoA_min": x["rhoA_min"], "rhoA_max": x["rhoA_max"],
@@ -734,7 +745,10 @@ def run_ours_3d(args):
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
-    step_ms = sum(a.elapsed_time(b) for a, b in pairs)
+    step_ms = sum(e[0].elapsed_time(e[1]) for e in pairs)
+    phase_ms = {"time_steps": step_ms / args.steps,
+                "diagnostics": sum(e[1].elapsed_time(e[2]) for e in pairs) / args.steps,
+                "contact_angle": sum(e[2].elapsed_time(e[3]) for e in pairs) / args.steps}
     launch_ms = step_ms / (args.inner * args.steps)  # one time step: density pass + march pass
     algo = BYTES_PER_NODE_3D[args.storage] * fluid
     peak, peak_kind = hbm_peak()

@@ -358,7 +358,7 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 void free_ctx(Ctx& c) {
     drop_graphs(c);
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
-                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.fields_all, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
+                    c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.ca_points, c.fields_all, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -801,7 +801,14 @@ lbm_status lbm_contact_angle(lbm_ctx* ctx, int32_t ci, const lbm_surface* surfac
         c.fields_version = c.version;
     }
     double o[4];
-    CUDA_TRY(launch_contact_angle(c, ci, *surface, o));
+    {
+        const cudaError_t e = launch_contact_angle(c, ci, *surface, o);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();  // clear the (non-sticky) allocation error
+            return fail(LBM_ENOMEM, "contact angle: out of device memory for the interface points");
+        }
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "contact angle: %s", cudaGetErrorString(e));
+    }
     if (npoints) *npoints = (int64_t)llround(o[2]);
     if (o[3] != 0.0) return fail(LBM_ESTATE, "case %d: only %.0f interface points", ci, o[2]);
     if (theta_deg) *theta_deg = o[0];
@@ -879,7 +886,7 @@ lbm_status lbm_contact_angle_all(lbm_ctx* ctx, const lbm_surface* surfaces, doub
         const cudaError_t e = enqueue_contact_angle_all(c, surfaces);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();  // clear the (non-sticky) allocation error
-            return fail(LBM_ENOMEM, "batched contact angle: out of device memory for the densities of all cases");
+            return fail(LBM_ENOMEM, "batched contact angle: out of device memory for the densities and points");
         }
         if (e != cudaSuccess) return fail(LBM_ECUDA, "batched contact angle: %s", cudaGetErrorString(e));
     }

@@ -8,8 +8,13 @@
 // residuals |p - c| - r.  Angle: cos theta = (R^2 + r^2 - d^2) / (2 r R) for a circular solid of
 // centre distance d; cos theta = -normal (c_y - y_w) / r for a flat wall.
 //
-// Every reduction writes one partial record per block, and a single thread combines the records in
-// block order, so results do not depend on scheduling.
+// Two launches per call.  The point pass reads the flags and the FP64 densities of every node once
+// and writes the crossings as keys (2 s + direction, s = Y nx + X) into a fixed segment per block of
+// 4,096 nodes, in a fixed order; the sign test of rho^e is an integer compare of the densities' bit
+// patterns (off the FP64 pipe, which is slow on this GPU), the interpolation is formed only at
+// crossings.  The fit runs one block per case over those points: centroid, Kasa moments, the
+// Gauss-Newton normal equations and the residual, each as a block sum in a fixed order, so results
+// do not depend on scheduling and the single-case and the batched call agree bit for bit.
 #include <math.h>
 
 #include <vector>
@@ -20,128 +25,123 @@ namespace lbm {
 
 namespace {
 
-constexpr int kCaThreads = 256;
-constexpr int kCaBlocks = 256;             // most blocks per case
-constexpr int kCaNodesPerBlock = 4096;
+constexpr int kCaThreads = 256;                                  // threads of a point block
+constexpr int kCaPerThread = 16;                                 // nodes per thread of a point block
+constexpr int kCaNodesPerBlock = kCaThreads * kCaPerThread;      // 4,096 consecutive nodes
+constexpr int kCaKeysPerBlock = 2 * kCaNodesPerBlock;            // at most two points per node
+constexpr int kCaFitThreads = 256;
+constexpr int kCaCache = 2048;                                   // points the fit keeps in shared memory
 constexpr int kCaVals = 9;
 
-// blocks of one case's passes: one per 4,096 nodes, 1..256 (the same in the single-case and the
-// batched call, so both sum the same partial records in the same order)
-int ca_blocks(long long n) {
-    const long long b = (n + kCaNodesPerBlock - 1) / kCaNodesPerBlock;
-    return (int)(b < 1 ? 1 : (b > kCaBlocks ? kCaBlocks : b));
-}
+// point blocks of one case: one per 4,096 nodes (the same in the single-case and the batched call,
+// so that both find the same points in the same order)
+int ca_blocks(long long n) { return (int)((n + kCaNodesPerBlock - 1) / kCaNodesPerBlock); }
 
-struct CaGeo {
+// One case of a contact-angle launch.
+struct CaCase {
     int nx, ny;
     const uint16_t* flags;  // node flags of the case
-    const double* rA;
+    const double* rA;       // FP64 densities of the case, [ny][nx]
     const double* rB;
+    lbm_surface surf;
+    long long blk;          // first point block: keys at blk * kCaKeysPerBlock, counts at blk
+    long long pfx;          // first entry of the case's prefix of the block counts (nb + 1 entries)
+    int nb;                 // point blocks
+    double* st;             // 16-double status record
 };
 
 // fluid and more than three cells from any non-fluid site (precomputed by the flags kernel)
-__device__ bool usable(const CaGeo& g, int X, int Y) {
-    return (g.flags[(long long)Y * g.nx + X] & (kSolidBit | kNearSolidBit)) == 0;
+__device__ __forceinline__ bool usable(uint16_t fl) { return (fl & (kSolidBit | kNearSolidBit)) == 0; }
+
+__device__ __forceinline__ double phi_of(double ra, double rb) { return (ra - rb) / (ra + rb); }
+
+// phi > 0 without the division and off the FP64 pipe.  When both densities lie in (0, 2^1023) the
+// sum is positive and finite, so phi has the sign of ra - rb (a difference of unequal doubles is
+// never zero), and positive doubles order like their bit patterns read as integers.  Any other
+// value (zero, negative, huge, non-finite) takes the quotient itself.
+__device__ __forceinline__ bool phi_positive(double ra, double rb) {
+    const long long ia = __double_as_longlong(ra), ib = __double_as_longlong(rb);
+    constexpr long long kLo = 1, kHi = 0x7FDFFFFFFFFFFFFFLL;  // smallest subnormal .. largest double below 2^1023
+    if (ia >= kLo && ia <= kHi && ib >= kLo && ib <= kHi) return ia > ib;
+    return phi_of(ra, rb) > 0.0;
 }
 
-__device__ double phi_of(double ra, double rb) { return (ra - rb) / (ra + rb); }
-
-// phi > 0 without the division where 0 < rho_A + rho_B < inf: the quotient then has the sign of
-// the difference, which is at least an ulp of the larger density and cannot underflow to zero.
-__device__ bool phi_positive(double ra, double rb) {
-    const double sum = ra + rb;
-    return (sum > 0.0 && sum < INFINITY) ? ra > rb : phi_of(ra, rb) > 0.0;
+// Crossings owned by node s = Y nx + X: towards (X+1, Y) (h) and towards (X, Y+1) (v).
+__device__ __forceinline__ void crossings(const CaCase& C, long long s, int X, int Y, int& h, int& v) {
+    h = v = 0;
+    if (!usable(C.flags[s])) return;
+    const bool pa = phi_positive(C.rA[s], C.rB[s]);
+    if (X + 1 < C.nx && usable(C.flags[s + 1])) h = pa != phi_positive(C.rA[s + 1], C.rB[s + 1]);
+    if (Y + 1 < C.ny && usable(C.flags[s + C.nx])) v = pa != phi_positive(C.rA[s + C.nx], C.rB[s + C.nx]);
 }
 
-// Up to two crossing points owned by node (X, Y): towards (X+1, Y) and towards (X, Y+1).  phi is
-// formed only at the two ends of a crossing.
-__device__ int node_points(const CaGeo& g, int X, int Y, double* px, double* py) {
-    int n = 0;
-    if (!usable(g, X, Y)) return 0;
-    const long long s = (long long)Y * g.nx + X;
-    const double ra = g.rA[s], rb = g.rB[s];
-    const bool pa = phi_positive(ra, rb);
-    if (X + 1 < g.nx && usable(g, X + 1, Y)) {
-        const double qa = g.rA[s + 1], qb = g.rB[s + 1];
-        if (pa != phi_positive(qa, qb)) {
-            const double a = phi_of(ra, rb), b = phi_of(qa, qb);
-            px[n] = X + a / (a - b);
-            py[n] = (double)Y;
-            ++n;
-        }
-    }
-    if (Y + 1 < g.ny && usable(g, X, Y + 1)) {
-        const double qa = g.rA[s + g.nx], qb = g.rB[s + g.nx];
-        if (pa != phi_positive(qa, qb)) {
-            const double a = phi_of(ra, rb), b = phi_of(qa, qb);
-            px[n] = (double)X;
-            py[n] = Y + a / (a - b);
-            ++n;
-        }
-    }
-    return n;
+// Interface point of key = 2 s + dir: the zero of the linear interpolation of phi between node s
+// and its neighbour along x (dir 0) or y (dir 1).
+__device__ __forceinline__ void point_of(const CaCase& C, uint32_t key, double& px, double& py) {
+    const int si = (int)(key >> 1);  // < 2^31: lattices hold at most 2^31 - 1 nodes
+    const long long s = si;
+    const long long q = (key & 1u) ? s + C.nx : s + 1;
+    const int X = si % C.nx, Y = si / C.nx;
+    const double a = phi_of(C.rA[s], C.rB[s]), b = phi_of(C.rA[q], C.rB[q]);
+    const double f = a / (a - b);
+    px = (key & 1u) ? (double)X : X + f;
+    py = (key & 1u) ? Y + f : (double)Y;
 }
 
-// st: 0 N, 1 xm, 2 ym, 3 cx, 4 cy, 5 r, 6 rms, 7 theta, 8 status (0 ok, 1 too few points)
-// Block lb of nb of one case: nodes lb * threads + tid, strided by nb * threads; its partial record
-// goes to out[0 .. kCaVals).
-__device__ void ca_pass_block(const CaGeo& g, int lb, int nb, int pass, const double* __restrict__ st,
-                              double* __restrict__ out) {
-    double acc[kCaVals];
-    for (int q = 0; q < kCaVals; ++q) acc[q] = 0.0;
-    const long long N = (long long)g.nx * g.ny;
-    const double xm = st[1], ym = st[2], cxv = st[3], cyv = st[4], r = st[5];
-    // node s = Y nx + X advanced by a fixed stride: one division per thread, not per node
-    const long long s0 = lb * (long long)blockDim.x + threadIdx.x, stride = (long long)nb * blockDim.x;
-    const int dX = (int)(stride % g.nx), dY = (int)(stride / g.nx);
-    int X = (int)(s0 % g.nx), Y = (int)(s0 / g.nx);
-    for (long long s = s0; s < N; s += stride) {
-        if (s != s0) {
-            X += dX;
-            Y += dY;
-            if (X >= g.nx) {
-                X -= g.nx;
+// Point pass: block (lb, case) scans nodes [lb * 4096, +4096) of its case, thread t the nodes
+// lb * 4096 + k * 256 + t (k = 0..15), and writes the keys of the crossings it finds to the block's
+// segment in a fixed order (k, then node, horizontal before vertical), and their count.
+__global__ void __launch_bounds__(kCaThreads) k_ca_points(const CaCase* __restrict__ cases, uint32_t* __restrict__ keys,
+                                                          int* __restrict__ counts) {
+    const CaCase& C = cases[blockIdx.y];
+    const int lb = blockIdx.x;
+    if (lb >= C.nb || C.surf.kind == LBM_SURFACE_NONE) return;
+    const long long N = (long long)C.nx * C.ny;
+    uint32_t* out = keys + (C.blk + lb) * (long long)kCaKeysPerBlock;
+    __shared__ int wsum[2][kCaThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long base = (long long)lb * kCaNodesPerBlock;
+    // (X, Y) of this thread's node, advanced by a fixed stride: one division per thread
+    int X = (int)((base + t) % C.nx), Y = (int)((base + t) / C.nx);
+    int running = 0;
+    for (int k = 0; k < kCaPerThread; ++k) {
+        const long long s = base + k * kCaThreads + t;
+        if (k > 0) {
+            X += kCaThreads;
+            while (X >= C.nx) {
+                X -= C.nx;
                 ++Y;
             }
         }
-        double px[2], py[2];
-        const int n = node_points(g, X, Y, px, py);
-        for (int k = 0; k < n; ++k) {
-            if (pass == 0) {
-                acc[0] += 1.0;
-                acc[1] += px[k];
-                acc[2] += py[k];
-            } else if (pass == 1) {
-                const double u = px[k] - xm, v = py[k] - ym;
-                acc[0] += u * u;
-                acc[1] += u * v;
-                acc[2] += v * v;
-                acc[3] += u * u * u;
-                acc[4] += u * v * v;
-                acc[5] += v * v * v;
-                acc[6] += v * u * u;
-            } else if (pass == 2) {
-                const double dx = px[k] - cxv, dy = py[k] - cyv;
-                const double d = sqrt(dx * dx + dy * dy);
-                const double res = d - r;
-                const double j0 = -dx / d, j1 = -dy / d, j2 = -1.0;
-                acc[0] += j0 * j0;
-                acc[1] += j0 * j1;
-                acc[2] += j0 * j2;
-                acc[3] += j1 * j1;
-                acc[4] += j1 * j2;
-                acc[5] += j2 * j2;
-                acc[6] += j0 * res;
-                acc[7] += j1 * res;
-                acc[8] += j2 * res;
-            } else {
-                const double dx = px[k] - cxv, dy = py[k] - cyv;
-                const double res = sqrt(dx * dx + dy * dy) - r;
-                acc[0] += res * res;
-            }
+        int h = 0, v = 0;
+        if (s < N) crossings(C, s, X, Y, h, v);
+        const int c = h + v;
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
         }
+        if (lane == 31) wsum[k & 1][warp] = incl;
+        __syncthreads();  // (one buffer per parity: the next writer of this one is two barriers away)
+        int before = running, total = 0;
+#pragma unroll
+        for (int w = 0; w < kCaThreads / 32; ++w) {
+            const int x = wsum[k & 1][w];
+            before += w < warp ? x : 0;
+            total += x;
+        }
+        int pos = before + incl - c;
+        if (h) out[pos++] = (uint32_t)(2 * s);
+        if (v) out[pos] = (uint32_t)(2 * s + 1);
+        running += total;
     }
-    __shared__ double red[kCaThreads / 32][kCaVals];
+    if (t == 0) counts[C.blk + lb] = running;
+}
+
+// Block-wide sum of kCaVals per-thread values in a fixed order (lane butterfly, then the warps in
+// order); the result is valid in thread 0.
+__device__ void block_sum(const double* acc, double (*red)[kCaVals], double* S) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < kCaVals; ++q) {
         double v = acc[q];
@@ -152,43 +152,9 @@ __device__ void ca_pass_block(const CaGeo& g, int lb, int nb, int pass, const do
     if (threadIdx.x == 0)
         for (int q = 0; q < kCaVals; ++q) {
             double v = 0.0;
-            for (int w = 0; w < kCaThreads / 32; ++w) v += red[w][q];
-            out[q] = v;
+            for (int w = 0; w < kCaFitThreads / 32; ++w) v += red[w][q];
+            S[q] = v;
         }
-}
-
-__global__ void k_ca_pass(CaGeo g, int pass, const double* __restrict__ st, double* __restrict__ part) {
-    ca_pass_block(g, blockIdx.x, gridDim.x, pass, st, part + (long long)blockIdx.x * kCaVals);
-}
-
-// Batched passes: block b belongs to case blk_case[b], whose blocks are [blk0[case], blk0[case+1]).
-struct CaBatch {
-    const CaGeo* geo;          // per case
-    const int* blk_case;       // per block
-    const int* blk0;           // per case + 1
-    const lbm_surface* surf;   // per case
-    double* st;                // per case: 16-double status record
-    double* part;              // per block: kCaVals partial sums
-};
-
-__global__ void k_ca_pass_all(CaBatch b, int pass) {
-    const int ci = b.blk_case[blockIdx.x];
-    if (b.surf[ci].kind == LBM_SURFACE_NONE) return;  // skipped: its partials are never read
-    const int b0 = b.blk0[ci];
-    ca_pass_block(b.geo[ci], blockIdx.x - b0, b.blk0[ci + 1] - b0, pass, b.st + 16 * (long long)ci,
-                  b.part + (long long)blockIdx.x * kCaVals);
-}
-
-// Sum of the per-block partial records by one warp: lane l adds blocks l, l+32, ... in order, then
-// a fixed butterfly combines the lanes (deterministic).
-__device__ void sum_parts(const double* part, int nblocks, double* out) {
-    const int lane = threadIdx.x & 31;
-    for (int q = 0; q < kCaVals; ++q) {
-        double v = 0.0;
-        for (int b = lane; b < nblocks; b += 32) v += part[b * kCaVals + q];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        out[q] = v;
-    }
 }
 
 // 3x3 solve by Gaussian elimination with partial pivoting.
@@ -218,18 +184,14 @@ __device__ void solve3(double A[3][3], double b[3], double x[3]) {
     }
 }
 
-__device__ void ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
-                         const lbm_surface& surf) {
-    double S[kCaVals];
-    sum_parts(part, nblocks, S);  // the whole warp
-    if (threadIdx.x != 0) return;
+// st: 0 N, 1 xm, 2 ym, 3 cx, 4 cy, 5 r, 6 rms, 7 theta, 8 status (0 ok, 1 too few points).
+// Stage 0 centroid; 1 Kasa fit in centroid coordinates; 2 one Gauss-Newton step on |p - c| - r;
+// 3 rms residual and the angle.
+__device__ void ca_solve(int pass, const double* S, double* st, const lbm_surface& surf) {
     if (pass == 0) {
-        st[0] = S[0];
-        st[8] = S[0] < 8.0 ? 1.0 : 0.0;
-        st[1] = S[0] > 0.0 ? S[1] / S[0] : 0.0;
-        st[2] = S[0] > 0.0 ? S[2] / S[0] : 0.0;
+        st[1] = S[1] / st[0];
+        st[2] = S[2] / st[0];
     } else if (pass == 1) {
-        if (st[8] != 0.0) return;
         const double Suu = S[0], Suv = S[1], Svv = S[2];
         const double b0 = 0.5 * (S[3] + S[4]), b1 = 0.5 * (S[5] + S[6]);
         const double det = Suu * Svv - Suv * Suv;
@@ -239,7 +201,6 @@ __device__ void ca_solve(int pass, int nblocks, const double* __restrict__ part,
         st[3] = st[1] + uc;
         st[4] = st[2] + vc;
     } else if (pass == 2) {
-        if (st[8] != 0.0) return;
         double A[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
         double b[3] = {-S[6], -S[7], -S[8]};
         double d[3];
@@ -248,7 +209,6 @@ __device__ void ca_solve(int pass, int nblocks, const double* __restrict__ part,
         st[4] += d[1];
         st[5] += d[2];
     } else {
-        if (st[8] != 0.0) return;
         st[6] = sqrt(S[0] / st[0]);
         const double cxv = st[3], cyv = st[4], r = st[5];
         double c;
@@ -263,91 +223,228 @@ __device__ void ca_solve(int pass, int nblocks, const double* __restrict__ part,
     }
 }
 
-__global__ void k_ca_solve(int pass, int nblocks, const double* __restrict__ part, double* __restrict__ st,
-                           lbm_surface surf) {
-    ca_solve(pass, nblocks, part, st, surf);
+// Fit: one block per case.  The block counts of the point pass are turned into a prefix, so that
+// point j of the case (in the pass's order) is found by a binary search; thread t takes points
+// t, t + 256, ... in every stage, so each stage's sums are formed in a fixed order.  The first
+// kCaCache points are kept in shared memory after the first stage.
+__global__ void __launch_bounds__(kCaFitThreads) k_ca_fit(const CaCase* __restrict__ cases,
+                                                          const uint32_t* __restrict__ keys,
+                                                          const int* __restrict__ counts, long long* __restrict__ pfx_all) {
+    const CaCase& C = cases[blockIdx.x];
+    if (C.surf.kind == LBM_SURFACE_NONE) return;
+    __shared__ double2 cache[kCaCache];
+    __shared__ double red[kCaFitThreads / 32][kCaVals];
+    __shared__ double sst[16];
+    __shared__ int scan_w[kCaFitThreads / 32];
+    __shared__ long long carry;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    long long* P = pfx_all + C.pfx;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < C.nb; b0 += kCaFitThreads) {
+        const int b = b0 + t;
+        const int c = b < C.nb ? counts[C.blk + b] : 0;
+        int incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) scan_w[warp] = incl;
+        __syncthreads();
+        long long before = carry, total = 0;
+        for (int w = 0; w < kCaFitThreads / 32; ++w) {
+            before += w < warp ? scan_w[w] : 0;
+            total += scan_w[w];
+        }
+        if (b < C.nb) P[b] = before + incl - c;
+        __syncthreads();
+        if (t == 0) carry += total;
+        __syncthreads();
+    }
+    const long long N = carry;
+    if (t == 0) P[C.nb] = N;
+    if (t < 16) sst[t] = 0.0;
+    __syncthreads();
+    if (t == 0) {
+        sst[0] = (double)N;
+        sst[8] = N < 8 ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (N >= 8) {
+        auto point = [&](long long j, double& px, double& py) {
+            int lo = 0, hi = C.nb - 1;  // the last block whose first point is at or before j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            point_of(C, keys[(C.blk + lo) * (long long)kCaKeysPerBlock + (j - P[lo])], px, py);
+        };
+        for (int pass = 0; pass < 4; ++pass) {
+            double acc[kCaVals];
+            for (int q = 0; q < kCaVals; ++q) acc[q] = 0.0;
+            const double xm = sst[1], ym = sst[2], cxv = sst[3], cyv = sst[4], r = sst[5];
+            for (long long j = t; j < N; j += kCaFitThreads) {
+                double px, py;
+                if (pass > 0 && j < kCaCache) {
+                    px = cache[j].x;
+                    py = cache[j].y;
+                } else {
+                    point(j, px, py);
+                    if (j < kCaCache) cache[j] = make_double2(px, py);
+                }
+                if (pass == 0) {
+                    acc[1] += px;
+                    acc[2] += py;
+                } else if (pass == 1) {
+                    const double u = px - xm, v = py - ym;
+                    acc[0] += u * u;
+                    acc[1] += u * v;
+                    acc[2] += v * v;
+                    acc[3] += u * u * u;
+                    acc[4] += u * v * v;
+                    acc[5] += v * v * v;
+                    acc[6] += v * u * u;
+                } else if (pass == 2) {
+                    const double dx = px - cxv, dy = py - cyv;
+                    const double d = sqrt(dx * dx + dy * dy);
+                    const double res = d - r;
+                    const double j0 = -dx / d, j1 = -dy / d, j2 = -1.0;
+                    acc[0] += j0 * j0;
+                    acc[1] += j0 * j1;
+                    acc[2] += j0 * j2;
+                    acc[3] += j1 * j1;
+                    acc[4] += j1 * j2;
+                    acc[5] += j2 * j2;
+                    acc[6] += j0 * res;
+                    acc[7] += j1 * res;
+                    acc[8] += j2 * res;
+                } else {
+                    const double dx = px - cxv, dy = py - cyv;
+                    const double res = sqrt(dx * dx + dy * dy) - r;
+                    acc[0] += res * res;
+                }
+            }
+            double S[kCaVals];
+            block_sum(acc, red, S);
+            if (t == 0) ca_solve(pass, S, sst, C.surf);
+            __syncthreads();
+        }
+    }
+    if (t < 16) C.st[t] = sst[t];
 }
 
-// one warp per case
-__global__ void k_ca_solve_all(CaBatch b, int pass) {
-    const int ci = blockIdx.x;
-    const lbm_surface surf = b.surf[ci];
-    if (surf.kind == LBM_SURFACE_NONE) return;
-    const int b0 = b.blk0[ci];
-    ca_solve(pass, b.blk0[ci + 1] - b0, b.part + (long long)b0 * kCaVals, b.st + 16 * (long long)ci, surf);
+// Device tables of the contact-angle launches: ncases + 1 case records (the last one serves the
+// single-case call), the keys and counts of every case's point blocks, and the prefixes.
+struct CaLayout {
+    size_t o_cases, o_keys, o_counts, o_pfx, total;
+    std::vector<long long> blk, pfx;
+    std::vector<int> nb;
+    long long nblk = 0;
+    explicit CaLayout(const Ctx& c) {
+        const int n = (int)c.hcases.size();
+        blk.resize(n);
+        pfx.resize(n);
+        nb.resize(n);
+        long long p = 0;
+        for (int i = 0; i < n; ++i) {
+            nb[i] = ca_blocks((long long)c.hcases[i].nx * c.hcases[i].ny);
+            blk[i] = nblk;
+            pfx[i] = p;
+            nblk += nb[i];
+            p += nb[i] + 1;
+        }
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        o_cases = 0;
+        o_keys = al((size_t)(n + 1) * sizeof(CaCase));
+        o_counts = o_keys + al((size_t)nblk * kCaKeysPerBlock * sizeof(uint32_t));
+        o_pfx = o_counts + al((size_t)nblk * sizeof(int));
+        total = o_pfx + al((size_t)p * sizeof(long long));
+    }
+};
+
+cudaError_t ensure_points(Ctx& c) {
+    if (c.ca_points) return cudaSuccess;
+    const CaLayout L(c);
+    cudaError_t e = cudaMalloc(&c.ca_points, L.total);
+    if (e != cudaSuccess) {
+        c.ca_points = nullptr;
+        return e;
+    }
+    c.device_bytes += (long long)L.total;
+    return cudaSuccess;
+}
+
+CaCase case_record(const Ctx& c, const CaLayout& L, int i, const double* rA, const double* rB,
+                   const lbm_surface& surf, double* st) {
+    const DevCase& d = c.hcases[i];
+    return CaCase{d.nx, d.ny, c.flags + d.d_off, rA, rB, surf, L.blk[i], L.pfx[i], L.nb[i], st};
+}
+
+cudaError_t launch_ca(Ctx& c, const CaLayout& L, int first_record, int nrec, int max_nb) {
+    const CaCase* cases = reinterpret_cast<const CaCase*>(c.ca_points + L.o_cases) + first_record;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(c.ca_points + L.o_keys);
+    int* counts = reinterpret_cast<int*>(c.ca_points + L.o_counts);
+    long long* pfx = reinterpret_cast<long long*>(c.ca_points + L.o_pfx);
+    for (int c0 = 0; c0 < nrec; c0 += 65535) {  // grid y: at most 65,535 cases per launch
+        const int m = nrec - c0 < 65535 ? nrec - c0 : 65535;
+        k_ca_points<<<dim3((unsigned)max_nb, (unsigned)m), kCaThreads, 0, c.stream>>>(cases + c0, keys, counts);
+    }
+    k_ca_fit<<<(unsigned)nrec, kCaFitThreads, 0, c.stream>>>(cases, keys, counts, pfx);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-// ctx->fields must already hold rho_A, rho_B of the case (dense).  host_out4 <- theta, rms, npoints,
-// status.
+// ctx->fields must already hold rho_A, rho_B of the case (dense).  The 16-double status record st
+// (device) receives theta at [7], rms at [6], points at [0], the too-few-points flag at [8].
 cudaError_t enqueue_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* st) {
-    const DevCase& C = c.hcases[ci];
-    const long long N = (long long)C.nx * C.ny;
-    CaGeo g{C.nx, C.ny, c.flags + C.d_off, c.fields, c.fields + N};
-    double* part = c.ca_work + 16;
-    const int nb = ca_blocks(N);
-    cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c.stream);
+    cudaError_t e = ensure_points(c);
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < 4; ++pass) {
-        k_ca_pass<<<nb, kCaThreads, 0, c.stream>>>(g, pass, st, part);
-        k_ca_solve<<<1, 32, 0, c.stream>>>(pass, nb, part, st, surf);
-    }
-    return cudaGetLastError();
+    const CaLayout L(c);
+    const int n = (int)c.hcases.size();
+    const long long N = (long long)c.hcases[ci].nx * c.hcases[ci].ny;
+    const CaCase rec = case_record(c, L, ci, c.fields, c.fields + N, surf, st);
+    e = cudaMemcpyAsync(c.ca_points + L.o_cases + (size_t)n * sizeof(CaCase), &rec, sizeof rec,
+                        cudaMemcpyHostToDevice, c.stream);
+    if (e != cudaSuccess) return e;
+    return launch_ca(c, L, n, 1, L.nb[ci]);
 }
 
 cudaError_t enqueue_contact_angle_all(Ctx& c, const lbm_surface* surf) {
     const int n = (int)c.hcases.size();
-    // block tables
-    std::vector<int> blk0(n + 1), blk_case;
-    for (int i = 0; i < n; ++i) {
-        blk0[i] = (int)blk_case.size();
-        const int nb = ca_blocks((long long)c.hcases[i].nx * c.hcases[i].ny);
-        blk_case.insert(blk_case.end(), nb, i);
-    }
-    blk0[n] = (int)blk_case.size();
-    const int nblk = blk0[n];
-    // one allocation: densities [2][dense_elems], geometry, tables, partials, surfaces
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t o_rho = 0, o_geo = al(2 * (size_t)c.dense_elems * sizeof(double));
-    const size_t o_bc = o_geo + al(n * sizeof(CaGeo)), o_b0 = o_bc + al(nblk * sizeof(int));
-    const size_t o_part = o_b0 + al((n + 1) * sizeof(int)), o_surf = o_part + al((size_t)nblk * kCaVals * sizeof(double));
-    const size_t total = o_surf + al(n * sizeof(lbm_surface));
-    cudaError_t e;
-    if (!c.ca_batch) {
-        e = cudaMalloc(&c.ca_batch, total);
-        if (e != cudaSuccess) return e;
-        c.ca_batch_bytes = total;
-        c.device_bytes += (long long)total;
-        double* rho = reinterpret_cast<double*>(c.ca_batch + o_rho);
-        std::vector<CaGeo> geo(n);
-        for (int i = 0; i < n; ++i) {
-            const DevCase& d = c.hcases[i];
-            geo[i] = CaGeo{d.nx, d.ny, c.flags + d.d_off, rho + d.d_off, rho + c.dense_elems + d.d_off};
-        }
-        e = cudaMemcpy(c.ca_batch + o_geo, geo.data(), n * sizeof(CaGeo), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c.ca_batch + o_bc, blk_case.data(), nblk * sizeof(int), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c.ca_batch + o_b0, blk0.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaMemcpyAsync(c.ca_batch + o_surf, surf, n * sizeof(lbm_surface), cudaMemcpyHostToDevice, c.stream);
+    cudaError_t e = ensure_points(c);
     if (e != cudaSuccess) return e;
-    double* rho = reinterpret_cast<double*>(c.ca_batch + o_rho);
+    if (!c.ca_batch) {  // FP64 densities of all cases, [2][dense_elems]
+        const size_t bytes = 2 * (size_t)c.dense_elems * sizeof(double);
+        e = cudaMalloc(&c.ca_batch, bytes);
+        if (e != cudaSuccess) {
+            c.ca_batch = nullptr;
+            return e;
+        }
+        c.ca_batch_bytes = bytes;
+        c.device_bytes += (long long)bytes;
+    }
+    double* rho = reinterpret_cast<double*>(c.ca_batch);
     if (c.ca_rho_version != c.version) {  // not already written at this state by the diagnostics
         e = launch_densities_all(c, rho, rho + c.dense_elems);
         if (e != cudaSuccess) return e;
         c.ca_rho_version = c.version;
     }
+    const CaLayout L(c);
+    std::vector<CaCase> recs(n);
+    int max_nb = 1;
+    for (int i = 0; i < n; ++i) {
+        const DevCase& d = c.hcases[i];
+        recs[i] = case_record(c, L, i, rho + d.d_off, rho + c.dense_elems + d.d_off, surf[i], c.ca_all + 16 * (size_t)i);
+        if (surf[i].kind != LBM_SURFACE_NONE && L.nb[i] > max_nb) max_nb = L.nb[i];
+    }
+    e = cudaMemcpyAsync(c.ca_points + L.o_cases, recs.data(), (size_t)n * sizeof(CaCase), cudaMemcpyHostToDevice,
+                        c.stream);
+    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c.ca_all, 0, (size_t)16 * n * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
-    CaBatch b{reinterpret_cast<const CaGeo*>(c.ca_batch + o_geo), reinterpret_cast<const int*>(c.ca_batch + o_bc),
-              reinterpret_cast<const int*>(c.ca_batch + o_b0), reinterpret_cast<const lbm_surface*>(c.ca_batch + o_surf),
-              c.ca_all, reinterpret_cast<double*>(c.ca_batch + o_part)};
-    for (int pass = 0; pass < 4; ++pass) {
-        k_ca_pass_all<<<nblk, kCaThreads, 0, c.stream>>>(b, pass);
-        k_ca_solve_all<<<n, 32, 0, c.stream>>>(b, pass);
-    }
-    return cudaGetLastError();
+    return launch_ca(c, L, 0, n, max_nb);
 }
 
 cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double* host_out4) {
@@ -366,6 +463,6 @@ cudaError_t launch_contact_angle(Ctx& c, int ci, const lbm_surface& surf, double
     return cudaSuccess;
 }
 
-int contact_work_doubles() { return 16 + kCaBlocks * kCaVals; }
+int contact_work_doubles() { return 16; }
 
 }  // namespace lbm

@@ -77,6 +77,7 @@ struct CaseParams {
     R gx, gy;
     R d1[2], d5[2];            // inlet: f_1 - f_3 and f_5 - f_7 (= f_8 - f_6) of f^eq(rho_in, u_in)
     R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
+    R rho0[2], om_rho0[2];     // rho0 and omega rho0 of the shifted storage (0 for FP32 / FP64)
     int inlet_profile;         // 1: the inlet differences above scale with 4 s (ny - s) / ny^2, s = y + 1/2
     int moving;                // 1: a walled y edge slides (u_wall nonzero)
     R prof_c;                  // 4 / ny^2
@@ -122,6 +123,8 @@ inline void fill_case_params_as(const DevCase& d, CaseParams<R>& P) {
         P.sh0[k] = (R)(wq(0) * d.rho0[k]);
         P.sh1[k] = (R)(wq(1) * d.rho0[k]);
         P.sh5[k] = (R)(wq(5) * d.rho0[k]);
+        P.rho0[k] = (R)d.rho0[k];
+        P.om_rho0[k] = (R)(d.omega[k] * d.rho0[k]);
     }
     P.G = (R)d.G; P.Gw2 = (R)d.Gw2; P.lam = (R)d.lam; P.delta = (R)d.delta;
     P.s1 = (R)d.s1; P.s2 = (R)d.s2; P.s3 = (R)d.s3; P.t2 = (R)d.t2; P.t3 = (R)d.t3;

@@ -89,9 +89,10 @@ struct Ctx {
     double* diag_out = nullptr;      // [ncases][kDiagN]
     double* ca_work = nullptr;       // contact-angle reductions
     double* ca_all = nullptr;        // [ncases][16] contact-angle status records of the batched call
-    unsigned char* ca_batch = nullptr;  // batched contact angle: densities of all cases, block tables,
-    size_t ca_batch_bytes = 0;          // partial sums, surfaces (allocated by its first call)
-    int ca_cap = 0;
+    unsigned char* ca_batch = nullptr;  // batched contact angle: FP64 densities of all cases
+    size_t ca_batch_bytes = 0;          // (allocated by its first call)
+    unsigned char* ca_points = nullptr; // contact angle: case records, interface-point keys (8 B per
+                                        // node of all cases), counts (allocated by the first call)
 
     // CUDA graph of kGraphSteps step launches
     cudaGraphExec_t graph = nullptr;

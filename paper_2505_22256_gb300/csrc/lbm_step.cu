@@ -77,11 +77,12 @@ __device__ __forceinline__ R shift_of(const Params<R>& P, int k, int i) {
     return i == 0 ? P.sh0[k] : (i <= 4 ? P.sh1[k] : P.sh5[k]);
 }
 
-// Load the pair of direction i at p (16-bit types add the storage shift of each component back).
-template <class S, class R>
+// Load the pair of direction i at p.  16-bit types hold h_i = f_i - w_i rho0; kAddShift adds the
+// shift back (f_i), otherwise the pair stays h_i (the step kernel works on h, see collide()).
+template <bool kAddShift, class S, class R>
 __device__ __forceinline__ V2<R> load_v2(const Pair<S>* p, const Params<R>& P, int i) {
     V2<R> v;
-    if constexpr (Store<S>::kShift) load_pair<S, R>(p, shift_of(P, 0, i), shift_of(P, 1, i), v.x, v.y);
+    if constexpr (Store<S>::kShift && kAddShift) load_pair<S, R>(p, shift_of(P, 0, i), shift_of(P, 1, i), v.x, v.y);
     else load_pair<S, R>(p, (R)0, (R)0, v.x, v.y);
     return v;
 }
@@ -92,7 +93,7 @@ __device__ __forceinline__ V2<R> load_v2(const Pair<S>* p, const Params<R>& P, i
 // and with global memory (state read-back).  The plain form assumes no blocked link and no open
 // column.  Pin: the rarely used constants (inlet).
 // ------------------------------------------------------------------------------------------------
-template <bool kGeneral, class S, class R, class I>
+template <bool kGeneral, class S, class R, class I, bool kAddShift = true>
 __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<S>* __restrict__ r0,
                                      const Pair<S>* __restrict__ rp, I ps, int c, uint16_t fl, bool inlet, bool outlet,
                                      const Params<R>& P, const Params<R>& Pin, int y, V2<R> (&f)[9]) {
@@ -115,7 +116,7 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
             src = blocked ? r0 : nsrc;
             off = blocked ? (I)opp(i) * ps + b : (I)i * ps + b - cx(i);
         }
-        f[i] = load_v2<S, R>(src + off, P, i);
+        f[i] = load_v2<kAddShift, S, R>(src + off, P, i);
     }
     if (kGeneral && inlet) {  // non-equilibrium bounce-back about f^eq(rho_in, (u_in(y), 0))
         R sc = (R)1;
@@ -316,23 +317,42 @@ __device__ __noinline__ Grad2<R> substitution_correction_call(const V2<R>* __res
 // and the odd part 3 w (om rho a + cF b).  With P = om rho a + cF b:
 //   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,   f*_0 = (1 - om) f_0 + w_0 C0.
 // Lanes are the components: rho, F, om and cF are (A, B) pairs; u is shared.
+// Lattice weights in the compute type.  FP64 takes 4/9, 1/9, 1/36 rounded to double.  In FP32 those
+// roundings sum to 1 + 7.5e-9, and since every step redistributes each node's mass with them, the
+// mass of an FP32 run grew by that much per step (3e-4 after 50,000 steps); the FP32 set below
+// sums to 1 exactly (w_0 + 4 w_1 + 4 w_5 = (14913082 + 4 * 3728270 + 3728270) 2^-25), and 4.5 w and
+// 3 w are exact in FP32 too.  Each weight is within 7.5e-8 (relative) of its value.
 template <class R>
+struct LatW {
+    static constexpr double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+};
+template <>
+struct LatW<float> {
+    static constexpr double w0 = 14913082.0 / 33554432.0, w1 = 3728270.0 / 33554432.0, w5 = 3728270.0 / 134217728.0;
+};
+
+// Shifted form (kShifted, 16-bit storage): f = h + w rho0 with rho0 per component, and the result
+// is stored as f* - w rho0.  Since (1 - om) w rho0 - w rho0 = -om w rho0 in every direction, the
+// same formula applies to h with C0 replaced by C0 - om rho0 (om_rho0 below), so neither the
+// loads nor the stores handle the shift per population.
+template <class R, bool kShifted = false>
 __device__ __forceinline__ void collide(const V2<R>* f, V2<R> rho, R ux, R uy, V2<R> Fx, V2<R> Fy, V2<R> om,
-                                        V2<R> cf, V2<R> (&out)[9]) {
+                                        V2<R> cf, V2<R> (&out)[9], V2<R> om_rho0 = V2<R>{}) {
     using V = V2<R>;
     const V om1 = vsub(vbc<R>(1), om);
     const V wr = vmul(om, rho);
     const V ux2 = vbc<R>(ux), uy2 = vbc<R>(uy);
     const V t = vfma(vbc<R>(-1.5), vfma(ux2, ux2, vmul(uy2, uy2)), vbc<R>(1));
     const V uF = vfma(uy2, Fy, vmul(ux2, Fx));
-    const V C0 = vfma(wr, t, vmul(vmul(vbc<R>(-3), cf), uF));
-    out[0] = vfma(om1, f[0], vmul(vbc<R>(4.0 / 9.0), C0));
-    const V s1 = vmul(vbc<R>(1.0 / 9.0), C0), s5 = vmul(vbc<R>(1.0 / 36.0), C0);
+    V C0 = vfma(wr, t, vmul(vmul(vbc<R>(-3), cf), uF));
+    if constexpr (kShifted) C0 = vsub(C0, om_rho0);
+    out[0] = vfma(om1, f[0], vmul(vbc<R>(LatW<R>::w0), C0));
+    const V s1 = vmul(vbc<R>(LatW<R>::w1), C0), s5 = vmul(vbc<R>(LatW<R>::w5), C0);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {  // pairs (1,3): e = (1,0); (2,4): (0,1); (5,7): (1,1); (6,8): (-1,1)
         const V a = p == 0 ? ux2 : p == 1 ? uy2 : p == 2 ? vadd(ux2, uy2) : vsub(uy2, ux2);
         const V b = p == 0 ? Fx : p == 1 ? Fy : p == 2 ? vadd(Fx, Fy) : vsub(Fy, Fx);
-        const double w = p < 2 ? 1.0 / 9.0 : 1.0 / 36.0;
+        const double w = p < 2 ? LatW<R>::w1 : LatW<R>::w5;
         const V cb = vmul(cf, b);
         const V P = vfma(wr, a, cb);
         const V sym = vfma(vbc<R>(4.5 * w), vmul(a, vadd(P, cb)), p < 2 ? s1 : s5);
@@ -377,10 +397,15 @@ struct StepArgs {
     double *o_rA, *o_rB, *o_ux, *o_uy, *diag_part;
 };
 
-// blocks per SM the launch bounds ask for: the same registers per thread at either width
+// blocks per SM the launch bounds ask for: the same registers per thread at either width.  16-bit
+// storage fits four 128-thread blocks per SM in shared memory (FP32 three, FP64 two), and needs the
+// warps: its launch is bound by instruction latency, not by DRAM.
+#ifndef LBM_MIN_BLOCKS_16
+#define LBM_MIN_BLOCKS_16 4
+#endif
 template <class S, int T>
 constexpr int step_min_blocks() {
-    return (sizeof(S) == 8 ? 2 : LBM_MIN_BLOCKS) * (128 / T);
+    return (sizeof(S) == 8 ? 2 : sizeof(S) == 2 ? LBM_MIN_BLOCKS_16 : LBM_MIN_BLOCKS) * (128 / T);
 }
 
 template <class S, class R, bool kFields, bool kWallInline, int T>
@@ -495,12 +520,14 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                 const Pair<S>* rm = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_m : so_p));
                 const Pair<S>* r0 = reinterpret_cast<const Pair<S>*>(s0);
                 const Pair<S>* rp = reinterpret_cast<const Pair<S>*>(smem + (dir > 0 ? so_p : so_m));
-                if (general) pull<true, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
-                else pull<false, S, R, int>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
-                // rho_k = sum_i f_i as a balanced tree (short dependency chains)
+                if (general) pull<true, S, R, int, false>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
+                else pull<false, S, R, int, false>(rm, r0, rp, BX, sc, st.fl, inlet, outlet, P, s_par, r, st.f);
+                // rho_k = sum_i f_i as a balanced tree (short dependency chains); 16-bit storage sums
+                // h_i = f_i - w_i rho0 and adds rho0 once (the weights sum to 1)
                 const V2<R>* f = st.f;
                 rho2 = vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])),
                             vadd(vadd(f[4], f[5]), vadd(f[6], vadd(f[7], f[8]))));
+                if constexpr (Store<S>::kShift) rho2 = vadd(rho2, V2<R>{s_par.rho0[0], s_par.rho0[1]});
                 if (st.fl & kWallBit) {
                     const long long o = C.d_off + (long long)wrap_row(r) * P.nx + X;
                     if (LBM_IDX_OK(o >= 0 && o < a.dense_total)) {
@@ -614,8 +641,9 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                 }
             } else {
                 V2<R> o[9];
-                collide<R>(f, r2, ux, uy, V2<R>{FAx, FBx}, V2<R>{FAy, FBy}, V2<R>{P.omega[0], P.omega[1]},
-                           V2<R>{P.cF[0], P.cF[1]}, o);
+                collide<R, Store<S>::kShift>(f, r2, ux, uy, V2<R>{FAx, FBx}, V2<R>{FAy, FBy},
+                                             V2<R>{P.omega[0], P.omega[1]}, V2<R>{P.cF[0], P.cF[1]}, o,
+                                             V2<R>{s_par.om_rho0[0], s_par.om_rho0[1]});
                 Pair<S>* out = fo + (long long)y * P.row + x + G;
                 // the row's nine pairs at columns x + G of planes 0..8 lie inside the case's block
                 const long long e0 = C.f_off + (long long)y * P.row + x + G;
@@ -623,10 +651,7 @@ __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a)
                                 e0 + 8 * P.plane < a.pop_pairs))
                     return;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    if constexpr (Store<S>::kShift) o[i] = vsub(o[i], V2<R>{shift_of(P, 0, i), shift_of(P, 1, i)});
-                    store_pair<S, R>(out + i * P.plane, o[i].x, o[i].y);
-                }
+                for (int i = 0; i < 9; ++i) store_pair<S, R>(out + i * P.plane, o[i].x, o[i].y);
                 if (P.bc_x == kPeriodic && (x < G || x >= P.nx - G)) {  // copy for the periodic wrap
                     const int gx = x < G ? x + P.nx + G : x - P.nx + G;
                     if (!LBM_IDX_OK(gx >= 0 && gx < P.plane)) return;

@@ -236,13 +236,18 @@ def test_fields_and_diagnostics_match_oracle():
 
 
 def test_mass_conservation_f32():
+    """Streaming, bounce-back and the collision conserve each component's mass (the Guo term has
+    no zeroth moment); in FP32 only rounding remains.  Over 20,000 steps this case drifts by about
+    4e-5 (measured on the GB300), from rounding that repeats at the many bulk nodes of nearly equal
+    state.  FP32 lattice weights that sum to 1 + 7.5e-9, as 4/9, 1/9 and 1/36 rounded one by one do,
+    would add 1.5e-4 and fail the bar."""
     sc = SCENARIOS["cylinder96"]()
     lat = lbm.Lattice(sc, "f32")
     m0 = lat.diagnostics()
-    lat.step(500)
+    lat.step(20000)
     m1 = lat.diagnostics()
     for k in ("mass_A", "mass_B"):
-        assert abs(m1[k] / m0[k] - 1) < 2e-5, (k, m0[k], m1[k])
+        assert abs(m1[k] / m0[k] - 1) < 1e-4, (k, m0[k], m1[k], m1[k] / m0[k] - 1)
     lat.close()
 
 

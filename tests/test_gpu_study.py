@@ -116,3 +116,51 @@ def test_sphere3d_records_match_the_oracle():
             assert r[key] == pytest.approx(od[key], rel=1e-9), (lam, key)
         assert r["theta"] == r["history"][-1] and not r["unstable"]
     assert s3.table(rows).count("\n") == 1 + len(rows)
+
+
+def test_sweep_records_match_the_oracle():
+    """The steady-state sweep driver on the scaled cylinder case (96 x 96, two angles, 200 FP64
+    steps): the angles after each interval, max |u| and the mass drift equal the oracle's."""
+    from paper_2505_22256_gb300 import study_sweep as sw
+
+    rows = sw.run(steps=200, check=100, storage="f64", n=96, angles=(30, 150))
+    cases = S.lambda_sweep_cylinder(n=96, seed=2, angles=(30, 150))
+    for sc, r in zip(cases, rows):
+        cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+        f0 = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+        m0 = f0.reshape(2, -1).sum(axis=1)
+        f = f0
+        for k in range(2):
+            f = oracle.run(cfg, sc.solid, f, 100)
+            th, _, _ = oracle.contact_angle(cfg, sc.solid, f, sc.surface)
+            assert r["theta_history"][k][1] == pytest.approx(th, abs=1e-6), (sc.name, k)
+        d = oracle.diagnostics(cfg, sc.solid, f)
+        assert r["umax"] == pytest.approx(d["umax"], rel=1e-8)
+        m1 = f.reshape(2, -1).sum(axis=1)
+        assert r["mass_drift_A"] == pytest.approx(m1[0] / m0[0] - 1, abs=1e-12)
+        assert r["mass_drift_B"] == pytest.approx(m1[1] / m0[1] - 1, abs=1e-12)
+        assert r["dtheta_last"] == pytest.approx(abs(r["theta_history"][1][1] - r["theta_history"][0][1]))
+    assert sw.table(rows).count("\n") == 1 + len(cases)
+
+
+def test_displacement_records_match_the_oracle():
+    """The porous displacement driver on a 256 x 128 medium, two intervals of 150 FP64 steps: mass,
+    saturation and front equal those of the oracle's state."""
+    from paper_2505_22256_gb300 import study_displacement as sd
+
+    sc = sd.case(256, 128)
+    rows = sd.run(sc, steps=300, check=150, storage="f64")
+    cfg = oracle.Config(nx=sc.nx, ny=sc.ny, **sc.params())
+    f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    for k, r in enumerate(rows):
+        f = oracle.run(cfg, sc.solid, f, 150)
+        rA, rB, _, _ = oracle.fields(cfg, sc.solid, f)
+        d = oracle.diagnostics(cfg, sc.solid, f)
+        want = sd.snapshot(sc, rA, rB)
+        assert r["step"] == 150 * (k + 1)
+        assert r["mass_A"] == pytest.approx(d["mass_A"], rel=1e-10)
+        assert r["mass_B"] == pytest.approx(d["mass_B"], rel=1e-10)
+        assert r["saturation_A"] == want["saturation_A"] and r["front_x"] == want["front_x"]
+        assert r["inflow_A_per_step"] == pytest.approx(1.0 * 0.005 * int((sc.solid[:, 0] == 0).sum()))
+        assert not r["unstable"]
+    assert sd.table(rows).count("\n") == 3 + len(rows)
