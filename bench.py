@@ -727,17 +727,22 @@ def run_ours_3d(args):
 
     def bench_step(pairs=None):
         if pairs is not None:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
         lat.step(args.inner)
         if pairs is not None:
-            b.record(stream)
-            pairs.append((a, b))
+            ev[1].record(stream)
         lat.diagnostics(allow_unstable=True)
+        if pairs is not None:
+            ev[2].record(stream)
         try:
-            return lat.contact_angle(sc.sphere)[0]
+            th = lat.contact_angle(sc.sphere)[0]
         except Exception:
-            return None
+            th = None
+        if pairs is not None:
+            ev[3].record(stream)
+            pairs.append(ev)
+        return th
 
     for _ in range(args.warmup):
         bench_step()
@@ -814,7 +819,7 @@ def run_ours_3d(args):
                      "peak_kind": peak_kind,
                      "kernel": "k3_rho + k3_march (one time step)", "algorithmic_bytes_per_launch": algo,
                      "launch_ms": launch_ms},
-        "e2e": e2e, "gpu_launches": (2 * args.inner + 3 + 9) * args.steps, "clocks": clk,
+        "e2e": e2e, "gpu_launches": (2 * args.inner + 3 + 9) * args.steps, "clocks": clk, "phase_ms_per_step": phase_ms,
         "mflups": world * fluid * args.inner * args.steps / (total_ms / 1e3) / 1e6,
         "sample_diagnostics": {"theta_deg": theta, "umax": d["umax"], "unstable": d["unstable"]},
     }

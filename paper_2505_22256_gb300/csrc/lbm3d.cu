@@ -47,6 +47,16 @@ __host__ __device__ __forceinline__ constexpr int e3z(int i) {
 }
 __host__ __device__ __forceinline__ constexpr int opp3(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
 __host__ __device__ __forceinline__ constexpr double w19(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+// The collision's weights in the compute type.  1/3, 1/18 and 1/36 rounded to FP32 one by one sum to
+// 1 + 2e-8, and every step redistributes each node's mass with them, so an FP32 run gained that much
+// mass per step; the FP32 set below sums to 1 exactly (w_0 + 6 w_1 + 12 w_2 = 1 with w_2 = w_1 / 2,
+// w_1 = 7456540 2^-27, w_0 = 11184812 2^-25), each weight within 1.2e-7 (relative) of its value.
+template <class R>
+__host__ __device__ __forceinline__ constexpr double w19c(int i) { return w19(i); }
+template <>
+__host__ __device__ __forceinline__ constexpr double w19c<float>(int i) {
+    return i == 0 ? 11184812.0 / 33554432.0 : (i <= 6 ? 7456540.0 / 134217728.0 : 3728270.0 / 134217728.0);
+}
 // eighth-order stencil weights by |e|^2 (0: not in the stencil)
 __host__ __device__ __forceinline__ constexpr double w92(int q) {
     return q == 1 ? 4.0 / 45.0 : q == 2 ? 1.0 / 21.0 : q == 3 ? 2.0 / 105.0 : q == 4 ? 5.0 / 504.0
@@ -556,8 +566,8 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
             const V uF = vfma(u2v[2], F[2], vfma(u2v[1], F[1], vmul(u2v[0], F[0])));
             const V C0 = vfma(wr, vbc<R>(tq), vmul(vmul(vbc<R>(-3), cf), uF));
             V o[19];
-            o[0] = vfma(om1, f[0], vmul(vbc<R>(w19(0)), C0));
-            const V sAx = vmul(vbc<R>(w19(1)), C0), sDg = vmul(vbc<R>(w19(7)), C0);
+            o[0] = vfma(om1, f[0], vmul(vbc<R>(w19c<R>(0)), C0));
+            const V sAx = vmul(vbc<R>(w19c<R>(1)), C0), sDg = vmul(vbc<R>(w19c<R>(7)), C0);
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
                 auto dot = [&](const V* vv) -> V {  // e_i . vv for a pair-valued vector
@@ -573,7 +583,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                     }
                     return r;
                 };
-                const double w = w19(i);
+                const double w = w19c<R>(i);
                 const V a = dot(u2v), b = dot(F);
                 const V cb = vmul(cf, b);
                 const V Pp = vfma(wr, a, cb);

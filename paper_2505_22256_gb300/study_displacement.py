@@ -3,9 +3,12 @@
 The 4096x2048 porous medium of disks (porosity 0.6) starts filled with component B; a velocity inlet
 at x = 0 injects A (rho_in = 1.0 for A, 0.03 for B, u_in = 0.005) and an outflow boundary closes
 x = nx - 1.  Every `check` steps the study reads the diagnostics and the fields and records:
-  * the mass of each component, and the change of A's mass since the start next to the inflow the
-    inlet prescribes, rho_in,A u_in H per step (H = fluid rows of the inlet column); before A reaches
-    the outlet A leaves nowhere, so the two must agree up to the inlet's density deviation;
+  * the mass of each component, and the change of A's mass per step since the start next to the
+    source the inlet rule adds, rho_in,A u_in H per step (H = fluid rows of the inlet column).  The
+    rule adds exactly that per step once the flow through the inlet column is steady; the mass
+    balance also holds what leaves or enters through the outflow column, whose copied populations
+    leave the pressure level free (dissolved A leaves with B, and B enters when the medium's
+    resistance raises the pressure);
   * the A saturation (share of fluid nodes where rho_A > rho_B) and the front: the largest x at
     which any fluid node is A-dominated, and the first time that front reaches the outlet column
     (breakthrough), with the saturation then.
@@ -90,10 +93,14 @@ def main(argv=None) -> int:
     ap.add_argument("--check", type=int, default=20000)
     ap.add_argument("--size", default="4096x2048")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
+    ap.add_argument("--u-in", type=float, default=None, help="inlet velocity (default 0.005)")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     nx, ny = map(int, args.size.split("x"))
-    rows = run(case(nx, ny), args.steps, args.check, args.storage)
+    sc = case(nx, ny)
+    if args.u_in is not None:
+        sc.u_in = args.u_in
+    rows = run(sc, args.steps, args.check, args.storage)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:

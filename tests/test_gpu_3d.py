@@ -112,11 +112,10 @@ def test_f64_matches_oracle_after_30_steps(name):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_f32_matches_oracle_after_100_steps(name):
-    """FP32 bar of the 3-D form after 100 steps: |d rho_k| <= 1e-5 rho_m (absolute, at the
-    main-phase density rho_m = 1) and |d u| <= 1e-6.  The FP32 state drifts from the FP64 one by a
-    few 1e-6 in absolute terms here (the 3-D stencil has 92 terms and 19 populations per
-    component); at the dissolved-phase level that is about 1e-5 relative, reported below and held
-    under 5e-5."""
+    """FP32 bar after 100 steps, as in 2-D: max relative |d rho_k| <= 1e-5 at every fluid node
+    (the dissolved phase included) and |d u| <= 1e-6.  Measured on the GB300: at most 5.3e-7
+    absolute and 2.3e-6 relative.  (With D3Q19 weights rounded to FP32 one by one, which sum to
+    1 + 2e-8, every node gained that much mass per step and the error reached 1.4e-5 relative.)"""
     sc = CASES[name]()
     cfg, f = orun(sc, 100)
     o = d3.fields3(cfg, sc.solid, f)
@@ -128,8 +127,8 @@ def test_f32_matches_oracle_after_100_steps(name):
     dabs = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (0, 1))
     drel = rel_rho(g, o, sc.solid)
     print(f"{name}: max |d rho| {dabs:.2e}, max relative {drel:.2e}")
+    assert drel <= 1e-5
     assert dabs <= 1e-5 * S.RHO_M
-    assert drel <= 5e-5
     assert max(float(np.max(np.abs(g[k] - o[k]))) for k in (2, 3, 4)) <= 1e-6
 
 
