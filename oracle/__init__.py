@@ -148,7 +148,8 @@ class _Cfg(ctypes.Structure):
                 ("Gw2", ctypes.c_double), ("delta", ctypes.c_double), ("g", ctypes.c_double * 2),
                 ("u_in", ctypes.c_double), ("rho_in", ctypes.c_double * 2),
                 ("wE8", ctypes.c_double * 5), ("inlet_profile", ctypes.c_int32), ("second_layer", ctypes.c_int32),
-                ("u_wall", ctypes.c_double * 2), ("adhesion_stencil", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("u_wall", ctypes.c_double * 2), ("adhesion_stencil", ctypes.c_int32), ("outlet", ctypes.c_int32),
+                ("rho_out", ctypes.c_double * 2)]
 
 
 @dataclass
@@ -175,6 +176,10 @@ class Config:
     # stencil of the adhesion sum of Eq. 9: "e8" (the 24-node stencil of the cohesion force, Sec. 2.4)
     # or "d2q9" (as printed: D2Q9 weights w_i over the eight first-layer neighbours)
     adhesion_stencil: str = "e8"
+    # outflow at x = nx-1 (Sec. 3.3): "copy" (entering populations from column nx-2) or "pressure"
+    # (Zou-He density condition holding rho_out per component)
+    outlet: str = "copy"
+    rho_out: tuple = (0.03, 1.0)
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
 
     def c(self) -> _Cfg:
@@ -195,6 +200,8 @@ class Config:
         s.u_wall[0], s.u_wall[1] = self.u_wall
         s.second_layer = {"psi_and_solid": 0, "psi": 1}[self.second_layer]
         s.adhesion_stencil = {"e8": 0, "d2q9": 1}[self.adhesion_stencil]
+        s.outlet = {"copy": 0, "pressure": 1}[self.outlet]
+        s.rho_out[0], s.rho_out[1] = self.rho_out
         for i, q in enumerate(SHELLS):
             s.wE8[i] = float(w[q])
         return s

@@ -57,10 +57,13 @@ typedef struct {
                                  eighth-order stencil of the cohesion force, Sec. 2.4) or
                                  ADHESION_D2Q9 (Eq. 9 as printed: the D2Q9 weights w_i over the
                                  eight first-layer neighbours) */
-    int32_t pad_;
+    int32_t outlet;   /* OUTLET_COPY (entering populations copied from column nx-2) or
+                         OUTLET_PRESSURE (Zou-He density condition, rho_out) at x = nx-1 */
+    double rho_out[2]; /* component densities held at the outlet by OUTLET_PRESSURE */
 } oracle_cfg;
 
 enum { ADHESION_E8 = 0, ADHESION_D2Q9 = 1 };
+enum { OUTLET_COPY = 0, OUTLET_PRESSURE = 1 };
 
 /* ---------------------------------------------------------------------------------------------
  * Lattice tables.
@@ -433,7 +436,12 @@ static double inlet_velocity(const oracle_cfg* c, int y) {
  * fstar.  Populations entering through x = 0 are given by non-equilibrium bounce-back about
  * f^eq(rho_in,k, (u(y), 0)) (the reading of the two-component Zou-He inlet; u(y) from
  * inlet_velocity); populations entering through x = nx-1 are copied from column nx-2 (outflow), or
- * bounced back if that node is solid. */
+ * bounced back if that node is solid.
+ * Pressure outlet (outlet = OUTLET_PRESSURE): per component the Zou-He density condition.  The three
+ * populations entering through x = nx-1 (e_3, e_6, e_7) are those that give the node the density
+ * rho_out[k] and no momentum along y, with non-equilibrium bounce-back along x: the first two
+ * conditions leave rho u_x = f0 + f2 + f4 + 2 (f1 + f5 + f8) - rho_out, and then
+ * f3 = f1 - (2/3) rho u_x, f7 = f5 + (f2 - f4)/2 - rho u_x / 6, f6 = f8 - (f2 - f4)/2 - rho u_x / 6. */
 static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const double* fstar, double* f) {
     size_t N = (size_t)c->nx * (size_t)c->ny;
     if (c->bc_x != BC_OPEN) return;
@@ -453,7 +461,17 @@ static void open_boundaries(const oracle_cfg* c, const uint8_t* solid, const dou
                 }
             /* outlet, x = nx-1 */
             size_t s1 = idx(c, c->nx - 1, y), s2 = idx(c, c->nx - 2, y);
-            if (!solid[s1])
+            if (!solid[s1] && c->outlet == OUTLET_PRESSURE) {
+                for (int k = 0; k < 2; k++) {
+                    double* g = f + (size_t)k * 9 * N + s1; /* g[i * N] = f_i^k at the node */
+                    double known = g[0] + g[2 * N] + g[4 * N] + 2.0 * (g[1 * N] + g[5 * N] + g[8 * N]);
+                    double rho_ux = known - c->rho_out[k];
+                    double dy = g[2 * N] - g[4 * N];
+                    g[3 * N] = g[1 * N] - 2.0 / 3.0 * rho_ux;
+                    g[7 * N] = g[5 * N] + 0.5 * dy - rho_ux / 6.0;
+                    g[6 * N] = g[8 * N] - 0.5 * dy - rho_ux / 6.0;
+                }
+            } else if (!solid[s1])
                 for (int k = 0; k < 2; k++)
                     for (int i = 0; i < 9; i++)
                         if (CX[i] < 0) {

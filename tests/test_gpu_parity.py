@@ -587,6 +587,25 @@ def test_contact_angle_routine_matches_oracle_on_the_same_state():
     lat.close()
 
 
+def test_contact_angle_beyond_the_points_the_fit_caches():
+    """A droplet of r = 400 on a 2048 x 2048 lattice has 2,605 interface points, more than
+    the 2,048 the fit keeps in shared memory after its first stage; the rest are formed again in
+    every stage.  The angle, the rms and the point count equal the oracle's on the same (initial)
+    state, and the batched call equals the single-case call bit for bit."""
+    sc = S.cylinder_droplet(2048, R=320.0, r=400.0, lam=0.8)
+    cfg = ocfg(sc)
+    f = oracle.init(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
+    lat = lbm.Lattice(sc, "f64")
+    th, rms, n = lat.contact_angle()
+    tb, rb, nb = lat.contact_angle_all()
+    oth, orms, on = oracle.contact_angle(cfg, sc.solid, f, sc.surface)
+    assert n == on and n > 2048, (n, on)
+    assert th == pytest.approx(oth, abs=1e-8)
+    assert rms == pytest.approx(orms, rel=1e-6, abs=1e-10)
+    assert (tb[0], rb[0], nb[0]) == (th, rms, n)
+    lat.close()
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_contact_angle_after_2000_steps(storage):
     """The 96x96 droplet-on-cylinder case: 2,000 steps, then theta within 0.5 degrees."""

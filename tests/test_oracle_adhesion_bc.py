@@ -285,3 +285,74 @@ def test_d2q9_adhesion_makes_the_second_layer_readings_identical():
     assert np.array_equal(outs["d2q9", "psi_and_solid"], outs["d2q9", "psi"])
     assert np.max(np.abs(outs["e8", "psi_and_solid"] - outs["e8", "psi"])) > 1e-8
     assert np.max(np.abs(outs["e8", "psi_and_solid"] - outs["d2q9", "psi"])) > 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# Pressure outlet (Zou-He density condition at x = nx-1), the alternative to the copy outflow
+# ---------------------------------------------------------------------------------------------
+def test_uniform_inflow_is_stationary_with_the_pressure_outlet():
+    """f = f^eq(rho_in, u_in) everywhere is a fixed point of collide + stream with the inlet and a
+    pressure outlet holding the same densities (Zou-He is exact on an equilibrium)."""
+    nx, ny, u = 12, 6, 0.02
+    solid = np.zeros((ny, nx), np.uint8)
+    cfg = _open_cfg(nx, ny, G=0.0, u_in=u, rho_in=(0.7, 0.3), outlet="pressure", rho_out=(0.7, 0.3))
+    f = np.zeros((2, 9, ny, nx))
+    for k, r in enumerate((0.7, 0.3)):
+        f[k] = oracle.feq(r, u, 0.0)[:, None, None]
+    f2 = oracle.run(cfg, solid, f, 5)
+    np.testing.assert_allclose(f2, f, rtol=1e-14, atol=1e-17)
+
+
+def test_pressure_outlet_solves_its_defining_conditions():
+    """At every fluid node of the outlet column, after streaming, the three entering populations
+    (e_3, e_6, e_7) are the solution of the three conditions that define the Zou-He density
+    boundary -- density rho_out[k], zero y-momentum, f_3 - f_1 = f^eq_3 - f^eq_1 -- found here by
+    a linear solve per node, independently of the oracle's closed form."""
+    rng = np.random.default_rng(5)
+    nx, ny = 10, 7
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    cfg = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=1.0, u_in=0.01, rho_in=(1.0, 0.03),
+                        outlet="pressure", rho_out=(0.05, 0.9))
+    fstar = rng.uniform(0.01, 0.2, (2, 9, ny, nx)) * (1 - solid)[None, None]
+    f = oracle.stream(cfg, solid, fstar)
+    for k in range(2):
+        for y in range(1, ny - 1):
+            g = f[k, :, y, nx - 1]
+            # unknowns (f3, f6, f7); rows: density, y-momentum, f3 - f1 = -(2/3) rho u_x with
+            # rho u_x = f1 + f5 + f8 - f3 - f6 - f7
+            A = np.array([[1.0, 1.0, 1.0], [0.0, 1.0, -1.0], [1.0 - 2.0 / 3.0, -2.0 / 3.0, -2.0 / 3.0]])
+            b = np.array([cfg.rho_out[k] - (g[0] + g[1] + g[2] + g[4] + g[5] + g[8]),
+                          -(g[2] + g[5] - g[4] - g[8]),
+                          g[1] - 2.0 / 3.0 * (g[1] + g[5] + g[8])])
+            x3, x6, x7 = np.linalg.solve(A, b)
+            assert g[3] == pytest.approx(x3, abs=1e-14)
+            assert g[6] == pytest.approx(x6, abs=1e-14)
+            assert g[7] == pytest.approx(x7, abs=1e-14)
+            assert g.sum() == pytest.approx(cfg.rho_out[k], abs=1e-14)
+            assert (g * CY).sum() == pytest.approx(0.0, abs=1e-14)
+
+
+def test_pressure_outlet_keeps_a_driven_channel_from_filling():
+    """A walled channel driven by the velocity inlet: with the copy outflow the lattice keeps
+    gaining mass (the outlet leaves the pressure level free); with the pressure outlet the total
+    mass settles, the inflow leaving through the outlet."""
+    nx, ny = 40, 12
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    r = np.where(solid == 1, 0.0, 1.0)
+    out = {}
+    for outlet in ("copy", "pressure"):
+        cfg = oracle.Config(nx=nx, ny=ny, bc_x="open", bc_y="wall", G=0.0, u_in=0.02, rho_in=(0.7, 0.3),
+                            outlet=outlet, rho_out=(0.7, 0.3), nthreads=1)
+        f = oracle.init(cfg, solid, 0.7 * r, 0.3 * r)
+        m = []
+        for _ in range(6):
+            f = oracle.run(cfg, solid, f, 1000)
+            m.append(f.sum())
+        out[outlet] = np.array(m)
+    grow_copy = out["copy"][-1] - out["copy"][-2]
+    grow_p = out["pressure"][-1] - out["pressure"][-2]
+    inflow_per_1000 = 1000 * 0.02 * (ny - 2) * 1.0
+    assert grow_copy > 0.25 * inflow_per_1000  # 88 per 1,000 steps against an inflow of 200
+    assert abs(grow_p) < 1e-5 * inflow_per_1000  # 1e-7 per 1,000 steps
