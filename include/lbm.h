@@ -99,6 +99,17 @@ typedef enum {
     LBM_ADHESION_D2Q9 = 1 /* as printed in Eq. 9: w_i = 1/9 (axes), 1/36 (diagonals), first layer only */
 } lbm_adhesion_stencil;
 
+/* Outflow at x = nx-1 of an open x (Sec. 3.3 names an outflow scheme without stating it).  The
+ * copy rule takes the populations entering through the outlet from column nx-2, or bounces them
+ * back when that node is solid; it leaves the pressure level free, so a channel driven by the
+ * velocity inlet through a resistive medium keeps gaining mass.  The pressure rule is the Zou-He
+ * density condition per component: the three entering populations give the node the densities
+ * rho_out and no momentum along y, with non-equilibrium bounce-back along x. */
+typedef enum {
+    LBM_OUTLET_COPY = 0,    /* default */
+    LBM_OUTLET_PRESSURE = 1
+} lbm_outlet;
+
 typedef struct {
     double tau[2];        /* relaxation times tau_A, tau_B (Eq. 2); each > 0.5 */
     double G_AB;          /* inter-component strength G_12 (Eq. 8), stencil weights with
@@ -121,7 +132,8 @@ typedef struct {
     int32_t second_layer;  /* lbm_second_layer: what a second-layer stencil node that is not a fluid
                               node takes from its first-layer partner x + sign(e) (Sec. 2.4, Table 1) */
     int32_t adhesion_stencil; /* lbm_adhesion_stencil (Eq. 9) */
-    int32_t pad_;             /* unused; its value is ignored */
+    int32_t outlet;           /* lbm_outlet (LBM_BC_OPEN): outflow rule at x = nx-1 */
+    double rho_out[2];        /* component densities held by LBM_OUTLET_PRESSURE; each > 0 */
 } lbm_params;
 
 /* Storage and arithmetic precision of the populations. */

@@ -92,6 +92,12 @@ lbm_status validate_case(const lbm_grid* g, const uint8_t* solid, const lbm_para
         return fail(LBM_EINVAL, "case %d: bad second_layer %d", idx, p->second_layer);
     if (p->adhesion_stencil != LBM_ADHESION_E8 && p->adhesion_stencil != LBM_ADHESION_D2Q9)
         return fail(LBM_EINVAL, "case %d: bad adhesion_stencil %d", idx, p->adhesion_stencil);
+    if (p->outlet != LBM_OUTLET_COPY && p->outlet != LBM_OUTLET_PRESSURE)
+        return fail(LBM_EINVAL, "case %d: bad outlet %d", idx, p->outlet);
+    if (p->outlet == LBM_OUTLET_PRESSURE &&
+        (g->bc_x != LBM_BC_OPEN || !finite(p->rho_out[0]) || !finite(p->rho_out[1]) || p->rho_out[0] <= 0.0 ||
+         p->rho_out[1] <= 0.0))
+        return fail(LBM_EINVAL, "case %d: the pressure outlet needs an open x and outlet densities > 0", idx);
     if (p->inlet_profile != LBM_INLET_UNIFORM && p->inlet_profile != LBM_INLET_POISEUILLE)
         return fail(LBM_EINVAL, "case %d: bad inlet profile", idx);
     if (p->inlet_profile == LBM_INLET_POISEUILLE && (g->bc_x != LBM_BC_OPEN || g->bc_y != LBM_BC_WALL))
@@ -143,6 +149,9 @@ DevCase make_desc(const lbm_grid& g, const lbm_params& p) {
     d.u_wall[0] = p.u_wall[0];
     d.u_wall[1] = p.u_wall[1];
     d.inlet_profile = p.inlet_profile;
+    d.outlet = p.outlet;
+    d.rho_out[0] = p.rho_out[0];
+    d.rho_out[1] = p.rho_out[1];
     return d;
 }
 
@@ -1099,6 +1108,7 @@ uint64_t params_hash(const Ctx& c) {
         mixd(p.g[0]); mixd(p.g[1]); mixd(p.u_in); mixd(p.rho_in[0]); mixd(p.rho_in[1]);
         mixd(p.rho0_store[0]); mixd(p.rho0_store[1]); mixd(p.u_wall[0]); mixd(p.u_wall[1]);
         mixi(p.inlet_profile); mixi(p.second_layer); mixi(p.adhesion_stencil);
+        mixi(p.outlet); mixd(p.rho_out[0]); mixd(p.rho_out[1]);
         mixi((int64_t)hc.mask_hash);
     }
     return h;

@@ -79,6 +79,8 @@ struct CaseParams {
     R sh0[2], sh1[2], sh5[2];  // storage shift w_i rho0 for the rest, axis and diagonal weights
     R rho0[2], om_rho0[2];     // rho0 and omega rho0 of the shifted storage (0 for FP32 / FP64)
     int inlet_profile;         // 1: the inlet differences above scale with 4 s (ny - s) / ny^2, s = y + 1/2
+    int outlet;                // 1: pressure outlet (Zou-He density condition holding rho_out)
+    R rho_out[2];
     int moving;                // 1: a walled y edge slides (u_wall nonzero)
     R prof_c;                  // 4 / ny^2
     R uw[2];                   // x-velocity of the lower / upper wall
@@ -106,6 +108,8 @@ struct DevCase {
     double rho0[2];         // storage shift per component
     double u_wall[2];       // x-velocity of the lower / upper wall of a walled y direction
     int inlet_profile;      // 0 uniform, 1 Poiseuille (peak u_in)
+    int outlet;             // 0 copy, 1 pressure
+    double rho_out[2];      // densities held by the pressure outlet
     CaseParams<float> pf;   // the above in FP32 and FP64 (filled by fill_case_params)
     CaseParams<double> pd;
 };
@@ -130,6 +134,9 @@ inline void fill_case_params_as(const DevCase& d, CaseParams<R>& P) {
     P.s1 = (R)d.s1; P.s2 = (R)d.s2; P.s3 = (R)d.s3; P.t2 = (R)d.t2; P.t3 = (R)d.t3;
     P.gx = (R)d.g[0]; P.gy = (R)d.g[1];
     P.inlet_profile = d.inlet_profile;
+    P.outlet = d.outlet;
+    P.rho_out[0] = (R)d.rho_out[0];
+    P.rho_out[1] = (R)d.rho_out[1];
     P.moving = (d.bc_y == kWall && (d.u_wall[0] != 0.0 || d.u_wall[1] != 0.0)) ? 1 : 0;
     P.prof_c = (R)(4.0 / ((double)d.ny * (double)d.ny));
     P.uw[0] = (R)d.u_wall[0];

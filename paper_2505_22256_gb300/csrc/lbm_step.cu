@@ -48,8 +48,15 @@ constexpr int kRing = 6;
 #ifndef LBM_MIN_BLOCKS
 #define LBM_MIN_BLOCKS 3
 #endif
-constexpr int kSlots = LBM_SLOTS;  // rows of f* resident or in flight in shared memory (>= 4)
-static_assert(kSlots >= 4, "the pull of a row needs three resident rows plus one in flight");
+#ifndef LBM_SLOTS_16
+#define LBM_SLOTS_16 LBM_SLOTS
+#endif
+// rows of f* resident or in flight in shared memory (>= 4), per storage type
+template <class S>
+constexpr int slots_of() {
+    return sizeof(S) == 2 ? LBM_SLOTS_16 : LBM_SLOTS;
+}
+static_assert(LBM_SLOTS >= 4 && LBM_SLOTS_16 >= 4, "the pull of a row needs three resident rows plus one in flight");
 
 template <class R>
 using Params = CaseParams<R>;
@@ -108,7 +115,8 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
             src = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
             off = (I)i * ps + c - cx(i);
         } else {
-            if (cx(i) > 0 && inlet) continue;  // entering through the inlet: set below
+            if (cx(i) > 0 && inlet) continue;               // entering through the inlet: set below
+            if (cx(i) < 0 && outlet && Pin.outlet) continue;  // pressure outlet: set below
             const bool blocked = (fl >> (i - 1)) & 1u;
             int b = c;
             if (cx(i) < 0 && outlet) b = (fl & kOutletOwnBit) ? c : c - 1;  // copied from upstream
@@ -128,6 +136,20 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
         f[1] = vfma(d1, s2, f[3]);
         f[5] = vfma(d5, s2, f[7]);
         f[8] = vfma(d5, s2, f[6]);
+    }
+    if (kGeneral && outlet && Pin.outlet) {
+        // Zou-He density condition per component (Sec. 3.3 outflow, pressure reading): the node gets
+        // the densities rho_out and no y-momentum, with non-equilibrium bounce-back along x.  The
+        // known populations give rho u_x = f0 + f2 + f4 + 2 (f1 + f5 + f8) - rho_out; shifted
+        // storage holds h = f - w rho0, whose known sum misses rho0 (those weights sum to 1).
+        V2<R> known = vadd(vadd(vadd(f[0], f[2]), f[4]), vmul(vbc<R>(2), vadd(vadd(f[1], f[5]), f[8])));
+        if constexpr (Store<S>::kShift && !kAddShift) known = vadd(known, V2<R>{Pin.rho0[0], Pin.rho0[1]});
+        const V2<R> rho_ux = vsub(known, V2<R>{Pin.rho_out[0], Pin.rho_out[1]});
+        const V2<R> dy = vsub(f[2], f[4]);
+        const V2<R> c6 = vmul(vbc<R>(1.0 / 6.0), rho_ux);
+        f[3] = vsub(f[1], vmul(vbc<R>(2.0 / 3.0), rho_ux));
+        f[7] = vsub(vfma(vbc<R>(0.5), dy, f[5]), c6);
+        f[6] = vsub(vsub(f[8], vmul(vbc<R>(0.5), dy)), c6);
     }
 }
 
@@ -374,9 +396,9 @@ struct SmemPlan {
     __host__ __device__ explicit SmemPlan(int T) {
         pop_bytes = ((size_t)T * 9 * sizeof(Pair<S>) + 127) / 128 * 128;
         slot_bytes = pop_bytes + ((size_t)(T + 8) * sizeof(uint16_t) + 127) / 128 * 128;  // + the flags row
-        ring_off = kSlots * slot_bytes;
+        ring_off = slots_of<S>() * slot_bytes;
         bar_off = (ring_off + 4 * kRing * (size_t)T * sizeof(R) + 7) / 8 * 8;
-        total = bar_off + kSlots * 8;
+        total = bar_off + slots_of<S>() * 8;
     }
 };
 
@@ -411,6 +433,7 @@ constexpr int step_min_blocks() {
 template <class S, class R, bool kFields, bool kWallInline, int T>
 __global__ void __launch_bounds__(T, step_min_blocks<S, T>()) k_step(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int kSlots = slots_of<S>();
     constexpr int Wi = T - 8;  // interior columns of a window
     const int t = threadIdx.x;
     constexpr int G = Layout<S>::G;

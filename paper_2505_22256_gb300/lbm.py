@@ -45,7 +45,7 @@ class lbm_params(ctypes.Structure):
                 ("G_w2", c_double), ("delta", c_double), ("g", c_double * 2), ("u_in", c_double),
                 ("rho_in", c_double * 2), ("rho0_store", c_double * 2), ("u_wall", c_double * 2),
                 ("inlet_profile", c_int32), ("second_layer", c_int32), ("adhesion_stencil", c_int32),
-                ("pad_", c_int32)]
+                ("outlet", c_int32), ("rho_out", c_double * 2)]
 
 
 class lbm_diag(ctypes.Structure):
@@ -163,11 +163,13 @@ def _host(a, dtype) -> np.ndarray:
 INLET = {"uniform": 0, "poiseuille": 1}
 SECOND_LAYER = {"psi_and_solid": 0, "psi": 1}  # lbm_second_layer
 ADHESION_STENCIL = {"e8": 0, "d2q9": 1}  # lbm_adhesion_stencil
+OUTLET = {"copy": 0, "pressure": 1}  # lbm_outlet
 
 
 def make_params(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8, g=(0.0, 0.0),
                 u_in=0.0, rho_in=(1.0, 0.03), rho0_store=(0.0, 0.0), u_wall=(0.0, 0.0), inlet_profile="uniform",
-                second_layer="psi_and_solid", adhesion_stencil="e8", **_ignored) -> lbm_params:
+                second_layer="psi_and_solid", adhesion_stencil="e8", outlet="copy", rho_out=(0.03, 1.0),
+                **_ignored) -> lbm_params:
     p = lbm_params()
     p.tau[0], p.tau[1] = tau
     p.G_AB = G
@@ -183,6 +185,8 @@ def make_params(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, d
     p.inlet_profile = INLET[inlet_profile]
     p.second_layer = SECOND_LAYER[second_layer]
     p.adhesion_stencil = ADHESION_STENCIL[adhesion_stencil]
+    p.outlet = OUTLET[outlet]
+    p.rho_out[0], p.rho_out[1] = rho_out
     return p
 
 

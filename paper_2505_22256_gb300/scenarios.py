@@ -97,6 +97,10 @@ class Scenario:
     # stencil of the adhesion sum of Eq. 9: e8 (the cohesion force's 24-node stencil) | d2q9 (as
     # printed: D2Q9 weights over the eight first-layer neighbours)
     adhesion_stencil: str = "e8"
+    # outflow at x = nx-1 of an open x: copy (from column nx-2) | pressure (Zou-He density
+    # condition holding rho_out per component)
+    outlet: str = "copy"
+    rho_out: tuple = (RHO_D, RHO_M)
     surface: dict | None = None  # for the contact angle: {"kind": "flat"|"circle", ...}
     # 16-bit storage keeps f_i - w_i rho0 per component; the dissolved-phase density serves both
     # phases best (ignored by FP32 / FP64 storage)
@@ -116,7 +120,7 @@ class Scenario:
                     G=self.G, lam=self.lam, Gw2=self.Gw2, delta=self.delta, g=tuple(self.g),
                     u_in=self.u_in, rho_in=tuple(self.rho_in), u_wall=tuple(self.u_wall),
                     inlet_profile=self.inlet_profile, second_layer=self.second_layer,
-                    adhesion_stencil=self.adhesion_stencil)
+                    adhesion_stencil=self.adhesion_stencil, outlet=self.outlet, rho_out=tuple(self.rho_out))
 
 
 def _grid(ny, nx):

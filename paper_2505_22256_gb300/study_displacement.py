@@ -94,12 +94,16 @@ def main(argv=None) -> int:
     ap.add_argument("--size", default="4096x2048")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--u-in", type=float, default=None, help="inlet velocity (default 0.005)")
+    ap.add_argument("--outlet", default="copy", choices=["copy", "pressure"],
+                    help="outflow rule: copy from column nx-2, or the Zou-He density condition holding "
+                         "the initial densities of the B-filled medium (0.03, 1.0)")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     nx, ny = map(int, args.size.split("x"))
     sc = case(nx, ny)
     if args.u_in is not None:
         sc.u_in = args.u_in
+    sc.outlet = args.outlet
     rows = run(sc, args.steps, args.check, args.storage)
     print(table(rows))
     if args.json:

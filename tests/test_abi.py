@@ -95,14 +95,20 @@ def test_invalid_parameters_are_rejected(lbm, field, value):
     ("periodic", "periodic", "u_wall", (0.01, 0.0)),    # sliding walls need walls in y
     ("open", "wall", "u_wall", (0.0, 0.01)),            # ... and a closed x
     ("periodic", "wall", "u_wall", (float("inf"), 0.0)),
+    ("periodic", "wall", "outlet", 1),                  # the pressure outlet needs an open x
+    ("open", "wall", "outlet", 2),                      # no such outlet
+    ("open", "wall", "rho_out", (0.0, 1.0)),            # outlet densities must be > 0
 ])
 def test_inlet_profile_and_sliding_wall_parameters_are_checked(lbm, bc_x, bc_y, field, value):
     solid, a, b = _case()
     p = lbm.make_params()
     if field == "u_wall":
         p.u_wall[0], p.u_wall[1] = value
+    elif field == "rho_out":
+        p.outlet = 1
+        p.rho_out[0], p.rho_out[1] = value
     else:
-        p.inlet_profile = value
+        setattr(p, field, value)
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(lbm.make_grid(16, 16, bc_x, bc_y), solid, p, a, b)
     assert e.value.status == lbm.LBM_EINVAL

@@ -60,6 +60,16 @@ def d2q9_adhesion(make, **kw):
     return build
 
 
+def with_attrs(make, **kw):
+    """The same case with some scenario attributes replaced."""
+    def build():
+        sc = make()
+        for k, v in kw.items():
+            setattr(sc, k, v)
+        return sc
+    return build
+
+
 def psi_only(make):
     """The same case with the second-layer reading that copies psi only (Sec. 2.4, Table 1)."""
     def build():
@@ -92,6 +102,11 @@ SCENARIOS = {
     "pillar8_d2q9": d2q9_adhesion(pillar_case),
     "gw2_equals_G_d2q9": d2q9_adhesion(lambda: S.cylinder_droplet(64, lam=1.7), Gw2=None),
     "flat64x48_d2q9_original": d2q9_adhesion(lambda: S.flat_droplet(64, 48, r=12, lam=0.4, scheme="original")),
+    "porous_open_pressure": with_attrs(small_porous, outlet="pressure"),
+    "square_obstacle_small_pressure": with_attrs(lambda: S.square_obstacle_channel(nx=140, ny=60, side=10,
+                                                                                  center=(49, 30), r=10.0,
+                                                                                  drop=(22, 30)),
+                                                 outlet="pressure", rho_out=(0.035, 0.98)),
     "square_obstacle_small_d2q9": d2q9_adhesion(lambda: S.square_obstacle_channel(nx=140, ny=60, side=10,
                                                                                  center=(49, 30), r=10.0,
                                                                                  drop=(22, 30))),
@@ -530,7 +545,6 @@ def test_checkpoint_roundtrip_is_bit_exact():
         raw_par = bytearray(bytes(par))
         mode_end = lbm.lbm_params.mode.offset + 4
         raw_par[mode_end:lbm.lbm_params.lambda_.offset] = b"\xab" * (lbm.lbm_params.lambda_.offset - mode_end)
-        raw_par[lbm.lbm_params.pad_.offset:lbm.lbm_params.pad_.offset + 4] = b"\xcd" * 4
         par2 = lbm.lbm_params.from_buffer_copy(bytes(raw_par))
         ctx2 = lbm.lbm_create(g, sc.solid, par2, sc.rhoA0, sc.rhoB0, lbm.LBM_STORE_F32)
         lbm.lbm_load(ctx2, p)
