@@ -115,8 +115,7 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
             src = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
             off = (I)i * ps + c - cx(i);
         } else {
-            if (cx(i) > 0 && inlet) continue;               // entering through the inlet: set below
-            if (cx(i) < 0 && outlet && Pin.outlet) continue;  // pressure outlet: set below
+            if (cx(i) > 0 && inlet) continue;  // entering through the inlet: set below
             const bool blocked = (fl >> (i - 1)) & 1u;
             int b = c;
             if (cx(i) < 0 && outlet) b = (fl & kOutletOwnBit) ? c : c - 1;  // copied from upstream
@@ -138,10 +137,11 @@ __device__ __forceinline__ void pull(const Pair<S>* __restrict__ rm, const Pair<
         f[8] = vfma(d5, s2, f[6]);
     }
     if (kGeneral && outlet && Pin.outlet) {
-        // Zou-He density condition per component (Sec. 3.3 outflow, pressure reading): the node gets
-        // the densities rho_out and no y-momentum, with non-equilibrium bounce-back along x.  The
-        // known populations give rho u_x = f0 + f2 + f4 + 2 (f1 + f5 + f8) - rho_out; shifted
-        // storage holds h = f - w rho0, whose known sum misses rho0 (those weights sum to 1).
+        // Zou-He density condition per component (Sec. 3.3 outflow, pressure reading), replacing the
+        // f3, f6, f7 the copy rule pulled above: the node gets the densities rho_out and no momentum
+        // along y, with non-equilibrium bounce-back along x.  The known populations give
+        // rho u_x = f0 + f2 + f4 + 2 (f1 + f5 + f8) - rho_out; shifted storage holds h = f - w rho0,
+        // whose known sum misses rho0 (those weights sum to 1).
         V2<R> known = vadd(vadd(vadd(f[0], f[2]), f[4]), vmul(vbc<R>(2), vadd(vadd(f[1], f[5]), f[8])));
         if constexpr (Store<S>::kShift && !kAddShift) known = vadd(known, V2<R>{Pin.rho0[0], Pin.rho0[1]});
         const V2<R> rho_ux = vsub(known, V2<R>{Pin.rho_out[0], Pin.rho_out[1]});
