@@ -345,9 +345,11 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, double limit_ms);
  * Drops the captured graph.  LBM_EINVAL for other values. */
 lbm_status lbm_set_wall_path(lbm_ctx* ctx, int32_t inline_correction);
 
-/* Time candidate launch shapes on the live state (both widths x both wall-list forms x the row
- * settings 0, -8, 16, 32, 64, 128; each for `steps` steps, after one warm-up launch) and keep the
- * fastest.  The state advances by the steps taken; best_ms (may be NULL)
+/* Time candidate launch shapes on the live state (the current shape first, then both widths x both
+ * wall-list forms x the row settings 0, -8, 16, 32, 64, 128; each twice for `steps` steps after one
+ * warm-up launch, keeping the faster time) and keep the fastest; a shape replaces the best so far
+ * only when it is at least 1 % faster, so that shapes within the timing noise do not trade places
+ * from run to run.  The state advances by the steps taken; best_ms (may be NULL)
  * receives the best time per step.  Synchronises. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms);
 

@@ -1041,18 +1041,29 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    // Candidates: the current shape first, then every other one.  Each is timed twice and keeps
+    // the faster time; another shape replaces the best only when it is at least 1 % faster, so
+    // that shapes within the timing noise of each other do not trade places from run to run.
+    struct Cand {
+        int w, t, r;
+    };
+    std::vector<Cand> cands{{c.wall_inline, c.block_threads, c.block_rows}};
+    for (int w = 0; w < 2; ++w)
+        for (int t : cand_t)
+            for (int r : cand_r)
+                if (!(w == cands[0].w && t == cands[0].t && r == cands[0].r)) cands.push_back({w, t, r});
     double best = 1e300;
     int bt = c.block_threads, br = c.block_rows, bw = c.wall_inline;
-    for (int w = 0; w < 2; ++w)
-    for (int t : cand_t)
-        for (int r : cand_r) {
-            c.wall_inline = w;
-            lbm_status s = lbm_set_launch(ctx, t, r);
-            if (s != LBM_OK) continue;
-            if (launch_step(c, c.cur, c.stream) != cudaSuccess) continue;
-            c.cur ^= 1;
-            ++c.steps;
-            ++c.version;
+    for (const Cand& cd : cands) {
+        c.wall_inline = cd.w;
+        lbm_status s = lbm_set_launch(ctx, cd.t, cd.r);
+        if (s != LBM_OK) continue;
+        if (launch_step(c, c.cur, c.stream) != cudaSuccess) continue;
+        c.cur ^= 1;
+        ++c.steps;
+        ++c.version;
+        double ms_best = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, c.stream);
             for (int k = 0; k < steps; ++k) {
                 launch_step(c, c.cur, c.stream);
@@ -1064,13 +1075,15 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps, double* best_ms) {
             if (cudaEventSynchronize(e1) != cudaSuccess) break;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms / steps < best) {
-                best = ms / steps;
-                bt = t;
-                br = r;
-                bw = w;
-            }
+            ms_best = ms < ms_best ? ms : ms_best;
         }
+        if (ms_best / steps < 0.99 * best || best == 1e300) {
+            best = ms_best / steps;
+            bt = cd.t;
+            br = cd.r;
+            bw = cd.w;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CUDA_TRY(cudaGetLastError());
