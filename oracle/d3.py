@@ -90,7 +90,7 @@ def e8_weights_3d() -> dict:
 class _Cfg3(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("nthreads", ctypes.c_int32), ("second_layer", ctypes.c_int32),
-                ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("lam", ctypes.c_double),
+                ("adhesion_stencil", ctypes.c_int32), ("pad_", ctypes.c_int32), ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("lam", ctypes.c_double),
                 ("Gw2", ctypes.c_double), ("delta", ctypes.c_double), ("g", ctypes.c_double * 3),
                 ("w", ctypes.c_double * 7)]
 
@@ -109,6 +109,9 @@ class Config3:
     delta: float = 0.8
     g: tuple = (0.0, 0.0, 0.0)
     second_layer: str = "psi_and_solid"  # or "psi" (Sec. 2.4, Table 1: what a replaced site copies)
+    # adhesion sum of Eq. 9: "e8" (the 92-offset stencil) or "d3q19" (as printed: D3Q19 weights over
+    # the 18 first-layer neighbours)
+    adhesion_stencil: str = "e8"
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
 
     def c(self) -> _Cfg3:
@@ -126,6 +129,7 @@ class Config3:
         for i, q in enumerate(SHELLS3):
             s.w[i] = float(w[q])
         s.second_layer = {"psi_and_solid": 0, "psi": 1}[self.second_layer]
+        s.adhesion_stencil = {"e8": 0, "d3q19": 1}[self.adhesion_stencil]
         return s
 
 

@@ -18,6 +18,8 @@
  *     and passed in);
  *   - second-layer reconstruction (Sec. 2.4, Table 1 in 2-D): a second-layer site x+e
  *     (|e|_inf = 2) that is not fluid takes the information of x + sign(e) componentwise;
+ *   - adhesion sum of Eq. 9 on the same 92 offsets, or (adhesion_stencil = 1) as printed, with the
+ *     D3Q19 weights over the 18 first-layer neighbours (the 3-D form of the 2-D option);
  *   - boundaries: periodic in x, y and z (the paper's case); solid nodes from the mask.
  *
  * State convention: f[k][i][z][y][x], k = 0 ("A") or 1 ("B"), i = 0..18, x fastest.  Solid nodes
@@ -36,6 +38,10 @@ typedef struct {
     int32_t nthreads;
     int32_t second_layer; /* 0: a replaced second-layer site takes psi and the solid switch of
                              x + sign(e); 1: psi only, the (solid) site keeping s = 1 */
+    int32_t adhesion_stencil; /* 0: the adhesion sum of Eq. 9 on the 92-offset stencil of the
+                                 cohesion force; 1: Eq. 9 as printed, in 3-D: the D3Q19 weights
+                                 w_i over the 18 first-layer neighbours */
+    int32_t pad_;
     double tau[2];    /* Eq. 2 */
     double G;         /* Eq. 8 */
     double lambda;    /* G_w1 / G_w2 */
@@ -153,6 +159,15 @@ static void node_forces3(const oracle3_cfg* c, const uint8_t* solid, const doubl
                 gB[0] += w * pB * ex; gB[1] += w * pB * ey; gB[2] += w * pB * ez;
                 a[0] += w * sw * ex; a[1] += w * sw * ey; a[2] += w * sw * ez;
             }
+    if (c->adhesion_stencil == 1) { /* a = sum_i w_i s(x + e_i) e_i over the D3Q19 velocities */
+        a[0] = a[1] = a[2] = 0.0;
+        for (int i = 1; i < 19; i++) {
+            double sw = solid[id3(c, x + C3X[i], y + C3Y[i], z + C3Z[i])] ? 1.0 : 0.0;
+            a[0] += W19[i] * sw * C3X[i];
+            a[1] += W19[i] * sw * C3Y[i];
+            a[2] += W19[i] * sw * C3Z[i];
+        }
+    }
     double ra = rA[s0], rb = rB[s0];
     double GwA = c->scheme == SCHEME3_IMPROVED ? c->Gw2 * local_G3((ra - rb) / (ra + rb), c->lambda, c->delta)
                                                : c->lambda * c->Gw2;

@@ -72,6 +72,12 @@ def _brute_forces(cfg, solid, rA, rB, x, y, z):
         gA += w[q] * pa * np.array(e)
         gB += w[q] * pb * np.array(e)
         a += w[q] * sw * np.array(e)
+    if cfg.adhesion_stencil == "d3q19":  # Eq. 9 as printed: D3Q19 weights over the first neighbours
+        a = np.zeros(3)
+        for e in itertools.product(range(-1, 2), repeat=3):
+            q = sum(t * t for t in e)
+            if q in (1, 2) and solid[site(x + e[0], y + e[1], z + e[2])]:
+                a += (1.0 / 18.0 if q == 1 else 1.0 / 36.0) * np.array(e)
     ra, rb = rA[z, y, x], rB[z, y, x]
     re = (ra - rb) / (ra + rb)
     lam, dl = cfg.lam, cfg.delta
@@ -88,8 +94,9 @@ def _brute_forces(cfg, solid, rA, rB, x, y, z):
     return FA, FB
 
 
-@pytest.mark.parametrize("second_layer", ["psi_and_solid", "psi"])
-def test_forces_match_brute_force_next_to_a_solid_block(second_layer):
+@pytest.mark.parametrize("second_layer,adhesion_stencil", [("psi_and_solid", "e8"), ("psi", "e8"),
+                                                            ("psi_and_solid", "d3q19"), ("psi", "d3q19")])
+def test_forces_match_brute_force_next_to_a_solid_block(second_layer, adhesion_stencil):
     n = 9
     solid = np.zeros((n, n, n), np.uint8)
     solid[3:6, 2:5, 4:7] = 1
@@ -97,7 +104,8 @@ def test_forces_match_brute_force_next_to_a_solid_block(second_layer):
     rng = np.random.default_rng(5)
     rA = np.where(solid, 0.0, 0.2 + 0.8 * rng.random((n, n, n)))
     rB = np.where(solid, 0.0, 0.2 + 0.8 * rng.random((n, n, n)))
-    cfg = d3.Config3(n, n, n, G=1.1, lam=0.6, Gw2=0.35, second_layer=second_layer)
+    cfg = d3.Config3(n, n, n, G=1.1, lam=0.6, Gw2=0.35, second_layer=second_layer,
+                     adhesion_stencil=adhesion_stencil)
     f = d3.init3(cfg, solid, rA, rB)
     FA, FB, _ = d3.forces3(cfg, solid, f)
     for (z, y, x) in [(2, 3, 5), (6, 3, 5), (4, 1, 5), (4, 5, 3), (0, 0, 0), (7, 6, 2), (4, 8, 8)]:
@@ -148,20 +156,22 @@ def test_uniform_state_stays_at_rest_and_momentum_is_conserved():
     assert max(abs(d["mom_x"]), abs(d["mom_y"]), abs(d["mom_z"])) < 1e-11
 
 
-def test_lambda_one_makes_improved_equal_original():
+@pytest.mark.parametrize("adhesion_stencil", ["e8", "d3q19"])
+def test_lambda_one_makes_improved_equal_original(adhesion_stencil):
     solid, rA, rB = _sphere_case(n=14, R=3.0, r=3.5)
     n = solid.shape[0]
     out = []
     for scheme in ("improved", "original"):
-        cfg = d3.Config3(n, n, n, scheme=scheme, G=1.205, lam=1.0, Gw2=0.3)
+        cfg = d3.Config3(n, n, n, scheme=scheme, G=1.205, lam=1.0, Gw2=0.3, adhesion_stencil=adhesion_stencil)
         out.append(d3.run3(cfg, solid, d3.init3(cfg, solid, rA, rB), 40))
     np.testing.assert_array_equal(out[0], out[1])
 
 
-def test_mirror_symmetry_of_a_symmetric_droplet_on_a_sphere():
+@pytest.mark.parametrize("adhesion_stencil", ["e8", "d3q19"])
+def test_mirror_symmetry_of_a_symmetric_droplet_on_a_sphere(adhesion_stencil):
     solid, rA, rB = _sphere_case(n=16, R=3.5, r=3.5, noise=False)
     n = solid.shape[0]
-    cfg = d3.Config3(n, n, n, G=1.205, lam=0.5, Gw2=0.3)
+    cfg = d3.Config3(n, n, n, G=1.205, lam=0.5, Gw2=0.3, adhesion_stencil=adhesion_stencil)
     f = d3.run3(cfg, solid, d3.init3(cfg, solid, rA, rB), 60)
     ra, rb, ux, uy, uz = d3.fields3(cfg, solid, f)
     for a in (ra, rb, uy, uz):  # x -> n-1-x mirror (the geometry is symmetric about x = (n-1)/2)
@@ -237,3 +247,27 @@ def test_laplace_law_3d():
     r2 = 1 - np.sum((np.array(dp) - pred) ** 2) / np.sum((np.array(dp) - np.mean(dp)) ** 2)
     assert slope > 0 and r2 > 0.99, (inv_r, dp)
     assert abs(icpt) < 0.15 * slope * min(inv_r), (slope, icpt)
+
+
+def test_d3q19_adhesion_by_hand_next_to_a_flat_wall():
+    """Eq. 9 as printed in 3-D, next to a solid plane z = 0 (uniform densities, no cohesion): the
+    first layer sees e_z = -1 on one axis and four diagonal velocities, a_z = -(1/18 + 4/36) = -1/6,
+    so F_k = G_w,k rho_k / 6 along +z; the second layer feels nothing; the two second-layer readings
+    give one state."""
+    n = 8
+    solid = np.zeros((n, n, n), np.uint8)
+    solid[0] = 1
+    rA = np.where(solid, 0.0, 0.8)
+    rB = np.where(solid, 0.0, 0.1)
+    cfg = d3.Config3(n, n, n, scheme="original", G=0.0, lam=0.5, Gw2=0.3, adhesion_stencil="d3q19", nthreads=1)
+    FA, FB, _ = d3.forces3(cfg, solid, d3.init3(cfg, solid, rA, rB))
+    np.testing.assert_allclose(FA[2, 1], 0.5 * 0.3 * 0.8 / 6.0, rtol=1e-14)
+    np.testing.assert_allclose(FB[2, 1], 0.3 * 0.1 / 6.0, rtol=1e-14)
+    np.testing.assert_allclose(FA[2, n - 1], -0.5 * 0.3 * 0.8 / 6.0, rtol=1e-14)  # periodic: the plane again
+    assert np.all(FA[:2] == 0.0) and np.all(FA[2, 2:n - 1] == 0.0)
+    solid, rA, rB = _sphere_case(n=14, R=3.0, r=3.5)
+    out = []
+    for layer in ("psi_and_solid", "psi"):
+        cfg = d3.Config3(14, 14, 14, G=1.205, lam=1.6, Gw2=0.3, second_layer=layer, adhesion_stencil="d3q19")
+        out.append(d3.run3(cfg, solid, d3.init3(cfg, solid, rA, rB), 30))
+    np.testing.assert_array_equal(out[0], out[1])
