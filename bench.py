@@ -660,7 +660,8 @@ def cpu_baseline_3d(seconds: float, storage: str | None = None) -> dict:
     nz, ny, nx = sc.shape
     p = sc.params()
     cfg = d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
-                     delta=p["delta"], g=p["g"], second_layer=p["second_layer"])
+                     delta=p["delta"], g=p["g"], second_layer=p["second_layer"],
+                     adhesion_stencil=p["adhesion_stencil"])
     f = d3.init3(cfg, sc.solid, sc.rhoA0, sc.rhoB0)
     need = PARITY_STEPS if storage else 1
     snap = None

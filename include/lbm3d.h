@@ -34,6 +34,16 @@ typedef struct {
     int32_t nx, ny, nz; /* lattice size, each >= 5; periodic in every direction */
 } lbm3d_grid;
 
+/* Stencil of the adhesion sum a(x) of Eq. 9 in 3-D.  The default takes the 92 offsets and weights
+ * of the cohesion sum (the same reading as the 2-D default); LBM3_ADHESION_D3Q19 takes the sum as
+ * printed with the weights of the velocity set, w = 1/18 (axes) and 1/36 (face diagonals), over the
+ * 18 first-layer neighbours.  Under LBM3_ADHESION_D3Q19 the second-layer reconstruction of Table 1
+ * feeds the cohesion sum only, so both lbm_second_layer readings give the same state. */
+typedef enum {
+    LBM3_ADHESION_E8 = 0,
+    LBM3_ADHESION_D3Q19 = 1
+} lbm3d_adhesion_stencil;
+
 typedef struct {
     double tau[2];   /* relaxation times (Eq. 2), each > 0.5 */
     double G_AB;     /* inter-component strength (Eq. 8) */
@@ -45,6 +55,8 @@ typedef struct {
     double G_w2;     /* adhesion parameter of component B */
     double delta;    /* half-width of Eqs. 11-12, in (0, 1] */
     double g[3];     /* body acceleration, F_k += rho_k g */
+    int32_t adhesion_stencil; /* lbm3d_adhesion_stencil: the stencil of Eq. 9 */
+    int32_t pad_;             /* set to 0 */
 } lbm3d_params;
 
 typedef struct {

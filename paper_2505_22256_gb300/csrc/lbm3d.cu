@@ -84,7 +84,13 @@ struct P3 {
     R omega[2], cF[2], G, Gw2, lam, delta, s1, s2, s3, t2, t3, g[3];
     int mode;
     int psi;  // second-layer reading: a replaced (solid) site copies psi only and keeps s = 1
+    int adh;  // 1: adhesion sum of Eq. 9 with the D3Q19 weights over the first layer
 };
+
+// Adhesion variants of the wall stencil: 0 the 92-offset sum with the solid switch of a replaced
+// second-layer site, 1 the same keeping s = 1 there, 2 the D3Q19 first-layer sum (Eq. 9 as printed).
+enum { kAdhE8 = 0, kAdhE8Psi = 1, kAdhD3Q19 = 2 };
+__host__ __device__ constexpr double w19q(int q) { return q == 1 ? 1.0 / 18.0 : (q == 2 ? 1.0 / 36.0 : 0.0); }
 
 __global__ void k3_flags(Geo3 g, const uint8_t* __restrict__ solid, uint32_t* __restrict__ flags) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
@@ -260,12 +266,13 @@ __global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t
                             const typename Rho2<R>::T v = rho[n];
                             va[side] = sol ? (R)0 : v.x;
                             vb[side] = sol ? (R)0 : v.y;
-                            vs[side] = (sol || (P.psi && own)) ? (R)1 : (R)0;
+                            vs[side] = (sol || (P.psi && !P.adh && own)) ? (R)1 : (R)0;
                         }
                         const R w = (R)wq, a = va[0] - va[1], b = vb[0] - vb[1], sw = vs[0] - vs[1];
                         gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
                         gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
-                        ad[0] += w * dx * sw; ad[1] += w * dy * sw; ad[2] += w * dz * sw;
+                        const R wa = P.adh ? (R)w19q(q) : w;  // q <= 2 sites are never replaced
+                        ad[0] += wa * dx * sw; ad[1] += wa * dy * sw; ad[2] += wa * dz * sw;
                     }
         }
         R GA = (R)0;
@@ -363,7 +370,7 @@ constexpr size_t k3_march_smem() {
 // solid second-layer site (Sec. 2.4), density 0 and solid switch 1 at a solid site; solid sites
 // hold -1 in the ring.  b0..b4: ring rows of the planes z-2..z+2 at the node.  (Inlined: an
 // out-of-line call measured 7 % slower on the full case and twice as slow on a small one.)
-template <class R, bool kPsi>
+template <class R, int kAdh>
 __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, const V2<R>* b2, const V2<R>* b3,
                                            const V2<R>* b4, V2<R>& gx, V2<R>& gy, V2<R>& gz, R (&ad)[3]) {
     using V = V2<R>;
@@ -393,23 +400,26 @@ __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, 
                     }
                     const bool sol = w.x < (R)0;
                     v[side] = sol ? vbc<R>(0) : w;
-                    vs[side] = (sol || (kPsi && own)) ? (R)1 : (R)0;
+                    vs[side] = (sol || (kAdh == kAdhE8Psi && own)) ? (R)1 : (R)0;
                 }
                 const V a = vsub(v[0], v[1]);
-                const R w = (R)wq, sw = vs[0] - vs[1];
                 gx = vfma(vbc<R>(wq * dx), a, gx);
                 gy = vfma(vbc<R>(wq * dy), a, gy);
                 gz = vfma(vbc<R>(wq * dz), a, gz);
-                ad[0] += w * dx * sw;
-                ad[1] += w * dy * sw;
-                ad[2] += w * dz * sw;
+                const double wa = kAdh == kAdhD3Q19 ? w19q(q) : wq;
+                if (wa != 0.0) {
+                    const R w = (R)wa, sw = vs[0] - vs[1];
+                    ad[0] += w * dx * sw;
+                    ad[1] += w * dy * sw;
+                    ad[2] += w * dz * sw;
+                }
             }
 }
 
 #ifndef LBM3_MIN_BLOCKS
 #define LBM3_MIN_BLOCKS 3
 #endif
-template <class R, bool kPsi>
+template <class R, int kAdh>
 __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
     k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
              const V2<R>* __restrict__ rho, V2<R>* __restrict__ fout) {
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 gy = vadd(hy[0], hy[1]);
                 gz = vadd(hz[0], hz[1]);
             } else {
-                wall_stencil3<R, kPsi>(bs[0], bs[1], bs[2], bs[3], bs[4], gx, gy, gz, ad);
+                wall_stencil3<R, kAdh>(bs[0], bs[1], bs[2], bs[3], bs[4], gx, gy, gz, ad);
             }
             const R rA = r2.x, rB = r2.y;
             R GA = (R)0;
@@ -902,6 +912,7 @@ P3<R> make_p3(const lbm3d_params& p) {
     for (int d = 0; d < 3; ++d) P.g[d] = (R)p.g[d];
     P.mode = p.mode;
     P.psi = p.second_layer == LBM_SECOND_LAYER_PSI;
+    P.adh = p.adhesion_stencil == LBM3_ADHESION_D3Q19;
     return P;
 }
 
@@ -923,6 +934,12 @@ cudaError_t scratch_for(lbm3d_ctx* c) {
     return cudaMalloc(&c->scratch, (size_t)38 * c->g.N * sizeof(double));
 }
 
+// the step kernel instance of the adhesion variant
+template <class R>
+auto march_kernel(const P3<R>& P) {
+    return P.adh ? k3_march<R, kAdhD3Q19> : (P.psi ? k3_march<R, kAdhE8Psi> : k3_march<R, kAdhE8>);
+}
+
 template <class R>
 cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gr = grid3(c->g);
@@ -934,10 +951,8 @@ cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
                   (unsigned)((c->g.nz + zc - 1) / zc));
     V2<R>* fo = reinterpret_cast<V2<R>*>(c->f[1 - c->cur]);
-    if (P.psi)
-        k3_march<R, true><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
-    else
-        k3_march<R, false><<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
+    auto* kern = march_kernel<R>(P);
+    kern<<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
     c->cur ^= 1;
     return cudaGetLastError();
 }
@@ -1018,6 +1033,8 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     if (p->mode != LBM_ADS_ORIGINAL && p->mode != LBM_ADS_IMPROVED) return report_error(LBM_EINVAL, "bad mode");
     if (p->second_layer != LBM_SECOND_LAYER_PSI_AND_SOLID && p->second_layer != LBM_SECOND_LAYER_PSI)
         return report_error(LBM_EINVAL, "bad second_layer");
+    if (p->adhesion_stencil != LBM3_ADHESION_E8 && p->adhesion_stencil != LBM3_ADHESION_D3Q19)
+        return report_error(LBM_EINVAL, "bad adhesion_stencil");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     long long nf = 0;
     for (long long s = 0; s < N; ++s) {
@@ -1110,10 +1127,10 @@ extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
     if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
     // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
     TRY3(c->storage == LBM_STORE_F64
-             ? cudaFuncSetAttribute(c->pd.psi ? k3_march<double, true> : k3_march<double, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_march_smem<double>())
-             : cudaFuncSetAttribute(c->pf.psi ? k3_march<float, true> : k3_march<float, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_march_smem<float>()),
+             ? cudaFuncSetAttribute(march_kernel<double>(c->pd), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k3_march_smem<double>())
+             : cudaFuncSetAttribute(march_kernel<float>(c->pf), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k3_march_smem<float>()),
          "step kernel attributes");
     for (int64_t t = 0; t < n; ++t) {
         const cudaError_t e = c->storage == LBM_STORE_F64 ? step_once<double>(c) : step_once<float>(c);

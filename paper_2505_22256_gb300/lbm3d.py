@@ -21,7 +21,11 @@ class lbm3d_grid(ctypes.Structure):
 class lbm3d_params(ctypes.Structure):
     _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("second_layer", c_int32),
                 ("lambda_", c_double),
-                ("G_w2", c_double), ("delta", c_double), ("g", c_double * 3)]
+                ("G_w2", c_double), ("delta", c_double), ("g", c_double * 3), ("adhesion_stencil", c_int32),
+                ("pad_", c_int32)]
+
+
+ADHESION_STENCIL3 = {"e8": 0, "d3q19": 1}
 
 
 class lbm3d_diag(ctypes.Structure):
@@ -61,7 +65,7 @@ def _lib():
 
 
 def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8,
-                 g=(0.0, 0.0, 0.0), second_layer="psi_and_solid") -> lbm3d_params:
+                 g=(0.0, 0.0, 0.0), second_layer="psi_and_solid", adhesion_stencil="e8") -> lbm3d_params:
     p = lbm3d_params()
     p.tau[0], p.tau[1] = tau
     p.G_AB = G
@@ -72,6 +76,7 @@ def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, 
     for i in range(3):
         p.g[i] = g[i]
     p.second_layer = lbm.SECOND_LAYER[second_layer]
+    p.adhesion_stencil = ADHESION_STENCIL3[adhesion_stencil]
     return p
 
 
@@ -82,11 +87,11 @@ def _c(a, dtype):
 class Lattice3:
     """One 3-D lattice on the GPU (periodic in x, y, z; solid mask; FP32 or FP64)."""
 
-    def __init__(self, solid, rhoA0, rhoB0, params: dict, storage: str = "f32", cuda_stream: int | None = None):
+    def __init__(self, solid, rhoA0, rhoB0, params, storage: str = "f32", cuda_stream: int | None = None):
         solid = _c(solid, np.uint8)
         self.nz, self.ny, self.nx = solid.shape
         g = lbm3d_grid(self.nx, self.ny, self.nz)
-        p = make_params3(**params)
+        p = params if isinstance(params, lbm3d_params) else make_params3(**params)
         a, b = _c(rhoA0, np.float64), _c(rhoB0, np.float64)
         ctx = c_void_p()
         st = lbm.STORAGE[storage]

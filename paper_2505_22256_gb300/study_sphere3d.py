@@ -4,9 +4,12 @@ The case is the paper's 200x200x280 periodic box: a solid sphere of radius 50 at
 and a droplet of A of radius 45 at (100, 100, 180).  The paper's three strength coefficients are
 lambda = 0.38, 1 and 2.1, for which it reports theta of about 45, 90 and 146 deg.  Each case steps
 in intervals, and after each interval the study fits the contact angle.  The table gives the final
-angle, its change over the last interval, max |u| and the density extrema.
+angle, its change over the last interval, max |u| and the density extrema.  --adhesion-stencil d3q19
+takes the adhesion sum of Eq. 9 as printed (first layer, D3Q19 weights) and --gw2-is-g sets
+G_w2 = G_AB, the paper's choice.
 
     python -m paper_2505_22256_gb300.study_sphere3d [--steps 30000] [--interval 5000] [--n 200]
+        [--adhesion-stencil e8|d3q19] [--gw2-is-g]
 """
 from __future__ import annotations
 
@@ -19,20 +22,25 @@ from . import lbm3d, scenarios as S
 PAPER_THETA = {0.38: 45.0, 1.0: 90.0, 2.1: 146.0}
 
 
-def case(lam: float, n: int = 200, second_layer: str = "psi_and_solid"):
+def case(lam: float, n: int = 200, second_layer: str = "psi_and_solid", adhesion_stencil: str = "e8",
+         gw2_is_g: bool = False):
     sc = S.sphere_droplet_3d(lam=lam) if n == 200 else S.sphere_droplet_3d_small(n, lam=lam)
     sc.second_layer = second_layer
+    sc.adhesion_stencil = adhesion_stencil
+    if gw2_is_g:
+        sc.Gw2 = sc.G
     return sc
 
 
 def run(lams=(0.38, 1.0, 2.1), steps: int = 30000, interval: int = 5000, storage: str = "f32",
-        n: int = 200, second_layer: str = "psi_and_solid") -> list[dict]:
+        n: int = 200, second_layer: str = "psi_and_solid", adhesion_stencil: str = "e8",
+        gw2_is_g: bool = False) -> list[dict]:
     """One record per lambda."""
     if interval < 1 or steps < interval:
         raise ValueError("need steps >= interval >= 1")
     out = []
     for lam in lams:
-        sc = case(lam, n, second_layer)
+        sc = case(lam, n, second_layer, adhesion_stencil, gw2_is_g)
         lat = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, sc.params(), storage)
         try:
             angles = []
@@ -46,7 +54,7 @@ def run(lams=(0.38, 1.0, 2.1), steps: int = 30000, interval: int = 5000, storage
         finally:
             lat.close()
         out.append({
-            "lambda": lam, "paper_theta": PAPER_THETA.get(lam), "n": n, "steps": steps, "theta": angles[-1],
+            "lambda": lam, "adhesion_stencil": adhesion_stencil, "G_w2": sc.Gw2, "paper_theta": PAPER_THETA.get(lam), "n": n, "steps": steps, "theta": angles[-1],
             "dtheta_last": abs(angles[-1] - angles[-2]) if len(angles) > 1 else float("nan"), "history": angles,
             "umax": d["umax"], "rhoA_min": d["rhoA_min"], "rhoA_max": d["rhoA_max"],
             "rhoB_min": d["rhoB_min"], "rhoB_max": d["rhoB_max"], "unstable": bool(d["unstable"]),
@@ -73,10 +81,12 @@ def main(argv=None) -> int:
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
     ap.add_argument("--lambdas", default="0.38,1,2.1")
     ap.add_argument("--second-layer", default="psi_and_solid", choices=["psi_and_solid", "psi"])
+    ap.add_argument("--adhesion-stencil", default="e8", choices=["e8", "d3q19"])
+    ap.add_argument("--gw2-is-g", action="store_true", help="G_w2 = G_AB (the paper's choice)")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     rows = run(tuple(float(v) for v in args.lambdas.split(",")), args.steps, args.interval, args.storage, args.n,
-               args.second_layer)
+               args.second_layer, args.adhesion_stencil, args.gw2_is_g)
     print(table(rows))
     if args.json:
         with open(args.json, "w") as fh:

@@ -199,7 +199,8 @@ def test_3d_struct_layouts_match_header(lbm, tmp_path):
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
 
 
-@pytest.mark.parametrize("what", ["tau", "lambda", "delta", "mode", "size", "storage", "density", "allsolid"])
+@pytest.mark.parametrize("what", ["tau", "lambda", "delta", "mode", "adhesion", "size", "storage", "density",
+                                  "allsolid"])
 def test_3d_invalid_input_is_rejected_before_any_device_work(lbm, what):
     from paper_2505_22256_gb300 import lbm3d
 
@@ -223,9 +224,12 @@ def test_3d_invalid_input_is_rejected_before_any_device_work(lbm, what):
         a[2, 3, 4] = -1.0
     elif what == "allsolid":
         solid = np.ones_like(solid)
-    if what == "mode":
+    if what in ("mode", "adhesion"):
         p = lbm3d.make_params3()
-        p.mode = 5
+        if what == "mode":
+            p.mode = 5
+        else:
+            p.adhesion_stencil = 2
         g = lbm3d.lbm3d_grid(n, n, n)
         ctx = ctypes.c_void_p()
         st = lbm3d._lib().lbm3d_create(ctypes.byref(g), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),

@@ -24,7 +24,8 @@ def ocfg(sc):
     nz, ny, nx = sc.shape
     p = sc.params()
     return d3.Config3(nx, ny, nz, scheme=p["scheme"], tau=p["tau"], G=p["G"], lam=p["lam"], Gw2=p["Gw2"],
-                      delta=p["delta"], g=p["g"], second_layer=p["second_layer"])
+                      delta=p["delta"], g=p["g"], second_layer=p["second_layer"],
+                      adhesion_stencil=p["adhesion_stencil"])
 
 
 def orun(sc, n):
@@ -48,11 +49,20 @@ def _psi(sc):
     return sc
 
 
+def _d3q19(sc, second_layer="psi_and_solid"):
+    """The adhesion sum of Eq. 9 as printed: D3Q19 weights over the first layer."""
+    sc.adhesion_stencil = "d3q19"
+    sc.second_layer = second_layer
+    return sc
+
+
 CASES = {
     "sphere24": lambda: S.sphere_droplet_3d_small(24, lam=0.6),
     "sphere24_hydrophobic": lambda: S.sphere_droplet_3d_small(24, lam=2.1, seed=4),
     "sphere24_original": lambda: S.sphere_droplet_3d_small(24, lam=0.5, scheme="original"),
     "sphere24_psi": lambda: _psi(S.sphere_droplet_3d_small(24, lam=1.7, seed=6)),
+    "sphere24_d3q19": lambda: _d3q19(S.sphere_droplet_3d_small(24, lam=0.6, seed=7)),
+    "sphere24_d3q19_original": lambda: _d3q19(S.sphere_droplet_3d_small(24, lam=1.8, scheme="original", seed=8)),
     "odd_box": lambda: S.sphere_droplet_3d(nx=21, ny=17, nz=26, R=5.0, sphere=(10.0, 8.0, 9.0), r=5.5,
                                            drop=(10.0, 8.0, 17.0), lam=1.3),
     # the step kernel's edges: a partial 32-column tile (nx = 40), a last tile three rows high
@@ -130,6 +140,19 @@ def test_f32_matches_oracle_after_100_steps(name):
     assert drel <= 1e-5
     assert dabs <= 1e-5 * S.RHO_M
     assert max(float(np.max(np.abs(g[k] - o[k]))) for k in (2, 3, 4)) <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_d3q19_adhesion_ignores_the_second_layer_reading(storage):
+    """Under the first-layer adhesion sum the second-layer reading of Table 1 only feeds the cohesion
+    sum, where both readings copy the same psi: the two give the same state bit for bit."""
+    out = []
+    for sl in ("psi_and_solid", "psi"):
+        lat = lattice(_d3q19(S.sphere_droplet_3d_small(24, lam=1.4, seed=5), sl), storage)
+        lat.step(20)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
