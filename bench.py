@@ -24,6 +24,7 @@ rank 0 prints the JSON line with the max time over ranks.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -271,26 +272,30 @@ def step_kernel_name(storage: str, info: dict) -> str:
 
 def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step", sources=KERNEL_SOURCES,
                       launch: dict | None = None):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this launch's nodes; None when
-    the summary is missing, was taken on a different version of the kernel source, or (launch given)
-    on another instantiation or launch shape of the kernel than the one timed."""
-    p = os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters.txt")
-    try:
-        kv = {}
-        with open(p) as fh:
-            for line in fh:
-                if ":" in line and not line.startswith("#"):
-                    k, v = line.split(":", 1)
-                    kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
-            return None
-        for key, want in (launch or {}).items():
-            if kv.get(key) != str(want):
-                return None
-        per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
-        return per_node * nodes_per_launch
-    except (OSError, KeyError, ValueError):
-        return None
+    """DRAM bytes per launch from a committed ncu summary, scaled to this launch's nodes; None when
+    no summary was taken on this version of the kernel source or (launch given) on this
+    instantiation and launch shape of the kernel.  A kernel may have several summaries, one per
+    instantiation or launch shape: profiles/<prefix>_<storage>_counters.txt and
+    profiles/<prefix>_<storage>_counters_<variant>.txt."""
+    paths = [os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters.txt")]
+    paths += sorted(glob.glob(os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters_*.txt")))
+    for p in paths:
+        try:
+            kv = {}
+            with open(p) as fh:
+                for line in fh:
+                    if ":" in line and not line.startswith("#"):
+                        k, v = line.split(":", 1)
+                        kv[k.strip()] = v.strip()
+            if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
+                continue
+            if any(kv.get(key) != str(want) for key, want in (launch or {}).items()):
+                continue
+            per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
+            return per_node * nodes_per_launch
+        except (OSError, KeyError, ValueError):
+            continue
+    return None
 
 
 # ------------------------------------------------------------------------------------------------

@@ -41,6 +41,16 @@ def test_committed_traffic_only_for_the_launch_it_was_taken_on(tmp_path, monkeyp
     assert bench.committed_traffic("f32", 2000, launch={**good, "kernel": "k_step<float, float, 0, 0, 128>"}) is None
     assert bench.committed_traffic("f32", 2000, launch={**good, "grid_blocks": 608}) is None
     assert bench.committed_traffic("f16", 2000, launch=good) is None  # no file
+    # a second summary for another instantiation is found beside the first
+    other = {**good, "kernel": "k_step<float, float, 0, 0, 128>", "block_rows": 38}
+    (prof / "k_step_f32_counters_wall_called.txt").write_text(
+        f"kernel_source_sha256_16: {h}\n"
+        "kernel: k_step<float, float, 0, 0, 128>\nblock_rows: 38\ngrid_blocks: 456\n"
+        "nodes_per_launch: 1000\ndram_bytes_per_launch: 160000\n")
+    assert bench.committed_traffic("f32", 2000, launch=other) == pytest.approx(320000)
+    assert bench.committed_traffic("f32", 2000, launch=good) == pytest.approx(300000)
+    assert bench.committed_traffic("f32", 2000, launch={**other, "block_rows": 46}) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda sources=None: "0" * 16)
     assert bench.committed_traffic("f32", 2000, launch=good) is None  # the sources changed
+    assert bench.committed_traffic("f32", 2000, launch=other) is None
 
