@@ -72,6 +72,11 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--wall-inline", type=int, default=None, choices=[0, 1],
                     help="with --no-autotune: the step kernel's wall-list form (1 inlined, 0 called)")
+    ap.add_argument("--launch-table", action="store_true",
+                    help="instead of the bench line: every launch shape the autotuner tries (wall-list "
+                         "form x block width x row chunks), one untimed and three timed steps each, one "
+                         "JSON line with the table (a capture of it under ncu gives the per-shape "
+                         "counters in the same order)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--split", action="store_true",
@@ -270,31 +275,44 @@ def step_kernel_name(storage: str, info: dict) -> str:
     return f"k_step<{STORE_TYPE[storage]}, 0, {info['wall_inline']}, {info['block_threads']}>"
 
 
+def counter_records(path: str) -> list[dict]:
+    """The records of a counter summary: `key: value` lines, `#` comments; a file may hold several
+    records separated by `---` lines, each inheriting the keys above the first separator."""
+    recs, cur = [], {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("---"):
+                recs.append(cur)
+                cur = {}
+            elif ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                cur[k.strip()] = v.strip()
+    recs.append(cur)
+    return recs if len(recs) == 1 else [{**recs[0], **r} for r in recs[1:]]
+
+
 def committed_traffic(storage: str, nodes_per_launch: int, prefix: str = "k_step", sources=KERNEL_SOURCES,
                       launch: dict | None = None):
     """DRAM bytes per launch from a committed ncu summary, scaled to this launch's nodes; None when
-    no summary was taken on this version of the kernel source or (launch given) on this
-    instantiation and launch shape of the kernel.  A kernel may have several summaries, one per
-    instantiation or launch shape: profiles/<prefix>_<storage>_counters.txt and
-    profiles/<prefix>_<storage>_counters_<variant>.txt."""
+    no record was taken on this version of the kernel source or (launch given) on this
+    instantiation and launch shape of the kernel.  The summaries are
+    profiles/<prefix>_<storage>_counters.txt and profiles/<prefix>_<storage>_counters_<variant>.txt."""
     paths = [os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters.txt")]
     paths += sorted(glob.glob(os.path.join(ROOT, "profiles", f"{prefix}_{storage}_counters_*.txt")))
     for p in paths:
         try:
-            kv = {}
-            with open(p) as fh:
-                for line in fh:
-                    if ":" in line and not line.startswith("#"):
-                        k, v = line.split(":", 1)
-                        kv[k.strip()] = v.strip()
-            if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
-                continue
-            if any(kv.get(key) != str(want) for key, want in (launch or {}).items()):
-                continue
-            per_node = float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"])
-            return per_node * nodes_per_launch
-        except (OSError, KeyError, ValueError):
+            recs = counter_records(p)
+        except OSError:
             continue
+        for kv in recs:
+            try:
+                if kv.get("kernel_source_sha256_16") != kernel_source_hash(sources):
+                    continue
+                if any(kv.get(key) != str(want) for key, want in (launch or {}).items()):
+                    continue
+                return float(kv["dram_bytes_per_launch"]) / float(kv["nodes_per_launch"]) * nodes_per_launch
+            except (KeyError, ValueError):
+                continue
     return None
 
 
@@ -454,6 +472,48 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+# the candidates of lbm_autotune: wall-list form, block width, row chunks (0 guided, < 0 guided with
+# short tail items, > 0 uniform)
+LAUNCH_SHAPES = [(w, t, r) for w in (0, 1) for t in (128, 64) for r in (0, -8, 16, 32, 64, 128)]
+
+
+def launch_table(args, lat, stream) -> int:
+    """Every launch shape the autotuner tries: one untimed and three single-launch steps each (under
+    ncu, launch k of the capture belongs to shape k // 4 of the printed order), then, in a second
+    pass, the mean time per launch over 16 steps in each shape.  Prints one JSON line."""
+    import torch
+
+    from paper_2505_22256_gb300 import lbm
+
+    shapes, rows = [], []
+    for w, t, r in LAUNCH_SHAPES:
+        try:
+            lbm.lbm_set_launch(lat.ctx, t, r)
+        except lbm.LbmError:
+            continue
+        lbm.lbm_set_wall_path(lat.ctx, w)
+        info = lat.info()
+        for _ in range(4):
+            lat.step(1)
+        shapes.append((w, t, r))
+        rows.append({"wall_inline": w, "block_threads": t, "rows_arg": r, "kernel": step_kernel_name(args.storage, info),
+                     "block_rows": info["block_rows"], "grid_blocks": info["grid_blocks"],
+                     "work_items": info["work_items"]})
+    for (w, t, r), row in zip(shapes, rows):
+        lbm.lbm_set_launch(lat.ctx, t, r)
+        lbm.lbm_set_wall_path(lat.ctx, w)
+        lat.step(2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(16)
+        e1.record(stream)
+        e1.synchronize()
+        row["ms_per_launch"] = e0.elapsed_time(e1) / 16
+    lat.close()
+    print(json.dumps({"launch_table": rows, "storage": args.storage, "workload": args.workload}))
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -486,6 +546,8 @@ def run_ours(args):
     surfaces = [c.surface for c in cases]
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(cases, storage=args.storage, cuda_stream=stream.cuda_stream)
+    if args.launch_table:
+        return launch_table(args, lat, stream)
     # launch shape (row-chunk height, wall-list path) picked by the library's autotuner on the live
     # state, before the timed region
     tuned_ms = None if args.no_autotune else lbm.lbm_autotune(lat.ctx, 4)
