@@ -69,6 +69,14 @@ CASES = {
     # (ny = 11 in tiles of 4) and z planes split into uneven chunks (37 = 13 + 13 + 11)
     "uneven_chunks": lambda: S.sphere_droplet_3d(nx=40, ny=11, nz=37, R=4.0, sphere=(20.0, 5.0, 9.0), r=4.5,
                                                  drop=(20.0, 5.0, 19.0), lam=0.9),
+    # one block in x (20 < 32 columns) and one chunk in z (10 planes): the step kernel's halo wraps
+    # back into its own columns and planes
+    "one_box": lambda: S.sphere_droplet_3d(nx=20, ny=12, nz=10, R=3.0, sphere=(10.0, 6.0, 3.0), r=3.0,
+                                           drop=(10.0, 6.0, 7.0), lam=0.8),
+    # blocks one column wide (33 = 32 + 1) and one row high (9 = 4 + 4 + 1), and a last chunk of
+    # one plane (257 = 16 x 16 + 1)
+    "thin_boxes": lambda: S.sphere_droplet_3d(nx=33, ny=9, nz=257, R=3.0, sphere=(31.0, 7.0, 100.0), r=3.5,
+                                              drop=(31.0, 7.0, 106.0), lam=1.2),
 }
 
 
