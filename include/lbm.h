@@ -214,7 +214,7 @@ lbm_status lbm_create(const lbm_grid* grid, const uint8_t* solid, const lbm_para
 lbm_status lbm_ensemble_create(int32_t ncases, const lbm_case* cases, int32_t storage,
                                void* cuda_stream, lbm_ctx** out);
 
-/* Release every device and host resource of the context (synchronises its stream).  NULL is a
+/* Release every device and host resource of the context (synchronises its streams).  NULL is a
  * no-op. */
 void lbm_destroy(lbm_ctx* ctx);
 
@@ -227,8 +227,9 @@ void lbm_destroy(lbm_ctx* ctx);
  * launches. */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
 
-/* Wait for the context's stream, giving up after timeout_s seconds (<= 0: wait without limit)
- * with LBM_ETIMEOUT.  Reports LBM_ECUDA for a device error of earlier asynchronous work. */
+/* Wait for the context's stream and, once the overlapped transfers have been used, its copy
+ * streams, giving up after timeout_s seconds (<= 0: wait without limit) with LBM_ETIMEOUT.
+ * Reports LBM_ECUDA for a device error of earlier asynchronous work. */
 lbm_status lbm_synchronize(lbm_ctx* ctx, double timeout_s);
 
 /* Re-initialise one case from new densities: f = f^eq(rho_k, 0).  rho_A0 / rho_B0 are [ny][nx]
@@ -259,6 +260,19 @@ lbm_status lbm_fields(lbm_ctx* ctx, int32_t case_index, double* rho_A, double* r
  * lbm_fields_all: rho_A, rho_B, ux, uy of every case, as lbm_fields; any output may be NULL. */
 lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0, int32_t on_device);
 lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy, int32_t on_device);
+
+/* The same two operations with host arrays, overlapped with the context's work: the calls only
+ * enqueue and return.  Host<->device copies run on two copy streams of the context, through
+ * double-buffered device staging, so that the copy of one call's fields to the host and of the
+ * next call's densities to the device proceed while the context's stream steps the lattice.  In
+ * stream order the state is set after all work enqueued before lbm_set_densities_all_async and
+ * the fields are those after all work enqueued before lbm_fields_all_async.  The host arrays
+ * (same layout as above) should be page-locked for the copies to overlap; the inputs must stay
+ * unchanged and the outputs unread until lbm_synchronize returns (which waits for the copy
+ * streams too).  The first call allocates 96 bytes per node of all cases (LBM_ENOMEM when that
+ * fails), held until lbm_destroy.  LBM_EINVAL for NULL densities; any field output may be NULL. */
+lbm_status lbm_set_densities_all_async(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0);
+lbm_status lbm_fields_all_async(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy);
 
 /* Global FP64 diagnostics of one case (host output; synchronises).  Returns LBM_EUNSTABLE, with
  * *out filled, when the state holds a non-finite or non-positive density. */

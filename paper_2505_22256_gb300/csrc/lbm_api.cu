@@ -366,6 +366,17 @@ lbm_status check_case(lbm_ctx* ctx, int ci) {
 
 void free_ctx(Ctx& c) {
     drop_graphs(c);
+    for (cudaStream_t st : {c.xs_in, c.xs_out})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t ev : {c.xin_ready[k], c.xin_free[k], c.xout_ready[k], c.xout_free[k]})
+            if (ev) cudaEventDestroy(ev);
+        if (c.xin[k]) cudaFree(c.xin[k]);
+        if (c.xout[k]) cudaFree(c.xout[k]);
+    }
     void* ptrs[] = {c.dcases, c.f[0], c.f[1], c.flags, c.wsub, c.wa, c.solid, c.wl_node, c.wl_subst, c.wl_seff,
                     c.wl_a, c.items, c.dense, c.fields, c.diag_part, c.diag_out, c.ca_work, c.ca_all, c.ca_batch, c.ca_points, c.fields_all, c.slide_list, c.tmaps, c.err, c.sched, c.gflags};
     for (void* p : ptrs)
@@ -648,13 +659,18 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n) {
 lbm_status lbm_synchronize(lbm_ctx* ctx, double timeout_s) {
     if (!ctx) return fail(LBM_EINVAL, "NULL context");
     Ctx& c = ctx->c;
+    // the overlapped transfers' copy streams first: their last copies follow the work they wait for
     if (timeout_s <= 0) {
+        for (cudaStream_t st : {c.xs_in, c.xs_out})
+            if (st) CUDA_TRY(cudaStreamSynchronize(st));
         CUDA_TRY(cudaStreamSynchronize(c.stream));
         return check_device_error(c);
     }
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        cudaError_t e = cudaStreamQuery(c.stream);
+        cudaError_t e = cudaSuccess;
+        for (cudaStream_t st : {c.xs_in, c.xs_out, c.stream})
+            if (st && e == cudaSuccess) e = cudaStreamQuery(st);
         if (e == cudaSuccess) return check_device_error(c);
         if (e != cudaErrorNotReady) return fail(LBM_ECUDA, "stream: %s", cudaGetErrorString(e));
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -760,6 +776,88 @@ lbm_status lbm_fields_all(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux
         if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], dst[q], total * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(cudaStreamSynchronize(c.stream));
     return check_device_error(c);
+}
+
+// Copy streams, staging buffers and events of the overlapped transfers.
+static lbm_status xfer_setup(Ctx& c) {
+    if (c.xs_in) return LBM_OK;
+    const size_t total = (size_t)c.dense_elems;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&c.xin[k], 2 * total * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c.xout[k], 4 * total * sizeof(double));
+        for (cudaEvent_t* ev : {&c.xin_ready[k], &c.xin_free[k], &c.xout_ready[k], &c.xout_free[k]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.xs_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.xs_in, cudaStreamNonBlocking);  // set last: marks done
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k) {
+            for (cudaEvent_t* ev : {&c.xin_ready[k], &c.xin_free[k], &c.xout_ready[k], &c.xout_free[k]})
+                if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
+            if (c.xin[k]) cudaFree(c.xin[k]), c.xin[k] = nullptr;
+            if (c.xout[k]) cudaFree(c.xout[k]), c.xout[k] = nullptr;
+        }
+        if (c.xs_out) cudaStreamDestroy(c.xs_out), c.xs_out = nullptr;
+        if (c.xs_in) cudaStreamDestroy(c.xs_in), c.xs_in = nullptr;
+        return fail(oom ? LBM_ENOMEM : LBM_ECUDA, "overlapped transfers: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_densities_all_async(lbm_ctx* ctx, const double* rho_A0, const double* rho_B0) {
+    NvtxRange nvtx_("lbm_set_densities_all_async");
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    if (!rho_A0 || !rho_B0) return fail(LBM_EINVAL, "NULL density");
+    Ctx& c = ctx->c;
+    lbm_status s = xfer_setup(c);
+    if (s != LBM_OK) return s;
+    const long long total = c.dense_elems;
+    const int k = c.xin_k;
+    c.xin_k ^= 1;
+    double* a = c.xin[k];
+    double* b = c.xin[k] + total;
+    // the copy may start as soon as the kernels that read this staging buffer last have run; the
+    // state is set in stream order, after everything enqueued before
+    CUDA_TRY(cudaStreamWaitEvent(c.xs_in, c.xin_free[k], 0));
+    CUDA_TRY(cudaMemcpyAsync(a, rho_A0, total * sizeof(double), cudaMemcpyHostToDevice, c.xs_in));
+    CUDA_TRY(cudaMemcpyAsync(b, rho_B0, total * sizeof(double), cudaMemcpyHostToDevice, c.xs_in));
+    CUDA_TRY(cudaEventRecord(c.xin_ready[k], c.xs_in));
+    CUDA_TRY(cudaStreamWaitEvent(c.stream, c.xin_ready[k], 0));
+    for (int ci = 0; ci < (int)c.hcases.size(); ++ci) {
+        const long long off = c.hcases[ci].d_off;
+        CUDA_TRY(launch_feq_rest(c, ci, a + off, b + off, c.dense));
+        CUDA_TRY(launch_set_state(c, ci, c.dense));
+    }
+    CUDA_TRY(cudaEventRecord(c.xin_free[k], c.stream));
+    ++c.version;
+    return LBM_OK;
+}
+
+lbm_status lbm_fields_all_async(lbm_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy) {
+    NvtxRange nvtx_("lbm_fields_all_async");
+    if (!ctx) return fail(LBM_EINVAL, "NULL context");
+    Ctx& c = ctx->c;
+    lbm_status s = xfer_setup(c);
+    if (s != LBM_OK) return s;
+    const long long total = c.dense_elems;
+    const int k = c.xout_k;
+    c.xout_k ^= 1;
+    double* dst[4];
+    for (int q = 0; q < 4; ++q) dst[q] = c.xout[k] + q * total;
+    // the fields pass may overwrite this staging buffer once its previous copy to the host is done;
+    // the copies then run on their own stream, beside whatever the context's stream does next
+    CUDA_TRY(cudaStreamWaitEvent(c.stream, c.xout_free[k], 0));
+    CUDA_TRY(launch_fields_all(c, dst[0], dst[1], dst[2], dst[3]));
+    CUDA_TRY(cudaEventRecord(c.xout_ready[k], c.stream));
+    CUDA_TRY(cudaStreamWaitEvent(c.xs_out, c.xout_ready[k], 0));
+    double* outs[4] = {rho_A, rho_B, ux, uy};
+    for (int q = 0; q < 4; ++q)
+        if (outs[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], dst[q], total * sizeof(double), cudaMemcpyDeviceToHost, c.xs_out));
+    CUDA_TRY(cudaEventRecord(c.xout_free[k], c.xs_out));
+    return LBM_OK;
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int32_t ci, lbm_diag* out) {

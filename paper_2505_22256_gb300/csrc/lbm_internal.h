@@ -85,6 +85,14 @@ struct Ctx {
     long long dense_cap = 0;
     double* fields = nullptr;        // [4][max case nodes]
     double* fields_all = nullptr;    // [4][all nodes] for the batched host transfers (on first use)
+    // overlapped host transfers (lbm_set_densities_all_async, lbm_fields_all_async; on first use):
+    // copy streams, double-buffered device staging and the events that order them with c.stream
+    cudaStream_t xs_in = nullptr, xs_out = nullptr;
+    double* xin[2] = {nullptr, nullptr};   // [2][all nodes] densities from the host
+    double* xout[2] = {nullptr, nullptr};  // [4][all nodes] fields for the host
+    cudaEvent_t xin_ready[2] = {nullptr, nullptr}, xin_free[2] = {nullptr, nullptr};
+    cudaEvent_t xout_ready[2] = {nullptr, nullptr}, xout_free[2] = {nullptr, nullptr};
+    int xin_k = 0, xout_k = 0;
     double* diag_part = nullptr;     // [nitems][kDiagN]
     double* diag_out = nullptr;      // [ncases][kDiagN]
     double* ca_work = nullptr;       // contact-angle reductions

@@ -33,7 +33,7 @@ SYMBOLS = ("lbm_create", "lbm_ensemble_create", "lbm_destroy", "lbm_step", "lbm_
            "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_set_launch", "lbm_autotune",
            "lbm_save", "lbm_load", "lbm_status_str", "lbm_last_error", "lbm_diagnostics_noalloc",
            "lbm_diagnostics_all", "lbm_contact_angle_all", "lbm_set_wall_path", "lbm_set_densities_all",
-           "lbm_fields_all", "lbm_selftest_wait_timeout")
+           "lbm_fields_all", "lbm_selftest_wait_timeout", "lbm_set_densities_all_async", "lbm_fields_all_async")
 
 
 class lbm_grid(ctypes.Structure):
@@ -124,6 +124,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_set_densities_all.argtypes = [ctx_p, c_void_p, c_void_p, c_int32]
     lib.lbm_selftest_wait_timeout.argtypes = [ctx_p, c_double]
     lib.lbm_fields_all.argtypes = [ctx_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]
+    lib.lbm_set_densities_all_async.argtypes = [ctx_p, c_void_p, c_void_p]
+    lib.lbm_fields_all_async.argtypes = [ctx_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.lbm_contact_angle_all.argtypes = [ctx_p, POINTER(lbm_surface), c_void_p, c_void_p, c_void_p]
     lib.lbm_status_str.argtypes = [c_int32]
     lib.lbm_status_str.restype = ctypes.c_char_p
@@ -275,6 +277,22 @@ def lbm_fields_all(ctx, rho_A=None, rho_B=None, ux=None, uy=None, on_device: boo
         if a is not None and not on_device:
             assert a.dtype == np.float64 and a.flags.c_contiguous
     _check(load_library().lbm_fields_all(ctx, _ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy), 1 if on_device else 0))
+
+
+def lbm_set_densities_all_async(ctx, rho_A0: np.ndarray, rho_B0: np.ndarray) -> None:
+    """lbm_set_densities_all from host arrays, enqueued: the arrays (C-contiguous float64, ideally
+    page-locked) must stay unchanged until lbm_synchronize returns."""
+    for a in (rho_A0, rho_B0):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(load_library().lbm_set_densities_all_async(ctx, rho_A0.ctypes.data, rho_B0.ctypes.data))
+
+
+def lbm_fields_all_async(ctx, rho_A=None, rho_B=None, ux=None, uy=None) -> None:
+    """lbm_fields_all into host arrays, enqueued: read them after lbm_synchronize returns."""
+    for a in (rho_A, rho_B, ux, uy):
+        if a is not None:
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(load_library().lbm_fields_all_async(ctx, _ptr(rho_A), _ptr(rho_B), _ptr(ux), _ptr(uy)))
 
 
 def lbm_selftest_wait_timeout(ctx, limit_ms: float) -> None:

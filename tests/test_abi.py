@@ -141,6 +141,12 @@ def test_null_context_is_rejected(lbm):
         lbm.lbm_step(None, 1)
     assert e.value.status == lbm.LBM_EINVAL
     lbm.lbm_destroy(None)  # no-op
+    a = np.zeros(4)
+    for call in (lambda: lbm.lbm_set_densities_all_async(None, a, a), lambda: lbm.lbm_fields_all_async(None, a),
+                 lambda: lbm.lbm_synchronize(None, 0.0)):
+        with pytest.raises(lbm.LbmError) as e:
+            call()
+        assert e.value.status == lbm.LBM_EINVAL
 
 
 def test_no_cpu_fallback_without_a_gb300(lbm):
