@@ -103,6 +103,22 @@ lbm_status lbm3d_set_populations(lbm3d_ctx* ctx, const double* f);
  * held until lbm3d_destroy) or on the device (on_device = 1: read on the context's stream). */
 lbm_status lbm3d_set_densities(lbm3d_ctx* ctx, const double* rho_A, const double* rho_B, int32_t on_device);
 
+/* lbm3d_set_densities and lbm3d_fields with host arrays, overlapped with the context's work: the
+ * calls only enqueue and return.  Host<->device copies run on two copy streams of the context
+ * through double-buffered device staging, so that one call's fields travel to the host, and the
+ * next call's densities to the device, while the context's stream steps the lattice.  In stream
+ * order the state is set after all work enqueued before lbm3d_set_densities_async, and the fields
+ * are those after all work enqueued before lbm3d_fields_async.  The host arrays (same layout as the
+ * blocking calls) should be page-locked for the copies to overlap; the inputs must stay unchanged
+ * and the outputs unread until lbm3d_synchronize returns.  The first call allocates 56 bytes per
+ * node (LBM_ENOMEM when that fails), held until lbm3d_destroy.  Any field output may be NULL. */
+lbm_status lbm3d_set_densities_async(lbm3d_ctx* ctx, const double* rho_A, const double* rho_B);
+lbm_status lbm3d_fields_async(lbm3d_ctx* ctx, double* rho_A, double* rho_B, double* ux, double* uy, double* uz);
+
+/* Wait for the context's stream and its copy streams; LBM_ECUDA for an error of earlier
+ * asynchronous work. */
+lbm_status lbm3d_synchronize(lbm3d_ctx* ctx);
+
 /* FP64 diagnostics over the fluid nodes (host output; synchronises).  LBM_EUNSTABLE when a
  * density is non-finite or <= 0, or a velocity non-finite (the record is still written). */
 lbm_status lbm3d_diagnostics(lbm3d_ctx* ctx, lbm3d_diag* out);

@@ -886,6 +886,14 @@ struct lbm3d_ctx {
     double* ca = nullptr;          // contact angle: status record + block partials
     double* scratch = nullptr;     // [38][N] doubles for population transfers and fields (on demand)
     double* dens = nullptr;        // [2][N] doubles for lbm3d_set_densities from host arrays (on demand)
+    // overlapped host transfers (lbm3d_set_densities_async, lbm3d_fields_async; on first use): copy
+    // streams, double-buffered device staging and the events that order them with the stream
+    cudaStream_t xs_in = nullptr, xs_out = nullptr;
+    double* xin[2] = {nullptr, nullptr};   // [2][N] densities from the host
+    double* xout[2] = {nullptr, nullptr};  // [5][N] fields for the host
+    cudaEvent_t xin_ready[2] = {nullptr, nullptr}, xin_free[2] = {nullptr, nullptr};
+    cudaEvent_t xout_ready[2] = {nullptr, nullptr}, xout_free[2] = {nullptr, nullptr};
+    int xin_k = 0, xout_k = 0;
 };
 
 namespace {
@@ -995,7 +1003,23 @@ cudaError_t ca_passes(lbm3d_ctx* c, const double* sc, double R_) {
     return cudaGetLastError();
 }
 
+void free_xfer3(lbm3d_ctx* c) {
+    for (cudaStream_t* st : {&c->xs_in, &c->xs_out})
+        if (*st) {
+            cudaStreamSynchronize(*st);
+            cudaStreamDestroy(*st);
+            *st = nullptr;
+        }
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t* ev : {&c->xin_ready[k], &c->xin_free[k], &c->xout_ready[k], &c->xout_free[k]})
+            if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
+        if (c->xin[k]) cudaFree(c->xin[k]), c->xin[k] = nullptr;
+        if (c->xout[k]) cudaFree(c->xout[k]), c->xout[k] = nullptr;
+    }
+}
+
 void free3(lbm3d_ctx* c) {
+    free_xfer3(c);
     void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->scratch, c->dens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1153,6 +1177,85 @@ extern "C" lbm_status lbm3d_fields(lbm3d_ctx* c, double* rA, double* rB, double*
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
                  "fields copy");
     if (!on_device) TRY3(cudaStreamSynchronize(c->stream), "fields");
+    return LBM_OK;
+}
+
+namespace {
+// copy streams, staging and events of the overlapped transfers
+lbm_status xfer3_setup(lbm3d_ctx* c) {
+    if (c->xs_in) return LBM_OK;
+    const size_t N = (size_t)c->g.N;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&c->xin[k], 2 * N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->xout[k], 5 * N * sizeof(double));
+        for (cudaEvent_t* ev : {&c->xin_ready[k], &c->xin_free[k], &c->xout_ready[k], &c->xout_free[k]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking);  // set last: marks done
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        free_xfer3(c);
+        return report_error(oom ? LBM_ENOMEM : LBM_ECUDA, "overlapped transfers: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" lbm_status lbm3d_set_densities_async(lbm3d_ctx* c, const double* rho_A, const double* rho_B) {
+    NvtxRange nvtx_("lbm3d_set_densities_async");
+    if (!c || !rho_A || !rho_B) return report_error(LBM_EINVAL, "NULL argument");
+    const lbm_status s = xfer3_setup(c);
+    if (s != LBM_OK) return s;
+    const long long N = c->g.N;
+    const int k = c->xin_k;
+    c->xin_k ^= 1;
+    double* a = c->xin[k];
+    double* b = c->xin[k] + N;
+    // the copy may start once the kernel that read this staging buffer two calls ago has run
+    TRY3(cudaStreamWaitEvent(c->xs_in, c->xin_free[k], 0), "transfer order");
+    TRY3(cudaMemcpyAsync(a, rho_A, N * sizeof(double), cudaMemcpyHostToDevice, c->xs_in), "upload");
+    TRY3(cudaMemcpyAsync(b, rho_B, N * sizeof(double), cudaMemcpyHostToDevice, c->xs_in), "upload");
+    TRY3(cudaEventRecord(c->xin_ready[k], c->xs_in), "transfer order");
+    TRY3(cudaStreamWaitEvent(c->stream, c->xin_ready[k], 0), "transfer order");
+    if (c->storage == LBM_STORE_F64)
+        k3_set_rest<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (double2*)c->f[c->cur]);
+    else k3_set_rest<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (float2*)c->f[c->cur]);
+    TRY3(cudaGetLastError(), "state kernel");
+    TRY3(cudaEventRecord(c->xin_free[k], c->stream), "transfer order");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_fields_async(lbm3d_ctx* c, double* rho_A, double* rho_B, double* ux, double* uy,
+                                         double* uz) {
+    NvtxRange nvtx_("lbm3d_fields_async");
+    if (!c) return report_error(LBM_EINVAL, "NULL context");
+    const lbm_status s = xfer3_setup(c);
+    if (s != LBM_OK) return s;
+    const long long N = c->g.N;
+    const int k = c->xout_k;
+    c->xout_k ^= 1;
+    // the fields pass may overwrite this staging buffer once its previous copy to the host is done;
+    // the copies then run on their own stream, beside the context's next work
+    TRY3(cudaStreamWaitEvent(c->stream, c->xout_free[k], 0), "transfer order");
+    TRY3(run_fields(c, c->xout[k], false), "fields kernels");
+    TRY3(cudaEventRecord(c->xout_ready[k], c->stream), "transfer order");
+    TRY3(cudaStreamWaitEvent(c->xs_out, c->xout_ready[k], 0), "transfer order");
+    double* outs[5] = {rho_A, rho_B, ux, uy, uz};
+    for (int q = 0; q < 5; ++q)
+        if (outs[q])
+            TRY3(cudaMemcpyAsync(outs[q], c->xout[k] + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->xs_out),
+                 "fields copy");
+    TRY3(cudaEventRecord(c->xout_free[k], c->xs_out), "transfer order");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3d_synchronize(lbm3d_ctx* c) {
+    if (!c) return report_error(LBM_EINVAL, "NULL context");
+    for (cudaStream_t st : {c->xs_in, c->xs_out, c->stream})
+        if (st) TRY3(cudaStreamSynchronize(st), "synchronize");
     return LBM_OK;
 }
 

@@ -11,7 +11,8 @@ import numpy as np
 from . import lbm
 
 SYMBOLS3 = ("lbm3d_create", "lbm3d_destroy", "lbm3d_step", "lbm3d_fields", "lbm3d_get_populations",
-            "lbm3d_set_populations", "lbm3d_diagnostics", "lbm3d_contact_angle", "lbm3d_set_densities")
+            "lbm3d_set_populations", "lbm3d_diagnostics", "lbm3d_contact_angle", "lbm3d_set_densities",
+            "lbm3d_set_densities_async", "lbm3d_fields_async", "lbm3d_synchronize")
 
 
 class lbm3d_grid(ctypes.Structure):
@@ -55,6 +56,9 @@ def _lib():
         lib.lbm3d_get_populations.argtypes = [c_void_p, c_void_p]
         lib.lbm3d_set_populations.argtypes = [c_void_p, c_void_p]
         lib.lbm3d_set_densities.argtypes = [c_void_p, c_void_p, c_void_p, c_int32]
+        lib.lbm3d_set_densities_async.argtypes = [c_void_p, c_void_p, c_void_p]
+        lib.lbm3d_fields_async.argtypes = [c_void_p] + [c_void_p] * 5
+        lib.lbm3d_synchronize.argtypes = [c_void_p]
         lib.lbm3d_diagnostics.argtypes = [c_void_p, POINTER(lbm3d_diag)]
         lib.lbm3d_contact_angle.argtypes = [c_void_p, POINTER(c_double), c_double, d, d, POINTER(c_int64)]
         for name in SYMBOLS3:
@@ -143,6 +147,22 @@ class Lattice3:
             a, b = _c(rho_A, np.float64), _c(rho_B, np.float64)
             assert a.shape == b.shape == (self.nz, self.ny, self.nx)
             lbm._check(_lib().lbm3d_set_densities(self.ctx, a.ctypes.data, b.ctypes.data, 0))
+
+    def set_densities_async(self, rho_A, rho_B):
+        """lbm3d_set_densities from host arrays, enqueued: the arrays ([nz][ny][nx] float64,
+        C-contiguous, ideally page-locked) must stay unchanged until sync() returns."""
+        for a in (rho_A, rho_B):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nx * self.ny * self.nz
+        lbm._check(_lib().lbm3d_set_densities_async(self.ctx, rho_A.ctypes.data, rho_B.ctypes.data))
+
+    def fields_async_into(self, rho_A, rho_B, ux, uy, uz):
+        """lbm3d_fields into host arrays, enqueued: read them after sync() returns."""
+        for a in (rho_A, rho_B, ux, uy, uz):
+            assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nx * self.ny * self.nz)
+        lbm._check(_lib().lbm3d_fields_async(self.ctx, *[lbm._ptr(o) for o in (rho_A, rho_B, ux, uy, uz)]))
+
+    def sync(self):
+        lbm._check(_lib().lbm3d_synchronize(self.ctx))
 
     def diagnostics(self, allow_unstable: bool = False) -> dict:
         d = lbm3d_diag()

@@ -205,6 +205,17 @@ def test_3d_struct_layouts_match_header(lbm, tmp_path):
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
 
 
+def test_3d_null_context_is_rejected(lbm):
+    from paper_2505_22256_gb300 import lbm3d
+
+    lib = lbm3d._lib()
+    a = np.zeros(4)
+    for st in (lib.lbm3d_set_densities_async(None, a.ctypes.data, a.ctypes.data),
+               lib.lbm3d_fields_async(None, a.ctypes.data, None, None, None, None), lib.lbm3d_synchronize(None),
+               lib.lbm3d_step(None, 1)):
+        assert st == lbm.LBM_EINVAL
+
+
 @pytest.mark.parametrize("what", ["tau", "lambda", "delta", "mode", "adhesion", "size", "storage", "density",
                                   "allsolid"])
 def test_3d_invalid_input_is_rejected_before_any_device_work(lbm, what):
