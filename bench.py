@@ -607,7 +607,7 @@ def run_ours(args):
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     peak, peak_kind = hbm_peak()
     traffic = committed_traffic(args.storage, nodes, launch={
-        "kernel": step_kernel_name(args.storage, info), "block_rows": info["block_rows"],
+        "workload": args.workload, "kernel": step_kernel_name(args.storage, info), "block_rows": info["block_rows"],
         "grid_blocks": info["grid_blocks"]})
     dall = lat.diagnostics_all(allow_unstable=True)
     d = dall[0]
