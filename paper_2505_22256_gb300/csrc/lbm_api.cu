@@ -748,11 +748,7 @@ lbm_status lbm_set_densities_all(lbm_ctx* ctx, const double* rho_A0, const doubl
         a = c.fields_all;
         b = c.fields_all + total;
     }
-    for (int ci = 0; ci < (int)c.hcases.size(); ++ci) {
-        const long long off = c.hcases[ci].d_off;
-        CUDA_TRY(launch_feq_rest(c, ci, a + off, b + off, c.dense));
-        CUDA_TRY(launch_set_state(c, ci, c.dense));
-    }
+    CUDA_TRY(launch_set_rest_all(c, a, b));
     ++c.version;
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c.stream));
     return LBM_OK;
@@ -826,11 +822,7 @@ lbm_status lbm_set_densities_all_async(lbm_ctx* ctx, const double* rho_A0, const
     CUDA_TRY(cudaMemcpyAsync(b, rho_B0, total * sizeof(double), cudaMemcpyHostToDevice, c.xs_in));
     CUDA_TRY(cudaEventRecord(c.xin_ready[k], c.xs_in));
     CUDA_TRY(cudaStreamWaitEvent(c.stream, c.xin_ready[k], 0));
-    for (int ci = 0; ci < (int)c.hcases.size(); ++ci) {
-        const long long off = c.hcases[ci].d_off;
-        CUDA_TRY(launch_feq_rest(c, ci, a + off, b + off, c.dense));
-        CUDA_TRY(launch_set_state(c, ci, c.dense));
-    }
+    CUDA_TRY(launch_set_rest_all(c, a, b));
     CUDA_TRY(cudaEventRecord(c.xin_free[k], c.stream));
     ++c.version;
     return LBM_OK;

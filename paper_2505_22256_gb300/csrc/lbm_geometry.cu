@@ -235,6 +235,63 @@ __global__ void k_wall_scatter(const DevCase* __restrict__ cases, int c, const i
     }
 }
 
+// f = f^eq(rho_k, 0) in every case at once (cases along blockIdx.y): the stored populations that
+// k_feq_rest followed by k_set_state write, computed straight from the densities (all cases back to
+// back, case c at d_off) with the same double-precision products, so the state is the same bit for
+// bit.  The stored f*_i at x is what the next pull takes: w_i rho(x + e_i) from a fluid neighbour,
+// w_i rho(x) across a blocked link or beyond an open edge (the outlet column's own value where the
+// copy rule keeps it); G ghost columns repeat the periodic edges.
+template <class S>
+__global__ void k_set_rest_all(const DevCase* __restrict__ cases, int G, const uint8_t* __restrict__ solid_all,
+                               const uint16_t* __restrict__ flags_all, const double* __restrict__ rhoA_all,
+                               const double* __restrict__ rhoB_all, Pair<S>* __restrict__ out_all) {
+    using R = typename ComputeOf<S>::type;
+    const DevCase C = cases[blockIdx.y];
+    const long long N = (long long)C.nx * C.ny;
+    const long long plane = C.pitch;
+    Pair<S>* out = out_all + C.f_off;
+    const double* rk[2] = {rhoA_all + C.d_off, rhoB_all + C.d_off};
+    const uint8_t* sol = solid_all + C.d_off;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(s % C.nx), Y = (int)(s / C.nx);
+        const uint16_t fl = flags_all[C.d_off + s];
+        const long long o = (long long)Y * 9 * C.pitch + X + G;
+        R ov[2][9];
+        for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                double v = 0.0;
+                if (!(fl & kSolidBit)) {
+                    int tx = X + cx(i), ty = Y + cy(i);
+                    long long src = s;
+                    int q = i;
+                    if (C.bc_x == kOpen && (tx < 0 || tx >= C.nx)) {
+                        q = (X == C.nx - 1 && (fl & kOutletOwnBit) && cx(i) > 0) ? opp(i) : i;
+                    } else if (i != 0 && ((fl >> (opp(i) - 1)) & 1u)) {
+                        q = opp(i);
+                    } else {
+                        tx += (tx < 0) ? C.nx : 0;
+                        tx -= (tx >= C.nx) ? C.nx : 0;
+                        ty += (ty < 0) ? C.ny : 0;
+                        ty -= (ty >= C.ny) ? C.ny : 0;
+                        src = (long long)ty * C.nx + tx;
+                    }
+                    v = wq(q) * (sol[src] ? 0.0 : rk[k][src]);  // the value k_feq_rest holds at src
+                    if constexpr (Store<S>::kShift) v -= wq(i) * C.rho0[k];
+                }
+                ov[k][i] = (R)v;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            Pair<S>* p = out + i * plane;
+            store_pair<S, R>(p + o, ov[0][i], ov[1][i]);
+            if (C.bc_x == kPeriodic && X < G) store_pair<S, R>(p + o + C.nx, ov[0][i], ov[1][i]);
+            if (C.bc_x == kPeriodic && X >= C.nx - G) store_pair<S, R>(p + o - C.nx, ov[0][i], ov[1][i]);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_flags(Ctx& c, int ci, int32_t* row_counts) {
@@ -273,6 +330,29 @@ cudaError_t launch_wall_cast(Ctx& c, int ci) {
     else
         k_wall_scatter<float><<<g, 256, 0, c.stream>>>(c.dcases, ci, c.wl_node, c.wl_a, c.nwall, c.dense_elems, (float*)c.wa);
     return cudaGetLastError();
+}
+
+cudaError_t launch_set_rest_all(Ctx& c, const double* rhoA_all, const double* rhoB_all) {
+    long long nmax = 0;
+    for (const auto& h : c.hcases) nmax = nmax > (long long)h.nx * h.ny ? nmax : (long long)h.nx * h.ny;
+    const int nc = (int)c.hcases.size(), G = ghost_cols(c.storage);
+    for (int c0 = 0; c0 < nc; c0 += 65535) {  // cases along gridDim.y, at most 65535 per launch
+        const int n = nc - c0 < 65535 ? nc - c0 : 65535;
+        // about 4,096 blocks in all, at least one per case
+        long long bx = ((nmax + 255) / 256 < 4096 ? (nmax + 255) / 256 : 4096);
+        bx = bx * 8 / n > 0 ? (bx * 8 / n < bx ? bx * 8 / n : bx) : 1;
+        const dim3 g((unsigned)bx, (unsigned)n);
+        const DevCase* dc = c.dcases + c0;
+        switch (c.storage) {
+            case LBM_STORE_F64: k_set_rest_all<double><<<g, 256, 0, c.stream>>>(dc, G, c.solid, c.flags, rhoA_all, rhoB_all, (Pair<double>*)c.f[c.cur]); break;
+            case LBM_STORE_F32: k_set_rest_all<float><<<g, 256, 0, c.stream>>>(dc, G, c.solid, c.flags, rhoA_all, rhoB_all, (Pair<float>*)c.f[c.cur]); break;
+            case LBM_STORE_F16_SHIFTED: k_set_rest_all<__half><<<g, 256, 0, c.stream>>>(dc, G, c.solid, c.flags, rhoA_all, rhoB_all, (Pair<__half>*)c.f[c.cur]); break;
+            default: k_set_rest_all<__nv_bfloat16><<<g, 256, 0, c.stream>>>(dc, G, c.solid, c.flags, rhoA_all, rhoB_all, (Pair<__nv_bfloat16>*)c.f[c.cur]); break;
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace lbm

@@ -129,6 +129,8 @@ cudaError_t launch_diag_all(Ctx& c, double* rhoA_all = nullptr, double* rhoB_all
 cudaError_t launch_fields_all(Ctx& c, double* rhoA_all, double* rhoB_all, double* ux_all, double* uy_all);
 cudaError_t launch_densities_all(Ctx& c, double* rhoA_all, double* rhoB_all);
 cudaError_t launch_set_state(Ctx& c, int case_index, const double* dense_f);
+// f = f^eq(rho_k, 0) in every case from densities of all cases back to back (one launch per 65,535 cases)
+cudaError_t launch_set_rest_all(Ctx& c, const double* rhoA_all, const double* rhoB_all);
 cudaError_t launch_get_state(Ctx& c, int case_index, double* dense_f);
 cudaError_t launch_feq_rest(Ctx& c, int case_index, const double* rhoA, const double* rhoB, double* dense_f);
 int step_smem_bytes(int storage, int threads);

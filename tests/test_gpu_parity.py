@@ -411,13 +411,15 @@ def test_ensemble_equals_single_cases():
     ens.close()
 
 
-def test_batched_transfers_equal_per_case_calls():
+@pytest.mark.parametrize("storage", ["f32", "f16", "f64"])
+def test_batched_transfers_equal_per_case_calls(storage):
     """lbm_fields_all and lbm_set_densities_all over an uneven ensemble give the per-case calls'
-    results bit for bit: fields to host arrays and to device arrays, densities from host arrays."""
+    results bit for bit: fields to host arrays and to device arrays, densities from host arrays
+    (one launch for all cases against the per-case f^eq and state kernels)."""
     import torch
 
     cases = [SCENARIOS["cylinder96"](), SCENARIOS["porous_open"](), SCENARIOS["ragged131x77"](), SCENARIOS["pillar8"]()]
-    ens = lbm.Lattice(cases, "f32")
+    ens = lbm.Lattice(cases, storage)
     ens.step(23)
     batch = ens.fields_all()
     flat = [np.concatenate([ens.fields(i)[q].ravel() for i in range(len(cases))]) for q in range(4)]
