@@ -86,7 +86,7 @@ def parse(argv=None):
 
 
 WORKLOADS = ("sweep", "throat", "porous", "ensemble", "compare", "obstacle", "couette", "sphere3d")
-BYTES_PER_NODE_3D = {"f32": 304, "f64": 608}  # 2 components x 19 populations, read + written
+BYTES_PER_NODE_3D = {"f32": 304, "f64": 608, "f16": 152, "bf16": 152}  # 2 components x 19 populations, read + written
 
 
 # ------------------------------------------------------------------------------------------------
@@ -789,7 +789,7 @@ def run_ours_3d(args):
     from paper_2505_22256_gb300 import lbm3d
 
     if args.storage not in BYTES_PER_NODE_3D:
-        raise SystemExit("the 3-D workload runs in f32 or f64")
+        raise SystemExit("the 3-D workload runs in f32, f64, f16 or bf16")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -57,6 +57,8 @@ typedef struct {
     double g[3];     /* body acceleration, F_k += rho_k g */
     int32_t adhesion_stencil; /* lbm3d_adhesion_stencil: the stencil of Eq. 9 */
     int32_t pad_;             /* set to 0 */
+    double rho0_store[2];     /* reference densities of the shifted 16-bit storage modes: populations
+                                 are stored as f_i^k - w_i rho0_store[k]; ignored for FP32/FP64 */
 } lbm3d_params;
 
 typedef struct {
@@ -71,8 +73,9 @@ typedef struct {
 
 /* Create a lattice.  solid: host [nz][ny][nx], nonzero = solid, at least one fluid node.
  * rho_A0, rho_B0: host initial densities, finite and > 0 at fluid nodes; the state starts at
- * f^eq(rho_k, 0).  storage: LBM_STORE_F32 (FP32 arithmetic) or LBM_STORE_F64.  cuda_stream may be
- * NULL (the library creates its own).  LBM_EINVAL for bad sizes, parameters or fields;
+ * f^eq(rho_k, 0).  storage (lbm_storage, lbm.h): LBM_STORE_F64, LBM_STORE_F32 (FP32 arithmetic),
+ * or LBM_STORE_F16_SHIFTED / LBM_STORE_BF16_SHIFTED (16-bit storage of f - w rho0_store, FP32
+ * arithmetic).  cuda_stream may be NULL (the library creates its own).  LBM_EINVAL for bad sizes, parameters or fields;
  * LBM_ENOMEM when device memory runs out; LBM_ECUDA for other CUDA errors and for devices other
  * than sm_103. */
 lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid, const lbm3d_params* params,

@@ -82,10 +82,28 @@ __device__ __forceinline__ long long site(const Geo3& g, int x, int y, int z) {
 template <class R>
 struct P3 {
     R omega[2], cF[2], G, Gw2, lam, delta, s1, s2, s3, t2, t3, g[3];
+    R sh[3][2];  // storage shifts w rho0_store[k] of the 16-bit storage modes, by weight class
     int mode;
     int psi;  // second-layer reading: a replaced (solid) site copies psi only and keeps s = 1
     int adh;  // 1: adhesion sum of Eq. 9 with the D3Q19 weights over the first layer
 };
+
+// Stored populations: FP64 and FP32 pairs as computed; the 16-bit types hold h = f - w_i rho0_k per
+// component (rho0 = lbm3d_params.rho0_store), which ld3 adds back (one rounding, the widening is
+// exact) and st3 takes off before rounding to 16 bits.
+__host__ __device__ __forceinline__ constexpr int wcls3(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
+template <class S, class R>
+__device__ __forceinline__ V2<R> ld3(const Pair<S>* p, const P3<R>& P, int i) {
+    V2<R> v;
+    if constexpr (Store<S>::kShift) load_pair<S, R>(p, P.sh[wcls3(i)][0], P.sh[wcls3(i)][1], v.x, v.y);
+    else load_pair<S, R>(p, (R)0, (R)0, v.x, v.y);
+    return v;
+}
+template <class S, class R>
+__device__ __forceinline__ void st3(Pair<S>* p, V2<R> v, const P3<R>& P, int i) {
+    if constexpr (Store<S>::kShift) store_pair<S, R>(p, v.x - P.sh[wcls3(i)][0], v.y - P.sh[wcls3(i)][1]);
+    else store_pair<S, R>(p, v.x, v.y);
+}
 
 // Adhesion variants of the wall stencil: 0 the 92-offset sum with the solid switch of a replaced
 // second-layer site, 1 the same keeping s = 1 there, 2 the D3Q19 first-layer sum (Eq. 9 as printed).
@@ -140,9 +158,9 @@ struct Rho2<double> {
 };
 
 // the node's 38 post-streaming populations (f[i]: component A, f[19 + i]: component B)
-template <class R>
-__device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const V2<R>* __restrict__ fs, uint32_t fl, int s,
-                                      R (&f)[38]) {
+template <class S, class R>
+__device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const Pair<S>* __restrict__ fs, const P3<R>& P,
+                                      uint32_t fl, int s, R (&f)[38]) {
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         int src, q;
@@ -153,15 +171,15 @@ __device__ __forceinline__ void pull3(const Geo3& g, const Nb3& nb, const V2<R>*
             src = i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i));
             q = i;
         }
-        const V2<R> v = fs[(long long)q * g.N + src];
+        const V2<R> v = ld3<S, R>(fs + (long long)q * g.N + src, P, q);
         f[i] = v.x;
         f[19 + i] = v.y;
     }
 }
 
-template <class R>
-__global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
-                                              typename Rho2<R>::T* __restrict__ rho) {
+template <class S, class R>
+__global__ void __launch_bounds__(128) k3_rho(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
+                                              const Pair<S>* __restrict__ fs, typename Rho2<R>::T* __restrict__ rho) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const int s = (z * g.ny + y) * g.nx + x;
@@ -175,7 +193,8 @@ __global__ void __launch_bounds__(128) k3_rho(Geo3 g, const uint32_t* __restrict
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const bool bl = i > 0 && ((fl >> (i - 1)) & 1u);
-            f[i] = fs[(long long)(bl ? opp3(i) : i) * g.N + (bl || i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i)))];
+            const int q = bl ? opp3(i) : i;
+            f[i] = ld3<S, R>(fs + (long long)q * g.N + (bl || i == 0 ? s : nb.at(-e3x(i), -e3y(i), -e3z(i))), P, q);
         }
         // rho_k = sum_i f_i as a balanced tree (rounding grows with the depth, not the count), both
         // components at once
@@ -201,9 +220,9 @@ __device__ __forceinline__ double d3_neutral(int q) {
 // Fields form of the step, one node per thread: the same pull, moments and forces as the step
 // kernel below, writing rho_A, rho_B, u (FP64) and per-block diagnostic records (block index
 // blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
-template <class R>
+template <class S, class R>
 __global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
-                                                 const uint8_t* __restrict__ solid, const V2<R>* __restrict__ fs,
+                                                 const uint8_t* __restrict__ solid, const Pair<S>* __restrict__ fs,
                                                  const typename Rho2<R>::T* __restrict__ rho,
                                                  double* __restrict__ o5, double* __restrict__ part) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
@@ -215,7 +234,7 @@ __global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t
     if (!(fl & k3Solid)) {
         const Nb3 nb(g, x, y, z);
         R f[38];
-        pull3<R>(g, nb, fs, fl, s, f);
+        pull3<S, R>(g, nb, fs, P, fl, s, f);
         // momentum from the differences of opposite populations (i odd, opp(i) = i + 1)
         R m[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
@@ -419,10 +438,10 @@ __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, 
 #ifndef LBM3_MIN_BLOCKS
 #define LBM3_MIN_BLOCKS 3
 #endif
-template <class R, int kAdh>
+template <class S, class R, int kAdh>
 __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
-    k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs,
-             const V2<R>* __restrict__ rho, V2<R>* __restrict__ fout) {
+    k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const Pair<S>* __restrict__ fs,
+             const V2<R>* __restrict__ rho, Pair<S>* __restrict__ fout) {
     using V = V2<R>;
     extern __shared__ __align__(16) unsigned char smem3[];
     V* ring = reinterpret_cast<V*>(smem3);
@@ -471,7 +490,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 src = i == 0 ? s : zoff[1 - e3z(i)] + nb.yo[2 - e3y(i)] + nb.xw[2 - e3x(i)];
                 q = i;
             }
-            f[i] = fs[(long long)q * g.N + src];
+            f[i] = ld3<S, R>(fs + (long long)q * g.N + src, P, q);
         }
     };
 
@@ -603,7 +622,7 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 o[i + 1] = vfma(om1, f[i + 1], vsub(sym, anti));
             }
 #pragma unroll
-            for (int i = 0; i < 19; ++i) fout[(long long)i * g.N + s] = o[i];
+            for (int i = 0; i < 19; ++i) st3<S, R>(fout + (long long)i * g.N + s, o[i], P, i);
         }
         if (z + 3 <= z1 + 1) store_plane(z + 3, nxt);
         __syncthreads();
@@ -624,8 +643,9 @@ __global__ void k3_diag_final(long long nblocks, const double* __restrict__ part
 }
 
 // post-streaming populations (FP64 [2][19][N]) <-> post-collision buffer
-template <class R>
-__global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const V2<R>* __restrict__ fs, double* __restrict__ f) {
+template <class S, class R>
+__global__ void k3_get(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags, const Pair<S>* __restrict__ fs,
+                       double* __restrict__ f) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
@@ -635,13 +655,14 @@ __global__ void k3_get(Geo3 g, const uint32_t* __restrict__ flags, const V2<R>* 
         for (int q = 0; q < 38; ++q) v[q] = (R)0;
     } else {
         const Nb3 nb(g, x, y, z);
-        pull3<R>(g, nb, fs, fl, (int)s, v);
+        pull3<S, R>(g, nb, fs, P, fl, (int)s, v);
     }
     for (int q = 0; q < 38; ++q) f[(long long)q * g.N + s] = (double)v[q];
 }
 
-template <class R>
-__global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ f, V2<R>* __restrict__ fs) {
+template <class S, class R>
+__global__ void k3_set(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags, const double* __restrict__ f,
+                       Pair<S>* __restrict__ fs) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
@@ -654,7 +675,8 @@ __global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double*
                 if (i > 0 && ((fl >> (opp3(i) - 1)) & 1u)) v[k] = (R)f[(long long)(19 * k + opp3(i)) * g.N + s];
                 else v[k] = (R)f[(long long)(19 * k + i) * g.N + (i == 0 ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i)))];
             }
-        fs[(long long)i * g.N + s] = V2<R>{v[0], v[1]};
+        if (fl & k3Solid) store_pair<S, R>(fs + (long long)i * g.N + s, (R)0, (R)0);
+        else st3<S, R>(fs + (long long)i * g.N + s, V2<R>{v[0], v[1]}, P, i);
     }
 }
 
@@ -662,9 +684,9 @@ __global__ void k3_set(Geo3 g, const uint32_t* __restrict__ flags, const double*
 // state k3_feq + k3_set give, bit for bit, without the [38][N] transfer scratch): the stored f*_i
 // at x is w_i rho(x + e_i), or w_i rho(x) when x + e_i is solid (the link comes back by
 // bounce-back), and 0 at solid nodes.
-template <class R>
-__global__ void k3_set_rest(Geo3 g, const uint32_t* __restrict__ flags, const double* __restrict__ rA,
-                            const double* __restrict__ rB, V2<R>* __restrict__ fs) {
+template <class S, class R>
+__global__ void k3_set_rest(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags, const double* __restrict__ rA,
+                            const double* __restrict__ rB, Pair<S>* __restrict__ fs) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long s = ((long long)z * g.ny + y) * g.nx + x;
@@ -676,7 +698,8 @@ __global__ void k3_set_rest(Geo3 g, const uint32_t* __restrict__ flags, const do
             const long long t = (bl || i == 0) ? s : site(g, x + e3x(i), y + e3y(i), z + e3z(i));
             v = V2<R>{(R)(w19(i) * rA[t]), (R)(w19(i) * rB[t])};
         }
-        fs[(long long)i * g.N + s] = v;
+        if (fl & k3Solid) store_pair<S, R>(fs + (long long)i * g.N + s, (R)0, (R)0);
+        else st3<S, R>(fs + (long long)i * g.N + s, v, P, i);
     }
 }
 
@@ -868,7 +891,8 @@ __global__ void k3_ca_solve(int pass, int nblocks, const double* __restrict__ pa
 // ------------------------------------------------------------------------------------------------
 struct lbm3d_ctx {
     int storage = LBM_STORE_F32;
-    size_t elem = 4;
+    size_t elem = 4;               // bytes per stored population value
+    size_t relem = 4;              // bytes per value of the compute type (densities)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Geo3 g{};
@@ -918,11 +942,28 @@ P3<R> make_p3(const lbm3d_params& p) {
     P.t2 = (R)(2.0 * (l - 1.0) / (dl * (1.0 + l)));
     P.t3 = (R)((l - 1.0) / (dl * dl * (1.0 + l)));
     for (int d = 0; d < 3; ++d) P.g[d] = (R)p.g[d];
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 2; ++k) P.sh[c][k] = (R)(w19(c == 0 ? 0 : (c == 1 ? 1 : 7)) * p.rho0_store[k]);
     P.mode = p.mode;
     P.psi = p.second_layer == LBM_SECOND_LAYER_PSI;
     P.adh = p.adhesion_stencil == LBM3_ADHESION_D3Q19;
     return P;
 }
+
+// Calls fn(S*, R*) (null pointers carrying the types) for the context's storage: the stored type S
+// and the compute type R.
+template <class Fn>
+cudaError_t with_types3(int storage, Fn&& fn) {
+    switch (storage) {
+        case LBM_STORE_F64: return fn((double*)nullptr, (double*)nullptr);
+        case LBM_STORE_F32: return fn((float*)nullptr, (float*)nullptr);
+        case LBM_STORE_F16_SHIFTED: return fn((__half*)nullptr, (float*)nullptr);
+        default: return fn((__nv_bfloat16*)nullptr, (float*)nullptr);
+    }
+}
+#define TYPES3(s_, r_)                                   \
+    using S = std::remove_pointer_t<decltype(s_)>;      \
+    using R = std::remove_pointer_t<decltype(r_)>
 
 // node kernels run blocks of 32 x 4 nodes (x, y), so that a block's stencil rows share L1
 dim3 grid3(const Geo3& g) { return dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz); }
@@ -942,51 +983,76 @@ cudaError_t scratch_for(lbm3d_ctx* c) {
     return cudaMalloc(&c->scratch, (size_t)38 * c->g.N * sizeof(double));
 }
 
-// the step kernel instance of the adhesion variant
+// the context's parameters in the compute type R
 template <class R>
-auto march_kernel(const P3<R>& P) {
-    return P.adh ? k3_march<R, kAdhD3Q19> : (P.psi ? k3_march<R, kAdhE8Psi> : k3_march<R, kAdhE8>);
+const P3<R>& p3_of(const lbm3d_ctx* c) {
+    return *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
+}
+template <class S>
+Pair<S>* state3(const lbm3d_ctx* c, int buf) {
+    return reinterpret_cast<Pair<S>*>(c->f[buf]);
 }
 
-template <class R>
+// the step kernel instance of the adhesion variant
+template <class S, class R>
+auto march_kernel(const P3<R>& P) {
+    return P.adh ? k3_march<S, R, kAdhD3Q19> : (P.psi ? k3_march<S, R, kAdhE8Psi> : k3_march<S, R, kAdhE8>);
+}
+
+template <class S, class R>
 cudaError_t step_once(lbm3d_ctx* c) {
     const dim3 gr = grid3(c->g);
-    const V2<R>* fs = reinterpret_cast<const V2<R>*>(c->f[c->cur]);
+    const Pair<S>* fs = state3<S>(c, c->cur);
     auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
-    k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
-    const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
+    const P3<R>& P = p3_of<R>(c);
+    k3_rho<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, fs, rho);
     const int zc = zchunk3(c->g);
     const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
                   (unsigned)((c->g.nz + zc - 1) / zc));
-    V2<R>* fo = reinterpret_cast<V2<R>*>(c->f[1 - c->cur]);
-    auto* kern = march_kernel<R>(P);
-    kern<<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, rho, fo);
+    auto* kern = march_kernel<S, R>(P);
+    kern<<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, reinterpret_cast<const V2<R>*>(rho),
+                                                         state3<S>(c, 1 - c->cur));
     c->cur ^= 1;
     return cudaGetLastError();
 }
 
 // densities of the current state into c->rho, then the fields form (o5 may be NULL)
-template <class R>
-cudaError_t fields_pass(lbm3d_ctx* c, double* o5, bool diag) {
-    const dim3 gr = grid3(c->g);
-    const V2<R>* fs = reinterpret_cast<const V2<R>*>(c->f[c->cur]);
-    auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
-    k3_rho<R><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, fs, rho);
-    const P3<R>& P = *reinterpret_cast<const P3<R>*>(sizeof(R) == 4 ? (const void*)&c->pf : (const void*)&c->pd);
-    k3_fields<R><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, c->solid, fs, rho, o5, c->part);
-    if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
-    return cudaGetLastError();
-}
-
 cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
-    return c->storage == LBM_STORE_F64 ? fields_pass<double>(c, o5, diag) : fields_pass<float>(c, o5, diag);
+    return with_types3(c->storage, [&](auto* s_, auto* r_) {
+        TYPES3(s_, r_);
+        const dim3 gr = grid3(c->g);
+        const Pair<S>* fs = state3<S>(c, c->cur);
+        auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
+        k3_rho<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, fs, rho);
+        k3_fields<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, c->solid, fs, rho, o5, c->part);
+        if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
+        return cudaGetLastError();
+    });
 }
 
-template <class R>
 cudaError_t density_pass(lbm3d_ctx* c) {
-    k3_rho<R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, reinterpret_cast<const V2<R>*>(c->f[c->cur]),
-                                                   reinterpret_cast<typename Rho2<R>::T*>(c->rho));
-    return cudaGetLastError();
+    return with_types3(c->storage, [&](auto* s_, auto* r_) {
+        TYPES3(s_, r_);
+        k3_rho<S, R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, state3<S>(c, c->cur),
+                                                           reinterpret_cast<typename Rho2<R>::T*>(c->rho));
+        return cudaGetLastError();
+    });
+}
+
+// the state from post-streaming populations (FP64 [38][N] on the device) / from densities
+cudaError_t set_state3(lbm3d_ctx* c, const double* f, int buf) {
+    return with_types3(c->storage, [&](auto* s_, auto* r_) {
+        TYPES3(s_, r_);
+        k3_set<S, R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, f, state3<S>(c, buf));
+        return cudaGetLastError();
+    });
+}
+cudaError_t set_rest3(lbm3d_ctx* c, const double* a, const double* b) {
+    return with_types3(c->storage, [&](auto* s_, auto* r_) {
+        TYPES3(s_, r_);
+        k3_set_rest<S, R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, a, b, state3<S>(c, c->cur));
+        return cudaGetLastError();
+    });
 }
 
 template <class R>
@@ -1047,10 +1113,11 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     if (grid->nx < 5 || grid->ny < 5 || grid->nz < 5) return report_error(LBM_EINVAL, "nx, ny, nz must be >= 5");
     if (grid->ny > 65535 || grid->nz > 65535) return report_error(LBM_EINVAL, "ny, nz must be <= 65535");
     if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) - 1) return report_error(LBM_EINVAL, "lattice too large (2^31 nodes)");
-    if (storage != LBM_STORE_F32 && storage != LBM_STORE_F64) return report_error(LBM_EINVAL, "3-D storage must be FP32 or FP64");
+    if (storage < LBM_STORE_F64 || storage > LBM_STORE_BF16_SHIFTED) return report_error(LBM_EINVAL, "bad storage %d", storage);
     for (int k = 0; k < 2; ++k)
         if (!fin(p->tau[k]) || p->tau[k] <= 0.5) return report_error(LBM_EINVAL, "tau[%d] must be > 0.5", k);
-    if (!fin(p->G_AB) || !fin(p->G_w2) || !fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2]))
+    if (!fin(p->G_AB) || !fin(p->G_w2) || !fin(p->g[0]) || !fin(p->g[1]) || !fin(p->g[2]) || !fin(p->rho0_store[0]) ||
+        !fin(p->rho0_store[1]))
         return report_error(LBM_EINVAL, "non-finite parameter");
     if (!fin(p->lambda) || p->lambda <= 0.0) return report_error(LBM_EINVAL, "lambda must be > 0");
     if (!fin(p->delta) || p->delta <= 0.0 || p->delta > 1.0) return report_error(LBM_EINVAL, "delta must lie in (0, 1]");
@@ -1093,7 +1160,8 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
         }                                                                                            \
     } while (0)
     c->storage = storage;
-    c->elem = storage == LBM_STORE_F64 ? 8 : 4;
+    c->elem = storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F32 ? 4 : 2);  // bytes per stored value
+    c->relem = storage == LBM_STORE_F64 ? 8 : 4;                                  // bytes per computed value
     c->g = Geo3{grid->nx, grid->ny, grid->nz, N};
     c->pf = make_p3<float>(*p);
     c->pd = make_p3<double>(*p);
@@ -1110,7 +1178,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     STEP3(cudaMalloc(&c->flags, N * sizeof(uint32_t)), "flags");
     STEP3(cudaMalloc(&c->f[0], 38 * N * c->elem), "population buffer");
     STEP3(cudaMalloc(&c->f[1], 38 * N * c->elem), "population buffer");
-    STEP3(cudaMalloc(&c->rho, 2 * N * c->elem), "densities");
+    STEP3(cudaMalloc(&c->rho, 2 * N * c->relem), "densities");
     STEP3(cudaMalloc(&c->part, c->nparts * k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->dout, k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->ca, (16 + kC3Blocks * kC3Vals) * sizeof(double)), "contact-angle scratch");
@@ -1127,8 +1195,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     // read before planes 36, 37 are overwritten by the same thread
     k3_feq<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->solid, c->scratch + 36 * N, c->scratch + 37 * N, c->scratch);
     STEP3(cudaGetLastError(), "init kernel");
-    if (storage == LBM_STORE_F64) k3_set<double><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double2*)c->f[0]);
-    else k3_set<float><<<gr, kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float2*)c->f[0]);
+    STEP3(set_state3(c, c->scratch, 0), "init kernel");
     STEP3(cudaGetLastError(), "init kernel");
     STEP3(cudaStreamSynchronize(c->stream), "initialisation");
     cudaFree(c->scratch);  // transfers allocate it again on demand
@@ -1149,17 +1216,17 @@ extern "C" lbm_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
     NvtxRange nvtx_("lbm3d_step");
     if (!c) return report_error(LBM_EINVAL, "NULL context");
     if (n < 0) return report_error(LBM_EINVAL, "n must be >= 0");
-    // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
-    TRY3(c->storage == LBM_STORE_F64
-             ? cudaFuncSetAttribute(march_kernel<double>(c->pd), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k3_march_smem<double>())
-             : cudaFuncSetAttribute(march_kernel<float>(c->pf), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k3_march_smem<float>()),
-         "step kernel attributes");
-    for (int64_t t = 0; t < n; ++t) {
-        const cudaError_t e = c->storage == LBM_STORE_F64 ? step_once<double>(c) : step_once<float>(c);
-        TRY3(e, "step kernels");
-    }
+    TRY3(with_types3(c->storage,
+                     [&](auto* s_, auto* r_) {
+                         TYPES3(s_, r_);
+                         // the step kernel's shared-memory ring exceeds the default dynamic limit in FP64
+                         cudaError_t e = cudaFuncSetAttribute(march_kernel<S, R>(p3_of<R>(c)),
+                                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)k3_march_smem<R>());
+                         for (int64_t t = 0; t < n && e == cudaSuccess; ++t) e = step_once<S, R>(c);
+                         return e;
+                     }),
+         "step kernels");
     return LBM_OK;
 }
 
@@ -1220,9 +1287,7 @@ extern "C" lbm_status lbm3d_set_densities_async(lbm3d_ctx* c, const double* rho_
     TRY3(cudaMemcpyAsync(b, rho_B, N * sizeof(double), cudaMemcpyHostToDevice, c->xs_in), "upload");
     TRY3(cudaEventRecord(c->xin_ready[k], c->xs_in), "transfer order");
     TRY3(cudaStreamWaitEvent(c->stream, c->xin_ready[k], 0), "transfer order");
-    if (c->storage == LBM_STORE_F64)
-        k3_set_rest<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (double2*)c->f[c->cur]);
-    else k3_set_rest<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (float2*)c->f[c->cur]);
+    TRY3(set_rest3(c, a, b), "state kernel");
     TRY3(cudaGetLastError(), "state kernel");
     TRY3(cudaEventRecord(c->xin_free[k], c->stream), "transfer order");
     return LBM_OK;
@@ -1262,8 +1327,14 @@ extern "C" lbm_status lbm3d_synchronize(lbm3d_ctx* c) {
 extern "C" lbm_status lbm3d_get_populations(lbm3d_ctx* c, double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
-    if (c->storage == LBM_STORE_F64) k3_get<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const double2*)c->f[c->cur], c->scratch);
-    else k3_get<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, (const float2*)c->f[c->cur], c->scratch);
+    TRY3(with_types3(c->storage,
+                     [&](auto* s_, auto* r_) {
+                         TYPES3(s_, r_);
+                         k3_get<S, R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags,
+                                                                            state3<S>(c, c->cur), c->scratch);
+                         return cudaGetLastError();
+                     }),
+         "read-back kernel");
     TRY3(cudaGetLastError(), "read-back kernel");
     TRY3(cudaMemcpyAsync(f, c->scratch, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read-back");
     TRY3(cudaStreamSynchronize(c->stream), "read-back");
@@ -1281,9 +1352,7 @@ extern "C" lbm_status lbm3d_set_densities(lbm3d_ctx* c, const double* rho_A, con
         a = c->dens;
         b = c->dens + N;
     }
-    if (c->storage == LBM_STORE_F64)
-        k3_set_rest<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (double2*)c->f[c->cur]);
-    else k3_set_rest<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, a, b, (float2*)c->f[c->cur]);
+    TRY3(set_rest3(c, a, b), "state kernel");
     TRY3(cudaGetLastError(), "state kernel");
     if (!on_device) TRY3(cudaStreamSynchronize(c->stream), "upload");
     return LBM_OK;
@@ -1293,8 +1362,7 @@ extern "C" lbm_status lbm3d_set_populations(lbm3d_ctx* c, const double* f) {
     if (!c || !f) return report_error(LBM_EINVAL, "NULL argument");
     TRY3(scratch_for(c), "transfer scratch");
     TRY3(cudaMemcpyAsync(c->scratch, f, (size_t)38 * c->g.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
-    if (c->storage == LBM_STORE_F64) k3_set<double><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (double2*)c->f[c->cur]);
-    else k3_set<float><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, c->flags, c->scratch, (float2*)c->f[c->cur]);
+    TRY3(set_state3(c, c->scratch, c->cur), "state kernel");
     TRY3(cudaGetLastError(), "state kernel");
     TRY3(cudaStreamSynchronize(c->stream), "upload");
     return LBM_OK;
@@ -1327,7 +1395,7 @@ extern "C" lbm_status lbm3d_contact_angle(lbm3d_ctx* c, const double* sc, double
                                           int64_t* npoints) {
     if (!c || !sc) return report_error(LBM_EINVAL, "NULL argument");
     if (!(R > 0.0) || !fin(sc[0]) || !fin(sc[1]) || !fin(sc[2])) return report_error(LBM_EINVAL, "bad sphere");
-    cudaError_t e = c->storage == LBM_STORE_F64 ? density_pass<double>(c) : density_pass<float>(c);
+    cudaError_t e = density_pass(c);
     TRY3(e, "density kernel");
     e = c->storage == LBM_STORE_F64 ? ca_passes<double>(c, sc, R) : ca_passes<float>(c, sc, R);
     TRY3(e, "contact-angle kernels");

@@ -23,7 +23,7 @@ class lbm3d_params(ctypes.Structure):
     _fields_ = [("tau", c_double * 2), ("G_AB", c_double), ("mode", c_int32), ("second_layer", c_int32),
                 ("lambda_", c_double),
                 ("G_w2", c_double), ("delta", c_double), ("g", c_double * 3), ("adhesion_stencil", c_int32),
-                ("pad_", c_int32)]
+                ("pad_", c_int32), ("rho0_store", c_double * 2)]
 
 
 ADHESION_STENCIL3 = {"e8": 0, "d3q19": 1}
@@ -69,7 +69,8 @@ def _lib():
 
 
 def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, delta=0.8,
-                 g=(0.0, 0.0, 0.0), second_layer="psi_and_solid", adhesion_stencil="e8") -> lbm3d_params:
+                 g=(0.0, 0.0, 0.0), second_layer="psi_and_solid", adhesion_stencil="e8",
+                 rho0_store=(0.0, 0.0)) -> lbm3d_params:
     p = lbm3d_params()
     p.tau[0], p.tau[1] = tau
     p.G_AB = G
@@ -81,6 +82,7 @@ def make_params3(tau=(1.0, 1.0), G=1.205, scheme="improved", lam=1.0, Gw2=None, 
         p.g[i] = g[i]
     p.second_layer = lbm.SECOND_LAYER[second_layer]
     p.adhesion_stencil = ADHESION_STENCIL3[adhesion_stencil]
+    p.rho0_store[0], p.rho0_store[1] = rho0_store
     return p
 
 

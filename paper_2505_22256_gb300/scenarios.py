@@ -444,6 +444,8 @@ class Scenario3:
     sphere: dict | None = None   # {"c": (x, y, z), "R": effective radius} for the contact angle
     second_layer: str = "psi_and_solid"  # or "psi" (Sec. 2.4, Table 1)
     adhesion_stencil: str = "e8"  # or "d3q19": Eq. 9 as printed, first layer, D3Q19 weights
+    # 16-bit storage keeps f_i - w_i rho0 per component; the dissolved-phase density serves both
+    rho0_store: tuple = (RHO_D, RHO_D)
 
     @property
     def shape(self):
@@ -452,7 +454,7 @@ class Scenario3:
     def params(self) -> dict:
         return dict(tau=tuple(self.tau), G=self.G, scheme=self.scheme, lam=self.lam, Gw2=self.Gw2,
                     delta=self.delta, g=tuple(self.g), second_layer=self.second_layer,
-                    adhesion_stencil=self.adhesion_stencil)
+                    adhesion_stencil=self.adhesion_stencil, rho0_store=tuple(self.rho0_store))
 
 
 def sphere_droplet_3d(nx: int = 200, ny: int = 200, nz: int = 280, R: float = 50.0, sphere=(100.0, 100.0, 100.0),

@@ -234,24 +234,26 @@ def test_3d_invalid_input_is_rejected_before_any_device_work(lbm, what):
         params["delta"] = 1.5
     elif what == "size":
         solid, a = solid[:, :, :4], a[:, :, :4]
-    elif what == "storage":
-        storage = "f16"
     elif what == "density":
         a = a.copy()
         a[2, 3, 4] = -1.0
     elif what == "allsolid":
         solid = np.ones_like(solid)
-    if what in ("mode", "adhesion"):
+    if what in ("mode", "adhesion", "storage"):
         p = lbm3d.make_params3()
+        st_code = 1
         if what == "mode":
             p.mode = 5
-        else:
+        elif what == "adhesion":
             p.adhesion_stencil = 2
+        else:
+            st_code = 9
         g = lbm3d.lbm3d_grid(n, n, n)
         ctx = ctypes.c_void_p()
         st = lbm3d._lib().lbm3d_create(ctypes.byref(g), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                        ctypes.byref(p), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, None, ctypes.byref(ctx))
+                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st_code, None,
+                                       ctypes.byref(ctx))
         assert st == lbm.LBM_EINVAL
         return
     with pytest.raises(lbm.LbmError) as e:

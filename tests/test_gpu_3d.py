@@ -93,13 +93,14 @@ def test_initial_state_and_population_roundtrip(name):
     lat.close()
 
 
-def test_step_count_split_does_not_change_the_state():
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_step_count_split_does_not_change_the_state(storage):
     """Seven steps at once, and one step at a time, give the same state bit for bit; zero steps
     leaves the state untouched and a negative count is refused."""
     sc = CASES["uneven_chunks"]()
     out = []
     for split in ([7], [1] * 7, [2, 0, 5]):
-        lat = lattice(sc, "f32")
+        lat = lattice(sc, storage)
         before = lat.populations()
         lat.step(0)
         np.testing.assert_array_equal(lat.populations(), before)
@@ -161,6 +162,28 @@ def test_d3q19_adhesion_ignores_the_second_layer_reading(storage):
         out.append(lat.populations())
         lat.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 5e-3), ("bf16", 5e-2)])
+def test_shifted_16bit_storage_error(storage, bound):
+    """16-bit storage of f - w rho0 (FP32 arithmetic) against the oracle after 100 steps, with the
+    workloads' shift rho0 = rho_d and without a shift: the same bars as the 2-D path, and the
+    shifted form no worse than the unshifted one."""
+    sc = CASES["sphere24"]()
+    cfg, f = orun(sc, 100)
+    o = d3.fields3(cfg, sc.solid, f)
+    errs = {}
+    for shift in ((S.RHO_D, S.RHO_D), (0.0, 0.0)):
+        p = sc.params()
+        p["rho0_store"] = shift
+        lat = lbm3d.Lattice3(sc.solid, sc.rhoA0, sc.rhoB0, p, storage)
+        lat.step(100)
+        errs[shift] = rel_rho(lat.fields(), o, sc.solid)
+        lat.close()
+    shifted, plain = errs[(S.RHO_D, S.RHO_D)], errs[(0.0, 0.0)]
+    print(f"{storage}: max rel |d rho| after 100 steps: shift rho_d {shifted:.3e}, no shift {plain:.3e}")
+    assert np.isfinite(shifted) and shifted <= bound
+    assert shifted <= plain * 1.05
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
