@@ -91,7 +91,7 @@ def _c(a, dtype):
 
 
 class Lattice3:
-    """One 3-D lattice on the GPU (periodic in x, y, z; solid mask; FP32 or FP64)."""
+    """One 3-D lattice on the GPU (periodic in x, y, z; solid mask; storage f64, f32, f16 or bf16)."""
 
     def __init__(self, solid, rhoA0, rhoB0, params, storage: str = "f32", cuda_stream: int | None = None):
         solid = _c(solid, np.uint8)
