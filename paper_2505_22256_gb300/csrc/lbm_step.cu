@@ -42,16 +42,19 @@ namespace {
 constexpr int kRing = 6;
 // Threads per block of the step kernel = window columns = density ring row length: 128, or 64 for
 // lattices too narrow to fill a 120-column window (both are built; the context picks one).
+// Rows of f* resident or in flight in shared memory (>= 4), per storage type: three rows feed a
+// pull, the rest are loads in flight.  FP32 takes six (on the seven-case sweep 0.1743 ms per launch
+// against 0.1772 with five; seven slots leave room for the 64-column form only); the 16-bit types
+// five (six measured 0.1533 against 0.1513 ms, four the same as five).
 #ifndef LBM_SLOTS
-#define LBM_SLOTS 5
+#define LBM_SLOTS 6
 #endif
 #ifndef LBM_MIN_BLOCKS
 #define LBM_MIN_BLOCKS 3
 #endif
 #ifndef LBM_SLOTS_16
-#define LBM_SLOTS_16 LBM_SLOTS
+#define LBM_SLOTS_16 5
 #endif
-// rows of f* resident or in flight in shared memory (>= 4), per storage type
 template <class S>
 constexpr int slots_of() {
     return sizeof(S) == 2 ? LBM_SLOTS_16 : LBM_SLOTS;
