@@ -28,21 +28,21 @@ def cases():
 
 
 def inputs(cs, k):
-    """Densities of round k: the cases' initial fields, scaled a little differently per round."""
+    """Densities of cycle k: the cases' initial fields, scaled a little differently per cycle."""
     a = np.concatenate([c.rhoA0.ravel() for c in cs]) * (1.0 + 0.01 * k)
     b = np.concatenate([c.rhoB0.ravel() for c in cs]) * (1.0 - 0.005 * k)
     return a, b
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_overlapped_rounds_equal_blocking_rounds(storage):
+def test_overlapped_cycles_equal_blocking_cycles(storage):
     cs = cases()
     total = sum(c.nx * c.ny for c in cs)
-    rounds = 4
-    # blocking: set, step, fields, one round at a time
+    cycles = 4
+    # blocking: set, step, fields, one cycle at a time
     ref = []
     lat = lbm.Lattice(cs, storage)
-    for k in range(rounds):
+    for k in range(cycles):
         a, b = inputs(cs, k)
         lbm.lbm_set_densities_all(lat.ctx, a, b, False)
         lat.step(7)
@@ -50,21 +50,21 @@ def test_overlapped_rounds_equal_blocking_rounds(storage):
         lbm.lbm_fields_all(lat.ctx, *out)
         ref.append(out)
     lat.close()
-    # overlapped: every round enqueued before anything is waited for; staging buffers alternate,
-    # so rounds 2 and 3 reuse the buffers of rounds 0 and 1
+    # overlapped: every cycle enqueued before anything is waited for; staging buffers alternate,
+    # so cycles 2 and 3 reuse the buffers of cycles 0 and 1
     lat = lbm.Lattice(cs, storage)
-    hin = [(pinned(total), pinned(total)) for _ in range(rounds)]
-    hout = [[pinned(total) for _ in range(4)] for _ in range(rounds)]
-    for k in range(rounds):
+    hin = [(pinned(total), pinned(total)) for _ in range(cycles)]
+    hout = [[pinned(total) for _ in range(4)] for _ in range(cycles)]
+    for k in range(cycles):
         hin[k][0][...], hin[k][1][...] = inputs(cs, k)
         for o in hout[k]:
             o[...] = np.nan
-    for k in range(rounds):
+    for k in range(cycles):
         lbm.lbm_set_densities_all_async(lat.ctx, *hin[k])
         lat.step(7)
         lbm.lbm_fields_all_async(lat.ctx, *hout[k])
     lat.sync()
-    for k in range(rounds):
+    for k in range(cycles):
         for q in range(4):
             np.testing.assert_array_equal(hout[k][q], ref[k][q])
     # a blocking call after the overlapped ones sees the same state
@@ -76,7 +76,7 @@ def test_overlapped_rounds_equal_blocking_rounds(storage):
 
 
 def test_partial_outputs_and_a_continuing_run():
-    """NULL field outputs are skipped; fields taken without re-initialising between rounds equal the
+    """NULL field outputs are skipped; fields taken without re-initialising between cycles equal the
     blocking calls' on the same run."""
     cs = cases()
     total = sum(c.nx * c.ny for c in cs)
