@@ -77,6 +77,8 @@ def parse(argv=None):
                          "form x block width x row chunks), one untimed and three timed steps each, one "
                          "JSON line with the table (a capture of it under ncu gives the per-shape "
                          "counters in the same order)")
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the FP16 storage form measured beside an FP32 line at one GPU")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--split", action="store_true",
@@ -346,11 +348,11 @@ def parity_record(storage, case, err_rho, err_u, bar_note=None) -> dict:
     return rec
 
 
-def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
+def cpu_baseline(args, seconds: float, parity: bool = False, also=()) -> dict:
     """The FP64 oracle timed on one case of the workload.  parity: also run that case on the GPU in
-    the bench's storage mode from the same initial state and report its error against the oracle's
-    fields after PARITY_STEPS steps (the oracle's first PARITY_STEPS steps are part of the timed
-    sample)."""
+    the bench's storage mode (and in each storage mode of `also`) from the same initial state and
+    report its error against the oracle's fields after PARITY_STEPS steps (the oracle's first
+    PARITY_STEPS steps are part of the timed sample)."""
     import numpy as np
 
     import oracle
@@ -392,14 +394,19 @@ def cpu_baseline(args, seconds: float, parity: bool = False) -> dict:
         from paper_2505_22256_gb300 import lbm
 
         o = oracle.fields(cfg, sc.solid, snap)
-        lat = lbm.Lattice(sc, args.storage)
-        lat.step(PARITY_STEPS)
-        g = lat.fields()
-        lat.close()
         fl = sc.solid == 0
-        err_rho = max(float(np.max(np.abs(g[k] - o[k])[fl] / o[k][fl])) for k in (0, 1))
-        err_u = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (2, 3))
-        out["parity"] = parity_record(args.storage, f"{sc.name} ({sc.nx}x{sc.ny})", err_rho, err_u)
+        for st in (args.storage, *also):
+            lat = lbm.Lattice(sc, st)
+            lat.step(PARITY_STEPS)
+            g = lat.fields()
+            lat.close()
+            err_rho = max(float(np.max(np.abs(g[k] - o[k])[fl] / o[k][fl])) for k in (0, 1))
+            err_u = max(float(np.max(np.abs(g[k] - o[k])[fl])) for k in (2, 3))
+            rec = parity_record(st, f"{sc.name} ({sc.nx}x{sc.ny})", err_rho, err_u)
+            if st == args.storage:
+                out["parity"] = rec
+            else:
+                out.setdefault("parity_storage_modes", {})[st] = rec
     return out
 
 
@@ -512,6 +519,47 @@ def launch_table(args, lat, stream) -> int:
     lat.close()
     print(json.dumps({"launch_table": rows, "storage": args.storage, "workload": args.workload}))
     return 0
+
+
+def storage_mode_line(args, cases, storage: str, stream) -> dict:
+    """The same workload in another storage mode, on the same GPU: the library's autotuner, then
+    MODE_STEPS bench steps (time steps only) timed with CUDA events on the library's stream, after
+    two untimed ones."""
+    import torch
+
+    from paper_2505_22256_gb300 import lbm
+
+    lat = lbm.Lattice(cases, storage=storage, cuda_stream=stream.cuda_stream)
+    try:
+        lbm.lbm_autotune(lat.ctx, 4)
+        info = lat.info()
+        lat.step(2 * args.inner)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(MODE_STEPS * args.inner)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        d = lat.diagnostics_all(allow_unstable=True)
+    finally:
+        lat.close()
+    launch_ms = ms / (MODE_STEPS * args.inner)
+    algo = BYTES_PER_NODE[storage] * info["fluid_nodes"]
+    peak, peak_kind = hbm_peak()
+    traffic = committed_traffic(storage, info["nodes"], launch={
+        "workload": args.workload, "kernel": step_kernel_name(storage, info), "block_rows": info["block_rows"],
+        "grid_blocks": info["grid_blocks"]})
+    return {"storage": storage, "value": info["nodes"] * MODE_STEPS * args.inner / (ms / 1e3) / 1e6, "unit": UNIT,
+            "launch_ms": launch_ms, "steps_timed": MODE_STEPS * args.inner,
+            "roofline": {"bound": "hbm", "achieved": algo / (launch_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": algo / (launch_ms / 1e3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_step", "algorithmic_bytes_per_launch": algo},
+            "launch": {"block_threads": info["block_threads"], "block_rows": info["block_rows"],
+                       "grid_blocks": info["grid_blocks"], "wall_inline": info["wall_inline"]},
+            "unstable_cases": sum(x["unstable"] for x in d)}
+
+
+MODE_STEPS = 5
 
 
 def run_ours(args):
@@ -709,9 +757,13 @@ def run_ours(args):
                                "case0_umax": d["umax"], "unstable_cases": sum(x["unstable"] for x in dall)},
     }
     lat.close()
+    modes = args.storage == "f32" and world == 1 and not args.no_modes
+    if modes:  # the FP16 storage form of the same workload (the metric reports it beside FP32)
+        line["storage_modes"] = {st: storage_mode_line(args, cases, st, stream) for st in ("f16",)}
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds, parity=True)
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds, parity=True,
+                                                also=("f16",) if modes else ())
         elif not args.no_cpu:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
