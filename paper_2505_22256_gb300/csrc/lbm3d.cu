@@ -631,7 +631,39 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
     }
 }
 
-// Combine the per-block records in block order (one warp; deterministic).
+// Combine the per-block records in two levels, each in a fixed order (deterministic): k3DiagMid
+// blocks each combine a contiguous range of records (a thread takes whole records, strided by the
+// block size; then a shuffle tree and the warps in order), then one warp combines their k3DiagMid
+// results (k3_diag_final).  A single warp over all records waited on one dependent load per record.
+constexpr int k3DiagMid = 256, k3DiagMidThreads = 256;
+__global__ void __launch_bounds__(k3DiagMidThreads) k3_diag_mid(long long nblocks, const double* __restrict__ part,
+                                                               double* __restrict__ mid) {
+    const long long per = (nblocks + gridDim.x - 1) / gridDim.x;
+    const long long b0 = (long long)blockIdx.x * per, b1 = b0 + per < nblocks ? b0 + per : nblocks;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    double v[k3DiagN];
+#pragma unroll
+    for (int q = 0; q < k3DiagN; ++q) v[q] = d3_neutral(q);
+    for (long long b = b0 + t; b < b1; b += k3DiagMidThreads) {
+#pragma unroll
+        for (int q = 0; q < k3DiagN; ++q) v[q] = d3_combine(q, v[q], part[b * k3DiagN + q]);
+    }
+    __shared__ double red[k3DiagMidThreads / 32][k3DiagN];
+#pragma unroll
+    for (int q = 0; q < k3DiagN; ++q) {
+        double x = v[q];
+        for (int off = 16; off > 0; off >>= 1) x = d3_combine(q, x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) red[warp][q] = x;
+    }
+    __syncthreads();
+    if (t < k3DiagN) {
+        double x = red[0][t];
+        for (int w = 1; w < k3DiagMidThreads / 32; ++w) x = d3_combine(t, x, red[w][t]);
+        mid[(long long)blockIdx.x * k3DiagN + t] = x;
+    }
+}
+
+// Combine records in record order (one warp; deterministic).
 __global__ void k3_diag_final(long long nblocks, const double* __restrict__ part, double* __restrict__ out) {
     const int lane = threadIdx.x;
     for (int q = 0; q < k3DiagN; ++q) {
@@ -1025,7 +1057,11 @@ cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
         auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
         k3_rho<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, fs, rho);
         k3_fields<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, c->solid, fs, rho, o5, c->part);
-        if (diag) k3_diag_final<<<1, 32, 0, c->stream>>>(c->nparts, c->part, c->dout);
+        if (diag) {
+            double* mid = c->part + c->nparts * k3DiagN;  // k3DiagMid records after the per-block ones
+            k3_diag_mid<<<k3DiagMid, k3DiagMidThreads, 0, c->stream>>>(c->nparts, c->part, mid);
+            k3_diag_final<<<1, 32, 0, c->stream>>>(k3DiagMid, mid, c->dout);
+        }
         return cudaGetLastError();
     });
 }
@@ -1179,7 +1215,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     STEP3(cudaMalloc(&c->f[0], 38 * N * c->elem), "population buffer");
     STEP3(cudaMalloc(&c->f[1], 38 * N * c->elem), "population buffer");
     STEP3(cudaMalloc(&c->rho, 2 * N * c->relem), "densities");
-    STEP3(cudaMalloc(&c->part, c->nparts * k3DiagN * sizeof(double)), "diagnostics");
+    STEP3(cudaMalloc(&c->part, (c->nparts + k3DiagMid) * k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->dout, k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->ca, (16 + kC3Blocks * kC3Vals) * sizeof(double)), "contact-angle scratch");
     STEP3(cudaMemsetAsync(c->f[0], 0, 38 * N * c->elem, c->stream), "memset");
