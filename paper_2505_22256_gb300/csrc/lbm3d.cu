@@ -14,8 +14,8 @@
 //             x + sign(e) (Sec. 2.4) and the solid switch; body force; velocity with Guo's
 //             half-force shift (Eq. 5); SRT collision with Guo forcing (Eqs. 1, 2, 6, 7) written to
 //             the other buffer.  Blocks march along z with the stencil's density planes in shared
-//             memory.  k3_fields is its fields form: rho and u in FP64 and per-block diagnostic sums
-//             instead of colliding.
+//             memory.  Its fields form (kFields) writes rho and u in FP64 and per-block diagnostic
+//             records instead of colliding.
 // Periodic in x, y and z.
 #include <math.h>
 #include <stdarg.h>
@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(128) k3_rho(Geo3 g, P3<R> P, const uint32_t* _
     rho[s] = r;
 }
 
-constexpr int k3DiagN = 12;  // mass A, mass B, mom x, y, z, umax, rhoA min/max, rhoB min/max, n, unstable
+// record: mass A, mass B, mom x, y, z, max |u|^2 (|u| after the last combine), rhoA min/max, rhoB
+// min/max, n, unstable
+constexpr int k3DiagN = 12;
 
 __device__ __forceinline__ double d3_combine(int q, double a, double b) {
     if (q == 5 || q == 7 || q == 9) return fmax(a, b);
@@ -215,149 +217,6 @@ __device__ __forceinline__ double d3_combine(int q, double a, double b) {
 }
 __device__ __forceinline__ double d3_neutral(int q) {
     return (q == 6 || q == 8) ? INFINITY : (q == 7 || q == 9) ? -INFINITY : 0.0;
-}
-
-// Fields form of the step, one node per thread: the same pull, moments and forces as the step
-// kernel below, writing rho_A, rho_B, u (FP64) and per-block diagnostic records (block index
-// blockIdx.x + gridDim.x (y + ny z)) instead of colliding.
-template <class S, class R>
-__global__ void __launch_bounds__(128) k3_fields(Geo3 g, P3<R> P, const uint32_t* __restrict__ flags,
-                                                 const uint8_t* __restrict__ solid, const Pair<S>* __restrict__ fs,
-                                                 const typename Rho2<R>::T* __restrict__ rho,
-                                                 double* __restrict__ o5, double* __restrict__ part) {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
-    const bool in = x < g.nx && y < g.ny;
-    const int s = (z * g.ny + (in ? y : 0)) * g.nx + (in ? x : 0);
-    const uint32_t fl = in ? flags[s] : k3Solid;
-    double rec[k3DiagN];
-    for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
-    if (!(fl & k3Solid)) {
-        const Nb3 nb(g, x, y, z);
-        R f[38];
-        pull3<S, R>(g, nb, fs, P, fl, s, f);
-        // momentum from the differences of opposite populations (i odd, opp(i) = i + 1)
-        R m[3] = {(R)0, (R)0, (R)0};
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            const R t = (f[i] - f[i + 1]) + (f[19 + i] - f[20 + i]);
-            m[0] += e3x(i) * t;
-            m[1] += e3y(i) * t;
-            m[2] += e3z(i) * t;
-        }
-        const typename Rho2<R>::T r0 = rho[s];
-        const R rA = r0.x, rB = r0.y;
-        R gA[3] = {(R)0, (R)0, (R)0}, gB[3] = {(R)0, (R)0, (R)0}, ad[3] = {(R)0, (R)0, (R)0};
-        // sums over symmetric pairs (e, -e): w e (psi(x+e) - psi(x-e)), the differences first
-        if (!(fl & k3Wall)) {  // no solid node in the stencil (solid density is 0 anyway)
-#pragma unroll
-            for (int dz = 0; dz <= 2; ++dz)
-#pragma unroll
-                for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-                    for (int dx = -2; dx <= 2; ++dx) {
-                        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;  // one of each pair
-                        const int q = dx * dx + dy * dy + dz * dz;
-                        if (w92(q) == 0.0) continue;
-                        const typename Rho2<R>::T p = __ldg(rho + nb.at(dx, dy, dz)), n = __ldg(rho + nb.at(-dx, -dy, -dz));
-                        const R w = (R)w92(q), a = p.x - n.x, b = p.y - n.y;
-                        gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
-                        gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
-                    }
-        } else {  // second-layer copy of x + sign(e) for non-fluid second-layer sites; solid switch
-            for (int dz = 0; dz <= 2; ++dz)
-                for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-                    for (int dx = -2; dx <= 2; ++dx) {
-                        if (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0))) continue;
-                        const int q = dx * dx + dy * dy + dz * dz;
-                        const double wq = w92(q);
-                        if (wq == 0.0) continue;
-                        const bool second = dx == 2 || dx == -2 || dy == 2 || dy == -2 || dz == 2 || dz == -2;
-                        R va[2], vb[2], vs[2];
-#pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            const int sg = side == 0 ? 1 : -1;
-                            const int ex = sg * dx, ey = sg * dy, ez = sg * dz;
-                            int n = nb.at(ex, ey, ez);
-                            const bool own = solid[n] != 0;
-                            if (second && own) n = nb.at((ex > 0) - (ex < 0), (ey > 0) - (ey < 0), (ez > 0) - (ez < 0));
-                            const bool sol = solid[n] != 0;
-                            const typename Rho2<R>::T v = rho[n];
-                            va[side] = sol ? (R)0 : v.x;
-                            vb[side] = sol ? (R)0 : v.y;
-                            vs[side] = (sol || (P.psi && !P.adh && own)) ? (R)1 : (R)0;
-                        }
-                        const R w = (R)wq, a = va[0] - va[1], b = vb[0] - vb[1], sw = vs[0] - vs[1];
-                        gA[0] += w * dx * a; gA[1] += w * dy * a; gA[2] += w * dz * a;
-                        gB[0] += w * dx * b; gB[1] += w * dy * b; gB[2] += w * dz * b;
-                        const R wa = P.adh ? (R)w19q(q) : w;  // q <= 2 sites are never replaced
-                        ad[0] += wa * dx * sw; ad[1] += wa * dy * sw; ad[2] += wa * dz * sw;
-                    }
-        }
-        R GA = (R)0;
-        if (fl & k3Wall) {
-            if (P.mode == 1) {
-                const R re = (rA - rB) / (rA + rB);
-                R h;
-                if (re > P.delta) h = P.lam;
-                else if (re > (R)0) h = P.s1 + re * (P.s2 + re * P.s3);
-                else if (re > -P.delta) h = P.s1 + re * (P.t2 + re * P.t3);
-                else h = (R)1;
-                GA = P.Gw2 * h;
-            } else {
-                GA = P.lam * P.Gw2;
-            }
-        }
-        R FA[3], FB[3], u[3];
-        const R rho = rA + rB;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            FA[d] = -P.G * rA * gB[d] - GA * rA * ad[d] + rA * P.g[d];
-            FB[d] = -P.G * rB * gA[d] - P.Gw2 * rB * ad[d] + rB * P.g[d];
-            u[d] = (m[d] + (R)0.5 * (FA[d] + FB[d])) / rho;
-        }
-        {
-            if (o5) {
-                o5[s] = (double)rA;
-                o5[g.N + s] = (double)rB;
-                o5[2 * g.N + s] = (double)u[0];
-                o5[3 * g.N + s] = (double)u[1];
-                o5[4 * g.N + s] = (double)u[2];
-            }
-            const double dr = (double)rho;
-            rec[0] = (double)rA;
-            rec[1] = (double)rB;
-            rec[2] = dr * (double)u[0];
-            rec[3] = dr * (double)u[1];
-            rec[4] = dr * (double)u[2];
-            const double um = sqrt((double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
-            rec[5] = um;
-            rec[6] = rec[7] = (double)rA;
-            rec[8] = rec[9] = (double)rB;
-            rec[10] = 1.0;
-            rec[11] = (!(rA > (R)0) || !(rB > (R)0) || !isfinite(um) || !isfinite((double)rA) || !isfinite((double)rB)) ? 1.0 : 0.0;
-        }
-    } else if (in && o5) {
-        for (int q = 0; q < 5; ++q) o5[q * g.N + s] = 0.0;
-    }
-    {
-        __shared__ double red[4][k3DiagN];
-        const int lane = threadIdx.x, warp = threadIdx.y;  // blocks of 32 x 4
-        for (int q = 0; q < k3DiagN; ++q) {
-            double v = rec[q];
-            for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
-            if (lane == 0) red[warp][q] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-            for (int q = 0; q < k3DiagN; ++q) {
-                double v = red[0][q];
-                for (int w2 = 1; w2 < 4; ++w2) v = d3_combine(q, v, red[w2][q]);
-                part[b * k3DiagN + q] = v;
-            }
-        }
-    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -438,10 +297,14 @@ __device__ __forceinline__ void wall_stencil3(const V2<R>* b0, const V2<R>* b1, 
 #ifndef LBM3_MIN_BLOCKS
 #define LBM3_MIN_BLOCKS 3
 #endif
-template <class S, class R, int kAdh>
+// kFields: the fields form.  In place of the collision each node writes rho_A, rho_B and u (FP64, o5
+// may be NULL) and adds its values to the thread's diagnostic record; each block writes one record
+// (block index blockIdx.x + gridDim.x (blockIdx.y + gridDim.y blockIdx.z)) to part.
+template <class S, class R, int kAdh, bool kFields = false>
 __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
     k3_march(Geo3 g, P3<R> P, int zc, const uint32_t* __restrict__ flags, const Pair<S>* __restrict__ fs,
-             const V2<R>* __restrict__ rho, Pair<S>* __restrict__ fout) {
+             const V2<R>* __restrict__ rho, Pair<S>* __restrict__ fout, double* __restrict__ o5,
+             double* __restrict__ part) {
     using V = V2<R>;
     extern __shared__ __align__(16) unsigned char smem3[];
     V* ring = reinterpret_cast<V*>(smem3);
@@ -493,6 +356,12 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
             f[i] = ld3<S, R>(fs + (long long)q * g.N + src, P, q);
         }
     };
+
+    double rec[k3DiagN];  // fields form: this thread's diagnostic record
+    if constexpr (kFields) {
+#pragma unroll
+        for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_neutral(q);
+    }
 
     // prologue: planes z0-2 .. z0+2 into the ring, plane z0+3 into registers, populations of z0
     uint32_t fl_nx = active ? flags[z0 * nxy + yx] : k3Solid;
@@ -584,50 +453,92 @@ __global__ void __launch_bounds__(k3T, sizeof(R) == 8 ? 2 : LBM3_MIN_BLOCKS)
                 F[d] = V{FA, FB};
                 u[d] = ((mv[d].x + mv[d].y) + (R)0.5 * (FA + FB)) * inv;
             }
-            // SRT collision with Guo forcing, per pair of directions (e, -e), both components at
-            // once.  With a = e.u, b = e.F_k, P = om rho a + cF b, C0 = om rho (1 - 1.5u^2) - 3 cF u.F:
-            //   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,  f*_0 = (1 - om) f_0 + w_0 C0
-            const V om = V{P.omega[0], P.omega[1]}, cf = V{P.cF[0], P.cF[1]};
-            const V om1 = vsub(vbc<R>(1), om);
-            const V wr = vmul(om, r2);
-            const V u2v[3] = {vbc<R>(u[0]), vbc<R>(u[1]), vbc<R>(u[2])};
-            const R tq = (R)1 - (R)1.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            const V uF = vfma(u2v[2], F[2], vfma(u2v[1], F[1], vmul(u2v[0], F[0])));
-            const V C0 = vfma(wr, vbc<R>(tq), vmul(vmul(vbc<R>(-3), cf), uF));
-            V o[19];
-            o[0] = vfma(om1, f[0], vmul(vbc<R>(w19c<R>(0)), C0));
-            const V sAx = vmul(vbc<R>(w19c<R>(1)), C0), sDg = vmul(vbc<R>(w19c<R>(7)), C0);
+            if constexpr (kFields) {
+                if (o5) {
+                    o5[s] = (double)rA;
+                    o5[g.N + s] = (double)rB;
+                    o5[2 * g.N + s] = (double)u[0];
+                    o5[3 * g.N + s] = (double)u[1];
+                    o5[4 * g.N + s] = (double)u[2];
+                }
+                const double dr = (double)(rA + rB);
+                // |u|^2; the square root is taken once, of the maximum (it is monotonic)
+                const double u2 = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
+                const bool bad = !(rA > (R)0) || !(rB > (R)0) || !isfinite(u2) || !isfinite((double)rA) ||
+                                 !isfinite((double)rB);
+                const double v[k3DiagN] = {(double)rA,       (double)rB, dr * (double)u[0], dr * (double)u[1],
+                                           dr * (double)u[2], u2,         (double)rA,        (double)rA,
+                                           (double)rB,        (double)rB, 1.0,               bad ? 1.0 : 0.0};
 #pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                auto dot = [&](const V* vv) -> V {  // e_i . vv for a pair-valued vector
-                    V r = vbc<R>(0);
-                    bool first = true;
+                for (int q = 0; q < k3DiagN; ++q) rec[q] = d3_combine(q, rec[q], v[q]);
+            } else {
+                // SRT collision with Guo forcing, per pair of directions (e, -e), both components at
+                // once.  With a = e.u, b = e.F_k, P = om rho a + cF b, C0 = om rho (1 - 1.5u^2) - 3 cF u.F:
+                //   f*_+- = (1 - om) f_+- + w (C0 + 4.5 a (P + cF b)) +- 3 w P,  f*_0 = (1 - om) f_0 + w_0 C0
+                const V om = V{P.omega[0], P.omega[1]}, cf = V{P.cF[0], P.cF[1]};
+                const V om1 = vsub(vbc<R>(1), om);
+                const V wr = vmul(om, r2);
+                const V u2v[3] = {vbc<R>(u[0]), vbc<R>(u[1]), vbc<R>(u[2])};
+                const R tq = (R)1 - (R)1.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                const V uF = vfma(u2v[2], F[2], vfma(u2v[1], F[1], vmul(u2v[0], F[0])));
+                const V C0 = vfma(wr, vbc<R>(tq), vmul(vmul(vbc<R>(-3), cf), uF));
+                V o[19];
+                o[0] = vfma(om1, f[0], vmul(vbc<R>(w19c<R>(0)), C0));
+                const V sAx = vmul(vbc<R>(w19c<R>(1)), C0), sDg = vmul(vbc<R>(w19c<R>(7)), C0);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const int e = d == 0 ? e3x(i) : d == 1 ? e3y(i) : e3z(i);
-                        if (e == 0) continue;
-                        if (first) r = e > 0 ? vv[d] : vsub(vbc<R>(0), vv[d]);
-                        else r = e > 0 ? vadd(r, vv[d]) : vsub(r, vv[d]);
-                        first = false;
-                    }
-                    return r;
-                };
-                const double w = w19c<R>(i);
-                const V a = dot(u2v), b = dot(F);
-                const V cb = vmul(cf, b);
-                const V Pp = vfma(wr, a, cb);
-                const V sym = vfma(vbc<R>(4.5 * w), vmul(a, vadd(Pp, cb)), i <= 6 ? sAx : sDg);
-                const V anti = vmul(vbc<R>(3.0 * w), Pp);
-                o[i] = vfma(om1, f[i], vadd(sym, anti));
-                o[i + 1] = vfma(om1, f[i + 1], vsub(sym, anti));
+                for (int i = 1; i < 19; i += 2) {
+                    auto dot = [&](const V* vv) -> V {  // e_i . vv for a pair-valued vector
+                        V r = vbc<R>(0);
+                        bool first = true;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const int e = d == 0 ? e3x(i) : d == 1 ? e3y(i) : e3z(i);
+                            if (e == 0) continue;
+                            if (first) r = e > 0 ? vv[d] : vsub(vbc<R>(0), vv[d]);
+                            else r = e > 0 ? vadd(r, vv[d]) : vsub(r, vv[d]);
+                            first = false;
+                        }
+                        return r;
+                    };
+                    const double w = w19c<R>(i);
+                    const V a = dot(u2v), b = dot(F);
+                    const V cb = vmul(cf, b);
+                    const V Pp = vfma(wr, a, cb);
+                    const V sym = vfma(vbc<R>(4.5 * w), vmul(a, vadd(Pp, cb)), i <= 6 ? sAx : sDg);
+                    const V anti = vmul(vbc<R>(3.0 * w), Pp);
+                    o[i] = vfma(om1, f[i], vadd(sym, anti));
+                    o[i + 1] = vfma(om1, f[i + 1], vsub(sym, anti));
+                }
+#pragma unroll
+                for (int i = 0; i < 19; ++i) st3<S, R>(fout + (long long)i * g.N + s, o[i], P, i);
             }
-#pragma unroll
-            for (int i = 0; i < 19; ++i) st3<S, R>(fout + (long long)i * g.N + s, o[i], P, i);
+        } else if constexpr (kFields) {  // solid node: zero fields
+            if (active && o5)
+                for (int q = 0; q < 5; ++q) o5[(long long)q * g.N + s] = 0.0;
         }
         if (z + 3 <= z1 + 1) store_plane(z + 3, nxt);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < k3HN; ++k) nxt[k] = nn[k];
+    }
+    if constexpr (kFields) {  // the block's record: warps by shuffles, then the warps in order
+        __shared__ double red[k3T / 32][k3DiagN];
+        const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+        for (int q = 0; q < k3DiagN; ++q) {
+            double v = rec[q];
+            for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (lane == 0) red[warp][q] = v;
+        }
+        __syncthreads();
+        if (t == 0) {
+            const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+            for (int q = 0; q < k3DiagN; ++q) {
+                double v = red[0][q];
+                for (int w = 1; w < k3T / 32; ++w) v = d3_combine(q, v, red[w][q]);
+                part[b * k3DiagN + q] = v;
+            }
+        }
     }
 }
 
@@ -663,14 +574,14 @@ __global__ void __launch_bounds__(k3DiagMidThreads) k3_diag_mid(long long nblock
     }
 }
 
-// Combine records in record order (one warp; deterministic).
+// Combine records in record order (one warp; deterministic); max |u| from max |u|^2.
 __global__ void k3_diag_final(long long nblocks, const double* __restrict__ part, double* __restrict__ out) {
     const int lane = threadIdx.x;
     for (int q = 0; q < k3DiagN; ++q) {
         double v = d3_neutral(q);
         for (long long b = lane; b < nblocks; b += 32) v = d3_combine(q, v, part[b * k3DiagN + q]);
         for (int off = 16; off > 0; off >>= 1) v = d3_combine(q, v, __shfl_xor_sync(0xffffffffu, v, off));
-        if (lane == 0) out[q] = v;
+        if (lane == 0) out[q] = q == 5 ? sqrt(v) : v;
     }
 }
 
@@ -752,7 +663,7 @@ __global__ void k3_feq(Geo3 g, const uint8_t* __restrict__ solid, const double* 
 // Contact angle on a sphere (FP64): interface points, algebraic sphere fit, one Gauss-Newton step
 // ------------------------------------------------------------------------------------------------
 constexpr int kC3Threads = 256;
-constexpr int kC3Blocks = 512;
+constexpr int kC3Blocks = 608;  // fixed (the summation order does not depend on the device): 4 x 152
 constexpr int kC3Vals = 14;
 
 template <class R>
@@ -760,7 +671,8 @@ struct Ca3 {
     Geo3 g;
     const uint32_t* flags;
     const typename Rho2<R>::T* rho;  // interleaved (rho_A, rho_B)
-};
+    uint8_t* cross;                  // per node: bit a set where the link to the +a neighbour crosses
+};                                   // rho^e = 0 (written by pass 0, read by the later passes)
 
 template <class R>
 __device__ __forceinline__ bool ca3_usable(const Ca3<R>& c, long long s) { return (c.flags[s] & (k3Solid | k3Near)) == 0; }
@@ -770,44 +682,79 @@ __device__ __forceinline__ bool phi3_pos(double a, double b) {
     const double sum = a + b;
     return (sum > 0.0 && sum < INFINITY) ? a > b : phi3(a, b) > 0.0;
 }
+// phi3_pos of densities in the compute type.  For finite FP32 values with a positive FP32 sum the
+// FP64 test reduces to a > b (the FP64 sum of two floats is finite and has the sign of their FP32
+// sum; the comparison is exact in either type), so FP32 takes it without the FP64 pipe; every other
+// case goes through the FP64 form.  The decision is the FP64 one bit for bit.
+__device__ __forceinline__ bool phi3_pos_r(float a, float b) {
+    if (isfinite(a) && isfinite(b) && a + b > 0.0f) return a > b;
+    return phi3_pos((double)a, (double)b);
+}
+__device__ __forceinline__ bool phi3_pos_r(double a, double b) { return phi3_pos(a, b); }
 
 // st: 0 N, 1-3 centroid, 4-6 centre, 7 r, 8 rms, 9 theta, 10 status (1: too few points)
-template <class R>
-__global__ void k3_ca_pass(Ca3<R> c, int pass, const double* __restrict__ st, double* __restrict__ part) {
+// One kernel per pass (kPass 0: count and centroid, 1: algebraic fit sums, 2: Gauss-Newton sums, 3:
+// residual), so that each holds only the sums it needs: the pass is bound by the latency of its
+// dependent loads, and fewer registers keep more warps resident.
+template <class R, int kPass>
+__global__ void __launch_bounds__(kC3Threads) k3_ca_pass(Ca3<R> c, const double* __restrict__ st,
+                                                        double* __restrict__ part) {
+    constexpr int pass = kPass;
+    constexpr int nv = pass == 0 ? 4 : pass == 1 ? 13 : pass == 2 ? 14 : 1;  // sums this pass forms
     double acc[kC3Vals];
+#pragma unroll
     for (int q = 0; q < kC3Vals; ++q) acc[q] = 0.0;
     const double m0 = st[1], m1 = st[2], m2 = st[3], c0 = st[4], c1 = st[5], c2 = st[6], r = st[7];
     const Geo3& g = c.g;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.N; s += (long long)gridDim.x * blockDim.x) {
-        if (!ca3_usable(c, s)) continue;
-        const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    const bool small = g.N < (1LL << 31);  // node index and coordinates in 32-bit arithmetic
+    // one node: pass 0 tests its three links and records the crossings, the later passes take the
+    // recorded ones (bits)
+    auto node = [&](long long s, uint32_t bits) {
+        int x, y, z;
+        if (small) {
+            const unsigned su = (unsigned)s, row = su / (unsigned)g.nx;
+            x = (int)(su - row * (unsigned)g.nx);
+            z = (int)(row / (unsigned)g.ny);
+            y = (int)(row - (unsigned)z * (unsigned)g.ny);
+        } else {
+            x = (int)(s % g.nx);
+            y = (int)((s / g.nx) % g.ny);
+            z = (int)(s / ((long long)g.nx * g.ny));
+        }
         const typename Rho2<R>::T r0 = c.rho[s];
         const double ra = (double)r0.x, rb = (double)r0.y;
-        const bool pa = phi3_pos(ra, rb);
+        const bool pa = phi3_pos_r(r0.x, r0.y);
+        uint32_t found = 0;
         for (int axis = 0; axis < 3; ++axis) {
-            const int lim = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
-            const int coord = axis == 0 ? x : (axis == 1 ? y : z);
-            if (coord + 1 >= lim) continue;  // no pair across the periodic seam
             const long long sn = s + (axis == 0 ? 1 : (axis == 1 ? (long long)g.nx : (long long)g.nx * g.ny));
-            if (!ca3_usable(c, sn)) continue;
+            if constexpr (pass == 0) {
+                const int lim = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+                const int coord = axis == 0 ? x : (axis == 1 ? y : z);
+                if (coord + 1 >= lim) continue;  // no pair across the periodic seam
+                if (!ca3_usable(c, sn)) continue;
+                const typename Rho2<R>::T r1 = c.rho[sn];
+                if (pa == phi3_pos_r(r1.x, r1.y)) continue;
+                found |= 1u << axis;
+            } else if (!((bits >> axis) & 1u)) {
+                continue;
+            }
             const typename Rho2<R>::T r1 = c.rho[sn];
             const double qa = (double)r1.x, qb = (double)r1.y;
-            if (pa == phi3_pos(qa, qb)) continue;
             const double a = phi3(ra, rb), b = phi3(qa, qb);
             double p[3] = {(double)x, (double)y, (double)z};
             p[axis] += a / (a - b);
-            if (pass == 0) {
+            if constexpr (pass == 0) {
                 acc[0] += 1.0;
                 acc[1] += p[0];
                 acc[2] += p[1];
                 acc[3] += p[2];
-            } else if (pass == 1) {
+            } else if constexpr (pass == 1) {
                 const double q0 = p[0] - m0, q1 = p[1] - m1, q2 = p[2] - m2, qq = q0 * q0 + q1 * q1 + q2 * q2;
                 acc[0] += q0 * q0; acc[1] += q0 * q1; acc[2] += q0 * q2;
                 acc[3] += q1 * q1; acc[4] += q1 * q2; acc[5] += q2 * q2;
                 acc[6] += q0; acc[7] += q1; acc[8] += q2;
                 acc[9] += q0 * qq; acc[10] += q1 * qq; acc[11] += q2 * qq; acc[12] += qq;
-            } else if (pass == 2) {
+            } else if constexpr (pass == 2) {
                 const double d0 = p[0] - c0, d1 = p[1] - c1, d2 = p[2] - c2;
                 const double d = sqrt(d0 * d0 + d1 * d1 + d2 * d2), res = d - r;
                 const double j[4] = {-d0 / d, -d1 / d, -d2 / d, -1.0};
@@ -821,19 +768,34 @@ __global__ void k3_ca_pass(Ca3<R> c, int pass, const double* __restrict__ st, do
                 acc[0] += res * res;
             }
         }
+        if constexpr (pass == 0) c.cross[s] = (uint8_t)found;
+    };
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
+    // one node per thread and step, so that the crossings of neighbouring nodes (they cluster along
+    // the interface) go to neighbouring lanes
+    for (long long s = tid; s < g.N; s += nth) {
+        if constexpr (pass == 0) {
+            if (ca3_usable(c, s)) node(s, 0u);
+            else c.cross[s] = 0;
+        } else {
+            const uint32_t b = c.cross[s];
+            if (b) node(s, b);
+        }
     }
     __shared__ double red[kC3Threads / 32][kC3Vals];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = 0; q < kC3Vals; ++q) {
+#pragma unroll
+    for (int q = 0; q < nv; ++q) {
         double v = acc[q];
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (lane == 0) red[warp][q] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int q = 0; q < kC3Vals; ++q) {
+        for (int q = 0; q < kC3Vals; ++q) {  // the sums a pass does not form are written as 0
             double v = 0.0;
-            for (int w = 0; w < kC3Threads / 32; ++w) v += red[w][q];
+            if (q < nv)
+                for (int w = 0; w < kC3Threads / 32; ++w) v += red[w][q];
             part[blockIdx.x * kC3Vals + q] = v;
         }
 }
@@ -940,6 +902,7 @@ struct lbm3d_ctx {
     long long nparts = 0;
     double* dout = nullptr;        // [k3DiagN]
     double* ca = nullptr;          // contact angle: status record + block partials
+    uint8_t* ca_cross = nullptr;   // contact angle: per-node crossing bits (N bytes)
     double* scratch = nullptr;     // [38][N] doubles for population transfers and fields (on demand)
     double* dens = nullptr;        // [2][N] doubles for lbm3d_set_densities from host arrays (on demand)
     // overlapped host transfers (lbm3d_set_densities_async, lbm3d_fields_async; on first use): copy
@@ -1025,10 +988,15 @@ Pair<S>* state3(const lbm3d_ctx* c, int buf) {
     return reinterpret_cast<Pair<S>*>(c->f[buf]);
 }
 
-// the step kernel instance of the adhesion variant
-template <class S, class R>
+// the step kernel instance of the adhesion variant (kFields: its fields form)
+template <class S, class R, bool kFields = false>
 auto march_kernel(const P3<R>& P) {
-    return P.adh ? k3_march<S, R, kAdhD3Q19> : (P.psi ? k3_march<S, R, kAdhE8Psi> : k3_march<S, R, kAdhE8>);
+    return P.adh ? k3_march<S, R, kAdhD3Q19, kFields>
+                 : (P.psi ? k3_march<S, R, kAdhE8Psi, kFields> : k3_march<S, R, kAdhE8, kFields>);
+}
+
+dim3 march_grid(const Geo3& g, int zc) {
+    return dim3((unsigned)((g.nx + k3TX - 1) / k3TX), (unsigned)((g.ny + k3TY - 1) / k3TY), (unsigned)((g.nz + zc - 1) / zc));
 }
 
 template <class S, class R>
@@ -1039,27 +1007,33 @@ cudaError_t step_once(lbm3d_ctx* c) {
     const P3<R>& P = p3_of<R>(c);
     k3_rho<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, P, c->flags, fs, rho);
     const int zc = zchunk3(c->g);
-    const dim3 gm((unsigned)((c->g.nx + k3TX - 1) / k3TX), (unsigned)((c->g.ny + k3TY - 1) / k3TY),
-                  (unsigned)((c->g.nz + zc - 1) / zc));
     auto* kern = march_kernel<S, R>(P);
-    kern<<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, reinterpret_cast<const V2<R>*>(rho),
-                                                         state3<S>(c, 1 - c->cur));
+    kern<<<march_grid(c->g, zc), kBlock3, k3_march_smem<R>(), c->stream>>>(
+        c->g, P, zc, c->flags, fs, reinterpret_cast<const V2<R>*>(rho), state3<S>(c, 1 - c->cur), nullptr, nullptr);
     c->cur ^= 1;
     return cudaGetLastError();
 }
 
-// densities of the current state into c->rho, then the fields form (o5 may be NULL)
+// densities of the current state into c->rho, then the fields form of the step kernel (o5 may be
+// NULL): the same pull, stencil sums, moments and forces as a step, per-block diagnostic records
 cudaError_t run_fields(lbm3d_ctx* c, double* o5, bool diag) {
     return with_types3(c->storage, [&](auto* s_, auto* r_) {
         TYPES3(s_, r_);
-        const dim3 gr = grid3(c->g);
         const Pair<S>* fs = state3<S>(c, c->cur);
         auto* rho = reinterpret_cast<typename Rho2<R>::T*>(c->rho);
-        k3_rho<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, fs, rho);
-        k3_fields<S, R><<<gr, kBlock3, 0, c->stream>>>(c->g, p3_of<R>(c), c->flags, c->solid, fs, rho, o5, c->part);
+        const P3<R>& P = p3_of<R>(c);
+        k3_rho<S, R><<<grid3(c->g), kBlock3, 0, c->stream>>>(c->g, P, c->flags, fs, rho);
+        const int zc = zchunk3(c->g);
+        const dim3 gm = march_grid(c->g, zc);
+        auto* kern = march_kernel<S, R, true>(P);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_march_smem<R>());
+        if (e != cudaSuccess) return e;
+        kern<<<gm, kBlock3, k3_march_smem<R>(), c->stream>>>(c->g, P, zc, c->flags, fs, reinterpret_cast<const V2<R>*>(rho),
+                                                             nullptr, o5, c->part);
         if (diag) {
-            double* mid = c->part + c->nparts * k3DiagN;  // k3DiagMid records after the per-block ones
-            k3_diag_mid<<<k3DiagMid, k3DiagMidThreads, 0, c->stream>>>(c->nparts, c->part, mid);
+            const long long nb = (long long)gm.x * gm.y * gm.z;  // <= c->nparts (one record per block)
+            double* mid = c->part + c->nparts * k3DiagN;         // k3DiagMid records after the per-block ones
+            k3_diag_mid<<<k3DiagMid, k3DiagMidThreads, 0, c->stream>>>(nb, c->part, mid);
             k3_diag_final<<<1, 32, 0, c->stream>>>(k3DiagMid, mid, c->dout);
         }
         return cudaGetLastError();
@@ -1093,13 +1067,14 @@ cudaError_t set_rest3(lbm3d_ctx* c, const double* a, const double* b) {
 
 template <class R>
 cudaError_t ca_passes(lbm3d_ctx* c, const double* sc, double R_) {
-    Ca3<R> ca{c->g, c->flags, reinterpret_cast<const typename Rho2<R>::T*>(c->rho)};
+    Ca3<R> ca{c->g, c->flags, reinterpret_cast<const typename Rho2<R>::T*>(c->rho), c->ca_cross};
     double* st = c->ca;
     double* part = c->ca + 16;
     cudaError_t e = cudaMemsetAsync(st, 0, 16 * sizeof(double), c->stream);
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < 4; ++pass) {
-        k3_ca_pass<R><<<kC3Blocks, kC3Threads, 0, c->stream>>>(ca, pass, st, part);
+        auto* kern = pass == 0 ? k3_ca_pass<R, 0> : pass == 1 ? k3_ca_pass<R, 1> : pass == 2 ? k3_ca_pass<R, 2> : k3_ca_pass<R, 3>;
+        kern<<<kC3Blocks, kC3Threads, 0, c->stream>>>(ca, st, part);
         k3_ca_solve<<<1, 32, 0, c->stream>>>(pass, kC3Blocks, part, st, sc[0], sc[1], sc[2], R_);
     }
     return cudaGetLastError();
@@ -1122,7 +1097,7 @@ void free_xfer3(lbm3d_ctx* c) {
 
 void free3(lbm3d_ctx* c) {
     free_xfer3(c);
-    void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->scratch, c->dens};
+    void* ptrs[] = {c->solid, c->flags, c->f[0], c->f[1], c->rho, c->part, c->dout, c->ca, c->ca_cross, c->scratch, c->dens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1218,6 +1193,7 @@ extern "C" lbm_status lbm3d_create(const lbm3d_grid* grid, const uint8_t* solid,
     STEP3(cudaMalloc(&c->part, (c->nparts + k3DiagMid) * k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->dout, k3DiagN * sizeof(double)), "diagnostics");
     STEP3(cudaMalloc(&c->ca, (16 + kC3Blocks * kC3Vals) * sizeof(double)), "contact-angle scratch");
+    STEP3(cudaMalloc(&c->ca_cross, (size_t)c->g.N), "contact-angle scratch");
     STEP3(cudaMemsetAsync(c->f[0], 0, 38 * N * c->elem, c->stream), "memset");
     STEP3(cudaMemsetAsync(c->f[1], 0, 38 * N * c->elem, c->stream), "memset");
     STEP3(cudaMemcpy(c->solid, solid, N, cudaMemcpyHostToDevice), "mask upload");
