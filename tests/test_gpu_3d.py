@@ -295,6 +295,24 @@ def test_contact_angle_routine_matches_oracle_on_the_same_state():
     assert rms == pytest.approx(orms, rel=1e-6, abs=1e-10)
 
 
+def test_contact_angle_follows_the_state_between_calls():
+    """The routine records the interface-crossing links of the state it measures and its fit passes
+    reuse them: a second call on another state (a drop at another place and size) must give the
+    oracle's angle for that state, not a mix with the first."""
+    a = S.sphere_droplet_3d_small(32, lam=0.6)
+    b = S.sphere_droplet_3d_small(32, lam=1.8)
+    cfg_a, fa = orun(a, 200)
+    cfg_b, fb = orun(b, 400)
+    lat = lattice(a, "f64")
+    for cfg, sc, f in ((cfg_a, a, fa), (cfg_b, b, fb), (cfg_a, a, fa)):
+        oth, _, on = d3.contact_angle_sphere(cfg, sc.solid, f, sc.sphere)
+        lat.set_populations(f)
+        th, _, n = lat.contact_angle(sc.sphere)
+        assert n == on
+        assert th == pytest.approx(oth, abs=1e-8)
+    lat.close()
+
+
 @pytest.mark.parametrize("lam", [0.38, 2.1])
 def test_contact_angle_after_1500_steps_within_half_a_degree(lam):
     """Sec. 3.5's case at 32 x 32 x 45: the GPU's angle after 1,500 FP32 steps is the oracle's
