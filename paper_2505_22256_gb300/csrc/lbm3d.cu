@@ -773,13 +773,19 @@ __global__ void __launch_bounds__(kC3Threads) k3_ca_pass(Ca3<R> c, const double*
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
     // one node per thread and step, so that the crossings of neighbouring nodes (they cluster along
     // the interface) go to neighbouring lanes
-    for (long long s = tid; s < g.N; s += nth) {
-        if constexpr (pass == 0) {
+    if constexpr (pass == 0) {
+        for (long long s = tid; s < g.N; s += nth) {
             if (ca3_usable(c, s)) node(s, 0u);
             else c.cross[s] = 0;
-        } else {
-            const uint32_t b = c.cross[s];
-            if (b) node(s, b);
+        }
+    } else {  // the same order; the bits of four steps are loaded together
+        for (long long s0 = tid; s0 < g.N; s0 += 4 * nth) {
+            uint32_t b[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = s0 + j * nth < g.N ? c.cross[s0 + j * nth] : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (b[j]) node(s0 + j * nth, b[j]);
         }
     }
     __shared__ double red[kC3Threads / 32][kC3Vals];
