@@ -261,6 +261,29 @@ def test_diagnostics_match_oracle():
     assert d["n_fluid"] == int((sc.solid == 0).sum()) and d["unstable"] == 0
 
 
+def test_diagnostics_agree_with_the_fields():
+    """The fields form writes the fields and the diagnostic records from the same node values: the
+    masses are the sums of the returned densities over the fluid nodes, the density extrema are
+    their extrema exactly, and the largest speed is that of the returned velocities."""
+    sc = S.sphere_droplet_3d_small(32, lam=0.6)
+    lat = lattice(sc, "f32")
+    lat.step(50)
+    rA, rB, ux, uy, uz = lat.fields()
+    d = lat.diagnostics()
+    lat.close()
+    fl = sc.solid == 0
+    assert d["n_fluid"] == int(fl.sum())
+    assert d["mass_A"] == pytest.approx(float(rA[fl].sum()), rel=1e-12)
+    assert d["mass_B"] == pytest.approx(float(rB[fl].sum()), rel=1e-12)
+    assert (d["rhoA_min"], d["rhoA_max"]) == (rA[fl].min(), rA[fl].max())
+    assert (d["rhoB_min"], d["rhoB_max"]) == (rB[fl].min(), rB[fl].max())
+    assert d["umax"] == pytest.approx(float(np.sqrt(ux ** 2 + uy ** 2 + uz ** 2)[fl].max()), rel=1e-14)
+    for k, u in (("mom_x", ux), ("mom_y", uy), ("mom_z", uz)):
+        ru = ((rA + rB) * u)[fl]  # the records form rho_A + rho_B in FP32 before widening it
+        assert abs(d[k] - ru.sum()) <= 1e-6 * np.abs(ru).sum(), k
+    assert (rA[~fl] == 0).all() and (ux[~fl] == 0).all()
+
+
 def test_mass_conservation_f32():
     sc = CASES["sphere24"]()
     lat = lattice(sc, "f32")
