@@ -250,6 +250,31 @@ def test_fields_and_diagnostics_match_oracle():
     lat.close()
 
 
+def test_diagnostics_agree_with_the_fields():
+    """Per case of an ensemble, the diagnostics pass and the fields pass form their results from the
+    same node values: the masses are the sums of the returned densities over the fluid nodes, the
+    density extrema are theirs exactly, and the largest speed and the momenta follow from the
+    returned velocities (|u|^2 and rho_A + rho_B are formed in FP32 before widening)."""
+    cases = [SCENARIOS["cylinder96"](), SCENARIOS["porous_open"]()]
+    lat = lbm.Lattice(cases, "f32")
+    lat.step(50)
+    for i, sc in enumerate(cases):
+        rA, rB, ux, uy = lat.fields(i)
+        d = lat.diagnostics(i)
+        fl = sc.solid == 0
+        assert d["n_fluid"] == int(fl.sum())
+        assert d["mass_A"] == pytest.approx(float(rA[fl].sum()), rel=1e-12)
+        assert d["mass_B"] == pytest.approx(float(rB[fl].sum()), rel=1e-12)
+        assert (d["rhoA_min"], d["rhoA_max"]) == (rA[fl].min(), rA[fl].max())
+        assert (d["rhoB_min"], d["rhoB_max"]) == (rB[fl].min(), rB[fl].max())
+        assert d["umax"] == pytest.approx(float(np.sqrt(ux ** 2 + uy ** 2)[fl].max()), rel=1e-6)
+        for k, u in (("mom_x", ux), ("mom_y", uy)):
+            ru = ((rA + rB) * u)[fl]
+            assert abs(d[k] - ru.sum()) <= 1e-6 * np.abs(ru).sum(), (sc.name, k)
+        assert (rA[~fl] == 0).all() and (ux[~fl] == 0).all()
+    lat.close()
+
+
 def test_mass_conservation_f32():
     """Streaming, bounce-back and the collision conserve each component's mass (the Guo term has
     no zeroth moment); in FP32 only rounding remains.  Over 20,000 steps this case drifts by about
